@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: dense MTTKRP throughput inside CP-ALS on one GB300.
+
+Workload (default): the correlation-shaped 4-way FP32 tensor 200x200x300x40
+(regions x regions x time windows x subjects, 480M entries, 1.92 GB), rank
+C = 25.  One step = one CP-ALS sweep through the C ABI (mtk_cp_als_sweep): for
+each of the 4 modes the MTTKRP, the FP64 Gram-Hadamard Cholesky solve and the
+Gram update, then the fit.  Metric = useful MTTKRP flops (4 modes x 2*I*C)
+per second of the whole sweep.
+
+Prints one JSON line (rank 0).  See the repository's design doc for the
+roofline bookkeeping.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Dense MTTKRP TFLOP/s & roofline %, mixed-precision vs FP32 at stated rel err"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="corr4", choices=["corr4", "cube512"])
+    ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | best")
+    ap.add_argument("--algo", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def workload(name):
+    if name == "corr4":
+        X, dims, U = synth.corr4()
+        desc = "corr4: 200x200x300x40 FP32 correlation-shaped (rank-10 CP, modes 0/1 symmetric, N(0,0.05^2) noise, clipped), rank C=25, factors uniform[0,1)"
+    else:
+        X, dims, U = synth.cube512()
+        desc = "cube512: 512^3 FP32 N(0,1), rank C=32, factors N(0,1)/sqrt(32)"
+    return X, tuple(dims), U, desc
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(X, dims, U, C, budget_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded prefix of the tensor for every mode."""
+    import oracle
+    Ud = [u.astype(np.float64) for u in U]
+    N = len(dims)
+    # calibrate on a small prefix, then size the sample to the time budget
+    n0 = 1 << 18
+    t0 = time.perf_counter()
+    for n in range(N):
+        oracle.mttkrp_range(X[:n0].astype(np.float64), 0, n0, dims, Ud, n)
+    dt = time.perf_counter() - t0
+    n_s = int(min(X.size, max(n0, n0 * budget_s / max(dt, 1e-6))))
+    n_s -= n_s % 1024
+    Xs = X[:n_s].astype(np.float64)
+    t0 = time.perf_counter()
+    for n in range(N):
+        oracle.mttkrp_range(Xs, 0, n_s, dims, Ud, n)
+    dt = time.perf_counter() - t0
+    flops = N * 2.0 * n_s * C
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {n_s} of {X.size} entries (natural order), all {N} modes, FP64 definition loop, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    X, dims, U, desc = workload(args.workload)
+    C = U[0].shape[1]
+    import oracle
+    Ud = [u.astype(np.float64) for u in U]
+    N = len(dims)
+    n_s = min(X.size, 1 << 22)
+    Xs = X[:n_s].astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.mttkrp_range(Xs, 0, n_s, dims, Ud, 0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for n in range(N):
+            oracle.mttkrp_range(Xs, 0, n_s, dims, Ud, n)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = N * 2.0 * n_s * C / t / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "sample_entries": n_s},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"first {n_s} entries, all {N} modes per step"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_1708_08976_gb300 as mtk
+    lib = mtk.load()
+    hbm_peak, bf16_peak, peak_kind = peaks()
+
+    X, dims, U, desc = workload(args.workload)
+    N = len(dims)
+    C = U[0].shape[1]
+    I = X.size
+    flops_step = N * 2.0 * I * C
+    Xd = torch.from_numpy(X).to(dev)
+    U0 = [torch.from_numpy(u).to(dev) for u in U]
+
+    # accuracy of each precision form on every mode (vs the FP64 oracle on sampled rows)
+    import oracle
+    Ud64 = [u.astype(np.float64) for u in U]
+    g = np.random.default_rng(123)
+    forms = {}
+    for prec in ("fp32", "bf16x2", "bf16x3"):
+        try:
+            errs, times = [], []
+            for n in range(N):
+                M = mtk.mttkrp(Xd, dims, U0, n, precision=prec)
+                rows = np.unique(np.concatenate([[0, dims[n] - 1], g.integers(0, dims[n], 6)]))
+                ref = oracle.mttkrp_rows_f32(X, dims, Ud64, n, rows)
+                got = M[torch.as_tensor(rows, device=dev)].double().cpu().numpy()
+                errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                for _ in range(2):
+                    mtk.mttkrp(Xd, dims, U0, n, precision=prec, out=M)
+                ts = []
+                for _ in range(5):
+                    ev0.record()
+                    mtk.mttkrp(Xd, dims, U0, n, precision=prec, out=M)
+                    ev1.record()
+                    ev1.synchronize()
+                    ts.append(ev0.elapsed_time(ev1) * 1e-3)
+                times.append(statistics.median(ts))
+            forms[prec] = {"rel_err_per_mode": errs, "mttkrp_us_per_mode": [t * 1e6 for t in times],
+                           "tflops_per_mode": [2.0 * I * C / t / 1e12 for t in times]}
+        except mtk.MtkError as e:
+            forms[prec] = {"unavailable": str(e)}
+    if args.precision == "best":
+        ok = {p: v for p, v in forms.items() if "unavailable" not in v and max(v["rel_err_per_mode"]) <= 1e-5}
+        prec = min(ok, key=lambda p: sum(ok[p]["mttkrp_us_per_mode"])) if ok else "fp32"
+    else:
+        prec = args.precision
+
+    Uw = [u.clone() for u in U0]
+    als = mtk.ALS(Xd, dims, Uw, algo=args.algo, precision=prec)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+
+    def reset_factors():
+        for a, b in zip(Uw, U0):
+            a.copy_(b)
+
+    for _ in range(args.warmup):
+        als.sweep()
+    torch.cuda.synchronize()
+    if als.status() != 0:
+        raise RuntimeError(f"device status {als.status()} after warm-up")
+    reset_factors()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = lib.mtk_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        als.sweep()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.mtk_launch_count() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    t_step = e0.elapsed_time(e1) * 1e-3 / args.steps
+
+    # per-launch duration of the dominant kernel (the MTTKRP contraction of every mode,
+    # timed on its launch stream; inputs 1.92 GB > L2)
+    per_mode = []
+    M = torch.empty((max(dims), C), dtype=torch.float32, device=dev)
+    for n in range(N):
+        out = M[: dims[n]]
+        ts = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mtk.mttkrp(Xd, dims, U0, n, precision=prec, algo=args.algo, out=out)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        per_mode.append(statistics.median(ts))
+    clocks = sampler.stop()
+
+    t_tensor = torch.tensor([t_step], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_tensor, op=torch.distributed.ReduceOp.MAX)
+    t_max = float(t_tensor.item())
+    value = world * flops_step / t_max / 1e12
+
+    # e2e: host buffers, H2D of the tensor + factors and D2H of factors + fit inside the region
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Uh = [torch.from_numpy(u).pin_memory() for u in U]
+        Uo = [torch.empty_like(u).pin_memory() for u in Uh]
+        fit_h = torch.empty((), dtype=torch.float64).pin_memory()
+        Xe = torch.empty_like(Xd)
+        Ue = [torch.empty_like(u) for u in U0]
+        alse = mtk.ALS(Xe, dims, Ue, algo=args.algo, precision=prec)
+        ksteps = max(3, min(args.steps, 5))
+        for it in range(ksteps + 1):
+            if it == 1:
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+            Xe.copy_(Xh, non_blocking=True)
+            for d_, h_ in zip(Ue, Uh):
+                d_.copy_(h_, non_blocking=True)
+            alse.normX2 = mtk.norm2(Xe, out=alse.normX2)
+            alse.sweep()
+            for h_, d_ in zip(Uo, Ue):
+                h_.copy_(d_, non_blocking=True)
+            fit_h.copy_(alse.fit, non_blocking=True)
+            torch.cuda.synchronize()
+        te = (time.perf_counter() - a) / ksteps
+        h2d = X.nbytes + sum(u.nbytes for u in U)
+        d2h = sum(u.nbytes for u in U) + 8
+        e2e = {"value": world * flops_step / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(X, dims, U, C)
+
+    bytes_mode = [4.0 * I + 4.0 * C * (sum(dims) - dims[n]) + 4.0 * dims[n] * C for n in range(N)]
+    achieved = sum(bytes_mode) / sum(per_mode) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else f"{prec} split products, f32 accumulate",
+        "data": "synthetic",
+        "config": {"workload": desc, "dims": list(dims), "rank": C, "step": "one CP-ALS sweep (4 MTTKRPs + FP64 Cholesky solves + Grams + fit)",
+                   "precision": prec, "algo": args.algo, "l2": "inputs (1.92 GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "MTTKRP contraction (mtk_mttkrp per mode, incl. split reduce)",
+                     "peak_kind": peak_kind},
+        "mttkrp_us_per_mode": [t * 1e6 for t in per_mode],
+        "roofline_frac_per_mode": [(b / hbm_peak / 1e9) / t for b, t in zip(bytes_mode, per_mode)],
+        "precision_forms": forms,
+        "fit_after_timed_sweeps": float(als.fit.item()),
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * mttkrp.h -- C ABI of libmttkrp, dense MTTKRP and CP-ALS on one GB300 GPU.
+ *
+ * Follows "Shared-Memory Parallelization of MTTKRP for Dense Tensors"
+ * (Hayashi, Ballard, Jiang, Tobia, 2017).  Conventions used by every call:
+ *
+ *  - Indices are 0-based (Section 2.1).  A tensor with dims I_0..I_{N-1} is a
+ *    dense FP32 array in the natural linearization l = sum_k i_k prod_{j<k} I_j,
+ *    mode 0 fastest (Section 2.1).  It is never reordered in memory.
+ *  - Factor matrices U_k are I_k x C FP32, row-major (C contiguous).  MTTKRP
+ *    outputs M are I_n x C FP32 row-major.  (The paper leaves the factor layout
+ *    open; this library fixes it.)
+ *  - Every float / double pointer argument is a DEVICE pointer unless stated.
+ *    Arrays of pointers (U, G) are HOST arrays whose elements are device
+ *    pointers.  dims / rows arrays are HOST arrays.
+ *  - The caller owns all memory, including the workspace `ws`; the library
+ *    allocates no device memory.  Workspace sizes come from the *_workspace
+ *    queries.  The first 256 bytes of every workspace hold the device status
+ *    word; zero them once (mtk_clear_status) before first use.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *    is the legacy default stream).  Host-detectable errors return at once with
+ *    no launch.  Errors found on the device (a non-positive-definite normal
+ *    matrix, an expired wait) are OR-ed into the status word and read back by
+ *    mtk_read_status.
+ *  - N <= 16, 1 <= C <= 256, every dim >= 1, every product of dims < 2^62.
+ *    Device pointers must be 4-byte aligned; 16-byte alignment enables the
+ *    vectorised and tensor-core paths.
+ *  - Functions are reentrant; the only global state is a monotonic, atomic
+ *    count of the kernel launches issued (mtk_launch_count).
+ */
+#ifndef MTTKRP_H
+#define MTTKRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes (return values and bits of the device status word) */
+typedef enum {
+    MTK_OK = 0,
+    MTK_EINVAL = 1,        /* bad argument (null pointer, bad size, misalignment) */
+    MTK_ECUDA = 3,         /* a CUDA launch or copy failed */
+    MTK_ENOTPD = 4,        /* normal-equation matrix not positive definite */
+    MTK_ETIMEOUT = 5,      /* a bounded device-side wait expired */
+    MTK_EUNSUPPORTED = 6,  /* option not available for this shape */
+    MTK_EWORKSPACE = 7     /* workspace too small */
+} mtk_status;
+
+/* MTTKRP algorithm (Section 4) */
+enum {
+    MTK_ALGO_AUTO = 0,          /* per-mode choice made by the library */
+    MTK_ALGO_FUSED = 1,         /* 1-step, KRP rows generated on chip, never stored */
+    MTK_ALGO_MATERIALIZED = 2,  /* 1-step with the full KRP written to the workspace
+                                   (Algorithm 2) */
+    MTK_ALGO_TWO_STEP = 3       /* partial MTTKRP + multi-TTV (Algorithm 4); at the
+                                   external modes it is the 1-step algorithm */
+};
+
+/* arithmetic of the tensor contraction */
+enum {
+    MTK_PREC_AUTO = 0,          /* currently MTK_PREC_FP32 */
+    MTK_PREC_FP32 = 1,          /* FP32 fused multiply-adds on the CUDA cores */
+    MTK_PREC_BF16X2 = 2,        /* tensor entries as 2 BF16 pieces, KRP entries as 3,
+                                   all 6 cross products on tcgen05, FP32 accumulate */
+    MTK_PREC_BF16X3 = 3         /* tensor entries as 3 BF16 pieces (9 products) */
+};
+
+typedef struct {
+    int algo;          /* MTK_ALGO_* */
+    int precision;     /* MTK_PREC_* */
+    int splits;        /* contraction splits across CTAs; 0 = automatic */
+    int reserved[5];   /* set to 0 */
+} mtk_opts;            /* NULL = all defaults */
+
+/* status helpers --------------------------------------------------------- */
+const char* mtk_status_string(int status);
+int mtk_version(void);
+
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all threads, all devices).  Differences around a region count its launches. */
+uint64_t mtk_launch_count(void);
+
+/* Zero the status word at the head of a workspace (async on stream). */
+int mtk_clear_status(void* ws, void* stream);
+
+/* Synchronise `stream`, then return the status word of `ws` (MTK_OK if
+   nothing was recorded).  *bits_out (host, may be NULL) gets the raw bits. */
+int mtk_read_status(const void* ws, void* stream, uint32_t* bits_out);
+
+/* Khatri-Rao product (Section 4.1, Algorithm 1) ---------------------------
+ * K = U_0 kr U_1 kr ... kr U_{Z-1}: the row of K for row indices
+ * (a_0, ..., a_{Z-1}) is U_0(a_0,:) * ... * U_{Z-1}(a_{Z-1},:), with the LAST
+ * operand's index fastest (Section 2.1 row rule).  U: host array of Z device
+ * pointers to rows[z] x C row-major matrices.  K: device, (prod rows) x C
+ * row-major, overwritten.  reuse = 1 shares each prefix product across the
+ * rows that follow it (Algorithm 1); reuse = 0 forms every row from scratch
+ * (the naive comparator of Section 5.2).  Z in [1, 16]. */
+int mtk_khatri_rao(const float* const* U, const int64_t* rows, int Z, int C,
+                   float* K, int reuse, void* stream);
+
+/* MTTKRP (Section 2.2; Algorithms 2-4) ----------------------------------
+ *   M(i_n, c) = sum_{all i_k, k != n} X(i_0..i_{N-1}) prod_{k != n} U_k(i_k, c)
+ * i.e. M = X_(n) (U_{N-1} kr ... kr U_{n+1} kr U_{n-1} kr ... kr U_0).
+ * X: device tensor (natural order).  dims: host, N entries.  U: host array of
+ * N device pointers (U[n] is not read, may be NULL).  M: device I_n x C,
+ * overwritten.  ws/ws_bytes: device workspace of at least
+ * mtk_mttkrp_workspace(...) bytes.  The result does not depend on the launch
+ * order of CTAs (fixed-order reduction). */
+size_t mtk_mttkrp_workspace(const int64_t* dims, int N, int C, int n, const mtk_opts* opts);
+int mtk_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U, int C,
+               int n, float* M, void* ws, size_t ws_bytes, const mtk_opts* opts,
+               void* stream);
+
+/* 2-step pieces (Section 4.3, Algorithm 4) -------------------------------
+ * Partial MTTKRP.  right = 1: T = X_(0:n) K_R, K_R = U_{N-1} kr ... kr U_{n+1}
+ * (R = prod_{k>n} I_k rows); T is the (I^L x I_n x C) tensor R of the paper in
+ * natural order, T[l + I^L i + I^L I_n c].  right = 0: T = X_(0:n-1)^T K_L,
+ * K_L = U_{n-1} kr ... kr U_0 (I^L rows); T[i + I_n r + I_n I^R c].
+ * Kp: device, the materialised partial KRP (row-major, C columns), e.g. from
+ * mtk_khatri_rao.  T: device, overwritten. */
+size_t mtk_partial_mttkrp_workspace(const int64_t* dims, int N, int C, int n, int right,
+                                    const mtk_opts* opts);
+int mtk_partial_mttkrp(const float* X, const int64_t* dims, int N, const float* Kp, int C,
+                       int n, int right, float* T, void* ws, size_t ws_bytes,
+                       const mtk_opts* opts, void* stream);
+
+/* Multi-TTV, the second step.  right = 1: M(i,c) = sum_l T[l + I^L i + I^L I_n c] K_L(l,c);
+ * right = 0: M(i,c) = sum_r T[i + I_n r + I_n I^R c] K_R(r,c).  Ko: device, the other
+ * partial KRP (K_L for right, K_R for left), row-major.  M: device I_n x C. */
+int mtk_multi_ttv(const float* T, const int64_t* dims, int N, const float* Ko, int C, int n,
+                  int right, float* M, void* stream);
+
+/* Gram matrices and the normal-equation solve (Section 2.2) -------------
+ * G = U^T U for an I x C FP32 matrix, accumulated in FP64; G: device C x C
+ * FP64 row-major.  ws: at least mtk_gram_workspace(I, C) bytes. */
+size_t mtk_gram_workspace(int64_t I, int C);
+int mtk_gram(const float* U, int64_t I, int C, double* G, void* ws, size_t ws_bytes,
+             void* stream);
+
+/* U_n = M H^{-1} with H = Hadamard_{k != n} G_k (FP64 Cholesky).  G: host array of
+ * N device pointers to C x C FP64 Grams (G[n] not read).  M: device In x C FP32.
+ * Un: device In x C FP32, written only if H is positive definite; otherwise
+ * left unchanged and MTK_ENOTPD is OR-ed into the status word.  Gn (device,
+ * may be NULL): receives Un^T Un of the result (FP64).  ws: at least
+ * mtk_solve_workspace(In, C) bytes. */
+size_t mtk_solve_workspace(int64_t In, int C);
+int mtk_gram_hadamard_solve(const double* const* G, int N, int C, int n, const float* M,
+                            int64_t In, float* Un, double* Gn, void* ws, size_t ws_bytes,
+                            void* stream);
+
+/* ||X||^2 in FP64 (fixed-order reduction).  out: device double. */
+size_t mtk_norm2_workspace(int64_t I);
+int mtk_norm2(const float* X, int64_t I, double* out, void* ws, size_t ws_bytes, void* stream);
+
+/* One CP-ALS sweep (Section 2.2): for n = 0..N-1, M = MTTKRP(X, n),
+ * H = Hadamard_{k != n} U_k^T U_k, U_n = M H^{-1}, the other factors fixed at
+ * their latest values.  U: host array of N device pointers, updated in place.
+ * normX2 (device, may be NULL): ||X||^2 from mtk_norm2; if given with fit
+ * (device, may be NULL), *fit = 1 - sqrt(max(0, ||X||^2 - 2<M_{N-1}, U_{N-1}> +
+ * sum(Hadamard_k G_k))) / ||X||.  No host synchronisation inside. */
+size_t mtk_cp_als_workspace(const int64_t* dims, int N, int C, const mtk_opts* opts);
+int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U, int C,
+                     const double* normX2, double* fit, void* ws, size_t ws_bytes,
+                     const mtk_opts* opts, void* stream);
+
+/* CP loss pieces (Section 2.2; the paper names the residual as a cost but gives
+ * no formula, this is the standard expansion of the squared norm):
+ *   r2 = ||X||^2 - 2 <M_m, U_m> + sum_{a,b} prod_k G_k(a,b),   G_k = U_k^T U_k,
+ * which equals ||X - [[U_0..U_{N-1}]]||^2 when M_m is the mode-m MTTKRP of X.
+ * normX2: device double (mtk_norm2).  M, Um: device Im x C.  G: host array of N
+ * device pointers to FP64 Grams.  r2, fit: device doubles, either may be NULL;
+ * fit = 1 - sqrt(max(0, r2)) / ||X||. */
+int mtk_cp_residual(const double* normX2, const float* M, const float* Um, int64_t Im,
+                    const double* const* G, int N, int C, double* r2, double* fit, void* stream);
+
+/* Gradient of f = 0.5 ||X - [[U]]||^2 with respect to U_n (MTTKRP is part of the
+ * gradient, Section 2.2):  grad = scale * (U_n H_n - M_n), H_n = Hadamard_{k != n} G_k.
+ * Un, Mn: device In x C FP32 (Mn = mode-n MTTKRP).  G: host array of N device
+ * pointers (G[n] not read).  scale: device float, may be NULL (= 1).  grad: device
+ * In x C FP32, may alias neither input. */
+int mtk_cp_gradient(const float* Un, const float* Mn, const double* const* G, int N, int C, int n,
+                    int64_t In, const float* scale, float* grad, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTTKRP_H */

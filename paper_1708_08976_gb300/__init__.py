@@ -1,0 +1,14 @@
+"""Dense MTTKRP and CP-ALS on one GB300 GPU (sm_103a), after "Shared-Memory
+Parallelization of MTTKRP for Dense Tensors" (Hayashi, Ballard, Jiang, Tobia).
+
+The compute lives in ``lib/libmttkrp.so`` (CUDA kernels behind the C ABI of
+``include/mttkrp.h``); this package is its thin torch binding.
+"""
+from .api import (ALS, ALGOS, PRECISIONS, CPLoss, Workspace, cp_gradient, cp_loss, cp_residual,
+                  default_workspace, gram, gram_hadamard_solve, khatri_rao, multi_ttv, mttkrp,
+                  norm2, partial_mttkrp)
+from ._lib import MtkError, load
+
+__all__ = ["ALS", "ALGOS", "PRECISIONS", "CPLoss", "Workspace", "cp_gradient", "cp_loss",
+           "cp_residual", "default_workspace", "gram", "gram_hadamard_solve", "khatri_rao",
+           "multi_ttv", "mttkrp", "norm2", "partial_mttkrp", "MtkError", "load"]

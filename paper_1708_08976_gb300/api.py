@@ -1,0 +1,346 @@
+"""Torch-facing binding of libmttkrp: argument marshalling only.
+
+Tensors are torch CUDA tensors (device memory); every computation runs in the
+library's CUDA kernels on the current torch stream.  Tensors are flat FP32
+arrays in the natural linearization (mode 0 fastest, Section 2.1 of the
+paper); factor matrices are ``I_k x C`` FP32 row-major; Gram matrices FP64.
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib as L
+
+ALGOS = {"auto": L.ALGO_AUTO, "fused": L.ALGO_FUSED, "materialized": L.ALGO_MATERIALIZED,
+         "two_step": L.ALGO_TWO_STEP}
+PRECISIONS = {"auto": L.PREC_AUTO, "fp32": L.PREC_FP32, "bf16x2": L.PREC_BF16X2,
+              "bf16x3": L.PREC_BF16X3}
+
+
+def _stream(dev) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _req(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _opts(algo="auto", precision="auto", splits=0):
+    return L.opts(ALGOS[algo] if isinstance(algo, str) else algo,
+                  PRECISIONS[precision] if isinstance(precision, str) else precision, splits)
+
+
+class Workspace:
+    """A device byte buffer owned by the caller side (torch), grown on demand.
+    The first 256 bytes are the library's status word, zeroed at allocation."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device if device is not None else "cuda")
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.zeros(nbytes, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+    def ptr(self, nbytes: int):
+        b = self.get(nbytes)
+        return b.data_ptr(), b.numel()
+
+    def status(self) -> int:
+        """Synchronise the stream and return the device status word (0 = ok)."""
+        if self.buf is None:
+            return 0
+        bits = L.ctypes.c_uint32(0)
+        return L.load().mtk_read_status(self.buf.data_ptr(), _stream(self.device), L.ctypes.byref(bits))
+
+    def clear(self):
+        if self.buf is not None:
+            L.check(L.load().mtk_clear_status(self.buf.data_ptr(), _stream(self.device)), "clear_status")
+
+
+_default_ws = {}
+
+
+def default_workspace(device) -> Workspace:
+    d = torch.device(device)
+    key = d.index if d.index is not None else torch.cuda.current_device()
+    if key not in _default_ws:
+        _default_ws[key] = Workspace(torch.device("cuda", key))
+    return _default_ws[key]
+
+
+def _factor_ptrs(U, dims, C, skip=None):
+    ptrs = []
+    for k, u in enumerate(U):
+        if k == skip and u is None:
+            ptrs.append(None)
+            continue
+        _req(u, torch.float32, f"U[{k}]")
+        if tuple(u.shape) != (int(dims[k]), C):
+            raise ValueError(f"U[{k}] must be {int(dims[k])} x {C}, got {tuple(u.shape)}")
+        ptrs.append(u.data_ptr())
+    return ptrs
+
+
+def _rank(U, skip=None):
+    for k, u in enumerate(U):
+        if u is not None and k != skip:
+            return int(u.shape[1])
+    for u in U:
+        if u is not None:
+            return int(u.shape[1])
+    raise ValueError("no factor matrix given")
+
+
+def mttkrp(X: torch.Tensor, dims: Sequence[int], U: Sequence[Optional[torch.Tensor]], n: int, *,
+           algo="auto", precision="auto", splits=0, out: Optional[torch.Tensor] = None,
+           ws: Optional[Workspace] = None) -> torch.Tensor:
+    """Mode-n MTTKRP M = X_(n) (U_{N-1} kr ... kr U_{n+1} kr U_{n-1} kr ... kr U_0)."""
+    _req(X, torch.float32, "X")
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    C = _rank(U, skip=n)
+    if X.numel() != int(torch.tensor(dims).prod()):
+        raise ValueError("X does not match dims")
+    ptrs = _factor_ptrs(U, dims, C, skip=n)
+    if out is None:
+        out = torch.empty((dims[n], C), dtype=torch.float32, device=X.device)
+    _req(out, torch.float32, "out")
+    o = _opts(algo, precision, splits)
+    lib = L.load()
+    d = L.dims_arr(dims)
+    need = lib.mtk_mttkrp_workspace(d, N, C, n, L.ctypes.byref(o))
+    if need == 0:
+        raise ValueError("invalid MTTKRP shape or options")
+    ws = ws or default_workspace(X.device)
+    wp, wb = ws.ptr(need)
+    L.check(lib.mtk_mttkrp(X.data_ptr(), d, N, L.ptr_arr(ptrs), C, n, out.data_ptr(), wp, wb,
+                           L.ctypes.byref(o), _stream(X.device)), "mtk_mttkrp")
+    return out
+
+
+def khatri_rao(U: Sequence[torch.Tensor], *, reuse: bool = True,
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """K = U_0 kr ... kr U_{Z-1}, last operand's row index fastest (Section 4.1)."""
+    C = int(U[0].shape[1])
+    rows = [int(u.shape[0]) for u in U]
+    for k, u in enumerate(U):
+        _req(u, torch.float32, f"U[{k}]")
+        if int(u.shape[1]) != C:
+            raise ValueError("all operands need the same number of columns")
+    J = 1
+    for r in rows:
+        J *= r
+    if out is None:
+        out = torch.empty((J, C), dtype=torch.float32, device=U[0].device)
+    _req(out, torch.float32, "out")
+    L.check(L.load().mtk_khatri_rao(L.ptr_arr([u.data_ptr() for u in U]), L.dims_arr(rows), len(U), C,
+                                    out.data_ptr(), 1 if reuse else 0, _stream(U[0].device)),
+            "mtk_khatri_rao")
+    return out
+
+
+def partial_mttkrp(X, dims, Kp, n, right: bool, *, precision="auto", splits=0, out=None, ws=None):
+    """First step of Algorithm 4 (see include/mttkrp.h for the output layout)."""
+    _req(X, torch.float32, "X")
+    _req(Kp, torch.float32, "Kp")
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    C = int(Kp.shape[1])
+    IL = 1
+    for d in dims[:n]:
+        IL *= d
+    IR = 1
+    for d in dims[n + 1:]:
+        IR *= d
+    size = (IL * dims[n] if right else dims[n] * IR) * C
+    if out is None:
+        out = torch.empty(size, dtype=torch.float32, device=X.device)
+    o = _opts("auto", precision, splits)
+    lib = L.load()
+    d = L.dims_arr(dims)
+    need = lib.mtk_partial_mttkrp_workspace(d, N, C, n, 1 if right else 0, L.ctypes.byref(o))
+    ws = ws or default_workspace(X.device)
+    wp, wb = ws.ptr(need)
+    L.check(lib.mtk_partial_mttkrp(X.data_ptr(), d, N, Kp.data_ptr(), C, n, 1 if right else 0,
+                                   out.data_ptr(), wp, wb, L.ctypes.byref(o), _stream(X.device)),
+            "mtk_partial_mttkrp")
+    return out
+
+
+def multi_ttv(T, dims, Ko, n, right: bool, *, out=None):
+    """Second step of Algorithm 4."""
+    _req(T, torch.float32, "T")
+    _req(Ko, torch.float32, "Ko")
+    dims = [int(d) for d in dims]
+    C = int(Ko.shape[1])
+    if out is None:
+        out = torch.empty((dims[n], C), dtype=torch.float32, device=T.device)
+    L.check(L.load().mtk_multi_ttv(T.data_ptr(), L.dims_arr(dims), len(dims), Ko.data_ptr(), C, n,
+                                   1 if right else 0, out.data_ptr(), _stream(T.device)), "mtk_multi_ttv")
+    return out
+
+
+def gram(U: torch.Tensor, *, out=None, ws=None) -> torch.Tensor:
+    """G = U^T U in FP64."""
+    _req(U, torch.float32, "U")
+    I, C = int(U.shape[0]), int(U.shape[1])
+    if out is None:
+        out = torch.empty((C, C), dtype=torch.float64, device=U.device)
+    lib = L.load()
+    ws = ws or default_workspace(U.device)
+    wp, wb = ws.ptr(lib.mtk_gram_workspace(I, C))
+    L.check(lib.mtk_gram(U.data_ptr(), I, C, out.data_ptr(), wp, wb, _stream(U.device)), "mtk_gram")
+    return out
+
+
+def gram_hadamard_solve(G: Sequence[Optional[torch.Tensor]], n: int, M: torch.Tensor, Un: torch.Tensor,
+                        *, Gn: Optional[torch.Tensor] = None, ws=None) -> torch.Tensor:
+    """U_n = M (Hadamard_{k != n} G_k)^{-1} in place (FP64 Cholesky)."""
+    _req(M, torch.float32, "M")
+    _req(Un, torch.float32, "Un")
+    N = len(G)
+    In, C = int(M.shape[0]), int(M.shape[1])
+    ptrs = []
+    for k, g in enumerate(G):
+        if k == n and g is None:
+            ptrs.append(None)
+        else:
+            ptrs.append(_req(g, torch.float64, f"G[{k}]").data_ptr())
+    lib = L.load()
+    ws = ws or default_workspace(M.device)
+    wp, wb = ws.ptr(lib.mtk_solve_workspace(In, C))
+    L.check(lib.mtk_gram_hadamard_solve(L.ptr_arr(ptrs), N, C, n, M.data_ptr(), In, Un.data_ptr(),
+                                        Gn.data_ptr() if Gn is not None else None, wp, wb,
+                                        _stream(M.device)), "mtk_gram_hadamard_solve")
+    return Un
+
+
+def norm2(X: torch.Tensor, *, out=None, ws=None) -> torch.Tensor:
+    """||X||^2 in FP64 (device scalar)."""
+    _req(X, torch.float32, "X")
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=X.device)
+    lib = L.load()
+    ws = ws or default_workspace(X.device)
+    wp, wb = ws.ptr(lib.mtk_norm2_workspace(X.numel()))
+    L.check(lib.mtk_norm2(X.data_ptr(), X.numel(), out.data_ptr(), wp, wb, _stream(X.device)), "mtk_norm2")
+    return out
+
+
+def cp_residual(normX2, M, Um, G, *, r2=None, fit=None):
+    """r2 = ||X - [[U]]||^2 via the inner-product identity; fit = 1 - sqrt(r2)/||X||."""
+    dev = M.device
+    if r2 is None:
+        r2 = torch.empty((), dtype=torch.float64, device=dev)
+    if fit is None:
+        fit = torch.empty((), dtype=torch.float64, device=dev)
+    ptrs = [_req(g, torch.float64, "G").data_ptr() for g in G]
+    L.check(L.load().mtk_cp_residual(normX2.data_ptr(), _req(M, torch.float32, "M").data_ptr(),
+                                     _req(Um, torch.float32, "Um").data_ptr(), int(M.shape[0]),
+                                     L.ptr_arr(ptrs), len(G), int(M.shape[1]), r2.data_ptr(),
+                                     fit.data_ptr(), _stream(dev)), "mtk_cp_residual")
+    return r2, fit
+
+
+def cp_gradient(Un, Mn, G, n, *, scale=None, out=None):
+    """scale * (U_n Hadamard_{k!=n}(G_k) - M_n)."""
+    dev = Un.device
+    if out is None:
+        out = torch.empty_like(Un)
+    ptrs = [None if (k == n and g is None) else _req(g, torch.float64, "G").data_ptr()
+            for k, g in enumerate(G)]
+    sp = None
+    if scale is not None:
+        sp = _req(scale, torch.float32, "scale").data_ptr()
+    L.check(L.load().mtk_cp_gradient(_req(Un, torch.float32, "Un").data_ptr(),
+                                     _req(Mn, torch.float32, "Mn").data_ptr(), L.ptr_arr(ptrs),
+                                     len(G), int(Un.shape[1]), n, int(Un.shape[0]), sp, out.data_ptr(),
+                                     _stream(dev)), "mtk_cp_gradient")
+    return out
+
+
+class ALS:
+    """CP-ALS driver: holds the workspace, ||X||^2 and the device fit scalar."""
+
+    def __init__(self, X, dims, U, *, algo="auto", precision="auto", splits=0):
+        self.X = _req(X, torch.float32, "X")
+        self.dims = [int(d) for d in dims]
+        self.U = list(U)
+        self.C = _rank(self.U)
+        _factor_ptrs(self.U, self.dims, self.C)
+        self.opts = _opts(algo, precision, splits)
+        lib = L.load()
+        self._d = L.dims_arr(self.dims)
+        need = lib.mtk_cp_als_workspace(self._d, len(self.dims), self.C, L.ctypes.byref(self.opts))
+        if need == 0:
+            raise ValueError("invalid CP-ALS shape or options")
+        self.ws = Workspace(X.device)
+        self.ws.get(need)
+        self.need = need
+        self.normX2 = norm2(X, ws=Workspace(X.device))
+        self.fit = torch.zeros((), dtype=torch.float64, device=X.device)
+        self._uptrs = L.ptr_arr([u.data_ptr() for u in self.U])
+
+    def sweep(self, with_fit: bool = True) -> None:
+        lib = L.load()
+        wp, wb = self.ws.ptr(self.need)
+        L.check(lib.mtk_cp_als_sweep(self.X.data_ptr(), self._d, len(self.dims), self._uptrs, self.C,
+                                     self.normX2.data_ptr() if with_fit else None,
+                                     self.fit.data_ptr() if with_fit else None, wp, wb,
+                                     L.ctypes.byref(self.opts), _stream(self.X.device)),
+                "mtk_cp_als_sweep")
+
+    def status(self) -> int:
+        return self.ws.status()
+
+
+class CPLoss(torch.autograd.Function):
+    """f(U_0..U_{N-1}) = 0.5 ||X - [[U_0..U_{N-1}]]||^2 with a hand-written backward:
+    df/dU_n = U_n Hadamard_{k!=n}(U_k^T U_k) - MTTKRP(X, n), for every mode n.
+    X is treated as a constant.  Usage: CPLoss.apply(X, dims, opts_dict, *U)."""
+
+    @staticmethod
+    def forward(ctx, X, dims, opts, *U):
+        dims = [int(d) for d in dims]
+        N = len(dims)
+        opts = dict(opts or {})
+        G = [gram(u) for u in U]
+        M = mttkrp(X, dims, list(U), N - 1, **opts)
+        nx2 = norm2(X)
+        r2, _ = cp_residual(nx2, M, U[N - 1], G)
+        ctx.save_for_backward(X, *U)
+        ctx.dims = dims
+        ctx.opts = opts
+        ctx.M_last = M
+        ctx.G = G
+        return (0.5 * r2).to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, go):
+        X, *U = ctx.saved_tensors
+        dims, opts, G = ctx.dims, ctx.opts, ctx.G
+        N = len(dims)
+        scale = go.detach().to(torch.float32).contiguous()
+        grads = []
+        for n in range(N):
+            if not ctx.needs_input_grad[3 + n]:
+                grads.append(None)
+                continue
+            M = ctx.M_last if n == N - 1 else mttkrp(X, dims, list(U), n, **opts)
+            grads.append(cp_gradient(U[n], M, G, n, scale=scale))
+        return (None, None, None, *grads)
+
+
+def cp_loss(X, dims, U, **opts):
+    return CPLoss.apply(X, list(dims), opts, *U)

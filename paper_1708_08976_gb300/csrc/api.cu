@@ -1,0 +1,591 @@
+// api.cu -- the extern "C" entry points declared in include/mttkrp.h: argument
+// checks, workspace layout and the choice of kernels.  No device memory is
+// allocated here; every buffer comes from the caller.
+#include <string.h>
+
+#include "mtk_internal.cuh"
+
+#include <atomic>
+
+using namespace mtk;
+
+namespace mtk {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace mtk
+
+namespace {
+
+constexpr int kBK = 32;           // contraction stage of the kernels (see contract_simt.cu)
+constexpr int kSimtBI = 64;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carve {                    // bump allocator over a caller workspace
+    char* base;
+    size_t off, cap;
+    void* take(size_t bytes) {
+        off = align256(off);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+mtk_opts defaults(const mtk_opts* o) {
+    mtk_opts d;
+    memset(&d, 0, sizeof(d));
+    if (o) d = *o;
+    if (d.algo < MTK_ALGO_AUTO || d.algo > MTK_ALGO_TWO_STEP) d.algo = -1;
+    if (d.precision == MTK_PREC_AUTO) d.precision = MTK_PREC_FP32;
+    return d;
+}
+
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
+int check_shape(const int64_t* dims, int N, int C, int n) {
+    if (!dims || N < 2 || N > MTK_MAXN || C < 1 || C > MTK_MAXC || n < 0 || n >= N)
+        return MTK_EINVAL;
+    int64_t p = 1;
+    for (int k = 0; k < N; ++k) {
+        if (dims[k] < 1) return MTK_EINVAL;
+        if (p > ((int64_t)1 << 62) / dims[k]) return MTK_EINVAL;
+        p *= dims[k];
+    }
+    if (p > ((int64_t)1 << 62) / C) return MTK_EINVAL;
+    return MTK_OK;
+}
+
+struct View { int64_t L, I, R; };
+
+View mode_view(const int64_t* dims, int N, int n) {
+    View v{1, dims[n], 1};
+    for (int k = 0; k < n; ++k) v.L *= dims[k];
+    for (int k = n + 1; k < N; ++k) v.R *= dims[k];
+    return v;
+}
+
+// --- contraction planning --------------------------------------------------
+struct ContractPlan {
+    int tc;                 // use the tensor-core kernel
+    int S, i_tiles, c_blocks;
+    size_t part_bytes;
+};
+
+ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int splits,
+                           const ContractParams* probe) {
+    ContractPlan pl;
+    pl.tc = (precision == MTK_PREC_BF16X2 || precision == MTK_PREC_BF16X3) ? 1 : 0;
+    const int BI = pl.tc ? (probe ? contract_tc_i_tile(*probe) : 128) : kSimtBI;
+    pl.i_tiles = (int)((I + BI - 1) / BI);
+    pl.c_blocks = pl.tc ? 1 : (C + 31) / 32;
+    int64_t S = splits;
+    if (S <= 0) {
+        const int64_t target = 152 * (pl.tc ? 1 : 4);
+        const int64_t tiles = (int64_t)pl.i_tiles * pl.c_blocks;
+        S = (target + tiles - 1) / tiles;
+        const int64_t maxS = (K + 4 * kBK - 1) / (4 * kBK);   // >= 4 stages per split
+        if (S > maxS) S = maxS;
+    }
+    if (S < 1) S = 1;
+    if (S > 4096) S = 4096;
+    pl.S = (int)S;
+    pl.part_bytes = pl.S > 1 ? (size_t)pl.S * I * C * sizeof(float) : 0;
+    return pl;
+}
+
+// factor list of mode n: U_0..U_{n-1}, U_{n+1}..U_{N-1} (first fastest)
+struct FactorList {
+    int Z;
+    const float* f[MTK_MAXN];
+    int64_t rad[MTK_MAXN];
+};
+
+FactorList mode_factors(const float* const* U, const int64_t* dims, int N, int n) {
+    FactorList fl;
+    fl.Z = 0;
+    for (int k = 0; k < N; ++k) {
+        if (k == n) continue;
+        fl.f[fl.Z] = U ? U[k] : nullptr;
+        fl.rad[fl.Z] = dims[k];
+        ++fl.Z;
+    }
+    return fl;
+}
+
+// leading factors merged into one materialised head when the first radix is < 32
+int head_merge_count(const FactorList& fl) {
+    if (fl.Z <= 1 || fl.rad[0] >= kBK) return 0;
+    int m = 0;
+    int64_t p = 1;
+    while (m < fl.Z && p < kBK) { p *= fl.rad[m]; ++m; }
+    return m;
+}
+
+size_t head_bytes(const FactorList& fl, int C) {
+    const int m = head_merge_count(fl);
+    if (m == 0) return 0;
+    int64_t rows = 1;
+    for (int z = 0; z < m; ++z) rows *= fl.rad[z];
+    return (size_t)rows * C * sizeof(float);
+}
+
+// Build the KRP operand from a factor list; materialises a merged head into `head`
+// (device scratch of head_bytes) with the KRP kernel when needed.
+cudaError_t make_operand(const FactorList& fl, int C, float* head, KrpOperand* W, cudaStream_t s) {
+    memset(W, 0, sizeof(*W));
+    const int m = head_merge_count(fl);
+    if (m == 0) {
+        W->f0 = fl.f[0];
+        W->rad0 = fl.rad[0];
+        W->ntail = fl.Z - 1;
+        for (int z = 1; z < fl.Z; ++z) { W->tail[z - 1] = fl.f[z]; W->tail_rad[z - 1] = fl.rad[z]; }
+        return cudaSuccess;
+    }
+    // head = U_{m-1} kr ... kr U_0 (first factor fastest)
+    const float* ops[MTK_MAXN];
+    int64_t rows[MTK_MAXN];
+    int64_t hr = 1;
+    for (int z = 0; z < m; ++z) { ops[z] = fl.f[m - 1 - z]; rows[z] = fl.rad[m - 1 - z]; hr *= fl.rad[z]; }
+    cudaError_t e = launch_krp(ops, rows, m, C, head, 1, s);
+    W->f0 = head;
+    W->rad0 = hr;
+    W->ntail = fl.Z - m;
+    for (int z = m; z < fl.Z; ++z) { W->tail[z - m] = fl.f[z]; W->tail_rad[z - m] = fl.rad[z]; }
+    return e;
+}
+
+int run_contract(ContractParams& p, const ContractPlan& pl, int precision, cudaStream_t s) {
+    cudaError_t e;
+    if (pl.tc) {
+        if (!contract_tc_supported(p, precision)) return MTK_EUNSUPPORTED;
+        e = launch_contract_tc(p, precision, s);
+    } else {
+        e = launch_contract_simt(p, pl.c_blocks, pl.i_tiles, s);
+    }
+    if (e != cudaSuccess) return MTK_ECUDA;
+    if (p.S > 1) {
+        e = launch_split_reduce(p.part, p.S, p.I, p.C, p.out, p.out_si, p.out_sc, s);
+        if (e != cudaSuccess) return MTK_ECUDA;
+    }
+    return MTK_OK;
+}
+
+// --- MTTKRP workspace layout --------------------------------------------------
+struct MttkrpLayout {
+    int algo;               // resolved algorithm
+    int right;              // two-step ordering
+    ContractPlan plan;
+    size_t head, krp_full, kl, kr, tmat, total;
+};
+
+int resolve_algo(int algo, int N, int n) {
+    if (algo == MTK_ALGO_AUTO) return MTK_ALGO_FUSED;
+    if (algo == MTK_ALGO_TWO_STEP && (n == 0 || n == N - 1)) return MTK_ALGO_FUSED;  // degenerates
+    return algo;
+}
+
+MttkrpLayout mttkrp_layout(const int64_t* dims, int N, int C, int n, const mtk_opts& o) {
+    MttkrpLayout ly;
+    memset(&ly, 0, sizeof(ly));
+    const View v = mode_view(dims, N, n);
+    ly.algo = resolve_algo(o.algo, N, n);
+    Carve cv{nullptr, kStatusBytes, 0};
+    if (ly.algo == MTK_ALGO_FUSED) {
+        FactorList fl = mode_factors(nullptr, dims, N, n);
+        ly.head = head_bytes(fl, C);
+        cv.take(ly.head);
+        ly.plan = plan_contract(v.I, v.L * v.R, C, o.precision, o.splits, nullptr);
+    } else if (ly.algo == MTK_ALGO_MATERIALIZED) {
+        ly.krp_full = (size_t)v.L * v.R * C * sizeof(float);
+        cv.take(ly.krp_full);
+        ly.plan = plan_contract(v.I, v.L * v.R, C, o.precision, o.splits, nullptr);
+    } else {  // two-step, internal mode
+        ly.right = (v.L > v.R) ? 0 : 1;       // left first iff I^L > I^R (Algorithm 4)
+        ly.kl = (size_t)v.L * C * sizeof(float);
+        ly.kr = (size_t)v.R * C * sizeof(float);
+        ly.tmat = (size_t)(ly.right ? v.L * v.I : v.I * v.R) * C * sizeof(float);
+        cv.take(ly.kl);
+        cv.take(ly.kr);
+        cv.take(ly.tmat);
+        const int64_t Ip = ly.right ? v.L * v.I : v.I * v.R;
+        const int64_t Kp = ly.right ? v.R : v.L;
+        ly.plan = plan_contract(Ip, Kp, C, o.precision, o.splits, nullptr);
+    }
+    cv.take(ly.plan.part_bytes);
+    ly.total = align256(cv.off);
+    return ly;
+}
+
+// ws: workspace laid out by mttkrp_layout (its first kStatusBytes are not used here);
+// status: the device status word the kernels report into.
+int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U, int C, int n,
+              float* M, void* ws, size_t ws_bytes, uint32_t* status, const mtk_opts& o,
+              cudaStream_t s) {
+    const MttkrpLayout ly = mttkrp_layout(dims, N, C, n, o);
+    if (ws_bytes < ly.total) return MTK_EWORKSPACE;
+    const View v = mode_view(dims, N, n);
+    Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+    ContractParams p;
+    memset(&p, 0, sizeof(p));
+    p.X = X;
+    p.C = C;
+    p.status = status;
+    if (ly.algo == MTK_ALGO_FUSED || ly.algo == MTK_ALGO_MATERIALIZED) {
+        p.L = v.L; p.I = v.I; p.R = v.R; p.K = v.L * v.R;
+        FactorList fl = mode_factors(U, dims, N, n);
+        if (ly.algo == MTK_ALGO_FUSED) {
+            float* head = static_cast<float*>(cv.take(ly.head));
+            if (make_operand(fl, C, head, &p.W, s) != cudaSuccess) return MTK_ECUDA;
+        } else {
+            float* K = static_cast<float*>(cv.take(ly.krp_full));
+            const float* ops[MTK_MAXN];
+            int64_t rows[MTK_MAXN];
+            for (int z = 0; z < fl.Z; ++z) { ops[z] = fl.f[fl.Z - 1 - z]; rows[z] = fl.rad[fl.Z - 1 - z]; }
+            if (launch_krp(ops, rows, fl.Z, C, K, 1, s) != cudaSuccess) return MTK_ECUDA;
+            p.W.f0 = K; p.W.rad0 = p.K; p.W.ntail = 0;
+        }
+        p.out = M; p.out_si = C; p.out_sc = 1;
+        p.S = ly.plan.S;
+        p.part = static_cast<float*>(cv.take(ly.plan.part_bytes));
+        return run_contract(p, ly.plan, o.precision, s);
+    }
+    // two-step (Algorithm 4)
+    float* KL = static_cast<float*>(cv.take(ly.kl));
+    float* KR = static_cast<float*>(cv.take(ly.kr));
+    float* T = static_cast<float*>(cv.take(ly.tmat));
+    {
+        const float* ops[MTK_MAXN];
+        int64_t rows[MTK_MAXN];
+        int Z = 0;
+        for (int k = n - 1; k >= 0; --k) { ops[Z] = U[k]; rows[Z] = dims[k]; ++Z; }
+        if (launch_krp(ops, rows, Z, C, KL, 1, s) != cudaSuccess) return MTK_ECUDA;
+        Z = 0;
+        for (int k = N - 1; k > n; --k) { ops[Z] = U[k]; rows[Z] = dims[k]; ++Z; }
+        if (launch_krp(ops, rows, Z, C, KR, 1, s) != cudaSuccess) return MTK_ECUDA;
+    }
+    if (ly.right) {
+        p.L = 1; p.I = v.L * v.I; p.R = v.R; p.K = v.R;
+        p.W.f0 = KR; p.W.rad0 = v.R;
+        p.out = T; p.out_si = 1; p.out_sc = v.L * v.I;
+    } else {
+        p.L = v.L; p.I = v.I * v.R; p.R = 1; p.K = v.L;
+        p.W.f0 = KL; p.W.rad0 = v.L;
+        p.out = T; p.out_si = 1; p.out_sc = v.I * v.R;
+    }
+    p.S = ly.plan.S;
+    p.part = static_cast<float*>(cv.take(ly.plan.part_bytes));
+    int st = run_contract(p, ly.plan, o.precision, s);
+    if (st) return st;
+    if (launch_multi_ttv(T, v.L, v.I, v.R, ly.right ? KL : KR, C, ly.right, M, s) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+int check_mttkrp_ptrs(const float* X, const float* const* U, int N, int n, const float* M,
+                      const void* ws) {
+    if (!X || !U || !M || !ws) return MTK_EINVAL;
+    if (!aligned4(X) || !aligned4(M)) return MTK_EINVAL;
+    for (int k = 0; k < N; ++k) {
+        if (k == n) continue;
+        if (!U[k] || !aligned4(U[k])) return MTK_EINVAL;
+    }
+    return MTK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mtk_status_string(int st) {
+    switch (st) {
+        case MTK_OK: return "ok";
+        case MTK_EINVAL: return "invalid argument";
+        case MTK_ECUDA: return "CUDA error";
+        case MTK_ENOTPD: return "normal-equation matrix not positive definite";
+        case MTK_ETIMEOUT: return "device wait expired";
+        case MTK_EUNSUPPORTED: return "unsupported option for this shape";
+        case MTK_EWORKSPACE: return "workspace too small";
+        default: return "unknown status";
+    }
+}
+
+int mtk_version(void) { return 100; }
+
+uint64_t mtk_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
+int mtk_clear_status(void* ws, void* stream) {
+    if (!ws) return MTK_EINVAL;
+    if (cudaMemsetAsync(ws, 0, kStatusBytes, (cudaStream_t)stream) != cudaSuccess) return MTK_ECUDA;
+    return MTK_OK;
+}
+
+int mtk_read_status(const void* ws, void* stream, uint32_t* bits_out) {
+    if (!ws) return MTK_EINVAL;
+    uint32_t bits = 0;
+    if (cudaMemcpyAsync(&bits, ws, sizeof(bits), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+        cudaSuccess)
+        return MTK_ECUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return MTK_ECUDA;
+    if (bits_out) *bits_out = bits;
+    for (int code = 1; code < 32; ++code)
+        if (bits & (1u << code)) return code;
+    return MTK_OK;
+}
+
+int mtk_khatri_rao(const float* const* U, const int64_t* rows, int Z, int C, float* K, int reuse,
+                   void* stream) {
+    if (!U || !rows || !K || Z < 1 || Z > MTK_MAXN || C < 1 || C > MTK_MAXC) return MTK_EINVAL;
+    int64_t J = 1;
+    for (int z = 0; z < Z; ++z) {
+        if (!U[z] || rows[z] < 1 || !aligned4(U[z])) return MTK_EINVAL;
+        if (J > ((int64_t)1 << 62) / rows[z]) return MTK_EINVAL;
+        J *= rows[z];
+    }
+    if (!aligned4(K)) return MTK_EINVAL;
+    if (launch_krp(U, rows, Z, C, K, reuse, (cudaStream_t)stream) != cudaSuccess) return MTK_ECUDA;
+    return MTK_OK;
+}
+
+size_t mtk_mttkrp_workspace(const int64_t* dims, int N, int C, int n, const mtk_opts* opts) {
+    if (check_shape(dims, N, C, n) != MTK_OK) return 0;
+    mtk_opts o = defaults(opts);
+    if (o.algo < 0) return 0;
+    return mttkrp_layout(dims, N, C, n, o).total;
+}
+
+int mtk_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U, int C, int n,
+               float* M, void* ws, size_t ws_bytes, const mtk_opts* opts, void* stream) {
+    int st = check_shape(dims, N, C, n);
+    if (st) return st;
+    st = check_mttkrp_ptrs(X, U, N, n, M, ws);
+    if (st) return st;
+    mtk_opts o = defaults(opts);
+    if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
+    return do_mttkrp(X, dims, N, U, C, n, M, ws, ws_bytes, static_cast<uint32_t*>(ws), o,
+                     (cudaStream_t)stream);
+}
+
+size_t mtk_partial_mttkrp_workspace(const int64_t* dims, int N, int C, int n, int right,
+                                    const mtk_opts* opts) {
+    if (check_shape(dims, N, C, n) != MTK_OK) return 0;
+    mtk_opts o = defaults(opts);
+    const View v = mode_view(dims, N, n);
+    const int64_t Ip = right ? v.L * v.I : v.I * v.R;
+    const int64_t Kp = right ? v.R : v.L;
+    ContractPlan pl = plan_contract(Ip, Kp, C, o.precision, o.splits, nullptr);
+    return align256(align256(kStatusBytes) + pl.part_bytes);
+}
+
+int mtk_partial_mttkrp(const float* X, const int64_t* dims, int N, const float* Kp, int C, int n,
+                       int right, float* T, void* ws, size_t ws_bytes, const mtk_opts* opts,
+                       void* stream) {
+    int st = check_shape(dims, N, C, n);
+    if (st) return st;
+    if (!X || !Kp || !T || !ws || !aligned4(X) || !aligned4(Kp) || !aligned4(T)) return MTK_EINVAL;
+    mtk_opts o = defaults(opts);
+    if (o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
+    if (ws_bytes < mtk_partial_mttkrp_workspace(dims, N, C, n, right, opts)) return MTK_EWORKSPACE;
+    const View v = mode_view(dims, N, n);
+    ContractParams p;
+    memset(&p, 0, sizeof(p));
+    p.X = X; p.C = C; p.status = static_cast<uint32_t*>(ws);
+    if (right) {
+        p.L = 1; p.I = v.L * v.I; p.R = v.R; p.K = v.R;
+        p.W.f0 = Kp; p.W.rad0 = v.R;
+        p.out = T; p.out_si = 1; p.out_sc = v.L * v.I;
+    } else {
+        p.L = v.L; p.I = v.I * v.R; p.R = 1; p.K = v.L;
+        p.W.f0 = Kp; p.W.rad0 = v.L;
+        p.out = T; p.out_si = 1; p.out_sc = v.I * v.R;
+    }
+    ContractPlan pl = plan_contract(p.I, p.K, C, o.precision, o.splits, nullptr);
+    p.S = pl.S;
+    Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+    p.part = static_cast<float*>(cv.take(pl.part_bytes));
+    return run_contract(p, pl, o.precision, (cudaStream_t)stream);
+}
+
+int mtk_multi_ttv(const float* T, const int64_t* dims, int N, const float* Ko, int C, int n,
+                  int right, float* M, void* stream) {
+    int st = check_shape(dims, N, C, n);
+    if (st) return st;
+    if (!T || !Ko || !M || !aligned4(T) || !aligned4(Ko) || !aligned4(M)) return MTK_EINVAL;
+    const View v = mode_view(dims, N, n);
+    if (launch_multi_ttv(T, v.L, v.I, v.R, Ko, C, right ? 1 : 0, M, (cudaStream_t)stream) !=
+        cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+size_t mtk_gram_workspace(int64_t I, int C) {
+    if (I < 1 || C < 1 || C > MTK_MAXC) return 0;
+    const int nch = gram_chunks(I);
+    return align256(kStatusBytes) + align256((size_t)(nch > 1 ? nch : 0) * C * C * sizeof(double));
+}
+
+int mtk_gram(const float* U, int64_t I, int C, double* G, void* ws, size_t ws_bytes, void* stream) {
+    if (!U || !G || !ws || I < 1 || C < 1 || C > MTK_MAXC || !aligned4(U)) return MTK_EINVAL;
+    if (ws_bytes < mtk_gram_workspace(I, C)) return MTK_EWORKSPACE;
+    double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + align256(kStatusBytes));
+    if (launch_gram(U, I, C, G, part, gram_chunks(I), (cudaStream_t)stream) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+size_t mtk_solve_workspace(int64_t In, int C) {
+    (void)In;
+    if (C < 1 || C > MTK_MAXC) return 0;
+    return align256(kStatusBytes) + align256((size_t)C * C * sizeof(double)) + 256;
+}
+
+int mtk_gram_hadamard_solve(const double* const* G, int N, int C, int n, const float* M,
+                            int64_t In, float* Un, double* Gn, void* ws, size_t ws_bytes,
+                            void* stream) {
+    if (!G || !M || !Un || !ws || N < 2 || N > MTK_MAXN || n < 0 || n >= N || C < 1 ||
+        C > MTK_MAXC || In < 1)
+        return MTK_EINVAL;
+    for (int k = 0; k < N; ++k)
+        if (k != n && !G[k]) return MTK_EINVAL;
+    if (ws_bytes < mtk_solve_workspace(In, C)) return MTK_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = static_cast<char*>(ws);
+    double* Hbuf = reinterpret_cast<double*>(w + align256(kStatusBytes));
+    int* flag = reinterpret_cast<int*>(w + align256(kStatusBytes) + align256((size_t)C * C * sizeof(double)));
+    if (launch_chol_solve(G, N, C, n, M, In, Un, Hbuf, flag, static_cast<uint32_t*>(ws), s) !=
+        cudaSuccess)
+        return MTK_ECUDA;
+    if (Gn) {
+        if (gram_chunks(In) > 1) return MTK_EUNSUPPORTED;   // use mtk_gram with its workspace
+        if (launch_gram(Un, In, C, Gn, nullptr, 1, s) != cudaSuccess) return MTK_ECUDA;
+    }
+    return MTK_OK;
+}
+
+size_t mtk_norm2_workspace(int64_t I) {
+    if (I < 1) return 0;
+    return align256(kStatusBytes) + align256((size_t)norm2_chunks(I) * sizeof(double));
+}
+
+int mtk_norm2(const float* X, int64_t I, double* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!X || !out || !ws || I < 1 || !aligned4(X)) return MTK_EINVAL;
+    if (ws_bytes < mtk_norm2_workspace(I)) return MTK_EWORKSPACE;
+    double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + align256(kStatusBytes));
+    if (launch_norm2(X, I, part, norm2_chunks(I), out, (cudaStream_t)stream) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+// --- CP-ALS sweep ----------------------------------------------------------------
+namespace {
+struct AlsLayout {
+    size_t mbuf, gbufs, gpart, hbuf, flag, mt, total;
+    int maxIn;
+};
+
+AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o) {
+    AlsLayout a;
+    memset(&a, 0, sizeof(a));
+    int64_t maxIn = 0, maxChunks = 1;
+    size_t mt = 0;
+    for (int k = 0; k < N; ++k) {
+        if (dims[k] > maxIn) maxIn = dims[k];
+        const int ch = gram_chunks(dims[k]);
+        if (ch > maxChunks) maxChunks = ch;
+        const size_t w = mttkrp_layout(dims, N, C, k, o).total;
+        if (w > mt) mt = w;
+    }
+    a.maxIn = (int)maxIn;
+    Carve cv{nullptr, kStatusBytes, 0};
+    a.mbuf = (size_t)maxIn * C * sizeof(float); cv.take(a.mbuf);
+    a.gbufs = (size_t)N * C * C * sizeof(double); cv.take(a.gbufs);
+    a.gpart = maxChunks > 1 ? (size_t)maxChunks * C * C * sizeof(double) : 0; cv.take(a.gpart);
+    a.hbuf = (size_t)C * C * sizeof(double); cv.take(a.hbuf);
+    a.flag = 256; cv.take(a.flag);
+    a.mt = mt; cv.take(a.mt);
+    a.total = align256(cv.off);
+    return a;
+}
+}  // namespace
+
+size_t mtk_cp_als_workspace(const int64_t* dims, int N, int C, const mtk_opts* opts) {
+    for (int n = 0; n < N; ++n)
+        if (check_shape(dims, N, C, n) != MTK_OK) return 0;
+    if (N < 2) return 0;
+    mtk_opts o = defaults(opts);
+    if (o.algo < 0) return 0;
+    return als_layout(dims, N, C, o).total;
+}
+
+int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U, int C,
+                     const double* normX2, double* fit, void* ws, size_t ws_bytes,
+                     const mtk_opts* opts, void* stream) {
+    if (N < 2) return MTK_EINVAL;
+    for (int n = 0; n < N; ++n) {
+        int st = check_shape(dims, N, C, n);
+        if (st) return st;
+    }
+    if (!X || !U || !ws || !aligned4(X)) return MTK_EINVAL;
+    for (int k = 0; k < N; ++k)
+        if (!U[k] || !aligned4(U[k])) return MTK_EINVAL;
+    if (fit && !normX2) return MTK_EINVAL;
+    mtk_opts o = defaults(opts);
+    if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
+    const AlsLayout a = als_layout(dims, N, C, o);
+    if (ws_bytes < a.total) return MTK_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+    uint32_t* status = static_cast<uint32_t*>(ws);
+    float* M = static_cast<float*>(cv.take(a.mbuf));
+    double* Gall = static_cast<double*>(cv.take(a.gbufs));
+    double* gpart = static_cast<double*>(cv.take(a.gpart));
+    double* Hbuf = static_cast<double*>(cv.take(a.hbuf));
+    int* flag = static_cast<int*>(cv.take(a.flag));
+    char* mws = static_cast<char*>(cv.take(a.mt));
+    const double* G[MTK_MAXN];
+    for (int k = 0; k < N; ++k) G[k] = Gall + (size_t)k * C * C;
+    for (int k = 0; k < N; ++k)
+        if (launch_gram(U[k], dims[k], C, const_cast<double*>(G[k]), gpart, gram_chunks(dims[k]), s) !=
+            cudaSuccess)
+            return MTK_ECUDA;
+    for (int n = 0; n < N; ++n) {
+        int st = do_mttkrp(X, dims, N, U, C, n, M, mws, a.mt, status, o, s);
+        if (st) return st;
+        if (launch_chol_solve(G, N, C, n, M, dims[n], U[n], Hbuf, flag, status, s) != cudaSuccess)
+            return MTK_ECUDA;
+        if (launch_gram(U[n], dims[n], C, const_cast<double*>(G[n]), gpart, gram_chunks(dims[n]), s) !=
+            cudaSuccess)
+            return MTK_ECUDA;
+    }
+    if (fit) {
+        if (launch_residual(normX2, M, U[N - 1], dims[N - 1], G, N, C, nullptr, fit, s) !=
+            cudaSuccess)
+            return MTK_ECUDA;
+    }
+    return MTK_OK;
+}
+
+int mtk_cp_residual(const double* normX2, const float* M, const float* Um, int64_t Im,
+                    const double* const* G, int N, int C, double* r2, double* fit, void* stream) {
+    if (!normX2 || !M || !Um || !G || N < 2 || N > MTK_MAXN || C < 1 || C > MTK_MAXC || Im < 1)
+        return MTK_EINVAL;
+    for (int k = 0; k < N; ++k)
+        if (!G[k]) return MTK_EINVAL;
+    if (launch_residual(normX2, M, Um, Im, G, N, C, r2, fit, (cudaStream_t)stream) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+int mtk_cp_gradient(const float* Un, const float* Mn, const double* const* G, int N, int C, int n,
+                    int64_t In, const float* scale, float* grad, void* stream) {
+    if (!Un || !Mn || !G || !grad || N < 2 || N > MTK_MAXN || n < 0 || n >= N || C < 1 ||
+        C > MTK_MAXC || In < 1)
+        return MTK_EINVAL;
+    for (int k = 0; k < N; ++k)
+        if (k != n && !G[k]) return MTK_EINVAL;
+    if (launch_gradient(Un, Mn, G, N, C, n, In, scale, grad, (cudaStream_t)stream) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+}  // extern "C"

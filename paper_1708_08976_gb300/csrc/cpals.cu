@@ -1,0 +1,323 @@
+// cpals.cu -- the non-MTTKRP parts of a CP-ALS factor update (Section 2.2):
+//   G_k = U_k^T U_k (FP32 products, FP64 accumulation), H = Hadamard_{k != n} G_k,
+//   U_n = M H^{-1} through an FP64 Cholesky factorisation (the reading of the
+//   pseudoinverse for positive-definite H), ||X||^2 and the fit.
+// All reductions use fixed trees and fixed chunk orders, so results do not
+// depend on scheduling.
+#include "mtk_internal.cuh"
+
+namespace mtk {
+namespace {
+
+constexpr int kGramRows = 32;       // rows of U staged per step
+constexpr int64_t kGramChunk = 4096;  // rows per CTA
+
+// partial Gram of rows [chunk*kGramChunk, ...) for the pairs of block blockIdx.y
+// (1024 pairs per block, 4 per thread); out = part + chunk*C*C (or G if one chunk)
+__global__ void __launch_bounds__(256)
+gram_partial_kernel(const float* __restrict__ U, int64_t I, int C, double* __restrict__ out) {
+    extern __shared__ float us[];                 // kGramRows x C
+    const int64_t r0 = (int64_t)blockIdx.x * kGramChunk;
+    const int64_t r1 = (r0 + kGramChunk < I) ? r0 + kGramChunk : I;
+    const int npairs = C * C;
+    const int pbase = blockIdx.y * 1024;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t rb = r0; rb < r1; rb += kGramRows) {
+        const int nr = (int)((r1 - rb) < kGramRows ? (r1 - rb) : kGramRows);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * C; e += blockDim.x) us[e] = U[rb * C + e];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = pbase + threadIdx.x + q * blockDim.x;
+            if (e < npairs) {
+                const int a = e / C, b = e % C;
+                double s = acc[q];
+                for (int r = 0; r < nr; ++r) s += (double)us[r * C + a] * (double)us[r * C + b];
+                acc[q] = s;
+            }
+        }
+    }
+    for (int q = 0; q < 4; ++q) {
+        const int e = pbase + threadIdx.x + q * blockDim.x;
+        if (e < npairs) out[(int64_t)blockIdx.x * npairs + e] = acc[q];
+    }
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunks, int C,
+                                   double* __restrict__ G) {
+    const int npairs = C * C;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npairs; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nchunks; ++k) s += part[(int64_t)k * npairs + e];
+        G[e] = s;
+    }
+}
+
+struct GramList {
+    const double* G[MTK_MAXN];
+};
+
+// H = Hadamard_{k != n} G_k, then H = L L^T in place (lower triangle), one CTA.
+// A is dynamic shared memory (C*C doubles) when it fits, else the global buffer.
+__global__ void __launch_bounds__(256)
+chol_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __restrict__ Hbuf,
+            int* __restrict__ flag, uint32_t* status, int use_smem) {
+    extern __shared__ double hs[];
+    double* A = use_smem ? hs : Hbuf;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+        double h = 1.0;
+        for (int k = 0; k < N; ++k)
+            if (k != n) h *= gl.G[k][e];
+        A[e] = h;
+    }
+    __syncthreads();
+    // right-looking Cholesky, column j at a time
+    for (int j = 0; j < C; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = A[j * C + j];
+            if (!(d > 0.0)) bad = 1;
+            A[j * C + j] = (d > 0.0) ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        if (bad) break;
+        const double ljj = A[j * C + j];
+        for (int i = j + 1 + threadIdx.x; i < C; i += blockDim.x) A[i * C + j] /= ljj;
+        __syncthreads();
+        // trailing update of the lower triangle: A(i,k) -= L(i,j) L(k,j), j < k <= i
+        const int m = C - j - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) A[i * C + k] -= A[i * C + j] * A[k * C + j];
+        }
+        __syncthreads();
+    }
+    if (use_smem)
+        for (int e = threadIdx.x; e < C * C; e += blockDim.x) Hbuf[e] = A[e];
+    if (threadIdx.x == 0) {
+        *flag = bad ? 0 : 1;
+        if (bad) set_status(status, MTK_ENOTPD);
+    }
+}
+
+// U_n(i,:) = M(i,:) H^{-1}: with H = L L^T, solve L y = m, L^T x = y.  One warp per row;
+// the dot products of each substitution step are reduced in a fixed shuffle tree.
+__global__ void __launch_bounds__(256)
+trsm_rows_kernel(const double* __restrict__ Lg, const int* __restrict__ flag, const float* M,
+                 int64_t In, int C, float* Un, int use_smem) {
+    extern __shared__ double sh[];
+    const int warps = blockDim.x / 32;
+    double* Ls = use_smem ? sh : nullptr;
+    double* ybase = sh + (use_smem ? C * C : 0);
+    if (use_smem) {
+        for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ls[e] = Lg[e];
+    }
+    __syncthreads();
+    if (*flag == 0) return;
+    const double* L = use_smem ? Ls : Lg;
+    const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+    double* y = ybase + (size_t)w * 2 * C;
+    double* x = y + C;
+    for (int64_t i = (int64_t)blockIdx.x * warps + w; i < In; i += (int64_t)gridDim.x * warps) {
+        const float* m = M + i * C;
+        for (int a = 0; a < C; ++a) {
+            double s = 0.0;
+            for (int k = lane; k < a; k += 32) s += L[a * C + k] * y[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) y[a] = ((double)m[a] - s) / L[a * C + a];
+            __syncwarp();
+        }
+        for (int a = C - 1; a >= 0; --a) {
+            double s = 0.0;
+            for (int k = a + 1 + lane; k < C; k += 32) s += L[k * C + a] * x[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) x[a] = (y[a] - s) / L[a * C + a];
+            __syncwarp();
+        }
+        for (int c = lane; c < C; c += 32) Un[i * C + c] = (float)x[c];
+        __syncwarp();
+    }
+}
+
+constexpr int64_t kNormChunk = 1 << 20;   // entries per CTA
+
+__global__ void __launch_bounds__(256)
+norm2_partial_kernel(const float* __restrict__ X, int64_t I, double* __restrict__ part) {
+    __shared__ double red[256];
+    const int64_t a = (int64_t)blockIdx.x * kNormChunk;
+    const int64_t b = (a + kNormChunk < I) ? a + kNormChunk : I;
+    double acc = 0.0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    if (vec) {
+        // a is a multiple of 4 (kNormChunk is), so X + a stays 16-byte aligned
+        const int64_t nv = (b - a) / 4;
+        const float4* xv = reinterpret_cast<const float4*>(X + a);
+        for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+            const float4 q = xv[v];
+            acc += (double)(q.x * q.x + q.y * q.y) + (double)(q.z * q.z + q.w * q.w);
+        }
+        for (int64_t e = a + nv * 4 + threadIdx.x; e < b; e += blockDim.x) {
+            const float q = X[e];
+            acc += (double)(q * q);
+        }
+    } else {
+        for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+            const float q = X[e];
+            acc += (double)(q * q);
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_chunks_kernel(const double* __restrict__ part, int n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += part[k];
+        *out = s;
+    }
+}
+
+// r2 = ||X||^2 - 2 <M, U> + sum_{a,b} prod_k G_k(a,b)  (= ||X - [[U]]||^2 when M is the
+// MTTKRP of the mode U belongs to), fit = 1 - sqrt(max(0, r2)) / ||X||
+__global__ void __launch_bounds__(256)
+residual_kernel(const double* __restrict__ normX2, const float* __restrict__ M,
+                const float* __restrict__ U, int64_t I, const __grid_constant__ GramList gl, int N,
+                int C, double* r2_out, double* fit) {
+    __shared__ double red[256];
+    double inner = 0.0;
+    for (int64_t e = threadIdx.x; e < I * C; e += blockDim.x) inner += (double)M[e] * (double)U[e];
+    double y2 = 0.0;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+        double h = 1.0;
+        for (int k = 0; k < N; ++k) h *= gl.G[k][e];
+        y2 += h;
+    }
+    red[threadIdx.x] = y2 - 2.0 * inner;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nx2 = *normX2;
+        const double r2 = nx2 + red[0];
+        if (r2_out) *r2_out = r2;
+        if (fit) *fit = 1.0 - sqrt(r2 > 0.0 ? r2 : 0.0) / sqrt(nx2);
+    }
+}
+
+// grad(i, b) = scale * (sum_a U(i,a) H(a,b) - M(i,b)),  H = Hadamard_{k != n} G_k
+__global__ void __launch_bounds__(256)
+gradient_kernel(const float* __restrict__ U, const float* __restrict__ M,
+                const __grid_constant__ GramList gl, int N, int C, int n, int64_t In,
+                const float* __restrict__ scale, float* __restrict__ grad) {
+    extern __shared__ double Hs[];
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+        double h = 1.0;
+        for (int k = 0; k < N; ++k)
+            if (k != n) h *= gl.G[k][e];
+        Hs[e] = h;
+    }
+    __syncthreads();
+    const double sc = scale ? (double)*scale : 1.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < In * C;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / C;
+        const int b = (int)(e % C);
+        double s = 0.0;
+        for (int a = 0; a < C; ++a) s += (double)U[i * C + a] * Hs[a * C + b];
+        grad[e] = (float)(sc * (s - (double)M[e]));
+    }
+}
+
+}  // namespace
+
+int gram_chunks(int64_t I) { return (int)((I + kGramChunk - 1) / kGramChunk); }
+
+cudaError_t launch_gram(const float* U, int64_t I, int C, double* G, double* part, int nchunks,
+                        cudaStream_t s) {
+    const size_t smem = (size_t)kGramRows * C * sizeof(float);
+    const unsigned pblocks = (unsigned)((C * C + 1023) / 1024);
+    if (nchunks <= 1) {
+        gram_partial_kernel<<<dim3(1, pblocks), 256, smem, s>>>(U, I, C, G);
+        note_launches(1);
+    } else {
+        gram_partial_kernel<<<dim3(nchunks, pblocks), 256, smem, s>>>(U, I, C, part);
+        note_launches(1);
+        gram_reduce_kernel<<<(C * C + 255) / 256, 256, 0, s>>>(part, nchunks, C, G);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const float* M,
+                              int64_t In, float* Un, double* Hbuf, int* flag, uint32_t* status,
+                              cudaStream_t s) {
+    GramList gl;
+    for (int k = 0; k < MTK_MAXN; ++k) gl.G[k] = (k < N) ? G[k] : nullptr;
+    const size_t hbytes = (size_t)C * C * sizeof(double);
+    const int chol_smem = hbytes <= 200 * 1024;
+    if (chol_smem) {
+        cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hbytes);
+    }
+    chol_kernel<<<1, 256, chol_smem ? hbytes : 0, s>>>(gl, N, C, n, Hbuf, flag, status, chol_smem);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int warps = 8;
+    const size_t ybytes = (size_t)warps * 2 * C * sizeof(double);
+    const int trsm_smem = (hbytes + ybytes) <= 200 * 1024;
+    const size_t smem = (trsm_smem ? hbytes : 0) + ybytes;
+    cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t blocks = (In + warps - 1) / warps;
+    int grid = (int)(blocks < 152 * 4 ? blocks : 152 * 4);
+    trsm_rows_kernel<<<grid, warps * 32, smem, s>>>(Hbuf, flag, M, In, C, Un, trsm_smem);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+int norm2_chunks(int64_t I) { return (int)((I + kNormChunk - 1) / kNormChunk); }
+
+cudaError_t launch_norm2(const float* X, int64_t I, double* part, int nchunks, double* out,
+                         cudaStream_t s) {
+    norm2_partial_kernel<<<nchunks, 256, 0, s>>>(X, I, part);
+    note_launches(1);
+    sum_chunks_kernel<<<1, 32, 0, s>>>(part, nchunks, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double* normX2, const float* M, const float* U, int64_t I,
+                            const double* const* G, int N, int C, double* r2, double* fit,
+                            cudaStream_t s) {
+    GramList gl;
+    for (int k = 0; k < MTK_MAXN; ++k) gl.G[k] = (k < N) ? G[k] : nullptr;
+    residual_kernel<<<1, 256, 0, s>>>(normX2, M, U, I, gl, N, C, r2, fit);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(const float* U, const float* M, const double* const* G, int N, int C,
+                            int n, int64_t In, const float* scale, float* grad, cudaStream_t s) {
+    GramList gl;
+    for (int k = 0; k < MTK_MAXN; ++k) gl.G[k] = (k < N) ? G[k] : nullptr;
+    const size_t smem = (size_t)C * C * sizeof(double);
+    cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t blocks = (In * C + 255) / 256;
+    int grid = (int)(blocks < 152 * 4 ? blocks : 152 * 4);
+    gradient_kernel<<<grid, 256, smem, s>>>(U, M, gl, N, C, n, In, scale, grad);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace mtk

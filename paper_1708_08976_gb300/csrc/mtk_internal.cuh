@@ -1,0 +1,85 @@
+// mtk_internal.cuh -- declarations shared by the libmttkrp translation units.
+//
+// Notation (Section 2.1 of the paper): for mode n of an N-way tensor,
+// I^L = prod_{k<n} I_k, I^R = prod_{k>n} I_k.  Every contraction in this library
+// is expressed on the 3-way view X3(l, i, r) = X[l + L*i + L*I*r] (L = I^L,
+// I = I_n, R = I^R), which is exactly the natural layout (Section 2.1): the
+// mode-n matricization is R contiguous row-major I x L blocks (Fig. 2).  The
+// contraction index is k = l + L*r in [0, L*R), and the Khatri-Rao weight of
+// k is W(k, c) = prod_z F_z(d_z(k), c), where d_z are the mixed-radix digits of
+// k over the factor list (first factor fastest).  For mode n of a tensor the
+// list is U_0..U_{n-1}, U_{n+1}..U_{N-1}, i.e. the rows of
+// U_{N-1} kr ... kr U_{n+1} kr U_{n-1} kr ... kr U_0 (Section 2.2).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "mttkrp.h"
+
+#define MTK_MAXN 16
+#define MTK_MAXC 256
+
+namespace mtk {
+
+// status word at the head of every workspace (first 256 bytes reserved)
+constexpr size_t kStatusBytes = 256;
+
+__device__ __forceinline__ void set_status(uint32_t* st, int code) {
+    if (st) atomicOr(st, 1u << code);
+}
+
+// Khatri-Rao operand of a contraction, split as W(k,c) = F0(k % rad0, c) * Q(k / rad0, c)
+// with Q(q, c) = prod_t tail[t](digit_t(q), c).  The host guarantees that either
+// rad0 >= 32 or there is no tail (ntail == 0), so a block of 32 consecutive k
+// meets at most two values of q.
+struct KrpOperand {
+    const float* f0;
+    int64_t rad0;
+    int ntail;
+    const float* tail[MTK_MAXN];
+    int64_t tail_rad[MTK_MAXN];
+};
+
+struct ContractParams {
+    const float* X;
+    int64_t L, I, R, K;    // view and contraction length K = L*R
+    int C;                 // columns of W and of the output
+    KrpOperand W;
+    int S;                 // number of contraction splits
+    float* out;            // final output, element (i, c) at out[i*out_si + c*out_sc]
+    int64_t out_si, out_sc;
+    float* part;           // S x I x C partials when S > 1
+    uint32_t* status;
+};
+
+// host-side count of kernel launches issued by the library (monotonic, atomic)
+void note_launches(int n);
+
+// ---- launchers (host side), defined in the .cu files -------------------------
+cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,
+                                 cudaStream_t s);
+cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, float* out,
+                                int64_t si, int64_t sc, cudaStream_t s);
+bool contract_tc_supported(const ContractParams& p, int precision);
+cudaError_t launch_contract_tc(const ContractParams& p, int precision, cudaStream_t s);
+int contract_tc_i_tile(const ContractParams& p);
+
+cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C, float* K,
+                       int reuse, cudaStream_t s);
+cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, const float* Ko,
+                             int C, int right, float* M, cudaStream_t s);
+cudaError_t launch_gram(const float* U, int64_t I, int C, double* G, double* part,
+                        int nchunks, cudaStream_t s);
+int gram_chunks(int64_t I);
+cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const float* M,
+                              int64_t In, float* Un, double* Hbuf, int* flag,
+                              uint32_t* status, cudaStream_t s);
+cudaError_t launch_norm2(const float* X, int64_t I, double* part, int nchunks, double* out,
+                         cudaStream_t s);
+int norm2_chunks(int64_t I);
+cudaError_t launch_residual(const double* normX2, const float* M, const float* U, int64_t I,
+                            const double* const* G, int N, int C, double* r2, double* fit,
+                            cudaStream_t s);
+cudaError_t launch_gradient(const float* U, const float* M, const double* const* G, int N, int C,
+                            int n, int64_t In, const float* scale, float* grad, cudaStream_t s);
+
+}  // namespace mtk

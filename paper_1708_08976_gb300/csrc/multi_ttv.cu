@@ -1,0 +1,70 @@
+// multi_ttv.cu -- second step of the 2-step MTTKRP (Section 4.3, Algorithm 4).
+//
+// right ordering (after R = X_(0:n) K_R):   M(i,c) = sum_l T[l + L*i + L*I*c] * K_L(l,c)
+//   One warp per output entry: the warp reads the contiguous run T[L*i + L*I*c ..+L)
+//   with coalesced loads, multiplies by the strided column K_L(:,c) (L1-resident) and
+//   reduces with warp shuffles in a fixed tree.
+// left ordering (after L = X_(0:n-1)^T K_L): M(i,c) = sum_r T[i + I*r + I*R*c] * K_R(r,c)
+//   One thread per output entry, consecutive threads on consecutive i (coalesced
+//   column-major reads of T), K_R(r,c) broadcast within a warp; r summed in order.
+// Both orderings are deterministic.  Both are HBM-bound on T.
+#include "mtk_internal.cuh"
+
+namespace mtk {
+namespace {
+
+__global__ void __launch_bounds__(256)
+multi_ttv_right_kernel(const float* __restrict__ T, int64_t L, int64_t I,
+                       const float* __restrict__ KL, int C, float* __restrict__ M) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = I * C;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t w = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x / 32); w < nw;
+         w += warps_total) {
+        const int64_t i = w / C;
+        const int c = (int)(w % C);
+        const float* t = T + L * i + L * I * c;
+        float s = 0.0f;
+        for (int64_t l = lane; l < L; l += 32) s = fmaf(t[l], __ldg(KL + l * C + c), s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) M[i * C + c] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+multi_ttv_left_kernel(const float* __restrict__ T, int64_t I, int64_t R,
+                      const float* __restrict__ KR, int C, float* __restrict__ M) {
+    const int64_t n = I * C;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / I);
+        const int64_t i = e % I;
+        const float* t = T + i + I * R * c;
+        float s = 0.0f;
+        for (int64_t r = 0; r < R; ++r) s = fmaf(t[I * r], __ldg(KR + r * C + c), s);
+        M[i * C + c] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, const float* Ko,
+                             int C, int right, float* M, cudaStream_t s) {
+    if (right) {
+        const int64_t nw = I * C;
+        int64_t blocks = (nw + 7) / 8;
+        int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+        multi_ttv_right_kernel<<<grid, 256, 0, s>>>(T, L, I, Ko, C, M);
+        note_launches(1);
+    } else {
+        const int64_t n = I * C;
+        int64_t blocks = (n + 255) / 256;
+        int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+        multi_ttv_left_kernel<<<grid, 256, 0, s>>>(T, I, R, Ko, C, M);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mtk

@@ -1,0 +1,84 @@
+"""CPU-only checks of the C ABI: the library loads and exports every symbol that
+include/mttkrp.h declares, and host-side argument checks reject bad calls
+before any launch (no GPU needed: nothing here reaches the device)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1708_08976_gb300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "mttkrp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(mtk_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_header_symbol():
+    lib = L.load()
+    names = header_functions()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in L.SIGNATURES, f"binding lacks a signature for {name}"
+
+
+def test_status_strings():
+    lib = L.load()
+    assert lib.mtk_status_string(L.MTK_OK) == b"ok"
+    assert b"positive definite" in lib.mtk_status_string(L.MTK_ENOTPD)
+    assert lib.mtk_version() >= 100
+
+
+def test_workspace_queries_and_bad_shapes():
+    lib = L.load()
+    d = L.dims_arr([60, 50, 40])
+    o = L.opts()
+    for n in range(3):
+        assert lib.mtk_mttkrp_workspace(d, 3, 8, n, ctypes.byref(o)) >= 256
+    assert lib.mtk_mttkrp_workspace(d, 3, 8, 3, ctypes.byref(o)) == 0      # n out of range
+    assert lib.mtk_mttkrp_workspace(d, 3, 0, 0, ctypes.byref(o)) == 0      # C < 1
+    assert lib.mtk_mttkrp_workspace(d, 3, 257, 0, ctypes.byref(o)) == 0    # C > 256
+    assert lib.mtk_mttkrp_workspace(d, 1, 8, 0, ctypes.byref(o)) == 0      # N < 2
+    bad = L.dims_arr([60, 0, 40])
+    assert lib.mtk_mttkrp_workspace(bad, 3, 8, 0, ctypes.byref(o)) == 0    # zero dim
+    huge = L.dims_arr([1 << 31, 1 << 31, 4])
+    assert lib.mtk_mttkrp_workspace(huge, 3, 8, 0, ctypes.byref(o)) == 0   # overflow
+    for algo in (L.ALGO_FUSED, L.ALGO_MATERIALIZED, L.ALGO_TWO_STEP):
+        oa = L.opts(algo=algo)
+        assert lib.mtk_mttkrp_workspace(d, 3, 8, 1, ctypes.byref(oa)) >= 256
+    assert lib.mtk_cp_als_workspace(d, 3, 8, None) >= 256
+
+
+def test_null_and_misaligned_pointers_rejected_before_launch():
+    lib = L.load()
+    d = L.dims_arr([4, 5, 6])
+    fake = 0x10000
+    U = L.ptr_arr([fake, fake, fake])
+    # null X / M / ws
+    assert lib.mtk_mttkrp(None, d, 3, U, 2, 0, fake, fake, 1 << 20, None, None) == L.MTK_EINVAL
+    assert lib.mtk_mttkrp(fake, d, 3, U, 2, 0, None, fake, 1 << 20, None, None) == L.MTK_EINVAL
+    assert lib.mtk_mttkrp(fake, d, 3, U, 2, 0, fake, None, 1 << 20, None, None) == L.MTK_EINVAL
+    # misaligned X
+    assert lib.mtk_mttkrp(fake + 2, d, 3, U, 2, 0, fake, fake, 1 << 20, None, None) == L.MTK_EINVAL
+    # a null factor other than U[n]
+    U2 = L.ptr_arr([fake, None, fake])
+    assert lib.mtk_mttkrp(fake, d, 3, U2, 2, 0, fake, fake, 1 << 20, None, None) == L.MTK_EINVAL
+    # workspace too small
+    assert lib.mtk_mttkrp(fake, d, 3, U, 2, 0, fake, fake, 16, None, None) == L.MTK_EWORKSPACE
+    # bad precision
+    o = L.opts(precision=9)
+    assert lib.mtk_mttkrp(fake, d, 3, U, 2, 0, fake, fake, 1 << 20, ctypes.byref(o), None) == L.MTK_EINVAL
+    # KRP with a zero-row operand / bad Z
+    assert lib.mtk_khatri_rao(U, L.dims_arr([3, 0]), 2, 2, fake, 1, None) == L.MTK_EINVAL
+    assert lib.mtk_khatri_rao(U, L.dims_arr([3]), 0, 2, fake, 1, None) == L.MTK_EINVAL
+    # fit requested without ||X||^2
+    assert lib.mtk_cp_als_sweep(fake, d, 3, U, 2, None, fake, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    # solve with n out of range
+    G = L.ptr_arr([fake, fake, fake])
+    assert lib.mtk_gram_hadamard_solve(G, 3, 2, 3, fake, 4, fake, None, fake, 1 << 20, None) == L.MTK_EINVAL
