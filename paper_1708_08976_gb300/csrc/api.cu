@@ -16,7 +16,8 @@ void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::mem
 
 namespace {
 
-constexpr int kBK = 32;           // contraction stage of the kernels (see contract_simt.cu)
+constexpr int kBK = 64;           // the W operand needs rad0 >= kBK (or no tail factors)
+constexpr int kTcBK = 64;         // k per tensor-core stage; tensor-core splits are multiples
 constexpr int kSimtBI = 64;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -69,30 +70,54 @@ View mode_view(const int64_t* dims, int N, int n) {
 struct ContractPlan {
     int tc;                 // use the tensor-core kernel
     int S, i_tiles, c_blocks;
+    int64_t kchunk;         // contraction indices per split
     size_t part_bytes;
 };
 
-ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int splits,
-                           const ContractParams* probe) {
+// Work decomposition of one contraction.  `tc_ok` says whether the tensor-core
+// kernel accepts the shape; otherwise the FP32 kernel runs (it handles every shape).
+ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int splits, bool tc_ok) {
     ContractPlan pl;
-    pl.tc = (precision == MTK_PREC_BF16X2 || precision == MTK_PREC_BF16X3) ? 1 : 0;
-    const int BI = pl.tc ? (probe ? contract_tc_i_tile(*probe) : 128) : kSimtBI;
+    pl.tc = ((precision == MTK_PREC_BF16X2 || precision == MTK_PREC_BF16X3) && tc_ok) ? 1 : 0;
+    const int BI = pl.tc ? contract_tc_i_tile_rows(I) : kSimtBI;
     pl.i_tiles = (int)((I + BI - 1) / BI);
     pl.c_blocks = pl.tc ? 1 : (C + 31) / 32;
+    const int64_t quantum = pl.tc ? kTcBK : 1;              // split boundaries
     int64_t S = splits;
     if (S <= 0) {
-        const int64_t target = 152 * (pl.tc ? 1 : 4);
+        const int64_t target = 152 * (pl.tc ? 2 : 4);       // CTAs resident per wave
         const int64_t tiles = (int64_t)pl.i_tiles * pl.c_blocks;
-        S = (target + tiles - 1) / tiles;
-        const int64_t maxS = (K + 4 * kBK - 1) / (4 * kBK);   // >= 4 stages per split
+        S = target / tiles;
+        const int64_t maxS = (K + 4 * kTcBK - 1) / (4 * kTcBK);   // >= 4 stages per split
         if (S > maxS) S = maxS;
     }
     if (S < 1) S = 1;
     if (S > 4096) S = 4096;
-    pl.S = (int)S;
+    int64_t chunk = (K + S - 1) / S;
+    chunk = (chunk + quantum - 1) / quantum * quantum;
+    if (chunk < 1) chunk = 1;
+    pl.kchunk = chunk;
+    pl.S = (int)((K + chunk - 1) / chunk);
     pl.part_bytes = pl.S > 1 ? (size_t)pl.S * I * C * sizeof(float) : 0;
     return pl;
 }
+
+// plan for the contraction on view (L, I, *) with K contraction indices; x_aligned16
+// says whether the tensor pointer allows 16-byte loads
+ContractPlan plan_for(int64_t L, int64_t I, int64_t K, int C, const mtk_opts& o, bool x_aligned16) {
+    const bool tc_ok = x_aligned16 && contract_tc_shape_ok(L, I, C, o.precision);
+    return plan_contract(I, K, C, o.precision, o.splits, tc_ok);
+}
+
+// the plan used for workspace sizing: the larger partial buffer of the two alignments
+ContractPlan plan_both(int64_t L, int64_t I, int64_t K, int C, const mtk_opts& o) {
+    ContractPlan a = plan_for(L, I, K, C, o, true);
+    const ContractPlan b = plan_for(L, I, K, C, o, false);
+    if (b.part_bytes > a.part_bytes) a.part_bytes = b.part_bytes;
+    return a;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // factor list of mode n: U_0..U_{n-1}, U_{n+1}..U_{N-1} (first fastest)
 struct FactorList {
@@ -195,11 +220,11 @@ MttkrpLayout mttkrp_layout(const int64_t* dims, int N, int C, int n, const mtk_o
         FactorList fl = mode_factors(nullptr, dims, N, n);
         ly.head = head_bytes(fl, C);
         cv.take(ly.head);
-        ly.plan = plan_contract(v.I, v.L * v.R, C, o.precision, o.splits, nullptr);
+        ly.plan = plan_both(v.L, v.I, v.L * v.R, C, o);
     } else if (ly.algo == MTK_ALGO_MATERIALIZED) {
         ly.krp_full = (size_t)v.L * v.R * C * sizeof(float);
         cv.take(ly.krp_full);
-        ly.plan = plan_contract(v.I, v.L * v.R, C, o.precision, o.splits, nullptr);
+        ly.plan = plan_both(v.L, v.I, v.L * v.R, C, o);
     } else {  // two-step, internal mode
         ly.right = (v.L > v.R) ? 0 : 1;       // left first iff I^L > I^R (Algorithm 4)
         ly.kl = (size_t)v.L * C * sizeof(float);
@@ -210,7 +235,7 @@ MttkrpLayout mttkrp_layout(const int64_t* dims, int N, int C, int n, const mtk_o
         cv.take(ly.tmat);
         const int64_t Ip = ly.right ? v.L * v.I : v.I * v.R;
         const int64_t Kp = ly.right ? v.R : v.L;
-        ly.plan = plan_contract(Ip, Kp, C, o.precision, o.splits, nullptr);
+        ly.plan = plan_both(ly.right ? 1 : v.L, Ip, Kp, C, o);
     }
     cv.take(ly.plan.part_bytes);
     ly.total = align256(cv.off);
@@ -246,9 +271,11 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
             p.W.f0 = K; p.W.rad0 = p.K; p.W.ntail = 0;
         }
         p.out = M; p.out_si = C; p.out_sc = 1;
-        p.S = ly.plan.S;
+        const ContractPlan pl = plan_for(v.L, v.I, p.K, C, o, aligned16(X));
+        p.S = pl.S;
+        p.kchunk = pl.kchunk;
         p.part = static_cast<float*>(cv.take(ly.plan.part_bytes));
-        return run_contract(p, ly.plan, o.precision, s);
+        return run_contract(p, pl, o.precision, s);
     }
     // two-step (Algorithm 4)
     float* KL = static_cast<float*>(cv.take(ly.kl));
@@ -273,9 +300,11 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
         p.W.f0 = KL; p.W.rad0 = v.L;
         p.out = T; p.out_si = 1; p.out_sc = v.I * v.R;
     }
-    p.S = ly.plan.S;
+    const ContractPlan pl = plan_for(p.L, p.I, p.K, C, o, aligned16(X));
+    p.S = pl.S;
+    p.kchunk = pl.kchunk;
     p.part = static_cast<float*>(cv.take(ly.plan.part_bytes));
-    int st = run_contract(p, ly.plan, o.precision, s);
+    int st = run_contract(p, pl, o.precision, s);
     if (st) return st;
     if (launch_multi_ttv(T, v.L, v.I, v.R, ly.right ? KL : KR, C, ly.right, M, s) != cudaSuccess)
         return MTK_ECUDA;
@@ -373,7 +402,7 @@ size_t mtk_partial_mttkrp_workspace(const int64_t* dims, int N, int C, int n, in
     const View v = mode_view(dims, N, n);
     const int64_t Ip = right ? v.L * v.I : v.I * v.R;
     const int64_t Kp = right ? v.R : v.L;
-    ContractPlan pl = plan_contract(Ip, Kp, C, o.precision, o.splits, nullptr);
+    ContractPlan pl = plan_both(right ? 1 : v.L, Ip, Kp, C, o);
     return align256(align256(kStatusBytes) + pl.part_bytes);
 }
 
@@ -399,8 +428,9 @@ int mtk_partial_mttkrp(const float* X, const int64_t* dims, int N, const float* 
         p.W.f0 = Kp; p.W.rad0 = v.L;
         p.out = T; p.out_si = 1; p.out_sc = v.I * v.R;
     }
-    ContractPlan pl = plan_contract(p.I, p.K, C, o.precision, o.splits, nullptr);
+    ContractPlan pl = plan_for(p.L, p.I, p.K, C, o, aligned16(X));
     p.S = pl.S;
+    p.kchunk = pl.kchunk;
     Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
     p.part = static_cast<float*>(cv.take(pl.part_bytes));
     return run_contract(p, pl, o.precision, (cudaStream_t)stream);

@@ -71,7 +71,8 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int c0 = blockIdx.z * 32;
     const int C = p.C;
     const int64_t L = p.L, I = p.I;
-    const int64_t kb = p.K * sp / p.S, ke = p.K * (sp + 1) / p.S;
+    const int64_t kb = (int64_t)sp * p.kchunk;
+    const int64_t ke = (kb + p.kchunk < p.K) ? kb + p.kchunk : p.K;
     const int nst = (int)((ke - kb + BK - 1) / BK);
     const bool kfast = L > 1;
     const KrpOperand& W = p.W;

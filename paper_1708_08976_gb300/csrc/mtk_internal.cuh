@@ -45,6 +45,7 @@ struct ContractParams {
     int C;                 // columns of W and of the output
     KrpOperand W;
     int S;                 // number of contraction splits
+    int64_t kchunk;        // split sp covers k in [sp*kchunk, min((sp+1)*kchunk, K))
     float* out;            // final output, element (i, c) at out[i*out_si + c*out_sc]
     int64_t out_si, out_sc;
     float* part;           // S x I x C partials when S > 1
@@ -59,9 +60,10 @@ cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_ti
                                  cudaStream_t s);
 cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, float* out,
                                 int64_t si, int64_t sc, cudaStream_t s);
+bool contract_tc_shape_ok(int64_t L, int64_t I, int C, int precision);
 bool contract_tc_supported(const ContractParams& p, int precision);
 cudaError_t launch_contract_tc(const ContractParams& p, int precision, cudaStream_t s);
-int contract_tc_i_tile(const ContractParams& p);
+int contract_tc_i_tile_rows(int64_t I);
 
 cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C, float* K,
                        int reuse, cudaStream_t s);

@@ -191,19 +191,36 @@ def test_norm2():
     assert abs(got - ref) / ref < 1e-6
 
 
+def oracle_sweep_with_cond(X, dims, U):
+    """The oracle's sweep, one mode at a time, with cond(H_n) of every solve."""
+    Uc = [u.copy() for u in U]
+    conds = []
+    for n in range(len(dims)):
+        H = oracle.gram_hadamard(dims, Uc, n)
+        conds.append(float(np.linalg.cond(H)))
+        Uc[n] = oracle.chol_solve(oracle.cholesky(H), oracle.mttkrp(X, dims, Uc, n))
+    return Uc, conds
+
+
 @pytest.mark.parametrize("algo", ["fused", "two_step", "materialized"])
 def test_als_sweep_tiny3(algo):
-    """One CP-ALS sweep on the 60x50x40 rank-8 case against the FP64 oracle sweep."""
+    """One CP-ALS sweep on the 60x50x40 rank-8 case against the FP64 oracle sweep.
+
+    The solve U_n = M H^{-1} amplifies the ~1e-7 relative error of an FP32 MTTKRP by
+    up to cond(H_n) (21, 68 and 327 for the three modes here), so factor n is held to
+    1e-6 + 2e-7 * cond(H_n); the fit to 1e-6 absolute."""
     X, dims, U = synth.tiny3()
     Xr = X.astype(np.float32).astype(np.float64)
     Ur = f32_round(U)
     ref_U, ref_fit = oracle.als_sweep(Xr, dims, Ur)
+    _, conds = oracle_sweep_with_cond(Xr, dims, Ur)
     Ud = factors_dev(U, torch)
     als = mtk.ALS(to_dev(X, torch), dims, Ud, algo=algo, precision="fp32")
     als.sweep()
     assert als.status() == 0
     for k in range(3):
-        assert rel_fro(Ud[k].cpu().numpy(), ref_U[k]) < 1e-5, (k, rel_fro(Ud[k].cpu().numpy(), ref_U[k]))
+        err = rel_fro(Ud[k].cpu().numpy(), ref_U[k])
+        assert err < 1e-6 + 2e-7 * conds[k], (k, err, conds[k])
     assert abs(als.fit.item() - ref_fit) < 1e-6
 
 
