@@ -38,7 +38,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="corr4", choices=["corr4", "cube512"])
+    ap.add_argument("--workload", default="corr4", choices=["corr4", "cube512", "corr4-small"])
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only run every mode's MTTKRP W+K times (for profiler captures)")
     ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | best")
     ap.add_argument("--algo", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,6 +60,9 @@ def workload(name):
     if name == "corr4":
         X, dims, U = synth.corr4()
         desc = "corr4: 200x200x300x40 FP32 correlation-shaped (rank-10 CP, modes 0/1 symmetric, N(0,0.05^2) noise, clipped), rank C=25, factors uniform[0,1)"
+    elif name == "corr4-small":
+        X, dims, U = synth.corr4(dims=(200, 200, 30, 40))
+        desc = "corr4-small: 200x200x30x40 FP32 correlation-shaped (same per-mode I_n as corr4, 1/10 of the entries), rank C=25"
     else:
         X, dims, U = synth.cube512()
         desc = "cube512: 512^3 FP32 N(0,1), rank C=32, factors N(0,1)/sqrt(32)"
@@ -195,6 +200,21 @@ def main():
     flops_step = N * 2.0 * I * C
     Xd = torch.from_numpy(X).to(dev)
     U0 = [torch.from_numpy(u).to(dev) for u in U]
+    if args.kernel_only:
+        prec = "bf16x3" if args.precision == "best" else args.precision
+        ts = []
+        for n in range(N):
+            for it in range(args.warmup + args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                mtk.mttkrp(Xd, dims, U0, n, precision=prec, algo=args.algo)
+                b.record()
+                b.synchronize()
+                if it >= args.warmup:
+                    ts.append((n, a.elapsed_time(b) * 1e3))
+        print(json.dumps({"kernel_only": True, "workload": desc, "precision": prec,
+                          "us": [[n, round(t, 1)] for n, t in ts]}), flush=True)
+        return 0
 
     # accuracy of each precision form on every mode (vs the FP64 oracle on sampled rows)
     import oracle

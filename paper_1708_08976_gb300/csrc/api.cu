@@ -70,16 +70,19 @@ View mode_view(const int64_t* dims, int N, int n) {
 struct ContractPlan {
     int tc;                 // use the tensor-core kernel
     int S, i_tiles, c_blocks;
-    int64_t kchunk;         // contraction indices per split
+    int64_t kchunk;         // contraction indices per split (padded space for tc)
     size_t part_bytes;
+    size_t image_bytes;     // B-operand image of the tensor-core path
 };
 
 // Work decomposition of one contraction.  `tc_ok` says whether the tensor-core
 // kernel accepts the shape; otherwise the FP32 kernel runs (it handles every shape).
-ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int splits, bool tc_ok) {
+ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int splits, bool tc_ok,
+                           int BI_tc) {
     ContractPlan pl;
+    pl.image_bytes = 0;
     pl.tc = ((precision == MTK_PREC_BF16X2 || precision == MTK_PREC_BF16X3) && tc_ok) ? 1 : 0;
-    const int BI = pl.tc ? contract_tc_i_tile_rows(I) : kSimtBI;
+    const int BI = pl.tc ? BI_tc : kSimtBI;
     pl.i_tiles = (int)((I + BI - 1) / BI);
     pl.c_blocks = pl.tc ? 1 : (C + 31) / 32;
     const int64_t quantum = pl.tc ? kTcBK : 1;              // split boundaries
@@ -102,20 +105,33 @@ ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int split
     return pl;
 }
 
-// plan for the contraction on view (L, I, *) with K contraction indices; x_aligned16
-// says whether the tensor pointer allows 16-byte loads
-ContractPlan plan_for(int64_t L, int64_t I, int64_t K, int C, const mtk_opts& o, bool x_aligned16) {
-    const bool tc_ok = x_aligned16 && contract_tc_shape_ok(L, I, C, o.precision);
-    return plan_contract(I, K, C, o.precision, o.splits, tc_ok);
+// plan for the contraction on view (L, I, *) against the factor list (radices frad,
+// first fastest; their product is the contraction length); x_aligned16 says whether
+// the tensor pointer allows 16-byte loads
+ContractPlan plan_for(int64_t L, int64_t I, const int64_t* frad, int nfac, int C, const mtk_opts& o,
+                      bool x_aligned16) {
+    int64_t K = 1;
+    for (int z = 0; z < nfac; ++z) K *= frad[z];
+    const bool tc_ok = x_aligned16 && nfac >= 1 && contract_tc_shape_ok(L, I, C, o.precision);
+    if (tc_ok) {
+        const TcPlan tp = contract_tc_plan(frad, nfac, I, C);
+        ContractPlan pl = plan_contract(I, tp.Kp, C, o.precision, o.splits, true, tp.BI);
+        pl.image_bytes = tp.image_bytes;
+        return pl;
+    }
+    return plan_contract(I, K, C, o.precision, o.splits, false, 0);
 }
 
-// the plan used for workspace sizing: the larger partial buffer of the two alignments
-ContractPlan plan_both(int64_t L, int64_t I, int64_t K, int C, const mtk_opts& o) {
-    ContractPlan a = plan_for(L, I, K, C, o, true);
-    const ContractPlan b = plan_for(L, I, K, C, o, false);
+// the plan used for workspace sizing: the larger scratch of the two alignments
+ContractPlan plan_both(int64_t L, int64_t I, const int64_t* frad, int nfac, int C, const mtk_opts& o) {
+    ContractPlan a = plan_for(L, I, frad, nfac, C, o, true);
+    const ContractPlan b = plan_for(L, I, frad, nfac, C, o, false);
     if (b.part_bytes > a.part_bytes) a.part_bytes = b.part_bytes;
+    if (b.image_bytes > a.image_bytes) a.image_bytes = b.image_bytes;
     return a;
 }
+
+size_t plan_scratch(const ContractPlan& pl) { return align256(pl.image_bytes) + align256(pl.part_bytes); }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -180,11 +196,17 @@ cudaError_t make_operand(const FactorList& fl, int C, float* head, KrpOperand* W
     return e;
 }
 
-int run_contract(ContractParams& p, const ContractPlan& pl, int precision, cudaStream_t s) {
+// scratch: device memory of plan_scratch(sized plan) bytes (image, then partials)
+int run_contract(ContractParams& p, const ContractPlan& pl, int precision, void* scratch,
+                 cudaStream_t s) {
     cudaError_t e;
+    char* sc = static_cast<char*>(scratch);
+    p.S = pl.S;
+    p.kchunk = pl.kchunk;
+    p.part = reinterpret_cast<float*>(sc + align256(pl.image_bytes));
     if (pl.tc) {
         if (!contract_tc_supported(p, precision)) return MTK_EUNSUPPORTED;
-        e = launch_contract_tc(p, precision, s);
+        e = launch_contract_tc(p, precision, sc, s);
     } else {
         e = launch_contract_simt(p, pl.c_blocks, pl.i_tiles, s);
     }
@@ -220,11 +242,12 @@ MttkrpLayout mttkrp_layout(const int64_t* dims, int N, int C, int n, const mtk_o
         FactorList fl = mode_factors(nullptr, dims, N, n);
         ly.head = head_bytes(fl, C);
         cv.take(ly.head);
-        ly.plan = plan_both(v.L, v.I, v.L * v.R, C, o);
+        ly.plan = plan_both(v.L, v.I, fl.rad, fl.Z, C, o);
     } else if (ly.algo == MTK_ALGO_MATERIALIZED) {
         ly.krp_full = (size_t)v.L * v.R * C * sizeof(float);
         cv.take(ly.krp_full);
-        ly.plan = plan_both(v.L, v.I, v.L * v.R, C, o);
+        const int64_t rad = v.L * v.R;
+        ly.plan = plan_both(v.L, v.I, &rad, 1, C, o);
     } else {  // two-step, internal mode
         ly.right = (v.L > v.R) ? 0 : 1;       // left first iff I^L > I^R (Algorithm 4)
         ly.kl = (size_t)v.L * C * sizeof(float);
@@ -235,11 +258,16 @@ MttkrpLayout mttkrp_layout(const int64_t* dims, int N, int C, int n, const mtk_o
         cv.take(ly.tmat);
         const int64_t Ip = ly.right ? v.L * v.I : v.I * v.R;
         const int64_t Kp = ly.right ? v.R : v.L;
-        ly.plan = plan_both(ly.right ? 1 : v.L, Ip, Kp, C, o);
+        ly.plan = plan_both(ly.right ? 1 : v.L, Ip, &Kp, 1, C, o);
     }
-    cv.take(ly.plan.part_bytes);
+    cv.take(plan_scratch(ly.plan));
     ly.total = align256(cv.off);
     return ly;
+}
+
+void set_factors(ContractParams& p, const float* const* f, const int64_t* rad, int nfac) {
+    p.nfac = nfac;
+    for (int z = 0; z < nfac; ++z) { p.fac[z] = f[z]; p.frad[z] = rad[z]; }
 }
 
 // ws: workspace laid out by mttkrp_layout (its first kStatusBytes are not used here);
@@ -261,7 +289,9 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
         FactorList fl = mode_factors(U, dims, N, n);
         if (ly.algo == MTK_ALGO_FUSED) {
             float* head = static_cast<float*>(cv.take(ly.head));
-            if (make_operand(fl, C, head, &p.W, s) != cudaSuccess) return MTK_ECUDA;
+            set_factors(p, fl.f, fl.rad, fl.Z);
+            const ContractPlan pl = plan_for(v.L, v.I, p.frad, p.nfac, C, o, aligned16(X));
+            if (!pl.tc && make_operand(fl, C, head, &p.W, s) != cudaSuccess) return MTK_ECUDA;
         } else {
             float* K = static_cast<float*>(cv.take(ly.krp_full));
             const float* ops[MTK_MAXN];
@@ -269,13 +299,12 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
             for (int z = 0; z < fl.Z; ++z) { ops[z] = fl.f[fl.Z - 1 - z]; rows[z] = fl.rad[fl.Z - 1 - z]; }
             if (launch_krp(ops, rows, fl.Z, C, K, 1, s) != cudaSuccess) return MTK_ECUDA;
             p.W.f0 = K; p.W.rad0 = p.K; p.W.ntail = 0;
+            const float* kf = K;
+            set_factors(p, &kf, &p.K, 1);
         }
         p.out = M; p.out_si = C; p.out_sc = 1;
-        const ContractPlan pl = plan_for(v.L, v.I, p.K, C, o, aligned16(X));
-        p.S = pl.S;
-        p.kchunk = pl.kchunk;
-        p.part = static_cast<float*>(cv.take(ly.plan.part_bytes));
-        return run_contract(p, pl, o.precision, s);
+        const ContractPlan pl = plan_for(v.L, v.I, p.frad, p.nfac, C, o, aligned16(X));
+        return run_contract(p, pl, o.precision, cv.take(plan_scratch(ly.plan)), s);
     }
     // two-step (Algorithm 4)
     float* KL = static_cast<float*>(cv.take(ly.kl));
@@ -295,16 +324,17 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
         p.L = 1; p.I = v.L * v.I; p.R = v.R; p.K = v.R;
         p.W.f0 = KR; p.W.rad0 = v.R;
         p.out = T; p.out_si = 1; p.out_sc = v.L * v.I;
+        const float* kf = KR;
+        set_factors(p, &kf, &p.K, 1);
     } else {
         p.L = v.L; p.I = v.I * v.R; p.R = 1; p.K = v.L;
         p.W.f0 = KL; p.W.rad0 = v.L;
         p.out = T; p.out_si = 1; p.out_sc = v.I * v.R;
+        const float* kf = KL;
+        set_factors(p, &kf, &p.K, 1);
     }
-    const ContractPlan pl = plan_for(p.L, p.I, p.K, C, o, aligned16(X));
-    p.S = pl.S;
-    p.kchunk = pl.kchunk;
-    p.part = static_cast<float*>(cv.take(ly.plan.part_bytes));
-    int st = run_contract(p, pl, o.precision, s);
+    const ContractPlan pl = plan_for(p.L, p.I, p.frad, p.nfac, C, o, aligned16(X));
+    int st = run_contract(p, pl, o.precision, cv.take(plan_scratch(ly.plan)), s);
     if (st) return st;
     if (launch_multi_ttv(T, v.L, v.I, v.R, ly.right ? KL : KR, C, ly.right, M, s) != cudaSuccess)
         return MTK_ECUDA;
@@ -402,8 +432,8 @@ size_t mtk_partial_mttkrp_workspace(const int64_t* dims, int N, int C, int n, in
     const View v = mode_view(dims, N, n);
     const int64_t Ip = right ? v.L * v.I : v.I * v.R;
     const int64_t Kp = right ? v.R : v.L;
-    ContractPlan pl = plan_both(right ? 1 : v.L, Ip, Kp, C, o);
-    return align256(align256(kStatusBytes) + pl.part_bytes);
+    ContractPlan pl = plan_both(right ? 1 : v.L, Ip, &Kp, 1, C, o);
+    return align256(align256(kStatusBytes) + plan_scratch(pl));
 }
 
 int mtk_partial_mttkrp(const float* X, const int64_t* dims, int N, const float* Kp, int C, int n,
@@ -428,12 +458,11 @@ int mtk_partial_mttkrp(const float* X, const int64_t* dims, int N, const float* 
         p.W.f0 = Kp; p.W.rad0 = v.L;
         p.out = T; p.out_si = 1; p.out_sc = v.I * v.R;
     }
-    ContractPlan pl = plan_for(p.L, p.I, p.K, C, o, aligned16(X));
-    p.S = pl.S;
-    p.kchunk = pl.kchunk;
+    const float* kf = Kp;
+    set_factors(p, &kf, &p.K, 1);
+    ContractPlan pl = plan_for(p.L, p.I, p.frad, p.nfac, C, o, aligned16(X));
     Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
-    p.part = static_cast<float*>(cv.take(pl.part_bytes));
-    return run_contract(p, pl, o.precision, (cudaStream_t)stream);
+    return run_contract(p, pl, o.precision, cv.take(plan_scratch(pl)), (cudaStream_t)stream);
 }
 
 int mtk_multi_ttv(const float* T, const int64_t* dims, int N, const float* Ko, int C, int n,

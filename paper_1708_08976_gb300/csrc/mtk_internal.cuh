@@ -43,7 +43,10 @@ struct ContractParams {
     const float* X;
     int64_t L, I, R, K;    // view and contraction length K = L*R
     int C;                 // columns of W and of the output
-    KrpOperand W;
+    KrpOperand W;          // the operand as the FP32 kernel consumes it
+    int nfac;              // the raw factor list (first factor = fastest digit of k)
+    const float* fac[MTK_MAXN];
+    int64_t frad[MTK_MAXN];
     int S;                 // number of contraction splits
     int64_t kchunk;        // split sp covers k in [sp*kchunk, min((sp+1)*kchunk, K))
     float* out;            // final output, element (i, c) at out[i*out_si + c*out_sc]
@@ -60,10 +63,21 @@ cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_ti
                                  cudaStream_t s);
 cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, float* out,
                                 int64_t si, int64_t sc, cudaStream_t s);
+// Tensor-core contraction plan.  The factor list is split into a head (the first
+// `head` factors, rad0 rows of their KRP, padded to rad0p = a multiple of 64) whose
+// split BF16 image is the B operand, and a tail applied as a per-run column scale.
+// The contraction runs over the padded index k' = q*rad0p + d0, Kp = (K/rad0)*rad0p.
+struct TcPlan {
+    int head;
+    int64_t rad0, rad0p, Kp;
+    int BI, CP, N;
+    size_t image_bytes;
+};
 bool contract_tc_shape_ok(int64_t L, int64_t I, int C, int precision);
+TcPlan contract_tc_plan(const int64_t* frad, int nfac, int64_t I, int C);
 bool contract_tc_supported(const ContractParams& p, int precision);
-cudaError_t launch_contract_tc(const ContractParams& p, int precision, cudaStream_t s);
-int contract_tc_i_tile_rows(int64_t I);
+// image: device scratch of plan.image_bytes (256-byte aligned)
+cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* image, cudaStream_t s);
 
 cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C, float* K,
                        int reuse, cudaStream_t s);
