@@ -70,6 +70,7 @@ View mode_view(const int64_t* dims, int N, int n) {
 struct ContractPlan {
     int tc;                 // use the tensor-core kernel
     int S, i_tiles, c_blocks;
+    int slabs;              // partial slabs summed by the split reduce (S * packed runs)
     int64_t kchunk;         // contraction indices per split (padded space for tc)
     size_t part_bytes;
     size_t image_bytes;     // B-operand image of the tensor-core path
@@ -101,7 +102,8 @@ ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int split
     if (chunk < 1) chunk = 1;
     pl.kchunk = chunk;
     pl.S = (int)((K + chunk - 1) / chunk);
-    pl.part_bytes = pl.S > 1 ? (size_t)pl.S * I * C * sizeof(float) : 0;
+    pl.slabs = pl.S;
+    pl.part_bytes = pl.slabs > 1 ? (size_t)pl.slabs * I * C * sizeof(float) : 0;
     return pl;
 }
 
@@ -114,9 +116,11 @@ ContractPlan plan_for(int64_t L, int64_t I, const int64_t* frad, int nfac, int C
     for (int z = 0; z < nfac; ++z) K *= frad[z];
     const bool tc_ok = x_aligned16 && nfac >= 1 && contract_tc_shape_ok(L, I, C, o.precision);
     if (tc_ok) {
-        const TcPlan tp = contract_tc_plan(frad, nfac, I, C);
+        const TcPlan tp = contract_tc_plan(frad, nfac, L, I, C);
         ContractPlan pl = plan_contract(I, tp.Kp, C, o.precision, o.splits, true, tp.BI);
         pl.image_bytes = tp.image_bytes;
+        pl.slabs = pl.S * tp.U;
+        pl.part_bytes = pl.slabs > 1 ? (size_t)pl.slabs * I * C * sizeof(float) : 0;
         return pl;
     }
     return plan_contract(I, K, C, o.precision, o.splits, false, 0);
@@ -211,8 +215,8 @@ int run_contract(ContractParams& p, const ContractPlan& pl, int precision, void*
         e = launch_contract_simt(p, pl.c_blocks, pl.i_tiles, s);
     }
     if (e != cudaSuccess) return MTK_ECUDA;
-    if (p.S > 1) {
-        e = launch_split_reduce(p.part, p.S, p.I, p.C, p.out, p.out_si, p.out_sc, s);
+    if (pl.slabs > 1) {
+        e = launch_split_reduce(p.part, pl.slabs, p.I, p.C, p.out, p.out_si, p.out_sc, s);
         if (e != cudaSuccess) return MTK_ECUDA;
     }
     return MTK_OK;

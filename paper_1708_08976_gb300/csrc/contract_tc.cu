@@ -33,11 +33,10 @@
 // tensor operand A is K-major when k runs along the contiguous mode (I^L > 1) and
 // MN-major when i is the contiguous index (mode 0, I^L = 1); B is K-major.
 //
-// Warp roles (288 threads): 8 converter warps load the tensor with coalesced
-// 16-byte loads straight into registers (one stage ahead), split it, store the
-// pieces, and drain the accumulator; one thread of warp 8 issues tcgen05.mma.
-// The tensor goes through registers rather than TMA because the split needs it
-// there; a TMA stage would add a shared-memory write and read per entry.
+// Warp roles: CONV_WARPS converter warps copy the tensor with 16-byte cp.async into
+// a thread-private staging ring in shared memory (several stages in flight without
+// holding registers), split it, store the pieces, and drain the accumulator; one
+// thread of the last warp issues tcgen05.mma.
 //
 // Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel sets
 // MTK_ETIMEOUT in the status word, stops, frees its TMEM and returns.
@@ -49,15 +48,27 @@
 namespace mtk {
 namespace {
 
+// pipeline shape (compile-time; the defaults are the tuned ones)
+#ifndef MTK_TC_CONV_WARPS
+#define MTK_TC_CONV_WARPS 8
+#endif
+#ifndef MTK_TC_AB_STAGES
+#define MTK_TC_AB_STAGES 3
+#endif
+
 constexpr int TC_BK = 64;                    // k per stage
 constexpr int TC_M = 128;                    // MMA M
-constexpr int CONV_WARPS = 8;
+constexpr int CONV_WARPS = MTK_TC_CONV_WARPS;
 constexpr int CONV_THREADS = CONV_WARPS * 32;
 constexpr int NTHREADS = CONV_THREADS + 32;  // + the MMA warp
+constexpr int QW = CONV_WARPS / 4;           // converter warps per TMEM sub-partition
+constexpr int NCH = (64 + 16 * QW - 1) / (16 * QW);   // 16-column chunks per drain thread
 constexpr int MAX_STAGES = 4;
+constexpr int MAX_STAGING = 4;               // stages of tensor data in flight per thread
 constexpr int GROUP = 2;                     // stages per accumulation chain
 constexpr int PIECE_BYTES = TC_M * 128;      // one BF16 piece of the 128 x 64 tensor tile
-constexpr int MAX_CB = 64;                   // columns per launch
+constexpr int MAX_CB = 64;                   // columns per launch (one 16-column chunk per drain thread)
+constexpr int RPT = 1024 / CONV_THREADS;     // tile rows (or row octets) per converter thread per stage
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 struct TcParams {
@@ -66,8 +77,9 @@ struct TcParams {
     int ntail;
     const float* tail[MTK_MAXN];
     int64_t tail_rad[MTK_MAXN];
-    int64_t rad0, rad0p, Kp;
-    int BI, CP, N, stages, mn_major, stage_bytes, b_off, b_bytes, tmem_cols;
+    int64_t rad0, rad0p, Kp, nruns;
+    int BI, U, CP, N, stages, P, mn_major, linear, nslabs;
+    int stage_bytes, b_off, b_bytes, stg_off, tmem_cols;
     uint32_t idesc;
 };
 
@@ -92,9 +104,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n selp.u32 %0, 1, 0, P;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -201,14 +213,6 @@ __device__ __forceinline__ uint32_t mnmajor_off(int i, int k) {    // 128 rows o
     return (uint32_t)((g * 2 + a) * 1024 + kr * 128 + (((chunk ^ kr) & 7) << 4) + (i & 7) * 2);
 }
 
-__device__ __forceinline__ float4 ldg_stream(const float* ptr) {
-    float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(ptr));
-    return v;
-}
-
 // ---- B image: the head KRP split into three BF16 pieces, in stage slices --------
 struct ImgArgs {
     int head, C, CP, N;
@@ -267,9 +271,8 @@ __device__ __forceinline__ float tail_product(const TcParams& tp, int64_t q, int
     return prod;
 }
 
-// PX: tensor pieces; NCH: 16-column chunks of the output per converter thread;
-// MN: the tensor operand is i-contiguous (I^L == 1)
-template <int PX, int NCH, bool MN>
+// PX: tensor pieces; MN: the tensor operand is i-contiguous (I^L == 1)
+template <int PX, bool MN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 contract_tc_kernel(const __grid_constant__ TcParams tp) {
     extern __shared__ uint8_t dsm_raw[];
@@ -279,7 +282,6 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
     __shared__ __align__(8) uint64_t acce_bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ float qsh[CONV_WARPS][NCH * 16];     // per-warp tail scale of its columns
 
     const ContractParams& p = tp.p;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -290,13 +292,14 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
 
     const int64_t I = p.I, L = p.L;
     const int C = p.C, CP = tp.CP, N = tp.N;
-    const int64_t i0 = (int64_t)blockIdx.x * tp.BI;
-    const int rows = (int)((I - i0) < tp.BI ? (I - i0) : tp.BI);
+    const int BI = tp.BI, U = tp.U;
+    const int64_t i0 = (int64_t)blockIdx.x * BI;
+    const int rows = (int)((I - i0) < BI ? (I - i0) : BI);   // rows of i in each packed group
     const int sp = blockIdx.y;
-    const int64_t kb = (int64_t)sp * p.kchunk;                 // padded contraction index
+    const int64_t kb = (int64_t)sp * p.kchunk;                 // padded index over run-groups
     const int64_t ke = (kb + p.kchunk < tp.Kp) ? kb + p.kchunk : tp.Kp;
     const int nst = (int)((ke - kb + TC_BK - 1) / TC_BK);
-    const int64_t rad0 = tp.rad0, rad0p = tp.rad0p;
+    const int64_t rad0 = tp.rad0, rad0p = tp.rad0p, nruns = tp.nruns;
     const int spr = (int)(rad0p / TC_BK);                      // stages per run
 
     if (t == 0) {
@@ -311,8 +314,8 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // zero the tensor pieces of every stage once: rows (K-major) or i-quads (MN-major)
-    // beyond the tile are never written again and must read as zero
+    // zero the tensor pieces of every stage once: rows beyond the packed tile are never
+    // written again and must read as zero
     for (int s = 0; s < ST; ++s) {
         uint4* z = reinterpret_cast<uint4*>(dsm + s * tp.stage_bytes);
         for (int e = t; e < tp.b_off / 16; e += NTHREADS) z[e] = make_uint4(0, 0, 0, 0);
@@ -381,69 +384,148 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ converters
-        // K-major: thread owns rows r_j = (t>>4) + 16 j and the k-quad 4*(t&15) of each
-        // stage.  MN-major: float4 f_j = t + 256 j of the (rows/4 i-quads) x 64 k stage.
-        const int kq = t & 15;
-        const int r0 = t >> 4;
-        const int nq = rows >> 2;
-        int32_t moff[8];                                 // MN-major: i + I*k within a stage
-        uint32_t msoff[8];
-        int mkl[8];
-        if constexpr (MN) {
+        // Tile row m (0..127) is (u, il) = (m / BI, m % BI): output row i0 + il of run
+        // q = qg*U + u of the current run-group qg.  Each thread moves RPT rows x 8
+        // values per stage as 2*RPT float4 (two adjacent 16-byte loads per row):
+        //   K-major:  rows m_j = (t>>3) + (CONV_THREADS/8) j, values k = 8*(t&7) .. +7;
+        //   MN-major: octet f_j = t + CONV_THREADS j of the (U*BI/8 row-octets) x 64 k stage,
+        //             values i = 8*(f % nmo) .. +7 at k = f / nmo.
+        // The 8 values become one 16-byte store per BF16 piece.
+        const int ko = t & 7;
+        const int nmo = (U * BI) >> 3;
+        const int tile_rows_all = U * BI;
+        int mrow[RPT];                                   // tile row (first of the octet, MN)
+        int mkl[RPT];                                    // k within the stage
+        uint32_t soff[RPT];
+        uint32_t hvalid = 0;                             // bit 2j+h: half h of row j holds real rows
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int f = t + CONV_THREADS * j;
-                const int iq = nq > 0 ? f % nq : 0, kl = nq > 0 ? f / nq : TC_BK;
-                const bool v = nq > 0 && kl < TC_BK;
-                mkl[j] = v ? kl : TC_BK;
-                moff[j] = v ? (int32_t)(4 * iq + I * kl) : 0;
-                msoff[j] = v ? mnmajor_off(4 * iq, kl) : 0u;
-            }
-        }
-        const uint32_t ksoff0 = kmajor_off(r0, 4 * kq);      // K-major: row r0, + 2048 per j
-        // load tracker: padded position of the next stage to load, its run q and offset d0
-        int64_t ld_k = kb, ld_q = kb / rad0p, ld_d0 = kb % rad0p;
-        // (l, r) of the real index q*rad0 + d0 + 4*kq of this thread's k-quad (K-major)
-        int64_t xl = 0, xr = 0;
-        if constexpr (!MN) {
-            const int64_t k0 = ld_q * rad0 + ld_d0 + 4 * kq;
-            xl = k0 % L;
-            xr = k0 / L;
-        }
-        auto load_stage = [&](float4 (&v)[8]) {
+        for (int j = 0; j < RPT; ++j) {
             if constexpr (!MN) {
-                const bool kval = (ld_d0 + 4 * kq < rad0) && (ld_k + 4 * kq < ke);
-                const float* base = p.X + xl + L * I * xr + L * (i0 + r0);
-                const int64_t jstep = 16 * L;
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    v[j] = (kval && r0 + 16 * j < rows) ? ldg_stream(base + j * jstep)
-                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int m = (t >> 3) + (CONV_THREADS / 8) * j;
+                const bool v = m < tile_rows_all && (m % BI) < rows;
+                mrow[j] = m < tile_rows_all ? m : -1;
+                mkl[j] = 8 * ko;
+                soff[j] = (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + (((ko ^ (m & 7)) & 7) << 4));
+                if (v) hvalid |= 3u << (2 * j);
             } else {
-                const float* base = p.X + i0 + I * (ld_q * rad0 + ld_d0);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    v[j] = (mkl[j] < TC_BK && ld_d0 + mkl[j] < rad0 && ld_k + mkl[j] < ke)
-                               ? ldg_stream(base + moff[j])
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int f = t + CONV_THREADS * j;
+                const int mo = nmo > 0 ? f % nmo : 0, kl = nmo > 0 ? f / nmo : TC_BK;
+                const int m = 8 * mo;
+                const bool inside = nmo > 0 && kl < TC_BK;
+                mrow[j] = inside ? m : -1;
+                mkl[j] = kl;
+                soff[j] = inside ? mnmajor_off(m, kl) : 0u;
+                if (inside && (m % BI) < rows) hvalid |= 1u << (2 * j);
+                if (inside && (m % BI) + 4 < rows) hvalid |= 2u << (2 * j);
             }
+        }
+        // staging ring: thread-private 16-byte slots, P stages deep
+        const uint32_t stg = dsm_s + (uint32_t)tp.stg_off + (uint32_t)(t * 16);
+        // load tracker: next stage to issue (padded index ld_k; run-group ld_qg; offset ld_d0)
+        int64_t ld_k = kb, ld_qg = kb / rad0p, ld_d0 = kb % rad0p;
+        int64_t xl = 0, xr = 0;                          // non-linear runs (U == 1): (l, r) of the octet
+        const float* rbase[RPT];                         // row base pointers (see set_bases)
+        uint32_t rmask = 0;                              // bit 2j+h: load allowed for this run-group
+        int64_t rbase_qg = -1;
+        if constexpr (!MN) {
+            if (!tp.linear) {
+                const int64_t k0 = ld_qg * rad0 + ld_d0 + 8 * ko;
+                xl = k0 % L;
+                xr = k0 / L;
+            }
+        }
+        // linear runs: rbase = address of (row, run q, d0 = 0) plus the thread's k offset;
+        // non-linear: rbase = address of the row at (l, r) = (0, 0)
+        auto set_bases = [&]() {
+            rmask = 0;
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                rbase[j] = p.X;
+                if (mrow[j] < 0) continue;
+                const int u = mrow[j] / BI, il = mrow[j] % BI;
+                if (!tp.linear) {
+                    rbase[j] = p.X + L * (i0 + il);
+                    rmask |= hvalid & (3u << (2 * j));
+                    continue;
+                }
+                const int64_t q = ld_qg * U + u;
+                if (q >= nruns) continue;
+                const int64_t k0 = q * rad0;             // first real contraction index of run q
+                if constexpr (MN) rbase[j] = p.X + (i0 + il) + I * (k0 + mkl[j]);
+                else rbase[j] = p.X + (k0 % L) + L * I * (k0 / L) + L * (i0 + il) + 8 * ko;
+                rmask |= hvalid & (3u << (2 * j));
+            }
+            rbase_qg = ld_qg;
+        };
+        auto issue = [&](int slot) {
+            if (rbase_qg != ld_qg && (tp.linear || rbase_qg < 0)) set_bases();
+            // values of the stage that exist: k < lim (run end and split end)
+            int64_t lim64 = rad0 - ld_d0;
+            if (ke - ld_k < lim64) lim64 = ke - ld_k;
+            const int lim = lim64 > TC_BK ? TC_BK : (int)lim64;
+            int64_t common0, common1;                    // offsets of the two halves
+            if constexpr (MN) {
+                common0 = I * ld_d0;
+                common1 = common0 + 4;
+            } else if (true) {
+                if (tp.linear) {
+                    common0 = ld_d0;
+                    common1 = ld_d0 + 4;
+                } else {
+                    common0 = xl + L * I * xr;
+                    common1 = (xl + 4 < L) ? common0 + 4 : (xl + 4 - L) + L * I * (xr + 1);
+                }
+            }
+            const uint32_t sbase = stg + (uint32_t)(slot * 2 * RPT * CONV_THREADS * 16);
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                const int kl0 = mkl[j], kl1 = MN ? mkl[j] : mkl[j] + 4;
+                const bool v0 = ((rmask >> (2 * j)) & 1u) && kl0 < lim;
+                const bool v1 = ((rmask >> (2 * j + 1)) & 1u) && kl1 < lim;
+                const float* s0 = v0 ? rbase[j] + common0 : p.X;
+                const float* s1 = v1 ? rbase[j] + common1 : p.X;
+                const uint32_t d0 = sbase + (uint32_t)((2 * j) * CONV_THREADS * 16);
+                const uint32_t d1 = d0 + (uint32_t)(CONV_THREADS * 16);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d0), "l"(s0), "r"(v0 ? 16 : 0) : "memory");
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d1), "l"(s1), "r"(v1 ? 16 : 0) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
             // advance to the next stage (skipping the padding at the end of a run)
-            const int64_t delta = (ld_d0 + TC_BK == rad0p) ? (rad0 - ld_d0) : TC_BK;
             if constexpr (!MN) {
-                xl += delta;
-                while (xl >= L) { xl -= L; ++xr; }
+                if (!tp.linear) {
+                    const int64_t delta = (ld_d0 + TC_BK == rad0p) ? (rad0 - ld_d0) : TC_BK;
+                    xl += delta;
+                    while (xl >= L) { xl -= L; ++xr; }
+                }
             }
             ld_k += TC_BK;
             ld_d0 += TC_BK;
-            if (ld_d0 == rad0p) { ld_d0 = 0; ++ld_q; }
+            if (ld_d0 == rad0p) { ld_d0 = 0; ++ld_qg; }
         };
 
-        // production tracker (stage index within its run)
+        // production tracker (stage index within its run, run-group)
         int pr_sir = (int)((kb % rad0p) / TC_BK);
-        int64_t pr_q = kb / rad0p;
+        int64_t pr_qg = kb / rad0p;
 
-        auto produce = [&](const float4 (&v)[8], int s) -> bool {
+        auto produce = [&](int s) -> bool {
             const int slot = s % ST;
+            const int pslot = s % tp.P;
+            // the thread's own copies of stage s are complete after this wait (P groups
+            // are always committed ahead of the stage being read)
+            switch (tp.P) {
+                case 2: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+                case 3: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+                default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+            }
+            const uint32_t sbase = stg + (uint32_t)(pslot * 2 * RPT * CONV_THREADS * 16);
+            float4 v[2 * RPT];
+#pragma unroll
+            for (int e = 0; e < 2 * RPT; ++e) {
+                const uint32_t a = sbase + (uint32_t)(e * CONV_THREADS * 16);
+                asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                             : "=f"(v[e].x), "=f"(v[e].y), "=f"(v[e].z), "=f"(v[e].w)
+                             : "r"(a));
+            }
             if (s >= ST) {
                 if (!mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)(((s / ST) - 1) & 1), &abort_flag, kWaitNs)) {
                     abort_flag = 1;
@@ -459,36 +541,37 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
                               (uint32_t)tp.b_bytes, fb);
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                uint32_t so;
-                if constexpr (!MN) {
-                    if (r0 + 16 * j >= rows) continue;
-                    so = ksoff0 + (uint32_t)(j * 2048);
-                } else {
-                    if (mkl[j] >= TC_BK) continue;
-                    so = msoff[j];
-                }
-                uint2 pcs[PX];
-                split4<PX>(v[j], pcs);
+            for (int j = 0; j < RPT; ++j) {
+                if (mrow[j] < 0) continue;
+                uint2 lo[PX], hi[PX];
+                split4<PX>(v[2 * j], lo);
+                split4<PX>(v[2 * j + 1], hi);
 #pragma unroll
-                for (int q = 0; q < PX; ++q) *reinterpret_cast<uint2*>(st + q * PIECE_BYTES + so) = pcs[q];
+                for (int q = 0; q < PX; ++q)
+                    *reinterpret_cast<uint4*>(st + q * PIECE_BYTES + soff[j]) =
+                        make_uint4(lo[q].x, lo[q].y, hi[q].x, hi[q].y);
             }
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&full_bar[slot]));
+            // the staging slot is free again (its values were consumed above)
+            if (s + tp.P < nst) issue(pslot);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
             return true;
         };
 
-        // accumulator drain state
-        const int sub = warp & 3, half = warp >> 2;
-        float acc[NCH * 16];
+        // accumulator drain state: this thread's tile row (its TMEM lane), its run offset,
+        // and its 16-column chunks cc = 16 * (quarter + QW * m) of the CP columns
+        const int sub = warp & 3, quarter = warp >> 2;
+        const int myrow = sub * 32 + lane;
+        const int myu = myrow / BI, myil = myrow % BI;
+        const bool myvalid = myu < U && myil < rows;
+        float acc[16 * NCH];
+        float qc[16 * NCH];
 #pragma unroll
-        for (int e = 0; e < NCH * 16; ++e) acc[e] = 0.0f;
-        float* qc = qsh[warp];                           // the columns are warp-uniform
-        for (int e = lane; e < NCH * 16; e += 32) qc[e] = 1.0f;
-        __syncwarp();
+        for (int e = 0; e < 16 * NCH; ++e) { acc[e] = 0.0f; qc[e] = 1.0f; }
         int64_t q_cached = -1;
-        auto drain = [&](int g, int64_t q) -> bool {
+        auto drain = [&](int g, int64_t qg) -> bool {
             const int b = g & 1;
             if (!mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((g >> 1) & 1), &abort_flag, kWaitNs)) {
                 abort_flag = 1;
@@ -496,83 +579,81 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
                 return false;
             }
             tc_fence_after();
-            if (tp.ntail > 0 && q != q_cached) {
-                __syncwarp();
-                for (int e = lane; e < NCH * 16; e += 32) {
-                    const int c = 16 * half + 32 * (e >> 4) + (e & 15);
-                    qc[e] = (c < C) ? tail_product(tp, q, c, C) : 0.0f;
-                }
-                q_cached = q;
-                __syncwarp();
-            }
+            const int64_t q = qg * U + myu;
+            const bool live = myvalid && q < nruns;
+            const bool newq = tp.ntail > 0 && q != q_cached && live;
 #pragma unroll
             for (int m = 0; m < NCH; ++m) {
-                const int cc = 16 * half + 32 * m;
-                if (cc < CP) {                            // warp-uniform
-                    float sum[16], v[16];
-                    const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(b * N + cc);
-                    tmem_ld16(ta, sum);
-                    tmem_ld_wait();
-                    tmem_ld16(ta + (uint32_t)CP, v);
-                    tmem_ld_wait();
+                const int cc = 16 * (quarter + QW * m);
+                if (cc >= CP) continue;                  // warp-uniform
+                if (newq) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sum[j] += v[j];
-                    tmem_ld16(ta + (uint32_t)(2 * CP), v);
-                    tmem_ld_wait();
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = cc + j;
+                        qc[16 * m + j] = (c < C) ? tail_product(tp, q, c, C) : 0.0f;
+                    }
+                }
+                float v0[16], v1[16], v2[16];
+                const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(b * N + cc);
+                tmem_ld16(ta, v0);
+                tmem_ld16(ta + (uint32_t)CP, v1);
+                tmem_ld16(ta + (uint32_t)(2 * CP), v2);
+                tmem_ld_wait();
+                if (live) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[m * 16 + j] = fmaf(sum[j] + v[j], qc[m * 16 + j], acc[m * 16 + j]);
+                    for (int j = 0; j < 16; ++j)
+                        acc[16 * m + j] = fmaf((v0[j] + v1[j]) + v2[j], qc[16 * m + j], acc[16 * m + j]);
                 }
             }
+            if (newq) q_cached = q;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
             return true;
         };
 
-        float4 va[8], vb[8];
         int g = 0;
         bool pending = false, ok = true;
         int pend_g = 0;
-        int64_t pend_q = 0;
-        // one production step: stage s from registers v, then drain the previous group
-        auto step = [&](const float4 (&v)[8], int s) -> bool {
-            if (!produce(v, s)) return false;
+        int64_t pend_qg = 0;
+        for (int sl = 0; sl < tp.P; ++sl) {
+            if (sl < nst) issue(sl);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        for (int s = 0; s < nst; ++s) {
+            if (!produce(s)) { ok = false; break; }
             const bool last = ((pr_sir + 1) % GROUP == 0) || (pr_sir + 1 == spr) || (s == nst - 1);
-            const int64_t q_s = pr_q;
-            if (++pr_sir == spr) { pr_sir = 0; ++pr_q; }
+            const int64_t qg_s = pr_qg;
+            if (++pr_sir == spr) { pr_sir = 0; ++pr_qg; }
             if (last) {
-                if (pending && !drain(pend_g, pend_q)) return false;
+                if (pending && !drain(pend_g, pend_qg)) { ok = false; break; }
                 pend_g = g;
-                pend_q = q_s;
+                pend_qg = qg_s;
                 pending = true;
                 ++g;
             }
-            return true;
-        };
-        if (nst > 0) load_stage(va);
-        for (int s = 0; s < nst && ok; s += 2) {
-            if (s + 1 < nst) load_stage(vb);
-            if (!step(va, s)) { ok = false; break; }
-            if (s + 1 >= nst) break;
-            if (s + 2 < nst) load_stage(va);
-            if (!step(vb, s + 1)) { ok = false; break; }
         }
-        if (ok && pending) ok = drain(pend_g, pend_q);
+        if (ok && pending) ok = drain(pend_g, pend_qg);
+        asm volatile("cp.async.wait_all;" ::: "memory");
 
         // ------------------------------------------------------------ epilogue
-        const int row = sub * 32 + lane;
-        if (ok && row < rows) {
-            const int64_t i = i0 + row;
+        // packed run offsets become separate partial slabs: slab = sp * U + u
+        if (ok && myvalid) {
+            const int64_t i = i0 + myil;
+            const int64_t slab = (int64_t)sp * U + myu;
 #pragma unroll
-            for (int m = 0; m < NCH; ++m)
+            for (int m = 0; m < NCH; ++m) {
+                const int cc = 16 * (quarter + QW * m);
+                if (cc >= CP) continue;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int c = 16 * half + 32 * m + j;
+                    const int c = cc + j;
                     if (c < C) {
-                        if (p.S == 1) p.out[i * p.out_si + c * p.out_sc] = acc[m * 16 + j];
-                        else p.part[((int64_t)sp * I + i) * C + c] = acc[m * 16 + j];
+                        if (tp.nslabs == 1) p.out[i * p.out_si + c * p.out_sc] = acc[16 * m + j];
+                        else p.part[(slab * I + i) * C + c] = acc[16 * m + j];
                     }
                 }
+            }
         }
         tc_fence_before();
     }
@@ -586,16 +667,16 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
 int tile_rows(int64_t I) {
     const int64_t tiles = (I + TC_M - 1) / TC_M;
     int64_t bi = (I + tiles - 1) / tiles;
-    bi = (bi + 3) & ~3LL;
+    bi = (bi + 7) & ~7LL;
     return (int)(bi > TC_M ? TC_M : bi);
 }
 
-template <int PX, int NCH, bool MN>
+template <int PX, bool MN>
 cudaError_t launch_variant(const TcParams& tp, dim3 grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PX, NCH, MN>,
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PX, MN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    contract_tc_kernel<PX, NCH, MN><<<grid, NTHREADS, smem, s>>>(tp);
+    contract_tc_kernel<PX, MN><<<grid, NTHREADS, smem, s>>>(tp);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -609,7 +690,7 @@ bool contract_tc_shape_ok(int64_t L, int64_t I, int C, int precision) {
     return L % 4 == 0;                                          // 16-byte loads along k
 }
 
-TcPlan contract_tc_plan(const int64_t* frad, int nfac, int64_t I, int C) {
+TcPlan contract_tc_plan(const int64_t* frad, int nfac, int64_t L, int64_t I, int C) {
     TcPlan pl;
     memset(&pl, 0, sizeof(pl));
     // head: fewest leading factors with >= 64 rows, <= 1/32 padding and a row count
@@ -628,8 +709,19 @@ TcPlan contract_tc_plan(const int64_t* frad, int nfac, int64_t I, int C) {
     pl.head = m;
     pl.rad0 = prod;
     pl.rad0p = (prod + TC_BK - 1) / TC_BK * TC_BK;
-    pl.Kp = (K / prod) * pl.rad0p;
-    pl.BI = tile_rows(I);
+    pl.nruns = K / prod;
+    // runs are contiguous in memory when i is the contiguous index or the head lies
+    // inside the modes left of n (rad0 divides I^L)
+    pl.linear = (L == 1 || L % prod == 0) ? 1 : 0;
+    // small I: pack U runs into the 128 MMA rows (needs contiguous runs)
+    pl.U = 1;
+    if (pl.linear && I <= TC_M / 2 && pl.nruns > 1 && (L > 1 || I % 8 == 0)) {
+        int64_t u = TC_M / I;
+        if (u > pl.nruns) u = pl.nruns;
+        pl.U = (int)u;
+    }
+    pl.BI = pl.U > 1 ? (int)I : tile_rows(I);
+    pl.Kp = ((pl.nruns + pl.U - 1) / pl.U) * pl.rad0p;
     pl.CP = (C + 15) & ~15;
     pl.N = 3 * pl.CP;
     pl.image_bytes = (size_t)(pl.rad0p / TC_BK) * pl.N * 128;
@@ -645,7 +737,7 @@ bool contract_tc_supported(const ContractParams& p, int precision) {
 }
 
 cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* image, cudaStream_t s) {
-    const TcPlan pl = contract_tc_plan(p.frad, p.nfac, p.I, p.C);
+    const TcPlan pl = contract_tc_plan(p.frad, p.nfac, p.L, p.I, p.C);
     TcParams tp;
     memset(&tp, 0, sizeof(tp));
     tp.p = p;
@@ -658,17 +750,27 @@ cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* ima
     tp.rad0 = pl.rad0;
     tp.rad0p = pl.rad0p;
     tp.Kp = pl.Kp;
+    tp.nruns = pl.nruns;
     tp.BI = pl.BI;
+    tp.U = pl.U;
     tp.CP = pl.CP;
     tp.N = pl.N;
+    tp.linear = pl.linear;
+    tp.nslabs = p.S * pl.U;
     tp.mn_major = p.L == 1 ? 1 : 0;
     const int px = precision == MTK_PREC_BF16X3 ? 3 : 2;
     tp.b_off = px * PIECE_BYTES;
     tp.b_bytes = pl.N * 128;
     tp.stage_bytes = tp.b_off + ((tp.b_bytes + 1023) & ~1023);
-    tp.stages = (int)((200 * 1024) / tp.stage_bytes);
-    if (tp.stages > MAX_STAGES) tp.stages = MAX_STAGES;
-    if (tp.stages < 2) tp.stages = 2;
+    tp.stages = MTK_TC_AB_STAGES;
+    const int stg_stage = 2 * RPT * CONV_THREADS * 16;           // 32 KB of staging per stage
+    const int budget = 222 * 1024;
+    while (tp.stages > 2 && budget - tp.stages * tp.stage_bytes < 2 * stg_stage) --tp.stages;
+    int P = (budget - tp.stages * tp.stage_bytes) / stg_stage;
+    if (P > MAX_STAGING) P = MAX_STAGING;
+    if (P < 2) P = 2;
+    tp.P = P;
+    tp.stg_off = tp.stages * tp.stage_bytes;
     int cols = 32;
     while (cols < 2 * pl.N) cols <<= 1;
     tp.tmem_cols = cols;
@@ -697,17 +799,12 @@ cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* ima
     if (e != cudaSuccess) return e;
 
     // 2) the contraction
-    const size_t smem = (size_t)tp.stages * tp.stage_bytes + 1024;
+    const size_t smem = (size_t)tp.stg_off + (size_t)tp.P * stg_stage + 1024;
     const int64_t tiles = (p.I + tp.BI - 1) / tp.BI;
     const dim3 grid((unsigned)tiles, (unsigned)p.S);
-    const int nch = pl.CP <= 32 ? 1 : 2;
     const bool mn = tp.mn_major != 0;
-    if (px == 3) {
-        if (nch == 1) return mn ? launch_variant<3, 1, true>(tp, grid, smem, s) : launch_variant<3, 1, false>(tp, grid, smem, s);
-        return mn ? launch_variant<3, 2, true>(tp, grid, smem, s) : launch_variant<3, 2, false>(tp, grid, smem, s);
-    }
-    if (nch == 1) return mn ? launch_variant<2, 1, true>(tp, grid, smem, s) : launch_variant<2, 1, false>(tp, grid, smem, s);
-    return mn ? launch_variant<2, 2, true>(tp, grid, smem, s) : launch_variant<2, 2, false>(tp, grid, smem, s);
+    if (px == 3) return mn ? launch_variant<3, true>(tp, grid, smem, s) : launch_variant<3, false>(tp, grid, smem, s);
+    return mn ? launch_variant<2, true>(tp, grid, smem, s) : launch_variant<2, false>(tp, grid, smem, s);
 }
 
 }  // namespace mtk

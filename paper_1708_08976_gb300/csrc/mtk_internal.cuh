@@ -67,14 +67,16 @@ cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, floa
 // `head` factors, rad0 rows of their KRP, padded to rad0p = a multiple of 64) whose
 // split BF16 image is the B operand, and a tail applied as a per-run column scale.
 // The contraction runs over the padded index k' = q*rad0p + d0, Kp = (K/rad0)*rad0p.
+// For small I (<= 64) with contiguous runs, U runs share the 128 MMA rows; each packed
+// run offset writes its own partial slab (S * U slabs in all).
 struct TcPlan {
     int head;
-    int64_t rad0, rad0p, Kp;
-    int BI, CP, N;
+    int64_t rad0, rad0p, Kp, nruns;
+    int BI, U, linear, CP, N;
     size_t image_bytes;
 };
 bool contract_tc_shape_ok(int64_t L, int64_t I, int C, int precision);
-TcPlan contract_tc_plan(const int64_t* frad, int nfac, int64_t I, int C);
+TcPlan contract_tc_plan(const int64_t* frad, int nfac, int64_t L, int64_t I, int C);
 bool contract_tc_supported(const ContractParams& p, int precision);
 // image: device scratch of plan.image_bytes (256-byte aligned)
 cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* image, cudaStream_t s);

@@ -69,6 +69,8 @@ TC_SHAPES = [
     ((64, 32, 48), 25), ((200, 20, 36), 25), ((8, 12, 100), 64), ((4, 130, 9), 8),
     ((12, 5, 8, 6), 16), ((40, 44, 3, 8), 32), ((130, 4, 66), 1), ((4, 4, 4, 4, 4), 3),
     ((6, 5, 7), 5), ((36, 36, 36), 65),
+    # small I_n with several runs of the head: run packing in the 128 MMA rows
+    ((64, 10, 40), 25), ((32, 16, 6, 40), 16), ((8, 64, 30), 12),
 ]
 
 
