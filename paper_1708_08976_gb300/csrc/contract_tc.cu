@@ -40,6 +40,8 @@
 //
 // Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel sets
 // MTK_ETIMEOUT in the status word, stops, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -60,7 +62,7 @@ constexpr int TC_BK = 64;                    // k per stage
 constexpr int TC_M = 128;                    // MMA M
 constexpr int CONV_WARPS = MTK_TC_CONV_WARPS;
 constexpr int CONV_THREADS = CONV_WARPS * 32;
-constexpr int NTHREADS = CONV_THREADS + 32;  // + the MMA warp
+constexpr int NTHREADS = CONV_THREADS + 64;  // + the MMA warp + the TMA producer warp
 constexpr int QW = CONV_WARPS / 4;           // converter warps per TMEM sub-partition
 constexpr int NCH = (64 + 16 * QW - 1) / (16 * QW);   // 16-column chunks per drain thread
 constexpr int MAX_STAGES = 4;
@@ -79,6 +81,7 @@ struct TcParams {
     int64_t tail_rad[MTK_MAXN];
     int64_t rad0, rad0p, Kp, nruns;
     int BI, U, CP, N, stages, P, mn_major, linear, nslabs;
+    int kwide;              // TMA, K-major: one 64-k box per row set (contiguous runs), else octet boxes
     int stage_bytes, b_off, b_bytes, stg_off, tmem_cols;
     uint32_t idesc;
 };
@@ -126,6 +129,22 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -271,13 +290,17 @@ __device__ __forceinline__ float tail_product(const TcParams& tp, int64_t q, int
     return prod;
 }
 
-// PX: tensor pieces; MN: the tensor operand is i-contiguous (I^L == 1)
-template <int PX, bool MN>
+// PX: tensor pieces; MN: the tensor operand is i-contiguous (I^L == 1);
+// TMA: the tensor is staged by TMA tile loads (tensor map `xmap`) issued by a producer
+// warp, else by per-thread 16-byte cp.async copies.
+template <int PX, bool MN, bool TMA>
 __global__ void __launch_bounds__(NTHREADS, 1)
-contract_tc_kernel(const __grid_constant__ TcParams tp) {
+contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ CUtensorMap xmap) {
     extern __shared__ uint8_t dsm_raw[];
     __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];
     __shared__ __align__(8) uint64_t empty_bar[MAX_STAGES];
+    __shared__ __align__(8) uint64_t xfull_bar[MAX_STAGING];
+    __shared__ __align__(8) uint64_t xempty_bar[MAX_STAGING];
     __shared__ __align__(8) uint64_t accf_bar[2];
     __shared__ __align__(8) uint64_t acce_bar[2];
     __shared__ uint32_t tmem_slot;
@@ -310,6 +333,10 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&accf_bar[b]), 1);
             mbar_init(smem_u32(&acce_bar[b]), CONV_WARPS);
+        }
+        for (int x = 0; x < MAX_STAGING; ++x) {
+            mbar_init(smem_u32(&xfull_bar[x]), 1);
+            mbar_init(smem_u32(&xempty_bar[x]), CONV_WARPS);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -382,6 +409,81 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
             }
         }
         __syncwarp();
+    } else if (warp == CONV_WARPS + 1) {
+        // ------------------------------------------------------------ TMA producer
+        if constexpr (TMA) {
+            if (lane == 0) {
+                const uint32_t stg0 = dsm_s + (uint32_t)tp.stg_off;
+                const uint32_t stg_bytes = (uint32_t)(2 * RPT * CONV_THREADS * 16);
+                // bytes every stage delivers (boxes include their out-of-range zeros)
+                const uint32_t bytes = (uint32_t)(U * BI * TC_BK * 4);
+                int64_t ld_qg = kb / rad0p, ld_d0 = kb % rad0p;
+                int64_t xl = 0, xr = 0;                 // non-linear runs: (l, r) of the stage start
+                if constexpr (!MN) {
+                    if (!tp.linear) {
+                        const int64_t k0 = ld_qg * rad0 + ld_d0;
+                        xl = k0 % L;
+                        xr = k0 / L;
+                    }
+                }
+                for (int s = 0; s < nst; ++s) {
+                    const int slot = s % tp.P;
+                    if (s >= tp.P &&
+                        !mbar_wait(smem_u32(&xempty_bar[slot]), (uint32_t)(((s / tp.P) - 1) & 1), &abort_flag, kWaitNs)) {
+                        abort_flag = 1;
+                        set_status(p.status, MTK_ETIMEOUT);
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&xfull_bar[slot]);
+                    const uint32_t dst = stg0 + (uint32_t)slot * stg_bytes;
+                    mbar_arrive_expect_tx(fb, bytes);
+                    for (int u = 0; u < U; ++u) {
+                        const int64_t q = ld_qg * U + u;
+                        if constexpr (MN) {
+                            // box (BI i, 64 k) of run q at d0; k = r for I^L == 1
+                            const int64_t r0 = q * rad0 + ld_d0;
+                            tma_load_2d(dst + (uint32_t)(u * BI * TC_BK * 4), &xmap, (int)(U > 1 ? 0 : i0),
+                                        (int)(r0 < ((int64_t)1 << 31) - 1 ? r0 : ((int64_t)1 << 31) - 1), fb);
+                        } else if (tp.kwide) {
+                            // one box (64 k, BI rows) of the contiguous run q
+                            const int64_t k0 = q * rad0;
+                            int64_t r = k0 / L;
+                            if (r > ((int64_t)1 << 31) - 1) r = ((int64_t)1 << 31) - 1;
+                            tma_load_3d(dst + (uint32_t)(u * BI * TC_BK * 4), &xmap, (int)((k0 % L) + ld_d0),
+                                        (int)(U > 1 ? 0 : i0), (int)r, fb);
+                        } else {
+                            // eight boxes (8 k, BI rows): one per k-octet plane
+                            for (int o = 0; o < 8; ++o) {
+                                int64_t l, r;
+                                if (tp.linear) {
+                                    const int64_t k0 = q * rad0;
+                                    l = (k0 % L) + ld_d0 + 8 * o;
+                                    r = k0 / L;
+                                } else {
+                                    l = xl + 8 * o;
+                                    r = xr;
+                                    while (l >= L) { l -= L; ++r; }
+                                }
+                                if (r > ((int64_t)1 << 31) - 1) r = ((int64_t)1 << 31) - 1;
+                                tma_load_3d(dst + (uint32_t)(o * TC_M * 32 + u * BI * 32), &xmap, (int)l,
+                                            (int)(U > 1 ? 0 : i0), (int)r, fb);
+                            }
+                        }
+                    }
+                    // next stage (skipping the padding at the end of a run)
+                    if constexpr (!MN) {
+                        if (!tp.linear) {
+                            const int64_t delta = (ld_d0 + TC_BK == rad0p) ? (rad0 - ld_d0) : TC_BK;
+                            xl += delta;
+                            while (xl >= L) { xl -= L; ++xr; }
+                        }
+                    }
+                    ld_d0 += TC_BK;
+                    if (ld_d0 == rad0p) { ld_d0 = 0; ++ld_qg; }
+                }
+            }
+        }
+        __syncwarp();
     } else {
         // ------------------------------------------------------------ converters
         // Tile row m (0..127) is (u, il) = (m / BI, m % BI): output row i0 + il of run
@@ -417,6 +519,41 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
                 soff[j] = inside ? mnmajor_off(m, kl) : 0u;
                 if (inside && (m % BI) < rows) hvalid |= 1u << (2 * j);
                 if (inside && (m % BI) + 4 < rows) hvalid |= 2u << (2 * j);
+            }
+        }
+        // TMA staging layouts (filled by the producer warp):
+        //   K-major, contiguous runs: rows of 64 floats; thread reads row (t>>4) + 16 j,
+        //             quad t&15;
+        //   K-major, other runs: eight planes (one per k-octet) of 128 rows x 8 floats; the
+        //             warp w reads plane w, rows (lane>>1) + 16 j, half lane&1 (4 floats);
+        //   MN-major: per packed run u, a (64 k) x (BI i) box; float4 f_j = t + 256 j is the
+        //             i-quad f % nq at k = f / nq (nq = U*BI/4).
+        uint32_t trd[8], tst[8];
+        uint32_t tvalid = 0;
+        if constexpr (TMA) {
+            const int nq = (U * BI) >> 2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if constexpr (!MN) {
+                    if (tp.kwide) {                      // rows of 64 floats: row (t>>4) + 16 j, quad t&15
+                        const int r = (t >> 4) + 16 * j, kq = t & 15;
+                        trd[j] = (uint32_t)(r * TC_BK * 4 + kq * 16);
+                        tst[j] = kmajor_off(r, 4 * kq);
+                        if (r < tile_rows_all) tvalid |= 1u << j;
+                    } else {
+                        const int r = (lane >> 1) + 16 * j, h = lane & 1;
+                        trd[j] = (uint32_t)(warp * TC_M * 32 + r * 32 + h * 16);
+                        tst[j] = kmajor_off(r, 8 * warp + 4 * h);
+                        if (r < tile_rows_all) tvalid |= 1u << j;
+                    }
+                } else {
+                    const int f = t + CONV_THREADS * j;
+                    const int mq = nq > 0 ? f % nq : 0, kl = nq > 0 ? f / nq : TC_BK;
+                    const int m = 4 * mq, u = m / BI, il = m % BI;
+                    trd[j] = (uint32_t)((u * BI * TC_BK + kl * BI + il) * 4);
+                    tst[j] = kl < TC_BK ? mnmajor_off(m, kl) : 0u;
+                    if (nq > 0 && kl < TC_BK) tvalid |= 1u << j;
+                }
             }
         }
         // staging ring: thread-private 16-byte slots, P stages deep
@@ -510,21 +647,41 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
         auto produce = [&](int s) -> bool {
             const int slot = s % ST;
             const int pslot = s % tp.P;
-            // the thread's own copies of stage s are complete after this wait (P groups
-            // are always committed ahead of the stage being read)
-            switch (tp.P) {
-                case 2: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-                case 3: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-                default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-            }
-            const uint32_t sbase = stg + (uint32_t)(pslot * 2 * RPT * CONV_THREADS * 16);
             float4 v[2 * RPT];
+            if constexpr (TMA) {
+                // the producer's boxes for stage s have landed
+                if (!mbar_wait(smem_u32(&xfull_bar[pslot]), (uint32_t)((s / tp.P) & 1), &abort_flag, kWaitNs)) {
+                    abort_flag = 1;
+                    set_status(p.status, MTK_ETIMEOUT);
+                    return false;
+                }
+                const uint32_t sbase = dsm_s + (uint32_t)tp.stg_off + (uint32_t)(pslot * 2 * RPT * CONV_THREADS * 16);
 #pragma unroll
-            for (int e = 0; e < 2 * RPT; ++e) {
-                const uint32_t a = sbase + (uint32_t)(e * CONV_THREADS * 16);
-                asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
-                             : "=f"(v[e].x), "=f"(v[e].y), "=f"(v[e].z), "=f"(v[e].w)
-                             : "r"(a));
+                for (int e = 0; e < 8; ++e) {
+                    v[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if ((tvalid >> e) & 1u)
+                        asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                     : "=f"(v[e].x), "=f"(v[e].y), "=f"(v[e].z), "=f"(v[e].w)
+                                     : "r"(sbase + trd[e]));
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&xempty_bar[pslot]));
+            } else {
+                // the thread's own copies of stage s are complete after this wait (P groups
+                // are always committed ahead of the stage being read)
+                switch (tp.P) {
+                    case 2: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+                    case 3: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+                    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+                }
+                const uint32_t sbase = stg + (uint32_t)(pslot * 2 * RPT * CONV_THREADS * 16);
+#pragma unroll
+                for (int e = 0; e < 2 * RPT; ++e) {
+                    const uint32_t a = sbase + (uint32_t)(e * CONV_THREADS * 16);
+                    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                 : "=f"(v[e].x), "=f"(v[e].y), "=f"(v[e].z), "=f"(v[e].w)
+                                 : "r"(a));
+                }
             }
             if (s >= ST) {
                 if (!mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)(((s / ST) - 1) & 1), &abort_flag, kWaitNs)) {
@@ -540,23 +697,36 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
                 bulk_copy_g2s(smem_u32(st + tp.b_off), tp.bimg + (int64_t)pr_sir * tp.b_bytes,
                               (uint32_t)tp.b_bytes, fb);
             }
+            if constexpr (TMA) {
 #pragma unroll
-            for (int j = 0; j < RPT; ++j) {
-                if (mrow[j] < 0) continue;
-                uint2 lo[PX], hi[PX];
-                split4<PX>(v[2 * j], lo);
-                split4<PX>(v[2 * j + 1], hi);
+                for (int e = 0; e < 8; ++e) {
+                    if (!((tvalid >> e) & 1u)) continue;
+                    uint2 pcs[PX];
+                    split4<PX>(v[e], pcs);
 #pragma unroll
-                for (int q = 0; q < PX; ++q)
-                    *reinterpret_cast<uint4*>(st + q * PIECE_BYTES + soff[j]) =
-                        make_uint4(lo[q].x, lo[q].y, hi[q].x, hi[q].y);
+                    for (int q = 0; q < PX; ++q) *reinterpret_cast<uint2*>(st + q * PIECE_BYTES + tst[e]) = pcs[q];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    if (mrow[j] < 0) continue;
+                    uint2 lo[PX], hi[PX];
+                    split4<PX>(v[2 * j], lo);
+                    split4<PX>(v[2 * j + 1], hi);
+#pragma unroll
+                    for (int q = 0; q < PX; ++q)
+                        *reinterpret_cast<uint4*>(st + q * PIECE_BYTES + soff[j]) =
+                            make_uint4(lo[q].x, lo[q].y, hi[q].x, hi[q].y);
+                }
             }
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&full_bar[slot]));
-            // the staging slot is free again (its values were consumed above)
-            if (s + tp.P < nst) issue(pslot);
-            else asm volatile("cp.async.commit_group;" ::: "memory");
+            if constexpr (!TMA) {
+                // the staging slot is free again (its values were consumed above)
+                if (s + tp.P < nst) issue(pslot);
+                else asm volatile("cp.async.commit_group;" ::: "memory");
+            }
             return true;
         };
 
@@ -616,9 +786,11 @@ contract_tc_kernel(const __grid_constant__ TcParams tp) {
         bool pending = false, ok = true;
         int pend_g = 0;
         int64_t pend_qg = 0;
-        for (int sl = 0; sl < tp.P; ++sl) {
-            if (sl < nst) issue(sl);
-            else asm volatile("cp.async.commit_group;" ::: "memory");
+        if constexpr (!TMA) {
+            for (int sl = 0; sl < tp.P; ++sl) {
+                if (sl < nst) issue(sl);
+                else asm volatile("cp.async.commit_group;" ::: "memory");
+            }
         }
         for (int s = 0; s < nst; ++s) {
             if (!produce(s)) { ok = false; break; }
@@ -671,14 +843,67 @@ int tile_rows(int64_t I) {
     return (int)(bi > TC_M ? TC_M : bi);
 }
 
-template <int PX, bool MN>
-cudaError_t launch_variant(const TcParams& tp, dim3 grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PX, MN>,
+template <int PX, bool MN, bool TMA>
+cudaError_t launch_variant(const TcParams& tp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PX, MN, TMA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    contract_tc_kernel<PX, MN><<<grid, NTHREADS, smem, s>>>(tp);
+    contract_tc_kernel<PX, MN, TMA><<<grid, NTHREADS, smem, s>>>(tp, map);
     note_launches(1);
     return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled, reached through the runtime (no link against libcuda); the
+// pointer is looked up once per process
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }();
+    return fn;
+}
+
+// TMA staging applies when the boxes below are legal and never straddle a run of l:
+// K-major: 8-float boxes at l multiples of 8 (I^L and the head rows divisible by 8);
+// MN-major: (BI x 64) boxes along (i, r).  Coordinates must fit in 32 bits.
+bool tma_eligible(const ContractParams& p, const TcPlan& pl) {
+#ifdef MTK_TC_CPASYNC_ONLY
+    return false;
+#endif
+    if (CONV_WARPS != 8) return false;
+    const int64_t lim = ((int64_t)1 << 31) - TC_BK;
+    if (p.L == 1) return p.I % 4 == 0 && pl.BI <= 256 && p.I < lim && p.R < lim;
+    return p.L % 8 == 0 && pl.rad0 % 8 == 0 && pl.BI % 4 == 0 && pl.BI <= 256 && p.L < lim && p.I < lim &&
+           p.R < lim;
+}
+
+bool encode_xmap(const ContractParams& p, const TcPlan& pl, CUtensorMap* map) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    CUresult r;
+    if (p.L == 1) {
+        const cuuint64_t dims[2] = {(cuuint64_t)p.I, (cuuint64_t)p.R};
+        const cuuint64_t strides[1] = {(cuuint64_t)p.I * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)pl.BI, (cuuint32_t)TC_BK};
+        const cuuint32_t es[2] = {1, 1};
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p.X), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[3] = {(cuuint64_t)p.L, (cuuint64_t)p.I, (cuuint64_t)p.R};
+        const cuuint64_t strides[2] = {(cuuint64_t)p.L * 4, (cuuint64_t)p.L * p.I * 4};
+        const cuuint32_t box[3] = {pl.linear ? (cuuint32_t)TC_BK : 8u, (cuuint32_t)pl.BI, 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(p.X), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -803,8 +1028,20 @@ cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* ima
     const int64_t tiles = (p.I + tp.BI - 1) / tp.BI;
     const dim3 grid((unsigned)tiles, (unsigned)p.S);
     const bool mn = tp.mn_major != 0;
-    if (px == 3) return mn ? launch_variant<3, true>(tp, grid, smem, s) : launch_variant<3, false>(tp, grid, smem, s);
-    return mn ? launch_variant<2, true>(tp, grid, smem, s) : launch_variant<2, false>(tp, grid, smem, s);
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    const bool tma = tma_eligible(p, pl) && encode_xmap(p, pl, &map);
+    tp.kwide = (tma && !mn && pl.linear) ? 1 : 0;
+    if (tma) {
+        if (px == 3) return mn ? launch_variant<3, true, true>(tp, map, grid, smem, s)
+                               : launch_variant<3, false, true>(tp, map, grid, smem, s);
+        return mn ? launch_variant<2, true, true>(tp, map, grid, smem, s)
+                  : launch_variant<2, false, true>(tp, map, grid, smem, s);
+    }
+    if (px == 3) return mn ? launch_variant<3, true, false>(tp, map, grid, smem, s)
+                           : launch_variant<3, false, false>(tp, map, grid, smem, s);
+    return mn ? launch_variant<2, true, false>(tp, map, grid, smem, s)
+              : launch_variant<2, false, false>(tp, map, grid, smem, s);
 }
 
 }  // namespace mtk
