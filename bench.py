@@ -276,11 +276,13 @@ def main():
     torch.cuda.synchronize()
     l0 = lib.mtk_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_sweeps")
     e0.record(stream)
     for _ in range(args.steps):
         als.sweep()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = lib.mtk_launch_count() - l0
     if world > 1:
         torch.distributed.barrier()

@@ -497,9 +497,10 @@ int mtk_gram(const float* U, int64_t I, int C, double* G, void* ws, size_t ws_by
 }
 
 size_t mtk_solve_workspace(int64_t In, int C) {
-    (void)In;
-    if (C < 1 || C > MTK_MAXC) return 0;
-    return align256(kStatusBytes) + align256((size_t)C * C * sizeof(double)) + 256;
+    if (In < 1 || C < 1 || C > MTK_MAXC) return 0;
+    const int nch = gram_chunks(In);
+    return align256(kStatusBytes) + align256(solve_scratch_doubles(C) * sizeof(double)) + 256 +
+           align256((size_t)(nch > 1 ? nch : 0) * C * C * sizeof(double));
 }
 
 int mtk_gram_hadamard_solve(const double* const* G, int N, int C, int n, const float* M,
@@ -514,13 +515,14 @@ int mtk_gram_hadamard_solve(const double* const* G, int N, int C, int n, const f
     cudaStream_t s = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
     double* Hbuf = reinterpret_cast<double*>(w + align256(kStatusBytes));
-    int* flag = reinterpret_cast<int*>(w + align256(kStatusBytes) + align256((size_t)C * C * sizeof(double)));
+    int* flag = reinterpret_cast<int*>(w + align256(kStatusBytes) + align256(solve_scratch_doubles(C) * sizeof(double)));
     if (launch_chol_solve(G, N, C, n, M, In, Un, Hbuf, flag, static_cast<uint32_t*>(ws), s) !=
         cudaSuccess)
         return MTK_ECUDA;
     if (Gn) {
-        if (gram_chunks(In) > 1) return MTK_EUNSUPPORTED;   // use mtk_gram with its workspace
-        if (launch_gram(Un, In, C, Gn, nullptr, 1, s) != cudaSuccess) return MTK_ECUDA;
+        double* gpart = reinterpret_cast<double*>(w + align256(kStatusBytes) +
+                                                  align256(solve_scratch_doubles(C) * sizeof(double)) + 256);
+        if (launch_gram(Un, In, C, Gn, gpart, gram_chunks(In), s) != cudaSuccess) return MTK_ECUDA;
     }
     return MTK_OK;
 }
@@ -563,7 +565,7 @@ AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o) {
     a.mbuf = (size_t)maxIn * C * sizeof(float); cv.take(a.mbuf);
     a.gbufs = (size_t)N * C * C * sizeof(double); cv.take(a.gbufs);
     a.gpart = maxChunks > 1 ? (size_t)maxChunks * C * C * sizeof(double) : 0; cv.take(a.gpart);
-    a.hbuf = (size_t)C * C * sizeof(double); cv.take(a.hbuf);
+    a.hbuf = solve_scratch_doubles(C) * sizeof(double); cv.take(a.hbuf);
     a.flag = 256; cv.take(a.flag);
     a.mt = mt; cv.take(a.mt);
     a.total = align256(cv.off);

@@ -10,7 +10,7 @@ namespace mtk {
 namespace {
 
 constexpr int kGramRows = 32;       // rows of U staged per step
-constexpr int64_t kGramChunk = 4096;  // rows per CTA
+constexpr int64_t kGramChunk = 32;    // rows per CTA (many CTAs: FP64 FMA throughput is low)
 
 // partial Gram of rows [chunk*kGramChunk, ...) for the pairs of block blockIdx.y
 // (1024 pairs per block, 4 per thread); out = part + chunk*C*C (or G if one chunk)
@@ -58,13 +58,16 @@ struct GramList {
     const double* G[MTK_MAXN];
 };
 
-// H = Hadamard_{k != n} G_k, then H = L L^T in place (lower triangle), one CTA.
-// A is dynamic shared memory (C*C doubles) when it fits, else the global buffer.
+// H = Hadamard_{k != n} G_k, its Cholesky factor H = L L^T and the inverse
+// H^{-1} = L^{-T} L^{-1}, all FP64, one CTA.  Scratch layout (doubles): work[C*C]
+// (used when the matrix does not fit in shared memory), diag[C], Hinv[C*C].
 __global__ void __launch_bounds__(256)
 chol_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __restrict__ Hbuf,
             int* __restrict__ flag, uint32_t* status, int use_smem) {
     extern __shared__ double hs[];
     double* A = use_smem ? hs : Hbuf;
+    double* diag = Hbuf + (size_t)C * C;
+    double* Hinv = diag + C;
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
     for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
@@ -74,7 +77,7 @@ chol_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __
         A[e] = h;
     }
     __syncthreads();
-    // right-looking Cholesky, column j at a time
+    // right-looking Cholesky, column j at a time (lower triangle)
     for (int j = 0; j < C; ++j) {
         if (threadIdx.x == 0) {
             const double d = A[j * C + j];
@@ -94,52 +97,58 @@ chol_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __
         }
         __syncthreads();
     }
-    if (use_smem)
-        for (int e = threadIdx.x; e < C * C; e += blockDim.x) Hbuf[e] = A[e];
+    if (!bad) {
+        // W = L^{-1} by forward substitution, one thread per column j: W(i, j) for i > j is
+        // kept at A[j*C + i] (the strict upper triangle is free), W(j, j) in diag[j]
+        for (int j = threadIdx.x; j < C; j += blockDim.x) {
+            const double wjj = 1.0 / A[j * C + j];
+            for (int i = j + 1; i < C; ++i) {
+                double sum = A[i * C + j] * wjj;
+                for (int k = j + 1; k < i; ++k) sum += A[i * C + k] * A[j * C + k];
+                A[j * C + i] = -sum / A[i * C + i];
+            }
+            diag[j] = wjj;
+        }
+        __syncthreads();
+        // Hinv(a, b) = sum_{k >= max(a,b)} W(k, a) W(k, b)
+        for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+            const int a = e / C, b = e % C;
+            const int k0 = a > b ? a : b;
+            double sum = 0.0;
+            for (int k = k0; k < C; ++k) {
+                const double wa = (k == a) ? diag[a] : A[a * C + k];
+                const double wb = (k == b) ? diag[b] : A[b * C + k];
+                sum += wa * wb;
+            }
+            Hinv[e] = sum;
+        }
+    }
     if (threadIdx.x == 0) {
         *flag = bad ? 0 : 1;
         if (bad) set_status(status, MTK_ENOTPD);
     }
 }
 
-// U_n(i,:) = M(i,:) H^{-1}: with H = L L^T, solve L y = m, L^T x = y.  One warp per row;
-// the dot products of each substitution step are reduced in a fixed shuffle tree.
+// U_n(i, b) = sum_a M(i, a) Hinv(a, b), FP64 accumulation, one thread per output entry;
+// nothing is written when H was not positive definite
 __global__ void __launch_bounds__(256)
-trsm_rows_kernel(const double* __restrict__ Lg, const int* __restrict__ flag, const float* M,
-                 int64_t In, int C, float* Un, int use_smem) {
-    extern __shared__ double sh[];
-    const int warps = blockDim.x / 32;
-    double* Ls = use_smem ? sh : nullptr;
-    double* ybase = sh + (use_smem ? C * C : 0);
-    if (use_smem) {
-        for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ls[e] = Lg[e];
-    }
+apply_inverse_kernel(const double* __restrict__ Hinv, const int* __restrict__ flag, const float* __restrict__ M,
+                     int64_t In, int C, float* __restrict__ Un) {
+    extern __shared__ double hsh[];
+    const bool in_smem = C <= 64;
+    if (in_smem)
+        for (int e = threadIdx.x; e < C * C; e += blockDim.x) hsh[e] = Hinv[e];
     __syncthreads();
     if (*flag == 0) return;
-    const double* L = use_smem ? Ls : Lg;
-    const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
-    double* y = ybase + (size_t)w * 2 * C;
-    double* x = y + C;
-    for (int64_t i = (int64_t)blockIdx.x * warps + w; i < In; i += (int64_t)gridDim.x * warps) {
+    const double* H = in_smem ? hsh : Hinv;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < In * C;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / C;
+        const int b = (int)(e % C);
         const float* m = M + i * C;
-        for (int a = 0; a < C; ++a) {
-            double s = 0.0;
-            for (int k = lane; k < a; k += 32) s += L[a * C + k] * y[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[a] = ((double)m[a] - s) / L[a * C + a];
-            __syncwarp();
-        }
-        for (int a = C - 1; a >= 0; --a) {
-            double s = 0.0;
-            for (int k = a + 1 + lane; k < C; k += 32) s += L[k * C + a] * x[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) x[a] = (y[a] - s) / L[a * C + a];
-            __syncwarp();
-        }
-        for (int c = lane; c < C; c += 32) Un[i * C + c] = (float)x[c];
-        __syncwarp();
+        double sum = 0.0;
+        for (int a = 0; a < C; ++a) sum += (double)m[a] * H[a * C + b];
+        Un[e] = (float)sum;
     }
 }
 
@@ -260,6 +269,8 @@ cudaError_t launch_gram(const float* U, int64_t I, int C, double* G, double* par
     return cudaGetLastError();
 }
 
+size_t solve_scratch_doubles(int C) { return 2 * (size_t)C * C + C; }
+
 cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const float* M,
                               int64_t In, float* Un, double* Hbuf, int* flag, uint32_t* status,
                               cudaStream_t s) {
@@ -274,14 +285,11 @@ cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int warps = 8;
-    const size_t ybytes = (size_t)warps * 2 * C * sizeof(double);
-    const int trsm_smem = (hbytes + ybytes) <= 200 * 1024;
-    const size_t smem = (trsm_smem ? hbytes : 0) + ybytes;
-    cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int64_t blocks = (In + warps - 1) / warps;
+    const double* Hinv = Hbuf + (size_t)C * C + C;
+    const size_t smem = C <= 64 ? hbytes : 0;
+    int64_t blocks = (In * C + 255) / 256;
     int grid = (int)(blocks < 152 * 4 ? blocks : 152 * 4);
-    trsm_rows_kernel<<<grid, warps * 32, smem, s>>>(Hbuf, flag, M, In, C, Un, trsm_smem);
+    apply_inverse_kernel<<<grid, 256, smem, s>>>(Hinv, flag, M, In, C, Un);
     note_launches(1);
     return cudaGetLastError();
 }

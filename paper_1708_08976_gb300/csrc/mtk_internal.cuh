@@ -88,6 +88,7 @@ cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, co
 cudaError_t launch_gram(const float* U, int64_t I, int C, double* G, double* part,
                         int nchunks, cudaStream_t s);
 int gram_chunks(int64_t I);
+size_t solve_scratch_doubles(int C);   // Hbuf of launch_chol_solve
 cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const float* M,
                               int64_t In, float* Un, double* Hbuf, int* flag,
                               uint32_t* status, cudaStream_t s);
