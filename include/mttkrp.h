@@ -114,6 +114,28 @@ int mtk_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U
                int n, float* M, void* ws, size_t ws_bytes, const mtk_opts* opts,
                void* stream);
 
+/* MTTKRP that allocates nothing (the paper has no counterpart: an interface for
+ * callers that cannot allocate device memory).  Same operation, arguments and
+ * results as mtk_mttkrp, but the workspace is a fixed device array of
+ * MTK_NOALLOC_SCRATCH_BYTES bytes inside the library; no cudaMalloc, cudaFree
+ * or allocating library routine is called.
+ *  - The first call on a device (the current device) looks up that device's
+ *    copy of the array; make that first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the previous
+ *    call's contents (the status word is cleared at the start of each call).
+ *    Calls whose work overlaps on the GPU (other streams, other host threads)
+ *    race on it: order them on one stream or serialise them.
+ *  - Returns MTK_EWORKSPACE, before any launch and with M untouched, when the
+ *    shape and options need more than MTK_NOALLOC_SCRATCH_BYTES of workspace
+ *    (mtk_mttkrp_workspace(...) tells).
+ *  - status_bits (host, may be NULL): if given, the call synchronises the
+ *    stream, stores the device status bits there and returns the lowest
+ *    recorded code, as mtk_read_status does; if NULL nothing is synchronised. */
+#define MTK_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* const* U,
+                       int C, int n, float* M, const mtk_opts* opts, uint32_t* status_bits,
+                       void* stream);
+
 /* 2-step pieces (Section 4.3, Algorithm 4) -------------------------------
  * Partial MTTKRP.  right = 1: T = X_(0:n) K_R, K_R = U_{N-1} kr ... kr U_{n+1}
  * (R = prod_{k>n} I_k rows); T is the (I^L x I_n x C) tensor R of the paper in

@@ -39,6 +39,7 @@ SIGNATURES = {
     "mtk_khatri_rao": (I32, [P, P, I32, I32, P, I32, P]),
     "mtk_mttkrp_workspace": (SZ, [P, I32, I32, I32, OPTS_P]),
     "mtk_mttkrp": (I32, [P, P, I32, P, I32, I32, P, P, SZ, OPTS_P, P]),
+    "mtk_mttkrp_noalloc": (I32, [P, P, I32, P, I32, I32, P, OPTS_P, U32P, P]),
     "mtk_partial_mttkrp_workspace": (SZ, [P, I32, I32, I32, I32, OPTS_P]),
     "mtk_partial_mttkrp": (I32, [P, P, I32, P, I32, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_multi_ttv": (I32, [P, P, I32, P, I32, I32, I32, P, P]),

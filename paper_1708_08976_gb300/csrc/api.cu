@@ -6,6 +6,11 @@
 #include "mtk_internal.cuh"
 
 #include <atomic>
+#include <mutex>
+
+// Device scratch of mtk_mttkrp_noalloc: one fixed array per device, part of the
+// module, so that entry point needs no allocation.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MTK_NOALLOC_SCRATCH_BYTES];
 
 using namespace mtk;
 
@@ -19,6 +24,7 @@ namespace {
 constexpr int kBK = 64;           // the W operand needs rad0 >= kBK (or no tail factors)
 constexpr int kTcBK = 64;         // k per tensor-core stage; tensor-core splits are multiples
 constexpr int kSimtBI = 64;
+constexpr int kNoAllocMaxDevices = 64;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -427,6 +433,37 @@ int mtk_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U
     if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
     return do_mttkrp(X, dims, N, U, C, n, M, ws, ws_bytes, static_cast<uint32_t*>(ws), o,
                      (cudaStream_t)stream);
+}
+
+int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* const* U, int C,
+                       int n, float* M, const mtk_opts* opts, uint32_t* status_bits, void* stream) {
+    int st = check_shape(dims, N, C, n);
+    if (st) return st;
+    st = check_mttkrp_ptrs(X, U, N, n, M, M);   // no caller workspace to check
+    if (st) return st;
+    mtk_opts o = defaults(opts);
+    if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
+    if (mttkrp_layout(dims, N, C, n, o).total > MTK_NOALLOC_SCRATCH_BYTES) return MTK_EWORKSPACE;
+    // set-up, once per device, with that device current
+    static std::mutex mu;
+    static void* dev_scratch[kNoAllocMaxDevices];
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return MTK_ECUDA;
+    void* ws;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!dev_scratch[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MTK_ECUDA;
+            dev_scratch[dev] = p;
+        }
+        ws = dev_scratch[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(ws, 0, kStatusBytes, s) != cudaSuccess) return MTK_ECUDA;
+    st = do_mttkrp(X, dims, N, U, C, n, M, ws, MTK_NOALLOC_SCRATCH_BYTES, static_cast<uint32_t*>(ws), o, s);
+    if (st || !status_bits) return st;
+    return mtk_read_status(ws, stream, status_bits);
 }
 
 size_t mtk_partial_mttkrp_workspace(const int64_t* dims, int N, int C, int n, int right,
