@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--workload", default="corr4", choices=["corr4", "cube512", "corr4-small"])
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run every mode's MTTKRP W+K times (for profiler captures)")
-    ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | best")
+    ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | planes | best")
     ap.add_argument("--algo", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -67,6 +67,22 @@ def workload(name):
         X, dims, U = synth.cube512()
         desc = "cube512: 512^3 FP32 N(0,1), rank C=32, factors N(0,1)/sqrt(32)"
     return X, tuple(dims), U, desc
+
+
+def time_calls(fn, reps, warm=2, stream=None):
+    """Average device time of one fn() call: `reps` calls back to back between two CUDA
+    events (the host enqueues faster than the GPU runs them, so host-side launch work
+    does not show up as GPU time)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) * 1e-3 / reps
 
 
 def dist_env():
@@ -201,17 +217,20 @@ def main():
     Xd = torch.from_numpy(X).to(dev)
     U0 = [torch.from_numpy(u).to(dev) for u in U]
     if args.kernel_only:
-        prec = "bf16x3" if args.precision == "best" else args.precision
+        prec = "planes" if args.precision == "best" else args.precision
+        Xs = mtk.split_tensor(Xd)[0] if prec == "planes" else None
         ts = []
         for n in range(N):
-            for it in range(args.warmup + args.steps):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                mtk.mttkrp(Xd, dims, U0, n, precision=prec, algo=args.algo)
-                b.record()
-                b.synchronize()
-                if it >= args.warmup:
-                    ts.append((n, a.elapsed_time(b) * 1e3))
+            if Xs is not None:
+                fn = lambda: mtk.mttkrp(Xd, dims, U0, n, Xs=Xs)
+            else:
+                fn = lambda: mtk.mttkrp(Xd, dims, U0, n, precision=prec, algo=args.algo)
+            if args.steps > 0:
+                ts.append((n, time_calls(fn, args.steps, warm=args.warmup) * 1e6))
+            else:
+                for _ in range(args.warmup):
+                    fn()
+        torch.cuda.synchronize()
         print(json.dumps({"kernel_only": True, "workload": desc, "precision": prec,
                           "us": [[n, round(t, 1)] for n, t in ts]}), flush=True)
         return 0
@@ -221,26 +240,26 @@ def main():
     Ud64 = [u.astype(np.float64) for u in U]
     g = np.random.default_rng(123)
     forms = {}
-    for prec in ("fp32", "bf16x2", "bf16x3"):
+    # the tensor split once into its BF16 planes (with ||X||^2 from the same pass)
+    Xs, _ = mtk.split_tensor(Xd)
+    torch.cuda.synchronize()
+    split_us = time_calls(lambda: mtk.split_tensor(Xd, out=Xs), 3) * 1e6
+
+    def call(prec, n, out=None):
+        if prec == "planes":
+            return mtk.mttkrp(Xd, dims, U0, n, Xs=Xs, out=out)
+        return mtk.mttkrp(Xd, dims, U0, n, precision=prec, out=out)
+
+    for prec in ("fp32", "bf16x2", "bf16x3", "planes"):
         try:
             errs, times = [], []
             for n in range(N):
-                M = mtk.mttkrp(Xd, dims, U0, n, precision=prec)
+                M = call(prec, n)
                 rows = np.unique(np.concatenate([[0, dims[n] - 1], g.integers(0, dims[n], 6)]))
                 ref = oracle.mttkrp_rows_f32(X, dims, Ud64, n, rows)
                 got = M[torch.as_tensor(rows, device=dev)].double().cpu().numpy()
                 errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
-                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                for _ in range(2):
-                    mtk.mttkrp(Xd, dims, U0, n, precision=prec, out=M)
-                ts = []
-                for _ in range(5):
-                    ev0.record()
-                    mtk.mttkrp(Xd, dims, U0, n, precision=prec, out=M)
-                    ev1.record()
-                    ev1.synchronize()
-                    ts.append(ev0.elapsed_time(ev1) * 1e-3)
-                times.append(statistics.median(ts))
+                times.append(time_calls(lambda: call(prec, n, out=M), 5))
             forms[prec] = {"rel_err_per_mode": errs, "mttkrp_us_per_mode": [t * 1e6 for t in times],
                            "tflops_per_mode": [2.0 * I * C / t / 1e12 for t in times]}
         except mtk.MtkError as e:
@@ -251,8 +270,9 @@ def main():
     else:
         prec = args.precision
 
+    planes = prec == "planes"
     Uw = [u.clone() for u in U0]
-    als = mtk.ALS(Xd, dims, Uw, algo=args.algo, precision=prec)
+    als = mtk.ALS(Xd, dims, Uw, algo=args.algo, precision="auto" if planes else prec, presplit=planes)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
 
@@ -294,15 +314,11 @@ def main():
     M = torch.empty((max(dims), C), dtype=torch.float32, device=dev)
     for n in range(N):
         out = M[: dims[n]]
-        ts = []
-        for _ in range(args.steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            mtk.mttkrp(Xd, dims, U0, n, precision=prec, algo=args.algo, out=out)
-            b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b) * 1e-3)
-        per_mode.append(statistics.median(ts))
+        if planes:
+            fn = lambda: mtk.mttkrp(Xd, dims, U0, n, Xs=als.Xs, out=out)
+        else:
+            fn = lambda: mtk.mttkrp(Xd, dims, U0, n, precision=prec, algo=args.algo, out=out)
+        per_mode.append(time_calls(fn, max(args.steps, 5), stream=stream))
     clocks = sampler.stop()
 
     t_tensor = torch.tensor([t_step], device=dev)
@@ -320,7 +336,7 @@ def main():
         fit_h = torch.empty((), dtype=torch.float64).pin_memory()
         Xe = torch.empty_like(Xd)
         Ue = [torch.empty_like(u) for u in U0]
-        alse = mtk.ALS(Xe, dims, Ue, algo=args.algo, precision=prec)
+        alse = mtk.ALS(Xe, dims, Ue, algo=args.algo, precision="auto" if planes else prec, presplit=planes)
         ksteps = max(3, min(args.steps, 5))
         for it in range(ksteps + 1):
             if it == 1:
@@ -329,7 +345,7 @@ def main():
             Xe.copy_(Xh, non_blocking=True)
             for d_, h_ in zip(Ue, Uh):
                 d_.copy_(h_, non_blocking=True)
-            alse.normX2 = mtk.norm2(Xe, out=alse.normX2)
+            alse.resplit()          # ||X||^2 (and the BF16 planes) of this step's tensor
             alse.sweep()
             for h_, d_ in zip(Uo, Ue):
                 h_.copy_(d_, non_blocking=True)
@@ -350,10 +366,15 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else f"{prec} split products, f32 accumulate",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "planes": "bf16x2 split products (tensor pre-split into BF16 hi/lo planes), f32 accumulate"}.get(
+            prec, f"{prec} split products, f32 accumulate"),
         "data": "synthetic",
         "config": {"workload": desc, "dims": list(dims), "rank": C, "step": "one CP-ALS sweep (4 MTTKRPs + FP64 Cholesky solves + Grams + fit)",
                    "precision": prec, "algo": args.algo, "l2": "inputs (1.92 GB) larger than L2; no flush",
+                   "tensor_split_us": split_us,
+                   "tensor_split": ("the BF16 planes and ||X||^2 are made once per CP-ALS run, outside the timed sweeps "
+                                    "(inside every e2e step)") if planes else "not used",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,

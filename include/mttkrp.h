@@ -136,6 +136,37 @@ int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* 
                        int C, int n, float* M, const mtk_opts* opts, uint32_t* status_bits,
                        void* stream);
 
+/* Tensor stored as two BF16 planes (Section 2.2: CP-ALS runs an MTTKRP for every mode
+ * of every sweep on the same tensor, so the tensor can be prepared once) ----------
+ * The split: hi = bf16_rn(x), lo = bf16_rn(x - hi) for every entry x (two-piece split
+ * of Henry, Tang and Heinecke, ARITH 2019; |x - hi - lo| <= 2^-16 |x|).  Xs holds hi at
+ * entries [0, I) and lo at [pitch, pitch + I), pitch = mtk_split_pitch(I), both in the
+ * natural linearization, as 16-bit BF16 words: mtk_split_bytes(I) bytes in all, the
+ * size of the FP32 tensor rounded up to 64 entries per plane.  Xs: device, 16-byte
+ * aligned, caller-owned.  normX2 (device double, may be NULL) receives ||X||^2 from
+ * the same pass (exact squares, compensated FP32 sums of 64 entries added in FP64,
+ * fixed order).  ws: at least mtk_split_workspace(I) bytes. */
+int64_t mtk_split_pitch(int64_t I);
+size_t mtk_split_bytes(int64_t I);
+size_t mtk_split_workspace(int64_t I);
+int mtk_split_tensor(const float* X, int64_t I, void* Xs, double* normX2, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* MTTKRP on the planes (the same operation as mtk_mttkrp, tensor entries carried as
+ * hi + lo, KRP entries as three BF16 pieces, all six cross products on tcgen05 with
+ * FP32 accumulation: the accuracy of MTK_PREC_BF16X2).  The tensor is read through TMA
+ * straight into the tensor-core operand, 4 bytes per entry.  Xs: from
+ * mtk_split_tensor for a tensor with these dims.  X (device, may be NULL): the FP32
+ * tensor, used only for shapes the planes kernel does not take (C > 64, I^L or I_n not
+ * a multiple of 8, ...), which then run mtk_mttkrp with MTK_PREC_BF16X2; with X NULL
+ * such shapes return MTK_EUNSUPPORTED.  opts: algo AUTO or FUSED, precision AUTO or
+ * BF16X2, splits = CTAs of the launch (0: one per SM); else MTK_EINVAL.  ws: at least
+ * mtk_mttkrp_split_workspace(...) bytes. */
+size_t mtk_mttkrp_split_workspace(const int64_t* dims, int N, int C, int n, const mtk_opts* opts);
+int mtk_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, const float* const* U,
+                     int C, int n, float* M, void* ws, size_t ws_bytes, const mtk_opts* opts,
+                     void* stream);
+
 /* 2-step pieces (Section 4.3, Algorithm 4) -------------------------------
  * Partial MTTKRP.  right = 1: T = X_(0:n) K_R, K_R = U_{N-1} kr ... kr U_{n+1}
  * (R = prod_{k>n} I_k rows); T is the (I^L x I_n x C) tensor R of the paper in
@@ -187,6 +218,13 @@ size_t mtk_cp_als_workspace(const int64_t* dims, int N, int C, const mtk_opts* o
 int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U, int C,
                      const double* normX2, double* fit, void* ws, size_t ws_bytes,
                      const mtk_opts* opts, void* stream);
+
+/* The same sweep with every MTTKRP on the tensor's BF16 planes (mtk_mttkrp_split).
+ * Xs: from mtk_split_tensor.  X: the FP32 tensor or NULL (see mtk_mttkrp_split).  opts
+ * as for mtk_mttkrp_split.  ws: mtk_cp_als_workspace(...) bytes (it covers both sweeps). */
+int mtk_cp_als_sweep_split(const void* Xs, const float* X, const int64_t* dims, int N, float* const* U,
+                           int C, const double* normX2, double* fit, void* ws, size_t ws_bytes,
+                           const mtk_opts* opts, void* stream);
 
 /* CP loss pieces (Section 2.2; the paper names the residual as a cost but gives
  * no formula, this is the standard expansion of the squared norm):

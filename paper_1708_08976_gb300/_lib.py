@@ -40,6 +40,12 @@ SIGNATURES = {
     "mtk_mttkrp_workspace": (SZ, [P, I32, I32, I32, OPTS_P]),
     "mtk_mttkrp": (I32, [P, P, I32, P, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_mttkrp_noalloc": (I32, [P, P, I32, P, I32, I32, P, OPTS_P, U32P, P]),
+    "mtk_split_pitch": (I64, [I64]),
+    "mtk_split_bytes": (SZ, [I64]),
+    "mtk_split_workspace": (SZ, [I64]),
+    "mtk_split_tensor": (I32, [P, I64, P, P, P, SZ, P]),
+    "mtk_mttkrp_split_workspace": (SZ, [P, I32, I32, I32, OPTS_P]),
+    "mtk_mttkrp_split": (I32, [P, P, P, I32, P, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_partial_mttkrp_workspace": (SZ, [P, I32, I32, I32, I32, OPTS_P]),
     "mtk_partial_mttkrp": (I32, [P, P, I32, P, I32, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_multi_ttv": (I32, [P, P, I32, P, I32, I32, I32, P, P]),
@@ -51,6 +57,7 @@ SIGNATURES = {
     "mtk_norm2": (I32, [P, I64, P, P, SZ, P]),
     "mtk_cp_als_workspace": (SZ, [P, I32, I32, OPTS_P]),
     "mtk_cp_als_sweep": (I32, [P, P, I32, P, I32, P, P, P, SZ, OPTS_P, P]),
+    "mtk_cp_als_sweep_split": (I32, [P, P, P, I32, P, I32, P, P, P, SZ, OPTS_P, P]),
     "mtk_cp_residual": (I32, [P, P, P, I64, P, I32, I32, P, P, P]),
     "mtk_cp_gradient": (I32, [P, P, P, I32, I32, I32, I64, P, P, P]),
 }

@@ -102,10 +102,37 @@ def _rank(U, skip=None):
     raise ValueError("no factor matrix given")
 
 
-def mttkrp(X: torch.Tensor, dims: Sequence[int], U: Sequence[Optional[torch.Tensor]], n: int, *,
+def split_tensor(X: torch.Tensor, *, out: Optional[torch.Tensor] = None,
+                 normX2: Optional[torch.Tensor] = None, ws: Optional[Workspace] = None):
+    """Split an FP32 tensor into its two BF16 planes (hi, lo) for mtk_mttkrp_split.
+    Returns (Xs, normX2): Xs an int16 tensor holding the planes' 16-bit words, normX2 a
+    device FP64 scalar with ||X||^2 from the same pass."""
+    _req(X, torch.float32, "X")
+    lib = L.load()
+    I = X.numel()
+    nwords = lib.mtk_split_bytes(I) // 2
+    if out is None:
+        out = torch.empty(nwords, dtype=torch.int16, device=X.device)
+    _req(out, torch.int16, "out")
+    if out.numel() < nwords:
+        raise ValueError(f"split planes need {nwords} 16-bit words")
+    if normX2 is None:
+        normX2 = torch.empty((), dtype=torch.float64, device=X.device)
+    ws = ws or default_workspace(X.device)
+    wp, wb = ws.ptr(lib.mtk_split_workspace(I))
+    L.check(lib.mtk_split_tensor(X.data_ptr(), I, out.data_ptr(), normX2.data_ptr(), wp, wb, _stream(X.device)),
+            "mtk_split_tensor")
+    return out, normX2
+
+
+def mttkrp(X: Optional[torch.Tensor], dims: Sequence[int], U: Sequence[Optional[torch.Tensor]], n: int, *,
            algo="auto", precision="auto", splits=0, out: Optional[torch.Tensor] = None,
-           ws: Optional[Workspace] = None) -> torch.Tensor:
-    """Mode-n MTTKRP M = X_(n) (U_{N-1} kr ... kr U_{n+1} kr U_{n-1} kr ... kr U_0)."""
+           ws: Optional[Workspace] = None, Xs: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Mode-n MTTKRP M = X_(n) (U_{N-1} kr ... kr U_{n+1} kr U_{n-1} kr ... kr U_0).
+    With Xs (the planes from split_tensor) the tensor is read from its BF16 planes
+    (mtk_mttkrp_split); X may then be None for shapes the planes kernel takes."""
+    if Xs is not None:
+        return _mttkrp_split(Xs, X, dims, U, n, algo=algo, precision=precision, splits=splits, out=out, ws=ws)
     _req(X, torch.float32, "X")
     dims = [int(d) for d in dims]
     N = len(dims)
@@ -126,6 +153,36 @@ def mttkrp(X: torch.Tensor, dims: Sequence[int], U: Sequence[Optional[torch.Tens
     wp, wb = ws.ptr(need)
     L.check(lib.mtk_mttkrp(X.data_ptr(), d, N, L.ptr_arr(ptrs), C, n, out.data_ptr(), wp, wb,
                            L.ctypes.byref(o), _stream(X.device)), "mtk_mttkrp")
+    return out
+
+
+def _mttkrp_split(Xs, X, dims, U, n, *, algo, precision, splits, out, ws):
+    _req(Xs, torch.int16, "Xs")
+    if X is not None:
+        _req(X, torch.float32, "X")
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    C = _rank(U, skip=n)
+    ptrs = _factor_ptrs(U, dims, C, skip=n)
+    NX = 1
+    for d in dims:
+        NX *= d
+    lib = L.load()
+    if Xs.numel() * 2 < lib.mtk_split_bytes(NX):
+        raise ValueError("Xs is too small for dims")
+    if out is None:
+        out = torch.empty((dims[n], C), dtype=torch.float32, device=Xs.device)
+    _req(out, torch.float32, "out")
+    o = _opts(algo, precision, splits)
+    d = L.dims_arr(dims)
+    need = lib.mtk_mttkrp_split_workspace(d, N, C, n, L.ctypes.byref(o))
+    if need == 0:
+        raise ValueError("invalid MTTKRP shape or options for the split tensor")
+    ws = ws or default_workspace(Xs.device)
+    wp, wb = ws.ptr(need)
+    L.check(lib.mtk_mttkrp_split(Xs.data_ptr(), X.data_ptr() if X is not None else None, d, N, L.ptr_arr(ptrs), C,
+                                 n, out.data_ptr(), wp, wb, L.ctypes.byref(o), _stream(Xs.device)),
+            "mtk_mttkrp_split")
     return out
 
 
@@ -271,10 +328,13 @@ def cp_gradient(Un, Mn, G, n, *, scale=None, out=None):
 
 
 class ALS:
-    """CP-ALS driver: holds the workspace, ||X||^2 and the device fit scalar."""
+    """CP-ALS driver: holds the workspace, ||X||^2 and the device fit scalar.
+    presplit=True splits X into its BF16 planes once (with ||X||^2 in the same pass) and
+    runs every MTTKRP on them (mtk_cp_als_sweep_split); precision is then bf16x2."""
 
-    def __init__(self, X, dims, U, *, algo="auto", precision="auto", splits=0):
+    def __init__(self, X, dims, U, *, algo="auto", precision="auto", splits=0, presplit=False):
         self.X = _req(X, torch.float32, "X")
+        self.presplit = bool(presplit)
         self.dims = [int(d) for d in dims]
         self.U = list(U)
         self.C = _rank(self.U)
@@ -288,18 +348,34 @@ class ALS:
         self.ws = Workspace(X.device)
         self.ws.get(need)
         self.need = need
-        self.normX2 = norm2(X, ws=Workspace(X.device))
+        self.Xs = None
+        if self.presplit:
+            self.Xs, self.normX2 = split_tensor(X, ws=Workspace(X.device))
+        else:
+            self.normX2 = norm2(X, ws=Workspace(X.device))
         self.fit = torch.zeros((), dtype=torch.float64, device=X.device)
         self._uptrs = L.ptr_arr([u.data_ptr() for u in self.U])
+
+    def resplit(self) -> None:
+        """Re-split X (after its contents changed) and refresh ||X||^2."""
+        if self.presplit:
+            split_tensor(self.X, out=self.Xs, normX2=self.normX2, ws=Workspace(self.X.device))
+        else:
+            norm2(self.X, out=self.normX2, ws=Workspace(self.X.device))
 
     def sweep(self, with_fit: bool = True) -> None:
         lib = L.load()
         wp, wb = self.ws.ptr(self.need)
-        L.check(lib.mtk_cp_als_sweep(self.X.data_ptr(), self._d, len(self.dims), self._uptrs, self.C,
-                                     self.normX2.data_ptr() if with_fit else None,
-                                     self.fit.data_ptr() if with_fit else None, wp, wb,
-                                     L.ctypes.byref(self.opts), _stream(self.X.device)),
-                "mtk_cp_als_sweep")
+        nx = self.normX2.data_ptr() if with_fit else None
+        fit = self.fit.data_ptr() if with_fit else None
+        st = _stream(self.X.device)
+        if self.presplit:
+            L.check(lib.mtk_cp_als_sweep_split(self.Xs.data_ptr(), self.X.data_ptr(), self._d, len(self.dims),
+                                               self._uptrs, self.C, nx, fit, wp, wb, L.ctypes.byref(self.opts), st),
+                    "mtk_cp_als_sweep_split")
+        else:
+            L.check(lib.mtk_cp_als_sweep(self.X.data_ptr(), self._d, len(self.dims), self._uptrs, self.C, nx, fit,
+                                         wp, wb, L.ctypes.byref(self.opts), st), "mtk_cp_als_sweep")
 
     def status(self) -> int:
         return self.ws.status()

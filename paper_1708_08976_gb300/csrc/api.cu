@@ -351,6 +351,56 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
     return MTK_OK;
 }
 
+// --- MTTKRP on a tensor split into BF16 planes ------------------------------------
+PlanesPlan planes_for(const int64_t* dims, int N, int C, int n, const mtk_opts& o) {
+    const View v = mode_view(dims, N, n);
+    const FactorList fl = mode_factors(nullptr, dims, N, n);
+    return planes_plan(v.L, v.I, fl.rad, fl.Z, C, n, planes_ctas(o.splits));
+}
+
+mtk_opts fallback_opts(const mtk_opts& o) {
+    mtk_opts f = o;
+    f.algo = MTK_ALGO_FUSED;
+    f.precision = MTK_PREC_BF16X2;
+    return f;
+}
+
+// workspace of one MTTKRP on the planes: the planes kernel's scratch when it takes the
+// shape, else that of the FP32-tensor path it falls back to
+size_t split_mttkrp_bytes(const int64_t* dims, int N, int C, int n, const mtk_opts& o) {
+    const PlanesPlan pl = planes_for(dims, N, C, n, o);
+    if (!pl.ok) return mttkrp_layout(dims, N, C, n, fallback_opts(o)).total;
+    return align256(align256(kStatusBytes) + planes_scratch_bytes(pl));
+}
+
+int do_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, const float* const* U,
+                    int C, int n, float* M, void* ws, size_t ws_bytes, uint32_t* status,
+                    const mtk_opts& o, cudaStream_t s) {
+    const PlanesPlan pl = planes_for(dims, N, C, n, o);
+    if (!pl.ok) {
+        if (!X) return MTK_EUNSUPPORTED;
+        return do_mttkrp(X, dims, N, U, C, n, M, ws, ws_bytes, status, fallback_opts(o), s);
+    }
+    if (ws_bytes < split_mttkrp_bytes(dims, N, C, n, o)) return MTK_EWORKSPACE;
+    const View v = mode_view(dims, N, n);
+    const FactorList fl = mode_factors(U, dims, N, n);
+    Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+    void* scratch = cv.take(planes_scratch_bytes(pl));
+    const int64_t NX = v.L * v.I * v.R;
+    if (launch_contract_planes(Xs, split_pitch(NX), v.L, v.I, v.R, fl.f, fl.rad, fl.Z, C, pl, M, C, 1,
+                               scratch, status, s) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+// the planes hold two BF16 pieces: precision AUTO or BF16X2, the fused algorithm
+int check_split_opts(const mtk_opts* raw) {
+    if (!raw) return MTK_OK;
+    if (raw->algo != MTK_ALGO_AUTO && raw->algo != MTK_ALGO_FUSED) return MTK_EINVAL;
+    if (raw->precision != MTK_PREC_AUTO && raw->precision != MTK_PREC_BF16X2) return MTK_EINVAL;
+    return MTK_OK;
+}
+
 int check_mttkrp_ptrs(const float* X, const float* const* U, int N, int n, const float* M,
                       const void* ws) {
     if (!X || !U || !M || !ws) return MTK_EINVAL;
@@ -464,6 +514,45 @@ int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* 
     st = do_mttkrp(X, dims, N, U, C, n, M, ws, MTK_NOALLOC_SCRATCH_BYTES, static_cast<uint32_t*>(ws), o, s);
     if (st || !status_bits) return st;
     return mtk_read_status(ws, stream, status_bits);
+}
+
+int64_t mtk_split_pitch(int64_t I) { return I < 1 ? 0 : split_pitch(I); }
+
+size_t mtk_split_bytes(int64_t I) { return I < 1 ? 0 : (size_t)(2 * split_pitch(I)) * 2; }
+
+size_t mtk_split_workspace(int64_t I) {
+    if (I < 1) return 0;
+    return align256(kStatusBytes) + align256((size_t)split_chunks(I) * sizeof(double));
+}
+
+int mtk_split_tensor(const float* X, int64_t I, void* Xs, double* normX2, void* ws, size_t ws_bytes,
+                     void* stream) {
+    if (!X || !Xs || !ws || I < 1 || !aligned4(X) || !aligned16(Xs)) return MTK_EINVAL;
+    if (ws_bytes < mtk_split_workspace(I)) return MTK_EWORKSPACE;
+    double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + align256(kStatusBytes));
+    if (launch_split_planes(X, I, Xs, part, normX2, (cudaStream_t)stream) != cudaSuccess) return MTK_ECUDA;
+    return MTK_OK;
+}
+
+size_t mtk_mttkrp_split_workspace(const int64_t* dims, int N, int C, int n, const mtk_opts* opts) {
+    if (check_shape(dims, N, C, n) != MTK_OK) return 0;
+    if (check_split_opts(opts) != MTK_OK) return 0;
+    return split_mttkrp_bytes(dims, N, C, n, defaults(opts));
+}
+
+int mtk_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, const float* const* U,
+                     int C, int n, float* M, void* ws, size_t ws_bytes, const mtk_opts* opts,
+                     void* stream) {
+    int st = check_shape(dims, N, C, n);
+    if (st) return st;
+    if (!Xs || !aligned16(Xs)) return MTK_EINVAL;
+    if (X && !aligned4(X)) return MTK_EINVAL;
+    st = check_mttkrp_ptrs(X ? X : static_cast<const float*>(Xs), U, N, n, M, ws);
+    if (st) return st;
+    if (check_split_opts(opts) != MTK_OK) return MTK_EINVAL;
+    mtk_opts o = defaults(opts);
+    return do_mttkrp_split(Xs, X, dims, N, U, C, n, M, ws, ws_bytes, static_cast<uint32_t*>(ws), o,
+                           (cudaStream_t)stream);
 }
 
 size_t mtk_partial_mttkrp_workspace(const int64_t* dims, int N, int C, int n, int right,
@@ -585,7 +674,8 @@ struct AlsLayout {
     int maxIn;
 };
 
-AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o) {
+// split = 1: the MTTKRPs read the tensor's BF16 planes (mtk_cp_als_sweep_split)
+AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o, int split) {
     AlsLayout a;
     memset(&a, 0, sizeof(a));
     int64_t maxIn = 0, maxChunks = 1;
@@ -594,7 +684,7 @@ AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o) {
         if (dims[k] > maxIn) maxIn = dims[k];
         const int ch = gram_chunks(dims[k]);
         if (ch > maxChunks) maxChunks = ch;
-        const size_t w = mttkrp_layout(dims, N, C, k, o).total;
+        const size_t w = split ? split_mttkrp_bytes(dims, N, C, k, o) : mttkrp_layout(dims, N, C, k, o).total;
         if (w > mt) mt = w;
     }
     a.maxIn = (int)maxIn;
@@ -616,24 +706,31 @@ size_t mtk_cp_als_workspace(const int64_t* dims, int N, int C, const mtk_opts* o
     if (N < 2) return 0;
     mtk_opts o = defaults(opts);
     if (o.algo < 0) return 0;
-    return als_layout(dims, N, C, o).total;
+    const size_t a = als_layout(dims, N, C, o, 0).total;
+    size_t b = 0;
+    if (check_split_opts(opts) == MTK_OK) b = als_layout(dims, N, C, o, 1).total;
+    return a > b ? a : b;
 }
 
-int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U, int C,
-                     const double* normX2, double* fit, void* ws, size_t ws_bytes,
-                     const mtk_opts* opts, void* stream) {
+namespace {
+// one sweep; Xs = NULL: MTTKRPs on the FP32 tensor, else on its BF16 planes (X may
+// then be NULL if every mode is taken by the planes kernel)
+int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float* const* U, int C,
+              const double* normX2, double* fit, void* ws, size_t ws_bytes, const mtk_opts* opts,
+              void* stream) {
     if (N < 2) return MTK_EINVAL;
     for (int n = 0; n < N; ++n) {
         int st = check_shape(dims, N, C, n);
         if (st) return st;
     }
-    if (!X || !U || !ws || !aligned4(X)) return MTK_EINVAL;
+    if ((!X && !Xs) || !U || !ws || (X && !aligned4(X)) || (Xs && !aligned16(Xs))) return MTK_EINVAL;
     for (int k = 0; k < N; ++k)
         if (!U[k] || !aligned4(U[k])) return MTK_EINVAL;
     if (fit && !normX2) return MTK_EINVAL;
     mtk_opts o = defaults(opts);
     if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
-    const AlsLayout a = als_layout(dims, N, C, o);
+    if (Xs && check_split_opts(opts) != MTK_OK) return MTK_EINVAL;
+    const AlsLayout a = als_layout(dims, N, C, o, Xs ? 1 : 0);
     if (ws_bytes < a.total) return MTK_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
@@ -651,7 +748,8 @@ int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U
             cudaSuccess)
             return MTK_ECUDA;
     for (int n = 0; n < N; ++n) {
-        int st = do_mttkrp(X, dims, N, U, C, n, M, mws, a.mt, status, o, s);
+        int st = Xs ? do_mttkrp_split(Xs, X, dims, N, U, C, n, M, mws, a.mt, status, o, s)
+                    : do_mttkrp(X, dims, N, U, C, n, M, mws, a.mt, status, o, s);
         if (st) return st;
         if (launch_chol_solve(G, N, C, n, M, dims[n], U[n], Hbuf, flag, status, s) != cudaSuccess)
             return MTK_ECUDA;
@@ -665,6 +763,21 @@ int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U
             return MTK_ECUDA;
     }
     return MTK_OK;
+}
+}  // namespace
+
+int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U, int C,
+                     const double* normX2, double* fit, void* ws, size_t ws_bytes,
+                     const mtk_opts* opts, void* stream) {
+    if (!X) return MTK_EINVAL;
+    return als_sweep(X, nullptr, dims, N, U, C, normX2, fit, ws, ws_bytes, opts, stream);
+}
+
+int mtk_cp_als_sweep_split(const void* Xs, const float* X, const int64_t* dims, int N, float* const* U,
+                           int C, const double* normX2, double* fit, void* ws, size_t ws_bytes,
+                           const mtk_opts* opts, void* stream) {
+    if (!Xs) return MTK_EINVAL;
+    return als_sweep(X, Xs, dims, N, U, C, normX2, fit, ws, ws_bytes, opts, stream);
 }
 
 int mtk_cp_residual(const double* normX2, const float* M, const float* Um, int64_t Im,

@@ -1,0 +1,995 @@
+// contract_split.cu -- the MTTKRP contraction on a tensor stored as two BF16 planes.
+//
+// CP-ALS (Section 2.2) runs an MTTKRP for every mode of every sweep on the same
+// tensor X.  Here X is split once into x = hi + lo, hi = bf16_rn(x), lo =
+// bf16_rn(x - hi) (the two-piece split of Henry, Tang and Heinecke, ARITH 2019),
+// and the two pieces are kept as two planes in the natural linearization (Section
+// 2.1).  The planes take exactly the bytes of the FP32 tensor, so every MTTKRP still
+// reads 4 bytes per entry, but the tensor-core operand is then a plain tile load:
+// TMA brings each 64-k tile of both planes into shared memory in the 128-byte-swizzled
+// layout that tcgen05.mma reads, and no thread touches tensor entries at all.
+//
+// The contraction is the one of contract_tc.cu (Algorithm 3's block structure on the
+// 3-way view of Fig. 2):
+//     M(i, c) = sum_q Q(q, c) * sum_h X3(h + H q, i) * Hd(h, c)
+// where the head Hd is the KRP of the first factors of the mode (H rows, split into
+// three BF16 pieces stacked along N = 3 * CP in an image of the B operand, one slice per
+// 64-k stage) and Q(q, c) is the product of the remaining factors' rows, applied when
+// the accumulator is drained from TMEM.  Drains happen at every run boundary and at
+// least every two stages, which bounds each tensor-core accumulation chain.
+//
+// Tensor operand: K-major (h along the contiguous mode, modes n > 0) or MN-major (i
+// contiguous, mode 0).  Rows of the 128-row MMA tile: one tile of BI <= 128 rows of i,
+// or, for I_n <= 64, U runs of the head packed one above the other (each packed run is
+// a separate partial slab).
+//
+// Warp roles (192 threads, one CTA per SM): warp 0 issues the TMA loads, warp 1 owns
+// TMEM and issues the MMAs, warps 2-5 drain the accumulators (one TMEM lane, i.e. one
+// row of M, per thread) and write the partial result.  Every mbarrier wait is bounded
+// (1 s of %globaltimer); on expiry the kernel sets MTK_ETIMEOUT, lets its own copies and
+// MMAs finish (again bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "mtk_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace mtk {
+namespace {
+
+using namespace tc;
+
+constexpr int PS_BK = 64;                    // k per stage
+constexpr int PS_M = 128;                    // MMA M
+constexpr int PS_GROUP = 2;                  // stages per accumulation chain
+constexpr int PS_MAX_A = 8;
+constexpr int PS_MAX_B = 6;
+constexpr int PS_MAX_BUF = 4;
+constexpr int PS_TILE = PS_M * 128;          // one plane of a 128 x 64 BF16 tile (16 KB)
+constexpr int PS_MN_ATOM = 64 * 128;         // MN-major: 64 k rows x 64 i (8 KB)
+constexpr unsigned long long kPsWaitNs = 1000000000ull;
+
+// L2 promotion of the tensor-map loads (0 none, 1 64 B, 2 128 B, 3 256 B), per operand
+// orientation.
+#ifndef MTK_PS_KM_PROMO
+#define MTK_PS_KM_PROMO 3
+#endif
+#ifndef MTK_PS_MN_PROMO
+#define MTK_PS_MN_PROMO 3
+#endif
+CUtensorMapL2promotion promo(int code) {
+    switch (code) {
+        case 0: return CU_TENSOR_MAP_L2_PROMOTION_NONE;
+        case 1: return CU_TENSOR_MAP_L2_PROMOTION_L2_64B;
+        case 2: return CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+        default: return CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+    }
+}
+
+struct PsParams {
+    int64_t I;              // output rows (I_n)
+    int64_t nruns;          // runs of the head along the contraction
+    int64_t Lq;             // K-major: runs per r (I^L / H)
+    int64_t stot;           // stages of one tile: ceil(nruns / U) * spr
+    int64_t H;              // head rows (the last chunk of a run holds H - 64 (spr - 1) of them)
+    int spr;                // stages per run (H padded to a multiple of 64, / 64)
+    int U, BI, MT;          // packed runs, rows per run group (tile rows), 128-row MMA tiles
+    int ldims;              // K-major tensor map rank: 5 (h, lq, i, r, plane) or 4 (h, i, r, plane)
+    int C, CP, N;           // N = 3 CP columns per accumulator
+    int sa, sb, nbuf, tmem_cols;
+    uint32_t idesc_hi, idesc_lo;
+    int a_stage, plane_bytes, b_bytes, b_stage, b_base;
+    int ntiles, s_full, s_last, nslab;
+    const uint8_t* bimg;
+    const float* qtab;      // Q(q, c) as [nruns][CP], or null (products formed in the drain)
+    int ntail;
+    const float* tail[MTK_MAXN];
+    int64_t tail_rad[MTK_MAXN];
+    float* out;
+    int64_t out_si, out_sc;
+    float* part;            // [slab][I][C] partials when nslab > 1
+    uint32_t* status;
+};
+
+template <int NCH, bool MN, int MT>
+__global__ void __launch_bounds__(96 + 128 * MT, 1)
+contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant__ CUtensorMap xmap) {
+    extern __shared__ uint8_t dsm_raw[];
+    __shared__ __align__(8) uint64_t afull[PS_MAX_A], aempty[PS_MAX_A];
+    __shared__ __align__(8) uint64_t bfull[PS_MAX_B], bempty[PS_MAX_B];
+    __shared__ __align__(8) uint64_t accf_bar[PS_MAX_BUF], acce_bar[PS_MAX_BUF];
+    __shared__ __align__(8) uint64_t fin_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t* dsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t dsm_s = smem_u32(dsm);
+    const int SA = p.sa, SB = p.sb, NB = p.nbuf;
+
+    // this CTA's tile of rows and its range of stages
+    int tile, sp, S_t;
+    {
+        const int b = (int)blockIdx.x;
+        if (b < (p.ntiles - 1) * p.s_full) {
+            tile = b / p.s_full;
+            sp = b % p.s_full;
+            S_t = p.s_full;
+        } else {
+            tile = p.ntiles - 1;
+            sp = b - (p.ntiles - 1) * p.s_full;
+            S_t = p.s_last;
+        }
+    }
+    const int64_t t0 = p.stot * sp / S_t, t1 = p.stot * (sp + 1) / S_t;
+    const int nst = (int)(t1 - t0);
+    const int64_t I = p.I;
+    const int U = p.U, BI = p.BI, spr = p.spr;
+    const int64_t i0 = (int64_t)tile * BI;
+    const int64_t nruns = p.nruns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(smem_u32(&afull[s]), 1);
+            mbar_init(smem_u32(&aempty[s]), 1);
+        }
+        for (int s = 0; s < SB; ++s) {
+            mbar_init(smem_u32(&bfull[s]), 1);
+            mbar_init(smem_u32(&bempty[s]), 1);
+        }
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), 4 * MT);
+        }
+        mbar_init(smem_u32(&fin_bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(p.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ tensor (A) producer
+        if (lane == 0) {
+            int issued = 0;
+            bool ok = true;
+            // position of the next stage: super-run sr, chunk j of the head (no divisions
+            // in the loop); per packed run g present, its (lq, r) coordinates
+            int64_t sr = t0 / spr;
+            int j = (int)(t0 - sr * spr);
+            int ng = 0;
+            int glq[16], gr[16];
+            auto set_groups = [&]() {
+                ng = 0;
+                while (ng < U && sr * U + ng < nruns) ++ng;
+                if (!MN) {
+                    const uint32_t Lq = (uint32_t)p.Lq;
+                    for (int g = 0; g < ng; ++g) {
+                        const uint32_t q = (uint32_t)(sr * U + g);
+                        const uint32_t r = q / Lq;
+                        glq[g] = (int)(q - r * Lq);
+                        gr[g] = (int)r;
+                    }
+                }
+            };
+            set_groups();
+            int nbox = 0;                                    // MN-major, U == 1: 64-row boxes present
+            if (MN && U == 1)
+                while (nbox < 2 * MT && i0 + 64 * nbox < I) ++nbox;
+            for (int s = 0; s < nst; ++s) {
+                const int slot = s % SA;
+                if (s >= SA && !mbar_wait(smem_u32(&aempty[slot]), (uint32_t)(((s / SA) - 1) & 1), &abort_flag,
+                                          kPsWaitNs)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = dsm_s + (uint32_t)(slot * p.a_stage);
+                const uint32_t fb = smem_u32(&afull[slot]);
+                uint32_t bytes;
+                if (MN) bytes = (uint32_t)(2 * (U == 1 ? nbox : ng) * PS_MN_ATOM);
+                else bytes = (uint32_t)(2 * ng * BI * 128);
+                mbar_arrive_expect_tx(fb, bytes);
+                for (int g = 0; g < ng; ++g) {
+#pragma unroll
+                    for (int pl = 0; pl < 2; ++pl) {
+                        const uint32_t dst = st + (uint32_t)(pl * p.plane_bytes);
+                        if (MN) {
+                            const int q = (int)(sr * U + g);
+                            if (U == 1) {
+                                for (int a = 0; a < nbox; ++a)
+                                    tma_load_4d(dst + (uint32_t)(a * PS_MN_ATOM), &xmap, (int)(i0 + 64 * a), 64 * j, q,
+                                                pl, fb);
+                            } else {
+                                tma_load_4d(dst + (uint32_t)(g * PS_MN_ATOM), &xmap, 0, 64 * j, q, pl, fb);
+                            }
+                        } else {
+                            const uint32_t d = dst + (uint32_t)(g * BI * 128);
+                            if (p.ldims == 5) tma_load_5d(d, &xmap, 64 * j, glq[g], (int)i0, gr[g], pl, fb);
+                            else tma_load_4d(d, &xmap, 64 * j, (int)i0, gr[g], pl, fb);
+                        }
+                    }
+                }
+                ++issued;
+                if (++j == spr) {
+                    j = 0;
+                    ++sr;
+                    set_groups();
+                }
+            }
+            if (!ok) {
+                abort_flag = 1;
+                set_status(p.status, MTK_ETIMEOUT);
+                // let the copies already issued land before the CTA leaves
+                const int first = issued > SA ? issued - SA : 0;
+                for (int s = first; s < issued; ++s) {
+                    volatile int never = 0;
+                    (void)mbar_wait(smem_u32(&afull[s % SA]), (uint32_t)((s / SA) & 1), &never, kPsWaitNs);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 2) {
+        // ------------------------------------------------------------ KRP image (B) producer
+        if (lane == 0) {
+            int issued = 0;
+            bool ok = true;
+            int j = (int)(t0 % spr);
+            for (int s = 0; s < nst; ++s) {
+                const int slot = s % SB;
+                if (s >= SB && !mbar_wait(smem_u32(&bempty[slot]), (uint32_t)(((s / SB) - 1) & 1), &abort_flag,
+                                          kPsWaitNs)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t fb = smem_u32(&bfull[slot]);
+                mbar_arrive_expect_tx(fb, (uint32_t)p.b_bytes);
+                bulk_copy_g2s(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage), p.bimg + (int64_t)j * p.b_bytes,
+                              (uint32_t)p.b_bytes, fb);
+                ++issued;
+                if (++j == spr) j = 0;
+            }
+            if (!ok) {
+                abort_flag = 1;
+                set_status(p.status, MTK_ETIMEOUT);
+                const int first = issued > SB ? issued - SB : 0;
+                for (int s = first; s < issued; ++s) {
+                    volatile int never = 0;
+                    (void)mbar_wait(smem_u32(&bfull[s % SB]), (uint32_t)((s / SB) & 1), &never, kPsWaitNs);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t a_lbo = MN ? (uint32_t)PS_MN_ATOM : 16u;
+            constexpr uint32_t a_sbo = 1024u;
+            constexpr uint32_t a_kstep = MN ? 2048u : 32u;
+            // k-steps of the last chunk of a run that hold head rows (the rest is padding)
+            const int64_t tail_rows = p.H - (int64_t)PS_BK * (spr - 1);
+            const int kk_last = (int)((tail_rows + 15) / 16);
+            int g = 0, gs = 0;
+            int j = (int)(t0 % spr);
+            bool ok = true;
+            uint32_t dcol = tmem;
+            for (int s = 0; s < nst; ++s) {
+                const int sa = s % SA, sb = s % SB;
+                if (!mbar_wait(smem_u32(&afull[sa]), (uint32_t)((s / SA) & 1), &abort_flag, kPsWaitNs) ||
+                    !mbar_wait(smem_u32(&bfull[sb]), (uint32_t)((s / SB) & 1), &abort_flag, kPsWaitNs)) {
+                    ok = false;
+                    break;
+                }
+                if (gs == 0) {
+                    const int b = g % NB;
+                    if (g >= NB && !mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)(((g / NB) - 1) & 1), &abort_flag,
+                                              kPsWaitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    dcol = tmem + (uint32_t)(b * MT * p.N);
+                }
+                tc_fence_after();
+                const uint32_t ast = dsm_s + (uint32_t)(sa * p.a_stage);
+                const uint32_t bst = dsm_s + (uint32_t)(p.b_base + sb * p.b_stage);
+                const int kk_n = (j == spr - 1) ? kk_last : PS_BK / 16;
+                for (int kk = 0; kk < kk_n; ++kk) {
+                    const uint64_t bdesc = make_desc(bst + kk * 32, 16, 1024);
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const uint32_t d = dcol + (uint32_t)(mt * p.N);
+                        const uint32_t a0 = ast + (uint32_t)(mt * PS_TILE) + kk * a_kstep;
+                        // hi plane x all three KRP pieces; lo plane x the first two (the
+                        // dropped lo * third-piece product is below 2^-24 of |x w|)
+                        mma_bf16(d, make_desc(a0, a_lbo, a_sbo), bdesc, p.idesc_hi, (gs == 0 && kk == 0) ? 0u : 1u);
+                        mma_bf16(d, make_desc(a0 + p.plane_bytes, a_lbo, a_sbo), bdesc, p.idesc_lo, 1u);
+                    }
+                }
+                mma_commit(smem_u32(&aempty[sa]));
+                mma_commit(smem_u32(&bempty[sb]));
+                ++gs;
+                const bool run_end = (++j == spr);
+                if (run_end) j = 0;
+                if (gs == PS_GROUP || run_end || s + 1 == nst) {
+                    mma_commit(smem_u32(&accf_bar[g % NB]));
+                    ++g;
+                    gs = 0;
+                }
+            }
+            if (!ok) {
+                abort_flag = 1;
+                set_status(p.status, MTK_ETIMEOUT);
+            }
+            // every MMA issued by this thread has completed once fin_bar flips
+            mma_commit(smem_u32(&fin_bar));
+            volatile int never = 0;
+            (void)mbar_wait(smem_u32(&fin_bar), 0u, &never, kPsWaitNs);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ drain + epilogue
+        const int dw = warp - 3;
+        const int sub = warp & 3;                    // TMEM sub-partition of this warp
+        const int mt = dw >> 2;                      // MMA tile
+        const int row = mt * 128 + sub * 32 + lane;  // row of the CTA tile = TMEM lane of tile mt
+        const int myg = U > 1 ? row / BI : 0;
+        const int myil = U > 1 ? row % BI : row;
+        const int64_t rows_here = (U > 1) ? I : ((I - i0) < BI ? (I - i0) : BI);
+        const bool rowvalid = myg < U && myil < rows_here;
+        const int C = p.C, CP = p.CP;
+        float acc[16 * NCH], qc[16 * NCH];
+#pragma unroll
+        for (int e = 0; e < 16 * NCH; ++e) {
+            acc[e] = 0.0f;
+            qc[e] = e < C ? 1.0f : 0.0f;
+        }
+        int64_t qcached = -1;
+        int g = 0, gs = 0;
+        int64_t sr = t0 / spr;                               // super-run of the next stage
+        int j = (int)(t0 - sr * spr);
+        bool ok = true;
+        for (int s = 0; s < nst; ++s) {
+            const int64_t sr_s = sr;
+            ++gs;
+            const bool run_end = (++j == spr);
+            if (run_end) {
+                j = 0;
+                ++sr;
+            }
+            if (!(gs == PS_GROUP || run_end || s + 1 == nst)) continue;
+            gs = 0;
+            const int b = g % NB;
+            const int64_t q = sr_s * U + myg;
+            const bool live = rowvalid && q < nruns;
+            if (live && p.ntail > 0 && q != qcached) {
+                // Q(q, c) = prod_z tail_z(digit_z(q), c): one row of the table, or the
+                // product formed here (digits once, then the columns)
+                if (p.qtab) {
+                    const float4* qr = reinterpret_cast<const float4*>(p.qtab + q * CP);
+#pragma unroll
+                    for (int e4 = 0; e4 < 4 * NCH; ++e4) {
+                        const float4 v = __ldg(qr + e4);
+                        qc[4 * e4] = v.x;
+                        qc[4 * e4 + 1] = v.y;
+                        qc[4 * e4 + 2] = v.z;
+                        qc[4 * e4 + 3] = v.w;
+                    }
+                } else {
+                    const float* rowp[MTK_MAXN];
+                    int64_t rem = q;
+                    for (int z = 0; z < p.ntail; ++z) {
+                        const int64_t rad = p.tail_rad[z];
+                        const int64_t nq = rem / rad;
+                        rowp[z] = p.tail[z] + (rem - nq * rad) * C;
+                        rem = nq;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16 * NCH; ++e) qc[e] = e < C ? __ldg(rowp[0] + e) : 0.0f;
+                    for (int z = 1; z < p.ntail; ++z) {
+#pragma unroll
+                        for (int e = 0; e < 16 * NCH; ++e)
+                            if (e < C) qc[e] *= __ldg(rowp[z] + e);
+                    }
+                }
+                qcached = q;
+            }
+            if (!mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((g / NB) & 1), &abort_flag, kPsWaitNs)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)((b * MT + mt) * p.N);
+            // 16-column chunks per TMEM round trip (one when two tiles share the registers)
+            constexpr int MB = (NCH >= 2 && MT == 1) ? 2 : 1;
+#pragma unroll
+            for (int m0 = 0; m0 < NCH; m0 += MB) {
+                float v[MB][3][16];
+#pragma unroll
+                for (int mm = 0; mm < MB; ++mm) {
+                    if (m0 + mm < NCH) {
+                        tmem_ld16(ta + 16 * (m0 + mm), v[mm][0]);
+                        tmem_ld16(ta + 16 * (m0 + mm) + CP, v[mm][1]);
+                        tmem_ld16(ta + 16 * (m0 + mm) + 2 * CP, v[mm][2]);
+                    }
+                }
+                tmem_ld_wait();
+                if (live) {
+#pragma unroll
+                    for (int mm = 0; mm < MB; ++mm) {
+                        if (m0 + mm < NCH) {
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const int e = 16 * (m0 + mm) + jj;
+                                acc[e] = fmaf((v[mm][2][jj] + v[mm][1][jj]) + v[mm][0][jj], qc[e], acc[e]);
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
+            ++g;
+        }
+        if (!ok) {
+            abort_flag = 1;
+            set_status(p.status, MTK_ETIMEOUT);
+        }
+        if (ok && rowvalid) {
+            const int64_t i = i0 + myil;
+            if (p.nslab == 1) {
+#pragma unroll
+                for (int e = 0; e < 16 * NCH; ++e)
+                    if (e < C) p.out[i * p.out_si + e * p.out_sc] = acc[e];
+            } else {
+                float* dst = p.part + (((int64_t)sp * U + myg) * I + i) * C;
+#pragma unroll
+                for (int e = 0; e < 16 * NCH; ++e)
+                    if (e < C) dst[e] = acc[e];
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+    }
+}
+
+// ---- per-call preparation: the B image of the head and the table of tail scales ----
+// Image slice j (one 64-k stage) is the 128-byte-swizzled K-major shared-memory image of
+// the N = 3 CP rows n = piece * CP + c, row n holding piece `piece` of Hd(64 j + d, c),
+// d = 0..63 (zero beyond the head's H rows and for c >= C).  Pieces: w0 = bf16_rn(w),
+// w1 = bf16_rn(w - w0), w2 = bf16_rn(w - w0 - w1).  Q(q, c) = prod over the tail
+// factors of their rows at the digits of q (first tail factor fastest), 0 for c >= C.
+struct PrepArgs {
+    int head, C, CP, N;
+    const float* fac[MTK_MAXN];
+    int64_t frad[MTK_MAXN];
+    int64_t H, Hp;
+    uint8_t* img;
+    int ntail;
+    const float* tail[MTK_MAXN];
+    int64_t tail_rad[MTK_MAXN];
+    int64_t nruns;
+    float* qtab;
+};
+
+__device__ __forceinline__ void split3(float w, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+    a = __float2bfloat16_rn(w);
+    const float r1 = w - __bfloat162float(a);
+    b = __float2bfloat16_rn(r1);
+    c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+__global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant__ PrepArgs a) {
+    const int64_t n_img = (a.Hp / 8) * a.CP;
+    const int64_t n_q = a.qtab ? a.nruns * a.CP : 0;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_img + n_q;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        if (it < n_img) {
+            const int c = (int)(it % a.CP);
+            const int64_t k0 = (it / a.CP) * 8;             // first head row of this octet
+            int64_t dig[MTK_MAXN];
+            int64_t rem = k0;
+            for (int z = 0; z < a.head; ++z) {
+                const int64_t nq = rem / a.frad[z];
+                dig[z] = rem - nq * a.frad[z];
+                rem = nq;
+            }
+            __nv_bfloat16 pc[3][8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                float w = 0.0f;
+                if (k0 + d < a.H && c < a.C) {
+                    w = 1.0f;
+                    for (int z = 0; z < a.head; ++z) w *= __ldg(a.fac[z] + dig[z] * a.C + c);
+                }
+                split3(w, pc[0][d], pc[1][d], pc[2][d]);
+                for (int z = 0; z < a.head; ++z) {           // next row: mixed-radix increment
+                    if (++dig[z] < a.frad[z]) break;
+                    dig[z] = 0;
+                }
+            }
+            const int64_t slice = k0 / PS_BK;
+            const int oct = (int)((k0 % PS_BK) / 8);
+            uint8_t* base = a.img + slice * (int64_t)(a.N * 128);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int n = q * a.CP + c;
+                const uint32_t off = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + (((oct ^ (n & 7)) & 7) << 4));
+                uint4 v;
+                v.x = (uint32_t)__bfloat16_as_ushort(pc[q][0]) | ((uint32_t)__bfloat16_as_ushort(pc[q][1]) << 16);
+                v.y = (uint32_t)__bfloat16_as_ushort(pc[q][2]) | ((uint32_t)__bfloat16_as_ushort(pc[q][3]) << 16);
+                v.z = (uint32_t)__bfloat16_as_ushort(pc[q][4]) | ((uint32_t)__bfloat16_as_ushort(pc[q][5]) << 16);
+                v.w = (uint32_t)__bfloat16_as_ushort(pc[q][6]) | ((uint32_t)__bfloat16_as_ushort(pc[q][7]) << 16);
+                *reinterpret_cast<uint4*>(base + off) = v;
+            }
+        } else {
+            const int64_t e = it - n_img;
+            const int64_t q = e / a.CP;
+            const int c = (int)(e - q * a.CP);
+            float prod = 0.0f;
+            if (c < a.C) {
+                prod = 1.0f;
+                int64_t rem = q;
+                for (int z = 0; z < a.ntail; ++z) {
+                    const int64_t nq = rem / a.tail_rad[z];
+                    prod *= __ldg(a.tail[z] + (rem - nq * a.tail_rad[z]) * a.C + c);
+                    rem = nq;
+                }
+            }
+            a.qtab[e] = prod;
+        }
+    }
+}
+
+// out(i, c) = sum of the partial slabs of i's tile, in slab order
+__global__ void planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI, int U, int ntiles,
+                                     int s_full, int s_last, float* __restrict__ out, int64_t si, int64_t sc) {
+    const int64_t n = I * C;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / C;
+        const int c = (int)(e % C);
+        const int64_t tile = U > 1 ? 0 : i / BI;
+        const int nsl = (tile < ntiles - 1 ? s_full : s_last) * U;
+        float v = 0.0f;
+        for (int s = 0; s < nsl; ++s) v += part[(int64_t)s * n + e];
+        out[i * si + c * sc] = v;
+    }
+}
+
+// ---- the split into planes, with ||X||^2 --------------------------------------------
+// (a, b) -> packed BF16 pairs hi = (bf16_rn(a), bf16_rn(b)) and lo = the BF16 rounding of
+// the remainders (exact in FP32); the first value in the low half (lower address)
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hw, uint32_t& lw) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hw = *reinterpret_cast<const uint32_t*>(&h);
+    lw = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__global__ void __launch_bounds__(256) split_planes_kernel(const float* __restrict__ X, int64_t NX, int64_t pitch,
+                                                           int64_t chunk, __nv_bfloat16* __restrict__ Xs,
+                                                           double* __restrict__ part) {
+    const int64_t b0 = (int64_t)blockIdx.x * chunk;
+    const int64_t b1 = (b0 + chunk < NX) ? b0 + chunk : NX;
+    __nv_bfloat16* hi = Xs;
+    __nv_bfloat16* lo = Xs + pitch;
+    // ||X||^2: each square is exact as p + e (p = x*x, e = fma(x, x, -p)); the p are summed
+    // with two-sum compensation in FP32 and (sum, compensation) are flushed into an FP64
+    // total every 64 entries, so the FP64 pipe (slow on this part) sees 2 adds per 64 entries
+    double ss = 0.0;
+    float S = 0.0f, cmp = 0.0f;
+    int cnt = 0;
+    auto add_sq = [&](float x) {
+        const float pp = x * x;
+        const float ee = fmaf(x, x, -pp);
+        const float t = S + pp;
+        const float z = t - S;
+        cmp += ((S - (t - z)) + (pp - z)) + ee;
+        S = t;
+    };
+    auto flush = [&]() {
+        ss += (double)S;
+        ss += (double)cmp;
+        S = 0.0f;
+        cmp = 0.0f;
+    };
+    const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((reinterpret_cast<uintptr_t>(Xs) & 15) == 0) &&
+                     (pitch % 4 == 0) && (chunk % 4 == 0);
+    if (vec) {
+        const int64_t n4 = (b1 - b0) / 4;
+        for (int64_t v = threadIdx.x; v < n4; v += blockDim.x) {
+            const int64_t e = b0 + 4 * v;
+            const float4 x = *reinterpret_cast<const float4*>(X + e);
+            uint2 hw, lw;
+            split_pair(x.x, x.y, hw.x, lw.x);
+            split_pair(x.z, x.w, hw.y, lw.y);
+            add_sq(x.x);
+            add_sq(x.y);
+            add_sq(x.z);
+            add_sq(x.w);
+            if (++cnt == 16) { flush(); cnt = 0; }
+            *reinterpret_cast<uint2*>(hi + e) = hw;
+            *reinterpret_cast<uint2*>(lo + e) = lw;
+        }
+        for (int64_t e = b0 + 4 * n4 + threadIdx.x; e < b1; e += blockDim.x) {
+            const float x = X[e];
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            hi[e] = h;
+            lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+            add_sq(x);
+        }
+    } else {
+        for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
+            const float x = X[e];
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            hi[e] = h;
+            lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+            add_sq(x);
+            if (++cnt == 64) { flush(); cnt = 0; }
+        }
+    }
+    flush();
+    // fixed-order block reduction
+    __shared__ double red[256];
+    red[threadIdx.x] = ss;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && part) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += part[k];
+        *out = s;
+    }
+}
+
+// block: warp 0 tensor producer, warp 1 MMA issuer (TMEM owner), warp 2 image producer,
+// then four drain warps per 128-row MMA tile
+template <int NCH, bool MN>
+cudaError_t launch_planes_variant(const PsParams& p, const CUtensorMap& map, int grid, size_t smem, cudaStream_t s) {
+    cudaError_t e;
+    if (p.MT == 2) {
+        e = cudaFuncSetAttribute(contract_planes_kernel<NCH, MN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        contract_planes_kernel<NCH, MN, 2><<<grid, 96 + 128 * 2, smem, s>>>(p, map);
+    } else {
+        e = cudaFuncSetAttribute(contract_planes_kernel<NCH, MN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        contract_planes_kernel<NCH, MN, 1><<<grid, 96 + 128, smem, s>>>(p, map);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+int num_sms() {
+    static int n = []() {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 152;
+        return v;
+    }();
+    return n;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+int64_t split_pitch(int64_t NX) { return round_up(NX, 64); }
+
+int split_chunks(int64_t NX) {
+    int64_t nb = (NX + 4095) / 4096;
+    if (nb > 1216) nb = 1216;
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+cudaError_t launch_split_planes(const float* X, int64_t NX, void* Xs, double* part, double* normX2,
+                                cudaStream_t s) {
+    const int nb = split_chunks(NX);
+    const int64_t chunk = round_up((NX + nb - 1) / nb, 1024);
+    const int grid = (int)((NX + chunk - 1) / chunk);
+    split_planes_kernel<<<grid, 256, 0, s>>>(X, NX, split_pitch(NX), chunk, static_cast<__nv_bfloat16*>(Xs), part);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !normX2) return e;
+    sum_partials_kernel<<<1, 32, 0, s>>>(part, grid, normX2);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int C, int n_left, int ctas) {
+    PlanesPlan pl;
+    memset(&pl, 0, sizeof(pl));
+    if (C < 1 || C > 64 || nfac < 1) return pl;
+    const int64_t lim = ((int64_t)1 << 31) - 1;
+    const bool mn = (L == 1);
+    if (mn) {
+        if (I % 8 != 0) return pl;
+    } else {
+        if (L % 8 != 0 || n_left < 1) return pl;
+    }
+    int64_t K = 1;
+    for (int z = 0; z < nfac; ++z) K *= frad[z];
+    pl.CP = (C + 15) & ~15;
+    pl.N = 3 * pl.CP;
+    // head: a prefix of the factor list (K-major: within the modes left of n).  The
+    // first prefix with >= 64 rows and <= 1/32 padding, else the least padding; its
+    // image must stay L2-resident and, when further left modes follow it, its rows must
+    // be a multiple of 8 (16-byte stride of the plane's tensor map).
+    const int mmax = mn ? nfac : n_left;
+    int best = -1;
+    double best_waste = 2.0;
+    int64_t prod = 1;
+    for (int m = 1; m <= mmax; ++m) {
+        prod *= frad[m - 1];
+        const int64_t padded = round_up(prod, PS_BK);
+        const size_t img = (size_t)(padded / PS_BK) * pl.N * 128;
+        if (img > ((size_t)32 << 20)) break;
+        if (!mn && m < n_left && prod % 8 != 0) continue;
+        const double waste = (double)(padded - prod) / (double)padded;
+        if (prod >= PS_BK && (padded - prod) * 32 <= prod) { best = m; break; }
+        if (waste < best_waste) { best_waste = waste; best = m; }
+    }
+    if (best < 0) return pl;
+    int64_t H = 1;
+    for (int z = 0; z < best; ++z) H *= frad[z];
+    pl.head = best;
+    pl.H = H;
+    pl.spr = (int)(round_up(H, PS_BK) / PS_BK);
+    pl.nruns = K / H;
+    pl.Lq = mn ? 1 : L / H;
+    if (H > lim || pl.nruns > lim || I > lim || (!mn && (K / L) > lim)) return pl;
+    pl.mn = mn ? 1 : 0;
+    // rows: small I_n packs U runs into one 128-row MMA tile; otherwise a CTA takes up to
+    // 256 rows of i (two 128-row MMA tiles), so that its loads cover more of each row of
+    // the tensor and each image slice serves more rows, when such tiles are at least 3/4
+    // full; else tiles of up to 128 rows
+    const int64_t t2 = (I + 2 * PS_M - 1) / (2 * PS_M);
+    const bool two = I > 64 && (double)I >= 0.75 * (double)(t2 * 2 * PS_M);
+    if (I <= 64) {
+        pl.MT = 1;
+        pl.ntiles = 1;
+        if (mn) {
+            pl.U = (int)(pl.nruns < 2 ? pl.nruns : 2);
+            pl.BI = 64;
+        } else {
+            pl.BI = (int)round_up(I, 8);
+            int64_t u = PS_M / pl.BI;
+            if (u > pl.nruns) u = pl.nruns;
+            pl.U = (int)u;
+        }
+    } else {
+        pl.U = 1;
+        pl.MT = two ? 2 : 1;
+        const int cap = PS_M * pl.MT;
+        if (mn) {
+            pl.BI = cap;
+        } else {
+            const int64_t t = (I + cap - 1) / cap;
+            pl.BI = (int)round_up((I + t - 1) / t, 8);
+        }
+        pl.ntiles = (int)((I + pl.BI - 1) / pl.BI);
+    }
+    pl.stot = ((pl.nruns + pl.U - 1) / pl.U) * pl.spr;
+    // CTAs per tile, proportional to the rows each tile reads; at least 4 stages each
+    const int T = pl.ntiles;
+    int64_t smax = pl.stot / 4;
+    if (smax < 1) smax = 1;
+    if (T >= ctas) {
+        pl.s_full = pl.s_last = 1;
+    } else if (T == 1) {
+        pl.s_full = pl.s_last = (int)(ctas < smax ? ctas : smax);
+    } else {
+        int64_t sf = (int64_t)ctas * pl.BI / I;
+        if (sf < 1) sf = 1;
+        int64_t sl = ctas - (int64_t)(T - 1) * sf;
+        if (sl < 1) sl = 1;
+        if (sf > smax) sf = smax;
+        if (sl > smax) sl = smax;
+        pl.s_full = (int)sf;
+        pl.s_last = (int)sl;
+    }
+    pl.grid = (T - 1) * pl.s_full + pl.s_last;
+    pl.nslab = (pl.s_full > pl.s_last ? pl.s_full : pl.s_last) * pl.U;
+    pl.image_bytes = (size_t)pl.spr * pl.N * 128;
+    // table of tail scales Q(q, c) when it is small
+    const size_t qbytes = (size_t)pl.nruns * pl.CP * sizeof(float);
+    pl.qtab_bytes = (nfac > best && qbytes <= ((size_t)32 << 20)) ? qbytes : 0;
+    pl.part_bytes = pl.nslab > 1 ? (size_t)pl.nslab * I * C * sizeof(float) : 0;
+    pl.ok = 1;
+    return pl;
+}
+
+size_t planes_scratch_bytes(const PlanesPlan& pl) {
+    return round_up((int64_t)pl.image_bytes, 256) + round_up((int64_t)pl.qtab_bytes, 256) +
+           round_up((int64_t)pl.part_bytes, 256);
+}
+
+int planes_ctas(int splits) { return splits > 0 ? splits : num_sms(); }
+
+cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int64_t I, int64_t R,
+                                   const float* const* fac, const int64_t* frad, int nfac, int C,
+                                   const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
+                                   void* scratch, uint32_t* status, cudaStream_t s) {
+    char* sc = static_cast<char*>(scratch);
+    uint8_t* image = reinterpret_cast<uint8_t*>(sc);
+    float* qtab = pl.qtab_bytes ? reinterpret_cast<float*>(sc + round_up((int64_t)pl.image_bytes, 256)) : nullptr;
+    float* part = reinterpret_cast<float*>(sc + round_up((int64_t)pl.image_bytes, 256) +
+                                           round_up((int64_t)pl.qtab_bytes, 256));
+
+    // 1) the B image of the head and the table of tail scales (one launch)
+    PrepArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.head = pl.head;
+    pa.C = C;
+    pa.CP = pl.CP;
+    pa.N = pl.N;
+    for (int z = 0; z < pl.head; ++z) {
+        pa.fac[z] = fac[z];
+        pa.frad[z] = frad[z];
+    }
+    pa.H = pl.H;
+    pa.Hp = (int64_t)pl.spr * PS_BK;
+    pa.img = image;
+    pa.ntail = nfac - pl.head;
+    for (int z = pl.head; z < nfac; ++z) {
+        pa.tail[z - pl.head] = fac[z];
+        pa.tail_rad[z - pl.head] = frad[z];
+    }
+    pa.nruns = pl.nruns;
+    pa.qtab = qtab;
+    {
+        const int64_t items = (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * pl.CP : 0);
+        int64_t blocks = (items + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        planes_prep_kernel<<<(int)blocks, 256, 0, s>>>(pa);
+        note_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+
+    // 2) the tensor map over both planes
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    CUresult r;
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    int ldims = 4;
+    if (pl.mn) {
+        const cuuint64_t dims[4] = {(cuuint64_t)I, (cuuint64_t)pl.H, (cuuint64_t)pl.nruns, 2};
+        const cuuint64_t strides[3] = {(cuuint64_t)I * 2, (cuuint64_t)I * pl.H * 2, (cuuint64_t)pitch * 2};
+        const cuuint32_t box[4] = {64, 64, 1, 1};
+        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Xs), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_MN_PROMO),
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else if (pl.Lq > 1) {
+        ldims = 5;
+        const cuuint64_t dims[5] = {(cuuint64_t)pl.H, (cuuint64_t)pl.Lq, (cuuint64_t)I, (cuuint64_t)R, 2};
+        const cuuint64_t strides[4] = {(cuuint64_t)pl.H * 2, (cuuint64_t)L * 2, (cuuint64_t)L * I * 2,
+                                       (cuuint64_t)pitch * 2};
+        const cuuint32_t box[5] = {64, 1, (cuuint32_t)pl.BI, 1, 1};
+        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(Xs), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)I, (cuuint64_t)R, 2};
+        const cuuint64_t strides[3] = {(cuuint64_t)L * 2, (cuuint64_t)L * I * 2, (cuuint64_t)pitch * 2};
+        const cuuint32_t box[4] = {64, (cuuint32_t)pl.BI, 1, 1};
+        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Xs), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+    // 3) the contraction
+    PsParams p;
+    memset(&p, 0, sizeof(p));
+    p.I = I;
+    p.nruns = pl.nruns;
+    p.Lq = pl.Lq;
+    p.stot = pl.stot;
+    p.H = pl.H;
+    p.spr = pl.spr;
+    p.U = pl.U;
+    p.BI = pl.BI;
+    p.MT = pl.MT;
+    p.ldims = ldims;
+    p.C = C;
+    p.CP = pl.CP;
+    p.N = pl.N;
+    p.plane_bytes = pl.MT * PS_TILE;
+    p.a_stage = 2 * p.plane_bytes;
+    p.b_bytes = pl.N * 128;
+    p.b_stage = (int)round_up(p.b_bytes, 1024);
+    // shared memory: A ring (tensor tiles, HBM latency) as deep as fits next to a
+    // shallower B ring (image slices, L2 latency)
+    // (one MMA tile: both rings equally deep, so the image slices are requested as early
+    // as the tensor tiles; two tiles: 3 + 2 stages fill the budget)
+    const int budget = 225 * 1024;
+    if (pl.MT == 1) {
+        p.sb = budget / (p.a_stage + p.b_stage);
+        if (p.sb > PS_MAX_B) p.sb = PS_MAX_B;
+    } else {
+        p.sb = 2;
+    }
+    p.sa = (budget - p.sb * p.b_stage) / p.a_stage;
+    if (p.sa > PS_MAX_A) p.sa = PS_MAX_A;
+    if (p.sa < 2 || p.sb < 2) return cudaErrorInvalidConfiguration;
+    p.b_base = p.sa * p.a_stage;
+    p.nbuf = 512 / (pl.MT * pl.N);
+    if (p.nbuf > PS_MAX_BUF) p.nbuf = PS_MAX_BUF;
+    if (p.nbuf < 1) return cudaErrorInvalidConfiguration;
+    int cols = 32;
+    while (cols < p.nbuf * pl.MT * pl.N) cols <<= 1;
+    p.tmem_cols = cols;
+    p.idesc_hi = idesc_bf16(PS_M, pl.N, pl.mn != 0);
+    p.idesc_lo = idesc_bf16(PS_M, 2 * pl.CP, pl.mn != 0);
+    p.ntiles = pl.ntiles;
+    p.s_full = pl.s_full;
+    p.s_last = pl.s_last;
+    p.nslab = pl.nslab;
+    p.bimg = image;
+    p.qtab = qtab;
+    p.ntail = nfac - pl.head;
+    for (int z = pl.head; z < nfac; ++z) {
+        p.tail[z - pl.head] = fac[z];
+        p.tail_rad[z - pl.head] = frad[z];
+    }
+    p.out = out;
+    p.out_si = out_si;
+    p.out_sc = out_sc;
+    p.part = part;
+    p.status = status;
+    const size_t smem = (size_t)p.sa * p.a_stage + (size_t)p.sb * p.b_stage + 1024;
+    const int nch = pl.CP / 16;
+    cudaError_t e;
+    if (pl.mn) {
+        switch (nch) {
+            case 1: e = launch_planes_variant<1, true>(p, map, pl.grid, smem, s); break;
+            case 2: e = launch_planes_variant<2, true>(p, map, pl.grid, smem, s); break;
+            case 3: e = launch_planes_variant<3, true>(p, map, pl.grid, smem, s); break;
+            default: e = launch_planes_variant<4, true>(p, map, pl.grid, smem, s); break;
+        }
+    } else {
+        switch (nch) {
+            case 1: e = launch_planes_variant<1, false>(p, map, pl.grid, smem, s); break;
+            case 2: e = launch_planes_variant<2, false>(p, map, pl.grid, smem, s); break;
+            case 3: e = launch_planes_variant<3, false>(p, map, pl.grid, smem, s); break;
+            default: e = launch_planes_variant<4, false>(p, map, pl.grid, smem, s); break;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    if (pl.nslab > 1) {
+        const int64_t n = I * C;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 1216) blocks = 1216;
+        planes_reduce_kernel<<<(int)blocks, 256, 0, s>>>(part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last,
+                                                         out, out_si, out_sc);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace mtk

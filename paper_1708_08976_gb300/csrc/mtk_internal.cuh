@@ -80,6 +80,36 @@ TcPlan contract_tc_plan(const int64_t* frad, int nfac, int64_t L, int64_t I, int
 bool contract_tc_supported(const ContractParams& p, int precision);
 // image: device scratch of plan.image_bytes (256-byte aligned)
 cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* image, cudaStream_t s);
+// The B image alone: the KRP of the first `head` factors (rad0 rows, padded to rad0p, a
+// multiple of 64) split into three BF16 pieces stacked along N = 3*CP, written as
+// rad0p/64 slices, each the 128-byte-swizzled K-major shared-memory image of one 64-k
+// stage (N rows x 128 bytes).
+cudaError_t launch_tc_image(const float* const* fac, const int64_t* frad, int head, int C, int CP,
+                            int64_t rad0, int64_t rad0p, void* image, cudaStream_t s);
+
+// ---- tensor stored as two BF16 planes (contract_split.cu) --------------------------
+// Planes of an NX-entry tensor: hi = bf16_rn(x) at [0, NX), lo = bf16_rn(x - hi) at
+// [pitch, pitch + NX), pitch = split_pitch(NX) (a multiple of 64 entries).
+int64_t split_pitch(int64_t NX);
+int split_chunks(int64_t NX);          // FP64 partials of ||X||^2 written by the split
+// part: split_chunks(NX) doubles; normX2 (may be NULL): receives ||X||^2
+cudaError_t launch_split_planes(const float* X, int64_t NX, void* Xs, double* part, double* normX2,
+                                cudaStream_t s);
+// Plan of the planes contraction for view (L, I, R) and the mode's factor list; ok = 0
+// when the shape is not taken (C > 64, I^L or I_n not a multiple of 8, ...).
+struct PlanesPlan {
+    int ok, mn, head, spr, U, BI, MT, CP, N, ntiles, s_full, s_last, nslab, grid;
+    int64_t H, nruns, Lq, stot;
+    size_t image_bytes, qtab_bytes, part_bytes;
+};
+PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int C, int n_left, int ctas);
+size_t planes_scratch_bytes(const PlanesPlan& pl);   // image + Q table + partials
+int planes_ctas(int splits);           // CTAs of one launch (0 = one per SM)
+// scratch: planes_scratch_bytes(pl) bytes, 256-byte aligned
+cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int64_t I, int64_t R,
+                                   const float* const* fac, const int64_t* frad, int nfac, int C,
+                                   const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
+                                   void* scratch, uint32_t* status, cudaStream_t s);
 
 cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C, float* K,
                        int reuse, cudaStream_t s);

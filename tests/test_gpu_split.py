@@ -1,0 +1,206 @@
+"""GPU parity of the MTTKRP on a tensor stored as two BF16 planes (mtk_split_tensor,
+mtk_mttkrp_split, mtk_cp_als_sweep_split) against the FP64 oracle.
+
+* The split itself is checked bit for bit against its definition: hi = bf16_rn(x),
+  lo = bf16_rn(x - hi), with the rounding done by torch on the CPU; ||X||^2 against
+  the oracle.
+* The contraction carries each tensor entry as hi + lo (error <= 2^-16 |x|) and each
+  KRP entry as three BF16 pieces, so it is held to the bf16x2 bound derived in
+  test_gpu_tc.py: 3x the expected representation error plus 2e-6 for FP32
+  accumulation.
+The shapes cover each branch of the planes kernel: K-major CTA tiles of up to 128 rows or
+of up to 256 rows as two MMA tiles (one or several per mode, ragged last tile), K-major with the head inside the modes left of n
+(5-D tensor map), runs packed into the MMA rows for I_n <= 64, MN-major (mode 0) with
+one to four 64-row boxes per CTA or packed runs, ranks C = 1..64 (one to four 16-column chunks), N = 2..5,
+heads shorter than one 64-k stage, several tail factors, and explicit CTA counts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import f32_round, factors_dev, rel_fro, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1708_08976_gb300 as mtk  # noqa: E402
+from paper_1708_08976_gb300 import _lib as L  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mtk.load()
+
+
+def bf16x2_bound(Xr, dims, Ur, n, ref):
+    M2 = oracle.mttkrp(Xr * Xr, dims, [u * u for u in Ur], n)
+    rho = np.sqrt(max(M2.sum(), 0.0)) / max(np.linalg.norm(ref), 1e-300)
+    return 3.0 * 2.0 ** -16 / np.sqrt(3.0) * rho + 2e-6
+
+
+def planes_ref(X32: torch.Tensor):
+    """hi, lo by their definition, BF16 round-to-nearest-even on the CPU (torch)."""
+    x = X32.cpu()
+    hi = x.to(torch.bfloat16)
+    lo = (x - hi.to(torch.float32)).to(torch.bfloat16)
+    return hi.view(torch.int16), lo.view(torch.int16)
+
+
+@pytest.mark.parametrize("n_entries", [1, 7, 64, 1000, 4099, 262147])
+def test_split_planes_bits_and_norm(n_entries):
+    g = np.random.default_rng(n_entries)
+    X = (g.standard_normal(n_entries) * np.exp(g.uniform(-20, 20, n_entries))).astype(np.float32)
+    X[::13] = 0.0
+    Xd = torch.from_numpy(X).cuda()
+    Xs, nx2 = mtk.split_tensor(Xd)
+    torch.cuda.synchronize()
+    pitch = L.load().mtk_split_pitch(n_entries)
+    assert pitch % 64 == 0 and pitch >= n_entries
+    hi, lo = planes_ref(Xd)
+    got = Xs.cpu()
+    assert torch.equal(got[:n_entries], hi)
+    assert torch.equal(got[pitch:pitch + n_entries], lo)
+    ref = oracle.norm2(X.astype(np.float64))
+    assert abs(nx2.item() - ref) <= 1e-12 * ref
+
+
+def run_split(X, dims, U, n, C, splits=0, with_x=True):
+    Xd = to_dev(X, torch)
+    Ud = factors_dev(U, torch)
+    Xs, _ = mtk.split_tensor(Xd)
+    M = mtk.mttkrp(Xd if with_x else None, dims, Ud, n, Xs=Xs, splits=splits)
+    torch.cuda.synchronize()
+    return M.double().cpu().numpy()
+
+
+SHAPES = [
+    # (dims, C): comment = what the modes exercise
+    ((64, 48, 40), 8),            # MN 64 rows; K-major L=64; 5-D map (head U_0 inside I^L=3072), packed I=40
+    ((200, 64, 30), 25),          # MN two tiles (72-row tail, two boxes); K-major packed 64 -> U=2
+    ((160, 40, 48), 17),          # MN ragged last tile of 32 rows (one box); heads of 40 rows (< one stage)
+    ((32, 64, 16), 16),           # MN packed (I_0 = 32, U = 2 runs); K-major I=64
+    ((32, 300, 20), 32),          # K-major three tiles of 104 rows over I = 300, head of 32 rows
+    ((256, 200), 33),             # N = 2: MN with one run; K-major with no tail
+    ((40, 40, 30, 8), 25),        # two tail factors; packed I = 8 (U = 16)
+    ((64, 16, 24, 40), 48),       # 5-D map with Lq = 384, packed U = 3
+    ((8, 8, 8, 8, 8), 64),        # N = 5, C = 64 (four chunks), packed U = 16
+    ((24, 136, 72), 1),           # C = 1; K-major two tiles (72 + 64 rows)
+    ((512, 8, 24), 16),           # MN two CTA tiles of 256 rows (two MMA tiles each)
+    ((16, 456, 12), 32),          # K-major CTA tiles of 232 + 224 rows (two MMA tiles, ragged)
+    ((200, 200, 8), 25),          # K-major 200 rows in one CTA; head of 200 rows: padding k-steps skipped
+]
+
+
+@pytest.mark.parametrize("dims,C", SHAPES)
+def test_mttkrp_split_parity(dims, C):
+    X, dims, U = synth.random_case(dims, C, seed=11 * sum(dims) + C)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    for n in range(len(dims)):
+        ref = oracle.mttkrp(Xr, dims, Ur, n)
+        got = run_split(X, dims, U, n, C)
+        err = rel_fro(got, ref)
+        tol = bf16x2_bound(Xr, dims, Ur, n, ref)
+        assert err < tol, (dims, C, n, err, tol)
+
+
+def test_mttkrp_split_without_fp32_tensor():
+    """Shapes the planes kernel takes need no FP32 tensor; others report EUNSUPPORTED."""
+    X, dims, U = synth.random_case((64, 48, 40), 8, seed=5)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    for n in range(3):
+        ref = oracle.mttkrp(Xr, dims, Ur, n)
+        got = run_split(X, dims, U, n, 8, with_x=False)
+        assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, n, ref)
+    X, dims, U = synth.tiny3()                       # mode 1 has I^L = 60 (not a multiple of 8)
+    Xd = to_dev(X, torch)
+    Xs, _ = mtk.split_tensor(Xd)
+    with pytest.raises(mtk.MtkError) as ei:
+        mtk.mttkrp(None, dims, factors_dev(U, torch), 1, Xs=Xs)
+    assert ei.value.status == L.MTK_EUNSUPPORTED
+    # with the FP32 tensor the same call runs the FP32-input tensor-core path
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    ref = oracle.mttkrp(Xr, dims, Ur, 1)
+    got = run_split(X, dims, U, 1, 8)
+    assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, 1, ref)
+
+
+@pytest.mark.parametrize("splits", [1, 3, 500])
+def test_mttkrp_split_cta_counts(splits):
+    """One CTA, a few, and a request for more CTAs than the plan allows (capped at four
+    stages per CTA)."""
+    X, dims, U = synth.random_case((48, 96, 24), 16, seed=splits)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    for n in range(3):
+        ref = oracle.mttkrp(Xr, dims, Ur, n)
+        got = run_split(X, dims, U, n, 16, splits=splits)
+        assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, n, ref), (splits, n)
+
+
+def test_mttkrp_split_deterministic():
+    X, dims, U = synth.random_case((72, 64, 50), 25, seed=3)
+    Xd = to_dev(X, torch)
+    Ud = factors_dev(U, torch)
+    Xs, _ = mtk.split_tensor(Xd)
+    for n in range(3):
+        a = mtk.mttkrp(Xd, dims, Ud, n, Xs=Xs).clone()
+        b = mtk.mttkrp(Xd, dims, Ud, n, Xs=Xs)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
+def test_split_rejects_bad_options():
+    X, dims, U = synth.random_case((64, 48, 40), 8, seed=5)
+    Xd = to_dev(X, torch)
+    Xs, _ = mtk.split_tensor(Xd)
+    for kw in ({"precision": "fp32"}, {"precision": "bf16x3"}, {"algo": "two_step"}):
+        with pytest.raises(ValueError):
+            mtk.mttkrp(Xd, dims, factors_dev(U, torch), 0, Xs=Xs, **kw)
+
+
+@pytest.mark.parametrize("case", ["tiny3", "all_planes"])
+def test_als_sweep_split(case):
+    """One CP-ALS sweep on the planes against the oracle's sweep (tiny3 has a mode that
+    falls back to the FP32 tensor)."""
+    if case == "tiny3":
+        X, dims, U = synth.tiny3()
+    else:
+        X, dims, U = synth.random_case((64, 48, 40), 8, seed=9, dist="uniform")
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    ref_U, ref_fit = oracle.als_sweep(Xr, dims, Ur)
+    Xd = to_dev(X, torch)
+    Ud = factors_dev(U, torch)
+    als = mtk.ALS(Xd, dims, Ud, presplit=True)
+    als.sweep()
+    assert als.status() == 0
+    for k in range(len(dims)):
+        err = rel_fro(Ud[k].double().cpu().numpy(), ref_U[k])
+        assert err < 2e-5, (case, k, err)
+    assert abs(als.fit.item() - ref_fit) < 2e-6
+    assert abs(als.normX2.item() - oracle.norm2(Xr)) <= 1e-12 * oracle.norm2(Xr)
+
+
+def test_corr4_split_full_M():
+    """Every mode of the 200x200x300x40 workload in the benchmark's configuration (one
+    CTA per SM), the whole M against the FP64 oracle: <= 1e-5 and within the bound."""
+    X, dims, U = synth.corr4()
+    X64 = X.astype(np.float64)
+    U64 = [u.astype(np.float64) for u in U]
+    Xd = torch.from_numpy(X).cuda()
+    Ud = [torch.from_numpy(u).cuda() for u in U]
+    Xs, nx2 = mtk.split_tensor(Xd)
+    assert abs(nx2.item() - oracle.norm2(X64)) <= 1e-12 * oracle.norm2(X64)
+    for n in range(4):
+        ref = oracle.mttkrp(X64, dims, U64, n)
+        got = mtk.mttkrp(None, dims, Ud, n, Xs=Xs).double().cpu().numpy()
+        err = rel_fro(got, ref)
+        assert err < 1e-5, (n, err)
+        tol = bf16x2_bound(X64, dims, U64, n, ref)
+        assert err < tol, (n, err, tol)
