@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="corr4", choices=["corr4", "cube512", "corr4-small"])
+    ap.add_argument("--workload", default="corr4", choices=["corr4", "cube512", "corr4-small", "corr4-mid"])
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run every mode's MTTKRP W+K times (for profiler captures)")
     ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | planes | best")
@@ -63,6 +63,9 @@ def workload(name):
     elif name == "corr4-small":
         X, dims, U = synth.corr4(dims=(200, 200, 30, 40))
         desc = "corr4-small: 200x200x30x40 FP32 correlation-shaped (same per-mode I_n as corr4, 1/10 of the entries), rank C=25"
+    elif name == "corr4-mid":
+        X, dims, U = synth.corr4(dims=(200, 200, 300, 12))
+        desc = "corr4-mid: 200x200x300x12 FP32 correlation-shaped (the mode-2 view of corr4 with 12 subjects), rank C=25"
     else:
         X, dims, U = synth.cube512()
         desc = "cube512: 512^3 FP32 N(0,1), rank C=32, factors N(0,1)/sqrt(32)"

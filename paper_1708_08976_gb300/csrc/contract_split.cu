@@ -77,7 +77,9 @@ struct PsParams {
     int spr;                // stages per run (H padded to a multiple of 64, / 64)
     int U, BI, MT;          // packed runs, rows per run group (tile rows), 128-row MMA tiles
     int ldims;              // K-major tensor map rank: 5 (h, lq, i, r, plane) or 4 (h, i, r, plane)
-    int C, CP, N;           // N = 3 CP columns per accumulator
+    int C, CP, N;           // N = 3 CP columns of the hi-plane accumulator
+    int lo_sep;             // the lo plane accumulates into its own 2 CP columns (one MMA tile)
+    int acc_cols;           // TMEM columns per accumulator buffer
     int sa, sb, nbuf, tmem_cols;
     uint32_t idesc_hi, idesc_lo;
     int a_stage, plane_bytes, b_bytes, b_stage, b_base;
@@ -185,10 +187,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             int nbox = 0;                                    // MN-major, U == 1: 64-row boxes present
             if (MN && U == 1)
                 while (nbox < 2 * MT && i0 + 64 * nbox < I) ++nbox;
+            int slot = 0;
+            uint32_t ph = 1;                                 // parity of the empty phase to wait for
             for (int s = 0; s < nst; ++s) {
-                const int slot = s % SA;
-                if (s >= SA && !mbar_wait(smem_u32(&aempty[slot]), (uint32_t)(((s / SA) - 1) & 1), &abort_flag,
-                                          kPsWaitNs)) {
+                if (s >= SA && !mbar_wait(smem_u32(&aempty[slot]), ph, &abort_flag, kPsWaitNs)) {
                     ok = false;
                     break;
                 }
@@ -219,6 +221,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     }
                 }
                 ++issued;
+                if (++slot == SA) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
                 if (++j == spr) {
                     j = 0;
                     ++sr;
@@ -243,10 +249,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             int issued = 0;
             bool ok = true;
             int j = (int)(t0 % spr);
+            int slot = 0;
+            uint32_t ph = 1;
             for (int s = 0; s < nst; ++s) {
-                const int slot = s % SB;
-                if (s >= SB && !mbar_wait(smem_u32(&bempty[slot]), (uint32_t)(((s / SB) - 1) & 1), &abort_flag,
-                                          kPsWaitNs)) {
+                if (s >= SB && !mbar_wait(smem_u32(&bempty[slot]), ph, &abort_flag, kPsWaitNs)) {
                     ok = false;
                     break;
                 }
@@ -255,6 +261,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 bulk_copy_g2s(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage), p.bimg + (int64_t)j * p.b_bytes,
                               (uint32_t)p.b_bytes, fb);
                 ++issued;
+                if (++slot == SB) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
                 if (++j == spr) j = 0;
             }
             if (!ok) {
@@ -271,56 +281,95 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
+            // Descriptors are formed once and advanced by constant 16-byte-unit offsets; ring
+            // slots and barrier phases are counters (no divisions in the loop): an MMA then
+            // issues at its math rate.
             constexpr uint32_t a_lbo = MN ? (uint32_t)PS_MN_ATOM : 16u;
-            constexpr uint32_t a_sbo = 1024u;
-            constexpr uint32_t a_kstep = MN ? 2048u : 32u;
+            constexpr uint32_t a_k16 = MN ? (2048u >> 4) : (32u >> 4);   // one K = 16 step
+            const uint64_t adesc0 = make_desc(dsm_s, a_lbo, 1024u);
+            const uint64_t bdesc0 = make_desc(dsm_s + (uint32_t)p.b_base, 16u, 1024u);
+            const uint64_t plane16 = (uint64_t)(p.plane_bytes >> 4);
+            const uint64_t a_st16 = (uint64_t)(p.a_stage >> 4), b_st16 = (uint64_t)(p.b_stage >> 4);
+            const uint32_t idh = p.idesc_hi, idl = p.idesc_lo;
+            const uint32_t ncol = (uint32_t)p.N;
             // k-steps of the last chunk of a run that hold head rows (the rest is padding)
             const int64_t tail_rows = p.H - (int64_t)PS_BK * (spr - 1);
             const int kk_last = (int)((tail_rows + 15) / 16);
             int g = 0, gs = 0;
             int j = (int)(t0 % spr);
+            int sa = 0, sb = 0, bi = 0;
+            uint32_t pa = 0, pb = 0, pe = 1;
+            uint64_t ad = adesc0, bd = bdesc0;
             bool ok = true;
             uint32_t dcol = tmem;
             for (int s = 0; s < nst; ++s) {
-                const int sa = s % SA, sb = s % SB;
-                if (!mbar_wait(smem_u32(&afull[sa]), (uint32_t)((s / SA) & 1), &abort_flag, kPsWaitNs) ||
-                    !mbar_wait(smem_u32(&bfull[sb]), (uint32_t)((s / SB) & 1), &abort_flag, kPsWaitNs)) {
+                if (!mbar_wait(smem_u32(&afull[sa]), pa, &abort_flag, kPsWaitNs) ||
+                    !mbar_wait(smem_u32(&bfull[sb]), pb, &abort_flag, kPsWaitNs)) {
                     ok = false;
                     break;
                 }
                 if (gs == 0) {
-                    const int b = g % NB;
-                    if (g >= NB && !mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)(((g / NB) - 1) & 1), &abort_flag,
-                                              kPsWaitNs)) {
+                    if (g >= NB && !mbar_wait(smem_u32(&acce_bar[bi]), pe, &abort_flag, kPsWaitNs)) {
                         ok = false;
                         break;
                     }
-                    dcol = tmem + (uint32_t)(b * MT * p.N);
+                    dcol = tmem + (uint32_t)(bi * p.acc_cols);
                 }
                 tc_fence_after();
-                const uint32_t ast = dsm_s + (uint32_t)(sa * p.a_stage);
-                const uint32_t bst = dsm_s + (uint32_t)(p.b_base + sb * p.b_stage);
                 const int kk_n = (j == spr - 1) ? kk_last : PS_BK / 16;
-                for (int kk = 0; kk < kk_n; ++kk) {
-                    const uint64_t bdesc = make_desc(bst + kk * 32, 16, 1024);
-                    for (int mt = 0; mt < MT; ++mt) {
-                        const uint32_t d = dcol + (uint32_t)(mt * p.N);
-                        const uint32_t a0 = ast + (uint32_t)(mt * PS_TILE) + kk * a_kstep;
-                        // hi plane x all three KRP pieces; lo plane x the first two (the
-                        // dropped lo * third-piece product is below 2^-24 of |x w|)
-                        mma_bf16(d, make_desc(a0, a_lbo, a_sbo), bdesc, p.idesc_hi, (gs == 0 && kk == 0) ? 0u : 1u);
-                        mma_bf16(d, make_desc(a0 + p.plane_bytes, a_lbo, a_sbo), bdesc, p.idesc_lo, 1u);
+                // hi plane x all three KRP pieces; lo plane x the first two (the dropped
+                // lo * third-piece product is below 2^-24 of |x w|).  One MMA tile: the lo
+                // plane has its own accumulator (columns N .. N + 2 CP).
+#pragma unroll
+                for (int kk = 0; kk < PS_BK / 16; ++kk) {
+                    if (kk < kk_n) {
+                        const uint64_t bk = bd + (uint64_t)(kk * 2);
+                        const uint32_t acc = (kk == 0 && gs == 0) ? 0u : 1u;
+                        if (MT == 1) {
+                            const uint64_t a0 = ad + (uint64_t)(kk * a_k16);
+                            mma_bf16(dcol, a0, bk, idh, acc);
+                            mma_bf16(dcol + ncol, a0 + plane16, bk, idl, acc);
+                        } else {
+#pragma unroll
+                            for (int mt = 0; mt < MT; ++mt) {
+                                const uint64_t a0 = ad + (uint64_t)(kk * a_k16 + mt * (PS_TILE >> 4));
+                                mma_bf16(dcol + (uint32_t)mt * ncol, a0, bk, idh, acc);
+                            }
+#pragma unroll
+                            for (int mt = 0; mt < MT; ++mt) {
+                                const uint64_t a0 = ad + (uint64_t)(kk * a_k16 + mt * (PS_TILE >> 4)) + plane16;
+                                mma_bf16(dcol + (uint32_t)mt * ncol, a0, bk, idl, 1u);
+                            }
+                        }
                     }
                 }
                 mma_commit(smem_u32(&aempty[sa]));
                 mma_commit(smem_u32(&bempty[sb]));
+                if (++sa == SA) {
+                    sa = 0;
+                    pa ^= 1u;
+                    ad = adesc0;
+                } else {
+                    ad += a_st16;
+                }
+                if (++sb == SB) {
+                    sb = 0;
+                    pb ^= 1u;
+                    bd = bdesc0;
+                } else {
+                    bd += b_st16;
+                }
                 ++gs;
                 const bool run_end = (++j == spr);
                 if (run_end) j = 0;
                 if (gs == PS_GROUP || run_end || s + 1 == nst) {
-                    mma_commit(smem_u32(&accf_bar[g % NB]));
+                    mma_commit(smem_u32(&accf_bar[bi]));
                     ++g;
                     gs = 0;
+                    if (++bi == NB) {                // next round of the buffers: group g
+                        bi = 0;                          // waits for drain #(g / NB - 1)
+                        pe ^= 1u;
+                    }
                 }
             }
             if (!ok) {
@@ -352,6 +401,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
         }
         int64_t qcached = -1;
         int g = 0, gs = 0;
+        int db = 0;                                          // accumulator buffer of group g
+        uint32_t dph = 0;                                    // and the parity of its next fill
         int64_t sr = t0 / spr;                               // super-run of the next stage
         int j = (int)(t0 - sr * spr);
         bool ok = true;
@@ -365,7 +416,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             }
             if (!(gs == PS_GROUP || run_end || s + 1 == nst)) continue;
             gs = 0;
-            const int b = g % NB;
+            const int b = db;
             const int64_t q = sr_s * U + myg;
             const bool live = rowvalid && q < nruns;
             if (live && p.ntail > 0 && q != qcached) {
@@ -400,35 +451,46 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 }
                 qcached = q;
             }
-            if (!mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((g / NB) & 1), &abort_flag, kPsWaitNs)) {
+            if (!mbar_wait(smem_u32(&accf_bar[b]), dph, &abort_flag, kPsWaitNs)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)((b * MT + mt) * p.N);
-            // 16-column chunks per TMEM round trip (one when two tiles share the registers)
-            constexpr int MB = (NCH >= 2 && MT == 1) ? 2 : 1;
+            const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(b * p.acc_cols + mt * p.N);
+            if (MT == 1) {
+                // hi accumulator (w0, w1, w2 at 0, CP, 2 CP) and lo accumulator (w0, w1 at
+                // N, N + CP); summed smallest first
 #pragma unroll
-            for (int m0 = 0; m0 < NCH; m0 += MB) {
-                float v[MB][3][16];
+                for (int m = 0; m < NCH; ++m) {
+                    float h0[16], h1[16], h2[16], l0[16], l1[16];
+                    tmem_ld16(ta + 16 * m, h0);
+                    tmem_ld16(ta + 16 * m + CP, h1);
+                    tmem_ld16(ta + 16 * m + 2 * CP, h2);
+                    tmem_ld16(ta + 16 * m + p.N, l0);
+                    tmem_ld16(ta + 16 * m + p.N + CP, l1);
+                    tmem_ld_wait();
+                    if (live) {
 #pragma unroll
-                for (int mm = 0; mm < MB; ++mm) {
-                    if (m0 + mm < NCH) {
-                        tmem_ld16(ta + 16 * (m0 + mm), v[mm][0]);
-                        tmem_ld16(ta + 16 * (m0 + mm) + CP, v[mm][1]);
-                        tmem_ld16(ta + 16 * (m0 + mm) + 2 * CP, v[mm][2]);
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const int e = 16 * m + jj;
+                            const float v = ((h2[jj] + l1[jj]) + (h1[jj] + l0[jj])) + h0[jj];
+                            acc[e] = fmaf(v, qc[e], acc[e]);
+                        }
                     }
                 }
-                tmem_ld_wait();
-                if (live) {
+            } else {
 #pragma unroll
-                    for (int mm = 0; mm < MB; ++mm) {
-                        if (m0 + mm < NCH) {
+                for (int m = 0; m < NCH; ++m) {
+                    float v0[16], v1[16], v2[16];
+                    tmem_ld16(ta + 16 * m, v0);
+                    tmem_ld16(ta + 16 * m + CP, v1);
+                    tmem_ld16(ta + 16 * m + 2 * CP, v2);
+                    tmem_ld_wait();
+                    if (live) {
 #pragma unroll
-                            for (int jj = 0; jj < 16; ++jj) {
-                                const int e = 16 * (m0 + mm) + jj;
-                                acc[e] = fmaf((v[mm][2][jj] + v[mm][1][jj]) + v[mm][0][jj], qc[e], acc[e]);
-                            }
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const int e = 16 * m + jj;
+                            acc[e] = fmaf((v2[jj] + v1[jj]) + v0[jj], qc[e], acc[e]);
                         }
                     }
                 }
@@ -437,6 +499,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
             ++g;
+            if (++db == NB) {
+                db = 0;
+                dph ^= 1u;
+            }
         }
         if (!ok) {
             abort_flag = 1;
@@ -937,11 +1003,13 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     if (p.sa > PS_MAX_A) p.sa = PS_MAX_A;
     if (p.sa < 2 || p.sb < 2) return cudaErrorInvalidConfiguration;
     p.b_base = p.sa * p.a_stage;
-    p.nbuf = 512 / (pl.MT * pl.N);
+    p.lo_sep = pl.MT == 1 ? 1 : 0;
+    p.acc_cols = pl.MT == 1 ? pl.N + 2 * pl.CP : pl.MT * pl.N;
+    p.nbuf = 512 / p.acc_cols;
     if (p.nbuf > PS_MAX_BUF) p.nbuf = PS_MAX_BUF;
     if (p.nbuf < 1) return cudaErrorInvalidConfiguration;
     int cols = 32;
-    while (cols < p.nbuf * pl.MT * pl.N) cols <<= 1;
+    while (cols < p.nbuf * p.acc_cols) cols <<= 1;
     p.tmem_cols = cols;
     p.idesc_hi = idesc_bf16(PS_M, pl.N, pl.mn != 0);
     p.idesc_lo = idesc_bf16(PS_M, 2 * pl.CP, pl.mn != 0);
