@@ -618,18 +618,32 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
     }
 }
 
-// out(i, c) = sum of the partial slabs of i's tile, in slab order
-__global__ void planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI, int U, int ntiles,
-                                     int s_full, int s_last, float* __restrict__ out, int64_t si, int64_t sc) {
+// out(i, c) = sum of the partial slabs of i's tile.  A block takes 32 consecutive outputs
+// and its 8 warps take interleaved slabs (warp w: slabs w, w + 8, ...); the 8 warp sums
+// are added in warp order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI,
+                                                            int U, int ntiles, int s_full, int s_last,
+                                                            float* __restrict__ out, int64_t si, int64_t sc) {
+    __shared__ float red[8][32];
     const int64_t n = I * C;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    float v = 0.0f;
+    if (e < n) {
         const int64_t i = e / C;
-        const int c = (int)(e % C);
         const int64_t tile = U > 1 ? 0 : i / BI;
         const int nsl = (tile < ntiles - 1 ? s_full : s_last) * U;
-        float v = 0.0f;
-        for (int s = 0; s < nsl; ++s) v += part[(int64_t)s * n + e];
-        out[i * si + c * sc] = v;
+        for (int s = w; s < nsl; s += 8) v += part[(int64_t)s * n + e];
+    }
+    red[w][lane] = v;
+    __syncthreads();
+    if (w == 0 && e < n) {
+        float t = red[0][lane];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) t += red[k][lane];
+        const int64_t i = e / C;
+        const int c = (int)(e % C);
+        out[i * si + c * sc] = t;
     }
 }
 
@@ -1050,10 +1064,9 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     if (e != cudaSuccess) return e;
     if (pl.nslab > 1) {
         const int64_t n = I * C;
-        int64_t blocks = (n + 255) / 256;
-        if (blocks > 1216) blocks = 1216;
-        planes_reduce_kernel<<<(int)blocks, 256, 0, s>>>(part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last,
-                                                         out, out_si, out_sc);
+        const int64_t blocks = (n + 31) / 32;
+        planes_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full,
+                                                              pl.s_last, out, out_si, out_sc);
         note_launches(1);
         e = cudaGetLastError();
     }

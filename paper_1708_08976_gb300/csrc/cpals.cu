@@ -9,16 +9,17 @@
 namespace mtk {
 namespace {
 
-constexpr int kGramRows = 32;       // rows of U staged per step
-constexpr int64_t kGramChunk = 32;    // rows per CTA (many CTAs: FP64 FMA throughput is low)
+constexpr int kGramRows = 8;        // rows of U staged per step
+constexpr int64_t kGramChunk = 8;     // rows per CTA, at least (many CTAs: the FP64 rate per
+constexpr int64_t kGramMaxChunks = 256;  // SM is low), at most this many chunks
 
-// partial Gram of rows [chunk*kGramChunk, ...) for the pairs of block blockIdx.y
+// partial Gram of rows [chunk*rpc, ...) for the pairs of block blockIdx.y
 // (1024 pairs per block, 4 per thread); out = part + chunk*C*C (or G if one chunk)
 __global__ void __launch_bounds__(256)
-gram_partial_kernel(const float* __restrict__ U, int64_t I, int C, double* __restrict__ out) {
+gram_partial_kernel(const float* __restrict__ U, int64_t I, int C, int64_t rpc, double* __restrict__ out) {
     extern __shared__ float us[];                 // kGramRows x C
-    const int64_t r0 = (int64_t)blockIdx.x * kGramChunk;
-    const int64_t r1 = (r0 + kGramChunk < I) ? r0 + kGramChunk : I;
+    const int64_t r0 = (int64_t)blockIdx.x * rpc;
+    const int64_t r1 = (r0 + rpc < I) ? r0 + rpc : I;
     const int npairs = C * C;
     const int pbase = blockIdx.y * 1024;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -124,6 +125,63 @@ chol_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __
         }
     }
     if (threadIdx.x == 0) {
+        *flag = bad ? 0 : 1;
+        if (bad) set_status(status, MTK_ENOTPD);
+    }
+}
+
+// H^{-1} for C <= 64 by Gauss-Jordan elimination in place, FP64, one CTA (textbook
+// Gauss-Jordan inversion without pivoting, which is stable for symmetric positive
+// definite matrices).  Its pivots are the squares of the Cholesky diagonal, so H is
+// positive definite iff every pivot is > 0; a pivot <= 0 flags MTK_ENOTPD exactly as the
+// Cholesky factorisation would.  Each of the C steps is one reciprocal and C^2
+// independent updates over 256 threads, so the dependent chain is C steps long (the
+// FP64 pipe of this part is narrow; long serial chains, not flop counts, set the time).
+// Hbuf layout as chol_kernel: Hinv[C*C] at Hbuf + C*C + C.
+__global__ void __launch_bounds__(256)
+inv_gj_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __restrict__ Hbuf,
+              int* __restrict__ flag, uint32_t* status) {
+    __shared__ double A[64 * 64];
+    __shared__ double prow[64], pcol[64];
+    __shared__ double rp;
+    __shared__ int bad;
+    const int t = threadIdx.x;
+    for (int e = t; e < C * C; e += blockDim.x) {
+        double h = 1.0;
+        for (int k = 0; k < N; ++k)
+            if (k != n) h *= gl.G[k][e];
+        A[e] = h;
+    }
+    if (t == 0) bad = 0;
+    __syncthreads();
+    for (int p = 0; p < C; ++p) {
+        if (t < C) {
+            prow[t] = A[p * C + t];
+            pcol[t] = A[t * C + p];
+        }
+        if (t == 0) {
+            const double d = A[p * C + p];
+            if (!(d > 0.0)) bad = 1;
+            rp = (d > 0.0) ? 1.0 / d : 0.0;
+        }
+        __syncthreads();
+        if (bad) break;
+        const double r = rp;
+        for (int e = t; e < C * C; e += blockDim.x) {
+            const int i = e / C, k = e - (e / C) * C;
+            double v;
+            if (i == p && k == p) v = r;
+            else if (i == p) v = prow[k] * r;
+            else if (k == p) v = -pcol[i] * r;
+            else v = A[e] - pcol[i] * prow[k] * r;
+            A[e] = v;
+        }
+        __syncthreads();
+    }
+    double* Hinv = Hbuf + (size_t)C * C + C;
+    if (!bad)
+        for (int e = t; e < C * C; e += blockDim.x) Hinv[e] = A[e];
+    if (t == 0) {
         *flag = bad ? 0 : 1;
         if (bad) set_status(status, MTK_ENOTPD);
     }
@@ -251,17 +309,21 @@ gradient_kernel(const float* __restrict__ U, const float* __restrict__ M,
 
 }  // namespace
 
-int gram_chunks(int64_t I) { return (int)((I + kGramChunk - 1) / kGramChunk); }
+int gram_chunks(int64_t I) {
+    const int64_t n = (I + kGramChunk - 1) / kGramChunk;
+    return (int)(n < kGramMaxChunks ? n : kGramMaxChunks);
+}
 
 cudaError_t launch_gram(const float* U, int64_t I, int C, double* G, double* part, int nchunks,
                         cudaStream_t s) {
     const size_t smem = (size_t)kGramRows * C * sizeof(float);
     const unsigned pblocks = (unsigned)((C * C + 1023) / 1024);
+    const int64_t rpc = (I + nchunks - 1) / (nchunks > 0 ? nchunks : 1);
     if (nchunks <= 1) {
-        gram_partial_kernel<<<dim3(1, pblocks), 256, smem, s>>>(U, I, C, G);
+        gram_partial_kernel<<<dim3(1, pblocks), 256, smem, s>>>(U, I, C, I, G);
         note_launches(1);
     } else {
-        gram_partial_kernel<<<dim3(nchunks, pblocks), 256, smem, s>>>(U, I, C, part);
+        gram_partial_kernel<<<dim3(nchunks, pblocks), 256, smem, s>>>(U, I, C, rpc, part);
         note_launches(1);
         gram_reduce_kernel<<<(C * C + 255) / 256, 256, 0, s>>>(part, nchunks, C, G);
         note_launches(1);
@@ -277,11 +339,15 @@ cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const
     GramList gl;
     for (int k = 0; k < MTK_MAXN; ++k) gl.G[k] = (k < N) ? G[k] : nullptr;
     const size_t hbytes = (size_t)C * C * sizeof(double);
-    const int chol_smem = hbytes <= 200 * 1024;
-    if (chol_smem) {
-        cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hbytes);
+    if (C <= 64) {
+        inv_gj_kernel<<<1, 256, 0, s>>>(gl, N, C, n, Hbuf, flag, status);
+    } else {
+        const int chol_smem = hbytes <= 200 * 1024;
+        if (chol_smem) {
+            cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hbytes);
+        }
+        chol_kernel<<<1, 256, chol_smem ? hbytes : 0, s>>>(gl, N, C, n, Hbuf, flag, status, chol_smem);
     }
-    chol_kernel<<<1, 256, chol_smem ? hbytes : 0, s>>>(gl, N, C, n, Hbuf, flag, status, chol_smem);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
