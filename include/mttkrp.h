@@ -167,6 +167,32 @@ int mtk_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N,
                      int C, int n, float* M, void* ws, size_t ws_bytes, const mtk_opts* opts,
                      void* stream);
 
+/* Batched MTTKRPs (Section 2.2) in one persistent launch ---------------------
+ * P independent problems, each one mode-n MTTKRP of its own tensor, all computed by one
+ * persistent kernel (plus one reduce launch), so that a batch of many small, uneven
+ * tensors costs two launches and can be captured in a CUDA graph.  FP32 fused
+ * multiply-adds on the CUDA cores, FP32 accumulation, fixed-order reductions (the
+ * result does not depend on scheduling).  Any dims (no alignment needed).
+ * Limits: P <= MTK_BATCH_MAXP, N in [2, MTK_BATCH_MAXN], C in [1, 32], and the
+ * contraction length prod_{k != n} dims[k] < 2^31; otherwise MTK_EINVAL.
+ * opts->splits: contraction indices per work unit (0 = automatic; the autotuner of the
+ * Python binding picks it by timing); algo and precision are ignored.
+ * ws: device, at least mtk_mttkrp_batched_workspace(...) bytes (first 256: status). */
+#define MTK_BATCH_MAXN 4
+#define MTK_BATCH_MAXP 192
+typedef struct {
+    const float* X;                    /* device tensor, natural order */
+    const float* U[MTK_BATCH_MAXN];    /* device factors, U[k] is dims[k] x C (U[n] not read) */
+    int64_t dims[MTK_BATCH_MAXN];
+    int N;                             /* order of this tensor */
+    int n;                             /* mode */
+    int C;                             /* rank */
+    float* M;                          /* device output, dims[n] x C, overwritten */
+} mtk_batch_problem;
+size_t mtk_mttkrp_batched_workspace(const mtk_batch_problem* probs, int P, const mtk_opts* opts);
+int mtk_mttkrp_batched(const mtk_batch_problem* probs, int P, void* ws, size_t ws_bytes, const mtk_opts* opts,
+                       void* stream);
+
 /* 2-step pieces (Section 4.3, Algorithm 4) -------------------------------
  * Partial MTTKRP.  right = 1: T = X_(0:n) K_R, K_R = U_{N-1} kr ... kr U_{n+1}
  * (R = prod_{k>n} I_k rows); T is the (I^L x I_n x C) tensor R of the paper in

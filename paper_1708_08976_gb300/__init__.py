@@ -4,11 +4,11 @@ Parallelization of MTTKRP for Dense Tensors" (Hayashi, Ballard, Jiang, Tobia).
 The compute lives in ``lib/libmttkrp.so`` (CUDA kernels behind the C ABI of
 ``include/mttkrp.h``); this package is its thin torch binding.
 """
-from .api import (ALS, ALGOS, PRECISIONS, CPLoss, Workspace, cp_gradient, cp_loss, cp_residual,
+from .api import (ALS, ALGOS, BatchedMTTKRP, mttkrp_batched, PRECISIONS, CPLoss, Workspace, cp_gradient, cp_loss, cp_residual,
                   default_workspace, gram, gram_hadamard_solve, khatri_rao, multi_ttv, mttkrp,
                   norm2, partial_mttkrp, split_tensor)
 from ._lib import MtkError, load
 
-__all__ = ["ALS", "ALGOS", "PRECISIONS", "CPLoss", "Workspace", "cp_gradient", "cp_loss",
+__all__ = ["ALS", "ALGOS", "BatchedMTTKRP", "mttkrp_batched", "PRECISIONS", "CPLoss", "Workspace", "cp_gradient", "cp_loss",
            "cp_residual", "default_workspace", "gram", "gram_hadamard_solve", "khatri_rao",
            "multi_ttv", "mttkrp", "norm2", "partial_mttkrp", "split_tensor", "MtkError", "load"]

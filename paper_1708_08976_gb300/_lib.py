@@ -29,6 +29,18 @@ class MtkOpts(ctypes.Structure):
 
 OPTS_P = ctypes.POINTER(MtkOpts)
 
+BATCH_MAXN = 4
+BATCH_MAXP = 192
+
+
+class MtkBatchProblem(ctypes.Structure):
+    """mtk_batch_problem of include/mttkrp.h."""
+    _fields_ = [("X", P), ("U", P * BATCH_MAXN), ("dims", I64 * BATCH_MAXN), ("N", I32), ("n", I32),
+                ("C", I32), ("M", P)]
+
+
+BATCH_P = ctypes.POINTER(MtkBatchProblem)
+
 # name -> (restype, argtypes); mirrors include/mttkrp.h
 SIGNATURES = {
     "mtk_status_string": (ctypes.c_char_p, [I32]),
@@ -46,6 +58,8 @@ SIGNATURES = {
     "mtk_split_tensor": (I32, [P, I64, P, P, P, SZ, P]),
     "mtk_mttkrp_split_workspace": (SZ, [P, I32, I32, I32, OPTS_P]),
     "mtk_mttkrp_split": (I32, [P, P, P, I32, P, I32, I32, P, P, SZ, OPTS_P, P]),
+    "mtk_mttkrp_batched_workspace": (SZ, [BATCH_P, I32, OPTS_P]),
+    "mtk_mttkrp_batched": (I32, [BATCH_P, I32, P, SZ, OPTS_P, P]),
     "mtk_partial_mttkrp_workspace": (SZ, [P, I32, I32, I32, I32, OPTS_P]),
     "mtk_partial_mttkrp": (I32, [P, P, I32, P, I32, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_multi_ttv": (I32, [P, P, I32, P, I32, I32, I32, P, P]),

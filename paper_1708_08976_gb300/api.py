@@ -327,6 +327,126 @@ def cp_gradient(Un, Mn, G, n, *, scale=None, out=None):
     return out
 
 
+def _batch_array(problems):
+    """problems: list of (X, dims, U, n, out) with torch CUDA tensors (U[n] may be None)."""
+    arr = (L.MtkBatchProblem * len(problems))()
+    keep = []
+    for p, (X, dims, U, n, out) in enumerate(problems):
+        dims = [int(d) for d in dims]
+        N = len(dims)
+        if N < 2 or N > L.BATCH_MAXN:
+            raise ValueError(f"batched problems need 2 <= N <= {L.BATCH_MAXN}")
+        C = _rank(U, skip=n)
+        _req(X, torch.float32, "X")
+        _req(out, torch.float32, "out")
+        ptrs = _factor_ptrs(U, dims, C, skip=n)
+        arr[p].X = X.data_ptr()
+        for k in range(N):
+            arr[p].U[k] = ptrs[k]
+            arr[p].dims[k] = dims[k]
+        arr[p].N, arr[p].n, arr[p].C = N, int(n), C
+        arr[p].M = out.data_ptr()
+        keep.append((X, U, out))
+    return arr, keep
+
+
+def mttkrp_batched(problems, *, splits=0, ws=None):
+    """Every problem (X, dims, U, n, out) of the list in one persistent launch
+    (mtk_mttkrp_batched); out is overwritten with the mode-n MTTKRP."""
+    arr, _ = _batch_array(problems)
+    o = _opts("auto", "auto", splits)
+    lib = L.load()
+    need = lib.mtk_mttkrp_batched_workspace(arr, len(problems), L.ctypes.byref(o))
+    if need == 0:
+        raise ValueError("invalid batched MTTKRP problems")
+    dev = problems[0][0].device
+    ws = ws or default_workspace(dev)
+    wp, wb = ws.ptr(need)
+    L.check(lib.mtk_mttkrp_batched(arr, len(problems), wp, wb, L.ctypes.byref(o), _stream(dev)),
+            "mtk_mttkrp_batched")
+
+
+class BatchedMTTKRP:
+    """A fixed batch of MTTKRP problems (X, dims, U, n, out), run as one persistent launch.
+
+    tune(): the autotuner; it times each candidate number of contraction indices per work
+    unit (the k-extent of the tiles) with CUDA events over back-to-back launches and keeps
+    the fastest (cached per batch signature for the process).
+    capture(): records the launch sequence in a CUDA graph; replay() then runs it."""
+
+    _tuned = {}
+    CANDIDATES = (0, 1024, 2048, 4096, 8192, 16384, 32768, 65536)
+
+    def __init__(self, problems, *, splits=0):
+        self.problems = list(problems)
+        self.parts = [self.problems[i:i + L.BATCH_MAXP] for i in range(0, len(self.problems), L.BATCH_MAXP)]
+        self.arrays = [_batch_array(p) for p in self.parts]
+        self.device = self.problems[0][0].device
+        self.splits = int(splits)
+        self.ws = Workspace(self.device)
+        self.graph = None
+        self.sig = tuple((tuple(int(d) for d in dims), int(n), _rank(U, skip=n)) for _, dims, U, n, _ in self.problems)
+
+    def _need(self, splits):
+        lib = L.load()
+        o = _opts("auto", "auto", splits)
+        need = 0
+        for arr, _ in self.arrays:
+            w = lib.mtk_mttkrp_batched_workspace(arr, len(arr), L.ctypes.byref(o))
+            if w == 0:
+                raise ValueError("invalid batched MTTKRP problems")
+            need = max(need, w)
+        return need
+
+    def run(self, splits=None):
+        splits = self.splits if splits is None else int(splits)
+        lib = L.load()
+        o = _opts("auto", "auto", splits)
+        wp, wb = self.ws.ptr(self._need(splits))
+        for arr, _ in self.arrays:
+            L.check(lib.mtk_mttkrp_batched(arr, len(arr), wp, wb, L.ctypes.byref(o), _stream(self.device)),
+                    "mtk_mttkrp_batched")
+
+    def tune(self, reps=5):
+        if self.sig in BatchedMTTKRP._tuned:
+            self.splits = BatchedMTTKRP._tuned[self.sig]
+            return self.splits
+        best, best_t = 0, None
+        for cand in self.CANDIDATES:
+            self.run(cand)
+            self.run(cand)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                self.run(cand)
+            b.record()
+            b.synchronize()
+            t = a.elapsed_time(b) / reps
+            if best_t is None or t < best_t:
+                best, best_t = cand, t
+        self.splits = best
+        BatchedMTTKRP._tuned[self.sig] = best
+        return best
+
+    def capture(self):
+        self.ws.get(self._need(self.splits))
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.run()
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+
 class ALS:
     """CP-ALS driver: holds the workspace, ||X||^2 and the device fit scalar.
     presplit=True splits X into its BF16 planes once (with ||X||^2 in the same pass) and

@@ -555,6 +555,45 @@ int mtk_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N,
                            (cudaStream_t)stream);
 }
 
+static int check_batch(const mtk_batch_problem* probs, int P) {
+    if (!probs || P < 1 || P > MTK_BATCH_MAXP || P > batched_max_problems()) return MTK_EINVAL;
+    for (int p = 0; p < P; ++p) {
+        const mtk_batch_problem& q = probs[p];
+        if (q.N < 2 || q.N > MTK_BATCH_MAXN || q.n < 0 || q.n >= q.N || q.C < 1 || q.C > 32) return MTK_EINVAL;
+        if (!q.X || !q.M || !aligned4(q.X) || !aligned4(q.M)) return MTK_EINVAL;
+        int64_t K = 1;
+        for (int k = 0; k < q.N; ++k) {
+            if (q.dims[k] < 1 || q.dims[k] >= ((int64_t)1 << 31)) return MTK_EINVAL;
+            if (k == q.n) continue;
+            if (!q.U[k] || !aligned4(q.U[k])) return MTK_EINVAL;
+            K *= q.dims[k];
+            if (K >= ((int64_t)1 << 31)) return MTK_EINVAL;
+        }
+    }
+    return MTK_OK;
+}
+
+size_t mtk_mttkrp_batched_workspace(const mtk_batch_problem* probs, int P, const mtk_opts* opts) {
+    if (check_batch(probs, P) != MTK_OK) return 0;
+    const mtk_opts o = defaults(opts);
+    const size_t f = batched_scratch_floats(probs, P, o.splits, 2 * planes_ctas(0));
+    if (f == (size_t)-1) return 0;
+    return align256(kStatusBytes) + align256(f * sizeof(float));
+}
+
+int mtk_mttkrp_batched(const mtk_batch_problem* probs, int P, void* ws, size_t ws_bytes, const mtk_opts* opts,
+                       void* stream) {
+    int st = check_batch(probs, P);
+    if (st) return st;
+    if (!ws) return MTK_EINVAL;
+    const mtk_opts o = defaults(opts);
+    if (ws_bytes < mtk_mttkrp_batched_workspace(probs, P, opts)) return MTK_EWORKSPACE;
+    float* scratch = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(kStatusBytes));
+    if (launch_batched(probs, P, o.splits, 2 * planes_ctas(0), scratch, (cudaStream_t)stream) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
 size_t mtk_partial_mttkrp_workspace(const int64_t* dims, int N, int C, int n, int right,
                                     const mtk_opts* opts) {
     if (check_shape(dims, N, C, n) != MTK_OK) return 0;

@@ -111,6 +111,16 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
                                    const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
                                    void* scratch, uint32_t* status, cudaStream_t s);
 
+// ---- batched MTTKRPs in one persistent launch (batched.cu) --------------------------
+typedef mtk_batch_problem BatchedProblem;
+int batched_max_problems();
+bool batched_plan_item(const int64_t* dims, int N, int n, int C, int64_t kchunk_target, int ctas,
+                       int* ntiles, int* nchunks, int* kchunk, int* CB);
+size_t batched_scratch_floats(const BatchedProblem* probs, int P, int64_t kchunk_target, int ctas);
+// scratch: batched_scratch_floats(...) floats, 256-byte aligned
+cudaError_t launch_batched(const BatchedProblem* probs, int P, int64_t kchunk_target, int ctas, float* scratch,
+                           cudaStream_t s);
+
 cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C, float* K,
                        int reuse, cudaStream_t s);
 cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, const float* Ko,
