@@ -29,6 +29,12 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "Dense MTTKRP TFLOP/s & roofline %, mixed-precision vs FP32 at stated rel err"
+
+# DRAM bytes (read + write) per MTTKRP launch of the planes contraction on the full
+# 200x200x300x40 workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of the
+# 200x200x30x40 case (one launch per mode, mean 203.9 MB), scaled by the 10x larger tensor.
+# Source: profiles/contract_planes_corr4-small_ncu.md (same kernel as this build).
+NCU_TRAFFIC_PER_LAUNCH = {"planes": 2.039e9}
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -45,6 +51,7 @@ def parse():
     ap.add_argument("--algo", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-tensor batched measurement")
     return ap.parse_args()
 
 
@@ -161,6 +168,43 @@ def cpu_baseline(X, dims, U, C, budget_s=12.0):
     flops = N * 2.0 * n_s * C
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {n_s} of {X.size} entries (natural order), all {N} modes, FP64 definition loop, {dt:.1f} s"}
+
+
+def batch_measure(mtk, torch, dev, hbm_peak):
+    """The 64-tensor batch (dims uniform in [64, 384], C in {8, 16, 32}): all 3 modes of
+    every tensor (192 MTTKRPs) as one graph-replayed persistent launch, against the same
+    192 MTTKRPs as sequential per-problem launches of the FP32 path."""
+    batch = synth.batch64()
+    probs = []
+    flops = 0.0
+    nbytes = 0.0
+    for X, dims, U in batch:
+        Xd = torch.from_numpy(X).to(dev)
+        Ud = [torch.from_numpy(u).to(dev) for u in U]
+        C = U[0].shape[1]
+        for n in range(3):
+            probs.append((Xd, dims, Ud, n, torch.empty((dims[n], C), dtype=torch.float32, device=dev)))
+            flops += 2.0 * X.size * C
+            nbytes += 4.0 * X.size + 4.0 * C * (sum(dims) - dims[n]) + 4.0 * dims[n] * C
+    plan = mtk.BatchedMTTKRP(probs)
+    choice = plan.tune()
+    plan.capture()
+    t_batch = time_calls(plan.replay, 10)
+    outs = [p[4].clone() for p in probs]
+
+    def seq():
+        for X, dims, U, n, out in probs:
+            mtk.mttkrp(X, dims, U, n, precision="fp32", out=out)
+    t_seq = time_calls(seq, 3, warm=1)
+    diff = max(float(torch.linalg.norm(a - p[4]) / torch.linalg.norm(p[4])) for a, p in zip(outs, probs))
+    return {"workload": "64 3-way FP32 tensors, dims uniform in [64,384], C in {8,16,32}, N(0,1) (seed 8); "
+                        "all 3 modes (192 MTTKRPs)",
+            "batched_graph_us": t_batch * 1e6, "batched_tflops": flops / t_batch / 1e12,
+            "batched_hbm_frac": nbytes / t_batch / 1e9 / hbm_peak,
+            "sequential_us": t_seq * 1e6, "sequential_tflops": flops / t_seq / 1e12,
+            "speedup": t_seq / t_batch, "autotuned_k_per_unit": choice,
+            "max_rel_diff_vs_sequential": diff, "launches_per_batch": 2,
+            "arith": "FP32 FMA on CUDA cores, FP32 accumulation (both forms)"}
 
 
 def run_reference(args):
@@ -360,6 +404,10 @@ def main():
         e2e = {"value": world * flops_step / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3}
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_measure(mtk, torch, dev, hbm_peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(X, dims, U, C)
@@ -380,7 +428,8 @@ def main():
                                     "(inside every e2e step)") if planes else "not used",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(prec),
+                     "traffic_unit": "bytes per MTTKRP launch (ncu, scaled from the 200x200x30x40 capture)",
                      "kernel": "MTTKRP contraction (mtk_mttkrp per mode, incl. split reduce)",
                      "peak_kind": peak_kind},
         "mttkrp_us_per_mode": [t * 1e6 for t in per_mode],
@@ -391,6 +440,7 @@ def main():
         "gpu_launches": int(launches),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "batch64": batch,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -13,8 +13,9 @@
 // tensor is read with plain coalesced loads.
 //
 // Register blocking: 256 threads, each a 4 x 4 block of (rows, columns); a tile is
-// BI = 4096 / CB rows x CB columns with CB = C rounded up to 8, 16 or 32.  Per k, a
-// thread reads 4 tensor values and 4 KRP values from shared memory for 16 FMAs.
+// BI = 4096 / CB rows x CB columns with CB = C rounded up to 8, 16 or 32, and 16 k-values
+// deep.  Per k, a thread reads 4 tensor values and 4 KRP values from shared memory for 16
+// FMAs; the next tile is loaded into registers while the current one is multiplied.
 #include <string.h>
 
 #include "mtk_internal.cuh"
@@ -22,7 +23,7 @@
 namespace mtk {
 namespace {
 
-constexpr int BT_KT = 16;                 // k per staged tile
+constexpr int BT_KQ = 64;                 // k-chunks of units are multiples of this
 constexpr int BT_THREADS = 256;
 
 struct BItem {
@@ -35,7 +36,7 @@ struct BItem {
     int L, I, R;             // 3-way view
     int C, CB;
     int ntiles, nchunks;
-    int kchunk;              // k per unit (multiple of BT_KT)
+    int kchunk;              // k per unit (multiple of BT_KQ)
     int unit0;               // first unit of this problem
 };
 
@@ -50,64 +51,104 @@ __device__ __forceinline__ int find_item(const BItem* it, int P, int u) {
 }
 
 template <int CB>
-__device__ void run_unit(const BItem& b, int tile, int chunk, float* xs, float* ws) {
+__device__ void run_unit(const BItem& bi, int tile, int chunk, float* xs, float* ws) {
+    constexpr int BT_KT = 16;                // k per staged tile
     constexpr int BI = 4096 / CB;
     constexpr int TR = BI / 4;               // threads along rows
+    constexpr int XPT = BT_KT * BI / BT_THREADS;    // tensor values staged per thread per tile
+    constexpr int WPT = (BT_KT * CB + BT_THREADS - 1) / BT_THREADS;
+    // the problem's fields in registers (the descriptor lives in the parameter space)
+    const float* __restrict__ X = bi.X;
+    const int L = bi.L, I = bi.I, C = bi.C, nf = bi.nf;
+    const float* f0 = bi.f[0];
+    const float* f1 = bi.f[1];
+    const float* f2 = bi.f[2];
+    const uint32_t r0 = (uint32_t)bi.rad[0], r1 = (uint32_t)bi.rad[1];
+    const int nchunks = bi.nchunks;
+    float* part = bi.part;
+    float* outp = bi.out;
     const int t = threadIdx.x;
     const int tr = t % TR, tc = t / TR;      // 4 rows at 4*tr, 4 columns at 4*tc
     const int i0 = tile * BI;
-    const int64_t k0 = (int64_t)chunk * b.kchunk;
-    int64_t k1 = k0 + b.kchunk;
-    const int64_t K = (int64_t)b.L * b.R;
+    const int64_t k0 = (int64_t)chunk * bi.kchunk;
+    int64_t k1 = k0 + bi.kchunk;
+    const int64_t K = (int64_t)L * bi.R;
     if (k1 > K) k1 = K;
-    const int C = b.C;
+    const int64_t LI = (int64_t)L * I;
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
-    const int64_t LI = (int64_t)b.L * b.I;
-    for (int64_t kb = k0; kb < k1; kb += BT_KT) {
-        __syncthreads();
-        // tensor tile: xs[kk][i] = X3(kb + kk, i0 + i)
-        if (b.L == 1) {
-            for (int e = t; e < BT_KT * BI; e += BT_THREADS) {
+
+    // staged values of the next tile (loaded while the current one is multiplied)
+    float xr[XPT], wr[WPT];
+    auto load = [&](int64_t kb) {
+        if (L == 1) {
+#pragma unroll
+            for (int j = 0; j < XPT; ++j) {
+                const int e = t + BT_THREADS * j;
                 const int i = e % BI, kk = e / BI;
                 const int64_t k = kb + kk;
-                float v = 0.0f;
-                if (k < k1 && i0 + i < b.I) v = __ldg(b.X + (i0 + i) + (int64_t)b.I * k);
-                xs[kk * (BI + 4) + i] = v;
+                xr[j] = (k < k1 && i0 + i < I) ? __ldg(X + (i0 + i) + (int64_t)I * k) : 0.0f;
             }
         } else {
             // this thread's k in the tile is fixed (e % BT_KT == t % BT_KT): split it once
             const int kk = t % BT_KT;
             const uint32_t k = (uint32_t)(kb + kk);
-            const uint32_t r = k / (uint32_t)b.L, l = k - r * (uint32_t)b.L;
-            const float* xk = b.X + l + LI * r;
-            const bool kin = (int64_t)k < k1;
-            for (int i = t / BT_KT; i < BI; i += BT_THREADS / BT_KT) {
-                float v = 0.0f;
-                if (kin && i0 + i < b.I) v = __ldg(xk + (int64_t)b.L * (i0 + i));
-                xs[kk * (BI + 4) + i] = v;
+            const uint32_t r = k / (uint32_t)L, l = k - r * (uint32_t)L;
+            const float* xk = X + l + LI * r;
+            const bool kin = (int64_t)(kb + kk) < k1;
+#pragma unroll
+            for (int j = 0; j < XPT; ++j) {
+                const int i = t / BT_KT + (BT_THREADS / BT_KT) * j;
+                xr[j] = (kin && i0 + i < I) ? __ldg(xk + (int64_t)L * (i0 + i)) : 0.0f;
             }
         }
-        // KRP tile: ws[kk][c] = prod_z F_z(digit_z(kb + kk), c)
-        for (int e = t; e < BT_KT * CB; e += BT_THREADS) {
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) {
+            const int e = t + BT_THREADS * j;
             const int c = e % CB, kk = e / CB;
             const int64_t k = kb + kk;
             float w = 0.0f;
-            if (k < k1 && c < C) {
-                w = 1.0f;
-                uint32_t rem = (uint32_t)k;
-                for (int z = 0; z < b.nf; ++z) {
-                    const uint32_t q = rem / (uint32_t)b.rad[z];
-                    w *= __ldg(b.f[z] + (int64_t)(rem - q * (uint32_t)b.rad[z]) * C + c);
-                    rem = q;
+            if (e < BT_KT * CB && k < k1 && c < C) {
+                const uint32_t u = (uint32_t)k;
+                const uint32_t q0 = u / r0;
+                w = __ldg(f0 + (int64_t)(u - q0 * r0) * C + c);
+                if (nf > 1) {
+                    const uint32_t q1 = q0 / r1;
+                    w *= __ldg(f1 + (int64_t)(q0 - q1 * r1) * C + c);
+                    if (nf > 2) w *= __ldg(f2 + (int64_t)q1 * C + c);
                 }
             }
-            ws[kk * CB + c] = w;
+            wr[j] = w;
         }
+    };
+    auto store = [&]() {
+        if (L == 1) {
+#pragma unroll
+            for (int j = 0; j < XPT; ++j) {
+                const int e = t + BT_THREADS * j;
+                xs[(e / BI) * (BI + 4) + (e % BI)] = xr[j];
+            }
+        } else {
+            const int kk = t % BT_KT;
+#pragma unroll
+            for (int j = 0; j < XPT; ++j) xs[kk * (BI + 4) + t / BT_KT + (BT_THREADS / BT_KT) * j] = xr[j];
+        }
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) {
+            const int e = t + BT_THREADS * j;
+            if (e < BT_KT * CB) ws[e] = wr[j];
+        }
+    };
+
+    if (k0 < k1) load(k0);
+    for (int64_t kb = k0; kb < k1; kb += BT_KT) {
         __syncthreads();
+        store();
+        __syncthreads();
+        if (kb + BT_KT < k1) load(kb + BT_KT);
 #pragma unroll
         for (int kk = 0; kk < BT_KT; ++kk) {
             const float4 xv = *reinterpret_cast<const float4*>(xs + kk * (BI + 4) + 4 * tr);
@@ -121,11 +162,11 @@ __device__ void run_unit(const BItem& b, int tile, int chunk, float* xs, float* 
         }
     }
     // write the partial (or the result when the problem has one chunk)
-    float* dst = b.nchunks == 1 ? b.out : b.part + (int64_t)chunk * b.I * C;
+    float* dst = nchunks == 1 ? outp : part + (int64_t)chunk * I * C;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int i = i0 + 4 * tr + a;
-        if (i >= b.I) continue;
+        if (i >= I) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int c = 4 * tc + q;
@@ -142,9 +183,9 @@ struct BatchParams {
 
 template <int MAXP>
 __global__ void __launch_bounds__(BT_THREADS, 2) mttkrp_batched_kernel(const __grid_constant__ BatchParams<MAXP> a) {
-    // xs: BT_KT x (BI + 4) floats (BI <= 512); ws: BT_KT x 32 floats
-    __shared__ __align__(16) float xs[BT_KT * (512 + 4)];
-    __shared__ __align__(16) float ws[BT_KT * 32];
+    // xs: 16 x (BI + 4) floats (BI <= 512); ws: 16 x CB floats
+    __shared__ __align__(16) float xs[16 * (512 + 4)];
+    __shared__ __align__(16) float ws[16 * 32];
     for (int u = blockIdx.x; u < a.nunits; u += gridDim.x) {
         const int p = find_item(a.it, a.P, u);
         const BItem& b = a.it[p];
@@ -201,9 +242,9 @@ bool batched_plan_item(const int64_t* dims, int N, int n, int C, int64_t kchunk_
         if (units < 1) units = 1;
         kc = (K + units - 1) / units;
     }
-    kc = round_up64(kc < 4 * BT_KT ? 4 * BT_KT : kc, BT_KT);
-    if (kc > K) kc = round_up64(K, BT_KT);
-    if (kc > lim) kc = lim / BT_KT * BT_KT;
+    kc = round_up64(kc < BT_KQ ? BT_KQ : kc, BT_KQ);
+    if (kc > K) kc = round_up64(K, BT_KQ);
+    if (kc > lim) kc = lim / BT_KQ * BT_KQ;
     *kchunk = (int)kc;
     *nchunks = (int)((K + kc - 1) / kc);
     return true;
@@ -223,7 +264,7 @@ static int64_t batch_kchunk(const BatchedProblem* probs, int P, int64_t kchunk_t
         work += K * ((q.dims[q.n] + 4096 / CB - 1) / (4096 / CB));
     }
     int64_t kc = work / (4 * (int64_t)(ctas > 0 ? ctas : 1));
-    return kc < 4 * BT_KT ? 4 * BT_KT : kc;
+    return kc < BT_KQ ? BT_KQ : kc;
 }
 
 cudaError_t launch_batched(const BatchedProblem* probs, int P, int64_t kchunk_target, int ctas, float* scratch,
