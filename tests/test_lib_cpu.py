@@ -82,3 +82,47 @@ def test_null_and_misaligned_pointers_rejected_before_launch():
     # solve with n out of range
     G = L.ptr_arr([fake, fake, fake])
     assert lib.mtk_gram_hadamard_solve(G, 3, 2, 3, fake, 4, fake, None, fake, 1 << 20, None) == L.MTK_EINVAL
+
+
+def test_split_and_batched_calls_rejected_before_launch():
+    """The planes entry points and the batched entry point check their arguments on the
+    host (these calls all fail before any launch)."""
+    lib = L.load()
+    fake = 0x10000
+    d = L.dims_arr([64, 48, 40])
+    U = L.ptr_arr([fake, fake, fake])
+    # split: pitch and sizes; null / misaligned planes
+    assert lib.mtk_split_pitch(100) % 64 == 0 and lib.mtk_split_pitch(100) >= 100
+    assert lib.mtk_split_bytes(100) == 4 * lib.mtk_split_pitch(100)
+    assert lib.mtk_split_workspace(0) == 0
+    assert lib.mtk_split_tensor(fake, 100, None, None, fake, 1 << 20, None) == L.MTK_EINVAL
+    assert lib.mtk_split_tensor(fake, 100, fake + 8, None, fake, 1 << 20, None) == L.MTK_EINVAL
+    assert lib.mtk_split_tensor(fake, 100, fake, None, fake, 8, None) == L.MTK_EWORKSPACE
+    # MTTKRP on the planes: options other than AUTO/BF16X2 and AUTO/FUSED are refused
+    for o in (L.opts(precision=L.PREC_FP32), L.opts(precision=L.PREC_BF16X3), L.opts(algo=L.ALGO_TWO_STEP)):
+        assert lib.mtk_mttkrp_split_workspace(d, 3, 8, 0, ctypes.byref(o)) == 0
+        assert lib.mtk_mttkrp_split(fake, fake, d, 3, U, 8, 0, fake, fake, 1 << 20, ctypes.byref(o),
+                                    None) == L.MTK_EINVAL
+    assert lib.mtk_mttkrp_split_workspace(d, 3, 8, 0, None) >= 256
+    assert lib.mtk_mttkrp_split(None, fake, d, 3, U, 8, 0, fake, fake, 1 << 20, None, None) == L.MTK_EINVAL
+    assert lib.mtk_mttkrp_split(fake + 4, fake, d, 3, U, 8, 0, fake, fake, 1 << 20, None, None) == L.MTK_EINVAL
+    assert lib.mtk_mttkrp_split(fake, fake, d, 3, U, 8, 0, fake, fake, 16, None, None) == L.MTK_EWORKSPACE
+    assert lib.mtk_cp_als_sweep_split(None, fake, d, 3, U, 8, None, None, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    # batched: rank, order, count and contraction-length limits
+    def prob(dims, n, C, X=fake, M=fake):
+        p = L.MtkBatchProblem()
+        p.X, p.M, p.N, p.n, p.C = X, M, len(dims), n, C
+        for k, dk in enumerate(dims):
+            p.dims[k] = dk
+            p.U[k] = fake
+        return p
+    arr = (L.MtkBatchProblem * 1)(prob([8, 9, 10], 1, 16))
+    assert lib.mtk_mttkrp_batched_workspace(arr, 1, None) >= 256
+    for bad in (prob([8, 9, 10], 1, 33), prob([8, 9, 10], 3, 8), prob([8, 9], 0, 8, X=None),
+                prob([8, 9, 10], 0, 8, M=fake + 2), prob([1 << 16, 1 << 16, 2], 2, 8)):
+        a1 = (L.MtkBatchProblem * 1)(bad)
+        assert lib.mtk_mttkrp_batched_workspace(a1, 1, None) == 0
+        assert lib.mtk_mttkrp_batched(a1, 1, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    big = (L.MtkBatchProblem * (L.BATCH_MAXP + 1))(*[prob([4, 4, 4], 0, 4) for _ in range(L.BATCH_MAXP + 1)])
+    assert lib.mtk_mttkrp_batched(big, L.BATCH_MAXP + 1, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    assert lib.mtk_mttkrp_batched(arr, 1, fake, 16, None, None) == L.MTK_EWORKSPACE
