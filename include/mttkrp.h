@@ -247,7 +247,13 @@ int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U
 
 /* The same sweep with every MTTKRP on the tensor's BF16 planes (mtk_mttkrp_split).
  * Xs: from mtk_split_tensor.  X: the FP32 tensor or NULL (see mtk_mttkrp_split).  opts
- * as for mtk_mttkrp_split.  ws: mtk_cp_als_workspace(...) bytes (it covers both sweeps). */
+ * as for mtk_mttkrp_split, and algo MTK_ALGO_TWO_STEP selects the dimension tree for
+ * N = 3 or 4 (Section 6 of the paper, reuse of partial MTTKRPs across modes): the partial
+ * contraction over modes >= 2 serves the updates of U_0 and U_1, the one over modes 0 and
+ * 1 (with the updated U_0, U_1) those of U_2 and U_3; each per-mode MTTKRP then follows by
+ * a multi-TTV (Algorithm 4).  The tensor is read twice per sweep instead of N times; the
+ * updates are the same Gauss-Seidel sequence.  Shapes the tree does not take run the
+ * per-mode sweep.  ws: mtk_cp_als_workspace(...) bytes (it covers every form). */
 int mtk_cp_als_sweep_split(const void* Xs, const float* X, const int64_t* dims, int N, float* const* U,
                            int C, const double* normX2, double* fit, void* ws, size_t ws_bytes,
                            const mtk_opts* opts, void* stream);

@@ -393,12 +393,72 @@ int do_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, 
     return MTK_OK;
 }
 
-// the planes hold two BF16 pieces: precision AUTO or BF16X2, the fused algorithm
-int check_split_opts(const mtk_opts* raw) {
+// the planes hold two BF16 pieces: precision AUTO or BF16X2, the fused algorithm (a
+// sweep also takes MTK_ALGO_TWO_STEP: the dimension tree below)
+int check_split_opts(const mtk_opts* raw, bool sweep = false) {
     if (!raw) return MTK_OK;
-    if (raw->algo != MTK_ALGO_AUTO && raw->algo != MTK_ALGO_FUSED) return MTK_EINVAL;
+    if (raw->algo != MTK_ALGO_AUTO && raw->algo != MTK_ALGO_FUSED && !(sweep && raw->algo == MTK_ALGO_TWO_STEP))
+        return MTK_EINVAL;
     if (raw->precision != MTK_PREC_AUTO && raw->precision != MTK_PREC_BF16X2) return MTK_EINVAL;
     return MTK_OK;
+}
+
+// --- dimension tree of a CP-ALS sweep on the planes (N = 3 or 4) ---------------------
+// The modes split into a left pair {0, 1} and the rest.  The right partial
+// T_R(i0, i1, c) = sum over the modes >= 2 of X * prod U_k is shared by the updates of
+// U_0 and U_1 (the factors it uses do not change in between), the left partial
+// T_L(i2, i3, c) = sum over modes 0, 1 by those of U_2 and U_3 (N = 4; for N = 3 the
+// mode-2 MTTKRP is run as it is).  Each partial is one planes contraction on another
+// 3-way view of the same planes; the per-mode MTTKRPs follow from it by multi-TTVs
+// (Section 4.3, Algorithm 4's second step).  The tensor is read twice per sweep.
+bool tree_shape(const int64_t* dims, int N, int C) { return (N == 3 || N == 4) && C <= 64 && dims; }
+
+PlanesPlan tree_plan(const int64_t* dims, int N, int C, int right, const mtk_opts& o) {
+    const int64_t A = dims[0] * dims[1];
+    int64_t B = 1;
+    for (int k = 2; k < N; ++k) B *= dims[k];
+    if (right) return planes_plan(1, A, dims + 2, N - 2, C, 0, planes_ctas(o.splits));
+    return planes_plan(A, B, dims, 2, C, 2, planes_ctas(o.splits));
+}
+
+bool tree_ok(const int64_t* dims, int N, int C, const mtk_opts& o) {
+    if (!tree_shape(dims, N, C)) return false;
+    if (!tree_plan(dims, N, C, 1, o).ok) return false;
+    return N == 3 || tree_plan(dims, N, C, 0, o).ok;
+}
+
+size_t tree_scratch(const int64_t* dims, int N, int C, const mtk_opts& o) {
+    size_t a = planes_scratch_bytes(tree_plan(dims, N, C, 1, o));
+    if (N == 4) {
+        const size_t b = planes_scratch_bytes(tree_plan(dims, N, C, 0, o));
+        if (b > a) a = b;
+    }
+    return align256(align256(kStatusBytes) + a);
+}
+
+// ws: status (unused) then the planes scratch; T: rows x C, C slowest
+int run_tree_partial(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int right, float* T,
+                     void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s) {
+    const PlanesPlan pl = tree_plan(dims, N, C, right, o);
+    if (!pl.ok) return MTK_EUNSUPPORTED;
+    const int64_t A = dims[0] * dims[1];
+    int64_t B = 1;
+    for (int k = 2; k < N; ++k) B *= dims[k];
+    const float* fac[MTK_MAXN];
+    int64_t frad[MTK_MAXN];
+    int nf = 0;
+    for (int k = right ? 2 : 0; k < (right ? N : 2); ++k) {
+        fac[nf] = U[k];
+        frad[nf] = dims[k];
+        ++nf;
+    }
+    Carve cv{static_cast<char*>(ws), kStatusBytes, 0};
+    void* scratch = cv.take(planes_scratch_bytes(pl));
+    cudaError_t e = right ? launch_contract_planes(Xs, split_pitch(A * B), 1, A, B, fac, frad, nf, C, pl, T, 1, A,
+                                                   scratch, status, s)
+                          : launch_contract_planes(Xs, split_pitch(A * B), A, B, 1, fac, frad, nf, C, pl, T, 1, B,
+                                                   scratch, status, s);
+    return e == cudaSuccess ? MTK_OK : MTK_ECUDA;
 }
 
 int check_mttkrp_ptrs(const float* X, const float* const* U, int N, int n, const float* M,
@@ -709,11 +769,12 @@ int mtk_norm2(const float* X, int64_t I, double* out, void* ws, size_t ws_bytes,
 // --- CP-ALS sweep ----------------------------------------------------------------
 namespace {
 struct AlsLayout {
-    size_t mbuf, gbufs, gpart, hbuf, flag, mt, total;
+    size_t mbuf, gbufs, gpart, hbuf, flag, mt, tree, total;
     int maxIn;
 };
 
-// split = 1: the MTTKRPs read the tensor's BF16 planes (mtk_cp_als_sweep_split)
+// split = 1: the MTTKRPs read the tensor's BF16 planes (mtk_cp_als_sweep_split);
+// split = 2: the same with the dimension tree
 AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o, int split) {
     AlsLayout a;
     memset(&a, 0, sizeof(a));
@@ -733,7 +794,13 @@ AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o, int s
     a.gpart = maxChunks > 1 ? (size_t)maxChunks * C * C * sizeof(double) : 0; cv.take(a.gpart);
     a.hbuf = solve_scratch_doubles(C) * sizeof(double); cv.take(a.hbuf);
     a.flag = 256; cv.take(a.flag);
+    if (split == 2) {                                   // dimension tree: partials T_R, T_L
+        const size_t ts = tree_scratch(dims, N, C, o);
+        if (ts > mt) mt = ts;
+        a.tree = (size_t)(dims[0] * dims[1] + (N == 4 ? dims[2] * dims[3] : 0)) * C * sizeof(float);
+    }
     a.mt = mt; cv.take(a.mt);
+    cv.take(a.tree);
     a.total = align256(cv.off);
     return a;
 }
@@ -747,7 +814,13 @@ size_t mtk_cp_als_workspace(const int64_t* dims, int N, int C, const mtk_opts* o
     if (o.algo < 0) return 0;
     const size_t a = als_layout(dims, N, C, o, 0).total;
     size_t b = 0;
-    if (check_split_opts(opts) == MTK_OK) b = als_layout(dims, N, C, o, 1).total;
+    if (check_split_opts(opts, true) == MTK_OK) {
+        b = als_layout(dims, N, C, o, 1).total;
+        if (tree_shape(dims, N, C)) {
+            const size_t t = als_layout(dims, N, C, o, 2).total;
+            if (t > b) b = t;
+        }
+    }
     return a > b ? a : b;
 }
 
@@ -768,9 +841,15 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
     if (fit && !normX2) return MTK_EINVAL;
     mtk_opts o = defaults(opts);
     if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
-    if (Xs && check_split_opts(opts) != MTK_OK) return MTK_EINVAL;
-    const AlsLayout a = als_layout(dims, N, C, o, Xs ? 1 : 0);
+    if (Xs && check_split_opts(opts, true) != MTK_OK) return MTK_EINVAL;
+    const bool tree = Xs && o.algo == MTK_ALGO_TWO_STEP && tree_ok(dims, N, C, o);
+    const AlsLayout a = als_layout(dims, N, C, o, tree ? 2 : (Xs ? 1 : 0));
     if (ws_bytes < a.total) return MTK_EWORKSPACE;
+    const mtk_opts om = [&]() {                         // per-mode MTTKRPs of a split sweep
+        mtk_opts q = o;
+        if (Xs) q.algo = MTK_ALGO_FUSED;
+        return q;
+    }();
     cudaStream_t s = (cudaStream_t)stream;
     Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
     uint32_t* status = static_cast<uint32_t*>(ws);
@@ -786,9 +865,30 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
         if (launch_gram(U[k], dims[k], C, const_cast<double*>(G[k]), gpart, gram_chunks(dims[k]), s) !=
             cudaSuccess)
             return MTK_ECUDA;
+    float* TR = tree ? reinterpret_cast<float*>(cv.take(a.tree)) : nullptr;
+    float* TL = tree && N == 4 ? TR + (size_t)dims[0] * dims[1] * C : nullptr;
     for (int n = 0; n < N; ++n) {
-        int st = Xs ? do_mttkrp_split(Xs, X, dims, N, U, C, n, M, mws, a.mt, status, o, s)
+        int st = MTK_OK;
+        if (tree && n < 2) {
+            // modes 0 and 1 from the right partial (computed once, with U_2.. as they are)
+            if (n == 0) {
+                st = run_tree_partial(Xs, dims, N, U, C, 1, TR, mws, status, om, s);
+                if (!st && launch_multi_ttv(TR, 1, dims[0], dims[1], U[1], C, 0, M, s) != cudaSuccess) st = MTK_ECUDA;
+            } else if (launch_multi_ttv(TR, dims[0], dims[1], 1, U[0], C, 1, M, s) != cudaSuccess) {
+                st = MTK_ECUDA;
+            }
+        } else if (tree && N == 4) {
+            // modes 2 and 3 from the left partial (with the updated U_0, U_1)
+            if (n == 2) {
+                st = run_tree_partial(Xs, dims, N, U, C, 0, TL, mws, status, om, s);
+                if (!st && launch_multi_ttv(TL, 1, dims[2], dims[3], U[3], C, 0, M, s) != cudaSuccess) st = MTK_ECUDA;
+            } else if (launch_multi_ttv(TL, dims[2], dims[3], 1, U[2], C, 1, M, s) != cudaSuccess) {
+                st = MTK_ECUDA;
+            }
+        } else {
+            st = Xs ? do_mttkrp_split(Xs, X, dims, N, U, C, n, M, mws, a.mt, status, om, s)
                     : do_mttkrp(X, dims, N, U, C, n, M, mws, a.mt, status, o, s);
+        }
         if (st) return st;
         if (launch_chol_solve(G, N, C, n, M, dims[n], U[n], Hbuf, flag, status, s) != cudaSuccess)
             return MTK_ECUDA;

@@ -861,6 +861,12 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     } else {
         pl.U = 1;
         pl.MT = two ? 2 : 1;
+        // more tiles than CTAs (a tall view such as a partial MTTKRP): the tile height
+        // with the fewer waves of tile-sized work (a 256-row tile costs two 128-row ones)
+        if (pl.MT == 2) {
+            const int64_t t2w = (I + 2 * PS_M - 1) / (2 * PS_M), t1w = (I + PS_M - 1) / PS_M;
+            if (t2w > ctas && ((t1w + ctas - 1) / ctas) < 2 * ((t2w + ctas - 1) / ctas)) pl.MT = 1;
+        }
         const int cap = PS_M * pl.MT;
         if (mn) {
             pl.BI = cap;

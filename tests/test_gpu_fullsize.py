@@ -111,14 +111,22 @@ def test_corr4_als_sweep(corr):
         Uc[n] = oracle.chol_solve(oracle.cholesky(H), oracle.mttkrp(X64, dims, Uc, n))
     ref_U, ref_fit = oracle.als_sweep(X64, dims, U64)
     del X64
-    for prec in ("bf16x3", "fp32"):
+    for prec in ("bf16x3", "fp32", "planes", "planes-tree"):
         Ud = [torch.from_numpy(u).cuda() for u in U]
-        als = mtk.ALS(Xd, dims, Ud, precision=prec)
+        if prec == "planes":
+            als = mtk.ALS(Xd, dims, Ud, presplit=True)
+        elif prec == "planes-tree":
+            als = mtk.ALS(Xd, dims, Ud, presplit=True, algo="two_step")
+        else:
+            als = mtk.ALS(Xd, dims, Ud, precision=prec)
         als.sweep()
         assert als.status() == 0
         for k in range(4):
             err = rel_fro(Ud[k].cpu().numpy(), ref_U[k])
-            assert err < 1e-5 + 2e-7 * conds[k], (prec, k, err, conds[k])
+            tol = 1e-5 + 2e-7 * conds[k]
+            if prec.startswith("planes"):       # bf16x2 accuracy of the MTTKRP (see test_gpu_split.py)
+                tol = 3e-5 + 1e-6 * conds[k]
+            assert err < tol, (prec, k, err, conds[k])
         assert abs(als.fit.item() - ref_fit) < 1e-5
 
 

@@ -204,3 +204,27 @@ def test_corr4_split_full_M():
         assert err < 1e-5, (n, err)
         tol = bf16x2_bound(X64, dims, U64, n, ref)
         assert err < tol, (n, err, tol)
+
+
+@pytest.mark.parametrize("dims,C", [((24, 16, 20, 8), 8), ((32, 24, 40), 12), ((40, 16, 24, 10), 25)])
+def test_als_sweep_dimension_tree(dims, C):
+    """The dimension-tree sweep (algo two_step on the planes: partials over modes >= 2 and
+    over modes 0, 1 shared by two updates each) against the oracle's Gauss-Seidel sweep,
+    and against the per-mode sweep on the same planes."""
+    X, dims, U = synth.random_case(dims, C, seed=sum(dims) + C, dist="uniform")
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    ref_U, ref_fit = oracle.als_sweep(Xr, dims, Ur)
+    Xd = to_dev(X, torch)
+    Ut = factors_dev(U, torch)
+    tree = mtk.ALS(Xd, dims, Ut, presplit=True, algo="two_step")
+    tree.sweep()
+    assert tree.status() == 0
+    Up = factors_dev(U, torch)
+    per = mtk.ALS(Xd, dims, Up, presplit=True)
+    per.sweep()
+    for k in range(len(dims)):
+        err = rel_fro(Ut[k].double().cpu().numpy(), ref_U[k])
+        assert err < 5e-5, (dims, k, err)
+        assert rel_fro(Ut[k].double().cpu().numpy(), Up[k].double().cpu().numpy()) < 5e-5
+    assert abs(tree.fit.item() - ref_fit) < 1e-5
