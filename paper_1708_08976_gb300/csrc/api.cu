@@ -723,6 +723,9 @@ int mtk_gram(const float* U, int64_t I, int C, double* G, void* ws, size_t ws_by
 
 size_t mtk_solve_workspace(int64_t In, int C) {
     if (In < 1 || C < 1 || C > MTK_MAXC) return 0;
+    if (als_update_supported(C))            // status, tickets, the update's scratch
+        return align256(kStatusBytes) + align256(als_ticket_bytes()) +
+               align256(als_update_scratch_bytes(als_update_ctas(In, nullptr), C));
     const int nch = gram_chunks(In);
     return align256(kStatusBytes) + align256(solve_scratch_doubles(C) * sizeof(double)) + 256 +
            align256((size_t)(nch > 1 ? nch : 0) * C * C * sizeof(double));
@@ -739,6 +742,28 @@ int mtk_gram_hadamard_solve(const double* const* G, int N, int C, int n, const f
     if (ws_bytes < mtk_solve_workspace(In, C)) return MTK_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
+    if (als_update_supported(C)) {
+        unsigned int* tick = reinterpret_cast<unsigned int*>(w + align256(kStatusBytes));
+        void* scratch = w + align256(kStatusBytes) + align256(als_ticket_bytes());
+        AlsUpdateArgs a;
+        memset(&a, 0, sizeof(a));
+        a.G = G;
+        a.N = N;
+        a.C = C;
+        a.n = n;
+        a.M = M;
+        a.In = In;
+        a.Un = Un;
+        a.gmode = Gn ? 2 : 0;
+        a.Gn = Gn;
+        a.scratch = scratch;
+        a.Pmax = als_update_ctas(In, nullptr);
+        a.tickets = tick;
+        a.status = static_cast<uint32_t*>(ws);
+        if (cudaMemsetAsync(tick, 0, als_ticket_bytes(), s) != cudaSuccess || launch_als_update(a, s) != cudaSuccess)
+            return MTK_ECUDA;
+        return MTK_OK;
+    }
     double* Hbuf = reinterpret_cast<double*>(w + align256(kStatusBytes));
     int* flag = reinterpret_cast<int*>(w + align256(kStatusBytes) + align256(solve_scratch_doubles(C) * sizeof(double)));
     if (launch_chol_solve(G, N, C, n, M, In, Un, Hbuf, flag, static_cast<uint32_t*>(ws), s) !=
@@ -769,7 +794,7 @@ int mtk_norm2(const float* X, int64_t I, double* out, void* ws, size_t ws_bytes,
 // --- CP-ALS sweep ----------------------------------------------------------------
 namespace {
 struct AlsLayout {
-    size_t mbuf, gbufs, gpart, hbuf, flag, mt, tree, total;
+    size_t mbuf, gbufs, gpart, hbuf, flag, upd, tick, mt, tree, total;
     int maxIn;
 };
 
@@ -791,9 +816,18 @@ AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o, int s
     Carve cv{nullptr, kStatusBytes, 0};
     a.mbuf = (size_t)maxIn * C * sizeof(float); cv.take(a.mbuf);
     a.gbufs = (size_t)N * C * C * sizeof(double); cv.take(a.gbufs);
-    a.gpart = maxChunks > 1 ? (size_t)maxChunks * C * C * sizeof(double) : 0; cv.take(a.gpart);
+    a.gpart = (maxChunks > 1 && !als_update_supported(C)) ? (size_t)maxChunks * C * C * sizeof(double) : 0;
+    cv.take(a.gpart);
     a.hbuf = solve_scratch_doubles(C) * sizeof(double); cv.take(a.hbuf);
     a.flag = 256; cv.take(a.flag);
+    if (als_update_supported(C)) {                      // one-launch updates and Grams
+        size_t u = gram_all_scratch_bytes(dims, N, C);
+        const size_t b = als_update_scratch_bytes(als_update_max_ctas(dims, N), C);
+        a.upd = u > b ? u : b;
+        a.tick = als_ticket_bytes();
+    }
+    cv.take(a.upd);
+    cv.take(a.tick);
     if (split == 2) {                                   // dimension tree: partials T_R, T_L
         const size_t ts = tree_scratch(dims, N, C, o);
         if (ts > mt) mt = ts;
@@ -858,13 +892,25 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
     double* gpart = static_cast<double*>(cv.take(a.gpart));
     double* Hbuf = static_cast<double*>(cv.take(a.hbuf));
     int* flag = static_cast<int*>(cv.take(a.flag));
+    void* upd = cv.take(a.upd);
+    unsigned int* tick = static_cast<unsigned int*>(cv.take(a.tick));
     char* mws = static_cast<char*>(cv.take(a.mt));
     const double* G[MTK_MAXN];
     for (int k = 0; k < N; ++k) G[k] = Gall + (size_t)k * C * C;
-    for (int k = 0; k < N; ++k)
-        if (launch_gram(U[k], dims[k], C, const_cast<double*>(G[k]), gpart, gram_chunks(dims[k]), s) !=
-            cudaSuccess)
+    const bool fused = als_update_supported(C);
+    if (fused) {
+        // Grams of all factors in one launch; every later update leaves the tickets at zero
+        double* Gw[MTK_MAXN];
+        for (int k = 0; k < N; ++k) Gw[k] = const_cast<double*>(G[k]);
+        if (cudaMemsetAsync(tick, 0, a.tick, s) != cudaSuccess ||
+            launch_gram_all(U, dims, N, C, Gw, upd, tick, s) != cudaSuccess)
             return MTK_ECUDA;
+    } else {
+        for (int k = 0; k < N; ++k)
+            if (launch_gram(U[k], dims[k], C, const_cast<double*>(G[k]), gpart, gram_chunks(dims[k]), s) !=
+                cudaSuccess)
+                return MTK_ECUDA;
+    }
     float* TR = tree ? reinterpret_cast<float*>(cv.take(a.tree)) : nullptr;
     float* TL = tree && N == 4 ? TR + (size_t)dims[0] * dims[1] * C : nullptr;
     for (int n = 0; n < N; ++n) {
@@ -890,13 +936,45 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
                     : do_mttkrp(X, dims, N, U, C, n, M, mws, a.mt, status, o, s);
         }
         if (st) return st;
+        if (fused) {
+            // U_n in one launch that may overlap the kernel before it.  Its Gram leaves as
+            // per-CTA partials that the next mode's update reduces (before it waits for its
+            // M); the last mode forms G_n itself, with the fit.
+            AlsUpdateArgs ua;
+            memset(&ua, 0, sizeof(ua));
+            ua.G = G;
+            ua.N = N;
+            ua.C = C;
+            ua.n = n;
+            ua.M = M;
+            ua.In = dims[n];
+            ua.Un = U[n];
+            const bool last = n == N - 1;
+            ua.gmode = last ? (fit ? 2 : 0) : 1;
+            ua.Gn = const_cast<double*>(G[n]);
+            ua.scratch = upd;
+            ua.Pmax = als_update_max_ctas(dims, N);
+            ua.parity = n & 1;
+            if (n > 0) {
+                ua.prevP = als_update_ctas(dims[n - 1], nullptr);
+                ua.nprev = n - 1;
+                ua.Gprev = const_cast<double*>(G[n - 1]);
+            }
+            ua.tickets = tick;
+            ua.normX2 = normX2;
+            ua.fit = fit;
+            ua.status = status;
+            ua.programmatic = true;
+            if (launch_als_update(ua, s) != cudaSuccess) return MTK_ECUDA;
+            continue;
+        }
         if (launch_chol_solve(G, N, C, n, M, dims[n], U[n], Hbuf, flag, status, s) != cudaSuccess)
             return MTK_ECUDA;
         if (launch_gram(U[n], dims[n], C, const_cast<double*>(G[n]), gpart, gram_chunks(dims[n]), s) !=
             cudaSuccess)
             return MTK_ECUDA;
     }
-    if (fit) {
+    if (fit && !fused) {
         if (launch_residual(normX2, M, U[N - 1], dims[N - 1], G, N, C, nullptr, fit, s) !=
             cudaSuccess)
             return MTK_ECUDA;

@@ -23,11 +23,13 @@
 // or, for I_n <= 64, U runs of the head packed one above the other (each packed run is
 // a separate partial slab).
 //
-// Warp roles (192 threads, one CTA per SM): warp 0 issues the TMA loads, warp 1 owns
-// TMEM and issues the MMAs, warps 2-5 drain the accumulators (one TMEM lane, i.e. one
-// row of M, per thread) and write the partial result.  Every mbarrier wait is bounded
-// (1 s of %globaltimer); on expiry the kernel sets MTK_ETIMEOUT, lets its own copies and
-// MMAs finish (again bounded), frees its TMEM and returns.
+// Warp roles (96 + 128 MT threads, one CTA per SM, MT = 128-row MMA tiles per CTA):
+// warp 0 issues the tensor TMA loads into the A ring, warp 1 owns TMEM and one of its
+// lanes issues the MMAs, warp 2 issues the image slices into the B ring, and 4 warps per
+// MMA tile drain the accumulators (one TMEM lane, i.e. one row of M, per thread) and
+// write the result or a partial slab.  Every mbarrier wait is bounded (1 s of
+// %globaltimer); on expiry the kernel sets MTK_ETIMEOUT, lets its own copies and MMAs
+// finish (again bounded), frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -91,7 +93,8 @@ struct PsParams {
     int64_t tail_rad[MTK_MAXN];
     float* out;
     int64_t out_si, out_sc;
-    float* part;            // [slab][I][C] partials when nslab > 1
+    float* part;            // partial slabs when nslab > 1: [slab][I][C], or [slab][C][I] (part_cm)
+    int part_cm;            // slabs in the output's column-major layout (out_si == 1)
     uint32_t* status;
 };
 
@@ -515,10 +518,17 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 for (int e = 0; e < 16 * NCH; ++e)
                     if (e < C) p.out[i * p.out_si + e * p.out_sc] = acc[e];
             } else {
-                float* dst = p.part + (((int64_t)sp * U + myg) * I + i) * C;
+                float* slab = p.part + ((int64_t)sp * U + myg) * I * C;
+                if (p.part_cm) {
 #pragma unroll
-                for (int e = 0; e < 16 * NCH; ++e)
-                    if (e < C) dst[e] = acc[e];
+                    for (int e = 0; e < 16 * NCH; ++e)
+                        if (e < C) slab[(int64_t)e * I + i] = acc[e];
+                } else {
+                    float* dst = slab + i * C;
+#pragma unroll
+                    for (int e = 0; e < 16 * NCH; ++e)
+                        if (e < C) dst[e] = acc[e];
+                }
             }
         }
         tc_fence_before();
@@ -618,32 +628,74 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
     }
 }
 
-// out(i, c) = sum of the partial slabs of i's tile.  A block takes 32 consecutive outputs
-// and its 8 warps take interleaved slabs (warp w: slabs w, w + 8, ...); the 8 warp sums
-// are added in warp order, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI,
-                                                            int U, int ntiles, int s_full, int s_last,
-                                                            float* __restrict__ out, int64_t si, int64_t sc) {
-    __shared__ float red[8][32];
-    const int64_t n = I * C;
+// out = sum of the partial slabs of each output's tile.  The slabs have the output's
+// layout (row-major [i][c] or column-major [c][i]; both dense), so one flat index f
+// addresses an output and its entry in every slab.  A block of W warps takes 32 Q
+// consecutive outputs, Q per lane (one float4 when Q = 4 and the 4 share their slab count
+// and the buffers allow it); warp w adds slabs w, w + W, ... in order and the W warp sums
+// are added in warp order, so the result does not depend on scheduling.  Many outputs
+// and few slabs (a tall partial MTTKRP): Q = 4, W <= 8; few outputs and many slabs: Q = 1
+// and up to 32 warps, so that enough loads are in flight.
+template <int Q>
+__global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI,
+                                                             int U, int ntiles, int s_full, int s_last,
+                                                             float* __restrict__ out, int colmajor, int vec) {
+    allow_dependent_launch();
+    __shared__ float red[32][32 * Q];
+    const int W = (int)(blockDim.x >> 5);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
-    float v = 0.0f;
-    if (e < n) {
-        const int64_t i = e / C;
+    const int64_t n = I * C;
+    const int64_t f0 = ((int64_t)blockIdx.x * 32 + lane) * Q;
+    auto slabs = [&](int64_t f) {
+        const int64_t i = colmajor ? f % I : f / C;
         const int64_t tile = U > 1 ? 0 : i / BI;
-        const int nsl = (tile < ntiles - 1 ? s_full : s_last) * U;
-        for (int s = w; s < nsl; s += 8) v += part[(int64_t)s * n + e];
-    }
-    red[w][lane] = v;
-    __syncthreads();
-    if (w == 0 && e < n) {
-        float t = red[0][lane];
+        return (tile < ntiles - 1 ? s_full : s_last) * U;
+    };
+    float v[Q];
 #pragma unroll
-        for (int k = 1; k < 8; ++k) t += red[k][lane];
-        const int64_t i = e / C;
-        const int c = (int)(e % C);
-        out[i * si + c * sc] = t;
+    for (int j = 0; j < Q; ++j) v[j] = 0.0f;
+    bool v4 = false;
+    if (f0 < n) {
+        const int ns = slabs(f0);
+        if (Q == 4) v4 = vec && f0 + 3 < n && slabs(f0 + 1) == ns && slabs(f0 + 2) == ns && slabs(f0 + 3) == ns;
+        if (v4) {
+            for (int sl = w; sl < ns; sl += W) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(part + (int64_t)sl * n + f0));
+                v[0] += x.x;
+                v[1 % Q] += x.y;
+                v[2 % Q] += x.z;
+                v[3 % Q] += x.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const int64_t f = f0 + j;
+                if (f < n) {
+                    const int nj = j == 0 ? ns : slabs(f);
+                    float a = 0.0f;
+                    for (int sl = w; sl < nj; sl += W) a += __ldg(part + (int64_t)sl * n + f);
+                    v[j] = a;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) red[w][lane * Q + j] = v[j];
+    __syncthreads();
+    if (w == 0 && f0 < n) {
+        float t[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) t[j] = red[0][lane * Q + j];
+        for (int k = 1; k < W; ++k)
+#pragma unroll
+            for (int j = 0; j < Q; ++j) t[j] += red[k][lane * Q + j];
+        if (v4) {
+            *reinterpret_cast<float4*>(out + f0) = make_float4(t[0], t[1 % Q], t[2 % Q], t[3 % Q]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                if (f0 + j < n) out[f0 + j] = t[j];
+        }
     }
 }
 
@@ -882,7 +934,23 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     int64_t smax = pl.stot / 4;
     if (smax < 1) smax = 1;
     if (T >= ctas) {
-        pl.s_full = pl.s_last = 1;
+        // more tiles than CTAs: T tiles run as ceil(T / ctas) waves of whole-tile CTAs.
+        // Splitting every tile's stages into s slabs makes the last wave's share of the
+        // time smaller; the cost in stage-times is waves(s) * (stot / s + ~4 stages of
+        // pipeline fill per CTA) plus the slab reduce (8 s I C bytes, ~5 MB per stage-time
+        // over the whole GPU)
+        int bs = 1;
+        double bc = 0.0;
+        for (int s = 1; s <= 16 && s <= smax; ++s) {
+            const int64_t waves = ((int64_t)T * s + ctas - 1) / ctas;
+            const double c = (double)waves * ((double)pl.stot / s + 4.0) +
+                             (s > 1 ? 8.0 * s * (double)I * C / 5.0e6 : 0.0);
+            if (s == 1 || c < bc * 0.98) {
+                bc = c;
+                bs = s;
+            }
+        }
+        pl.s_full = pl.s_last = bs;
     } else if (T == 1) {
         pl.s_full = pl.s_last = (int)(ctas < smax ? ctas : smax);
     } else {
@@ -1048,6 +1116,10 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     p.out_si = out_si;
     p.out_sc = out_sc;
     p.part = part;
+    // slabs in the output's layout; the output is row-major (si = C, sc = 1) or
+    // column-major (si = 1, sc = I)
+    if (!((out_si == C && out_sc == 1) || (out_si == 1 && out_sc == I))) return cudaErrorInvalidValue;
+    p.part_cm = (out_si == 1 && C > 1) ? 1 : 0;
     p.status = status;
     const size_t smem = (size_t)p.sa * p.a_stage + (size_t)p.sb * p.b_stage + 1024;
     const int nch = pl.CP / 16;
@@ -1070,9 +1142,17 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     if (e != cudaSuccess) return e;
     if (pl.nslab > 1) {
         const int64_t n = I * C;
-        const int64_t blocks = (n + 31) / 32;
-        planes_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full,
-                                                              pl.s_last, out, out_si, out_sc);
+        const int vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
+                        ((reinterpret_cast<uintptr_t>(part) & 15) == 0);
+        if (n >= 65536) {
+            const int W = pl.nslab < 8 ? pl.nslab : 8;
+            planes_reduce_kernel<4><<<(unsigned)((n + 127) / 128), 32 * W, 0, s>>>(
+                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, vec);
+        } else {
+            const int W = pl.nslab < 32 ? pl.nslab : 32;
+            planes_reduce_kernel<1><<<(unsigned)((n + 31) / 32), 32 * W, 0, s>>>(
+                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, 0);
+        }
         note_launches(1);
         e = cudaGetLastError();
     }

@@ -138,6 +138,47 @@ int norm2_chunks(int64_t I);
 cudaError_t launch_residual(const double* normX2, const float* M, const float* U, int64_t I,
                             const double* const* G, int N, int C, double* r2, double* fit,
                             cudaStream_t s);
+// factor update of a CP-ALS step in one launch (als_update.cu), C <= 64: U_n = M H^{-1}
+// (FP64 L D L^T of H = Hadamard_{k != n} G_k) and the Gram of the new U_n:
+//   gmode 0: none; 1: per-CTA partials only, in buffer `parity` of the scratch, reduced by
+//   the next update (prevP = this launch's CTA count, nprev = n, the other parity), whose
+//   CTA 0 writes G_nprev to Gprev; 2: G_n written to Gn, and the fit when normX2 is given.
+// Tickets (gmode 2): als_ticket_bytes() of zeros, left at zero.  programmatic: launched with
+// programmatic stream serialisation (the factorisation may run while the previous kernel
+// of the stream runs; M is read after that kernel completed).
+struct AlsUpdateArgs {
+    const double* const* G;
+    int N, C, n;
+    const float* M;
+    int64_t In;
+    float* Un;
+    int gmode;
+    double* Gn;
+    void* scratch;
+    int Pmax, parity;
+    int prevP, nprev;
+    double* Gprev;
+    unsigned int* tickets;
+    const double* normX2;
+    double* fit;
+    double* r2;
+    uint32_t* status;
+    bool programmatic;
+};
+bool als_update_supported(int C);
+size_t als_ticket_bytes();
+int als_update_ctas(int64_t In, int64_t* rows);
+int als_update_max_ctas(const int64_t* dims, int N);
+size_t als_update_scratch_bytes(int Pmax, int C);
+cudaError_t launch_als_update(const AlsUpdateArgs& a, cudaStream_t s);
+// G_k = U_k^T U_k for k = 0..N-1 in one launch (C <= 64; same tickets)
+size_t gram_all_scratch_bytes(const int64_t* I, int N, int C);
+cudaError_t launch_gram_all(const float* const* U, const int64_t* I, int N, int C, double* const* G,
+                            void* scratch, unsigned int* tickets, cudaStream_t s);
+// a kernel that the next kernel of its stream may overlap (programmatic dependent launch)
+__device__ __forceinline__ void allow_dependent_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 cudaError_t launch_gradient(const float* U, const float* M, const double* const* G, int N, int C,
                             int n, int64_t In, const float* scale, float* grad, cudaStream_t s);
 

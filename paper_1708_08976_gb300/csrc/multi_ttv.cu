@@ -5,9 +5,11 @@
 //   with coalesced loads, multiplies by the strided column K_L(:,c) (L1-resident) and
 //   reduces with warp shuffles in a fixed tree.
 // left ordering (after L = X_(0:n-1)^T K_L): M(i,c) = sum_r T[i + I*r + I*R*c] * K_R(r,c)
-//   One thread per output entry, consecutive threads on consecutive i (coalesced
-//   column-major reads of T), K_R(r,c) broadcast within a warp; r summed in order.
-// Both orderings are deterministic.  Both are HBM-bound on T.
+//   A block takes 32 consecutive i (one per lane: coalesced column-major reads of T) of
+//   one column c; its 8 warps take r = w, w + 8, ... (K_R(r,c) broadcast within a warp)
+//   and their sums are added in warp order.
+// Both orderings are deterministic.  Both are HBM-bound on T.  Both let the next kernel
+// of the stream start early (its own griddepcontrol.wait still waits for them to finish).
 #include "mtk_internal.cuh"
 
 namespace mtk {
@@ -16,6 +18,7 @@ namespace {
 __global__ void __launch_bounds__(256)
 multi_ttv_right_kernel(const float* __restrict__ T, int64_t L, int64_t I,
                        const float* __restrict__ KL, int C, float* __restrict__ M) {
+    allow_dependent_launch();
     const int lane = threadIdx.x & 31;
     const int64_t nw = I * C;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x / 32);
@@ -35,15 +38,27 @@ multi_ttv_right_kernel(const float* __restrict__ T, int64_t L, int64_t I,
 __global__ void __launch_bounds__(256)
 multi_ttv_left_kernel(const float* __restrict__ T, int64_t I, int64_t R,
                       const float* __restrict__ KR, int C, float* __restrict__ M) {
-    const int64_t n = I * C;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / I);
-        const int64_t i = e % I;
-        const float* t = T + i + I * R * c;
+    allow_dependent_launch();
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nib = (I + 31) / 32;
+    for (int64_t b = blockIdx.x; b < nib * C; b += gridDim.x) {
+        const int c = (int)(b / nib);
+        const int64_t i = (b - (int64_t)c * nib) * 32 + lane;
         float s = 0.0f;
-        for (int64_t r = 0; r < R; ++r) s = fmaf(t[I * r], __ldg(KR + r * C + c), s);
-        M[i * C + c] = s;
+        if (i < I) {
+            const float* t = T + i + I * R * c;
+            for (int64_t r = w; r < R; r += 8) s = fmaf(t[I * r], __ldg(KR + r * C + c), s);
+        }
+        red[w][lane] = s;
+        __syncthreads();
+        if (w == 0 && i < I) {
+            float a = red[0][lane];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) a += red[k][lane];
+            M[i * C + c] = a;
+        }
+        __syncthreads();
     }
 }
 
@@ -58,9 +73,8 @@ cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, co
         multi_ttv_right_kernel<<<grid, 256, 0, s>>>(T, L, I, Ko, C, M);
         note_launches(1);
     } else {
-        const int64_t n = I * C;
-        int64_t blocks = (n + 255) / 256;
-        int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+        const int64_t blocks = (I + 31) / 32 * C;
+        int grid = (int)(blocks < 152 * 8 ? blocks : 152 * 8);
         multi_ttv_left_kernel<<<grid, 256, 0, s>>>(T, I, R, Ko, C, M);
         note_launches(1);
     }
