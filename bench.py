@@ -30,11 +30,14 @@ import synth  # noqa: E402
 
 METRIC = "Dense MTTKRP TFLOP/s & roofline %, mixed-precision vs FP32 at stated rel err"
 
-# DRAM bytes (read + write) per MTTKRP launch of the planes contraction on the full
-# 200x200x300x40 workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of the
-# 200x200x30x40 case (one launch per mode, mean 203.9 MB), scaled by the 10x larger tensor.
-# Source: profiles/contract_planes_corr4-small_ncu.md (same kernel as this build).
-NCU_TRAFFIC_PER_LAUNCH = {"planes": 2.039e9}
+# DRAM bytes (read + write) per launch of the planes contraction on the full
+# 200x200x300x40 workload, from ncu dram__bytes_read.sum + dram__bytes_write.sum on the
+# 200x200x30x40 case: reads scaled by the 10x larger tensor, writes by the output size.
+#   tree: mean of the two partials (n = 1 right: 192.77 MB read + 4.54 MB written;
+#         n = 2 left: 207.00 MB + 0.06 MB) -> 1.9323e9 and 2.0706e9 per full launch;
+#   planes: mean of the four per-mode launches (200.63 MB read, 0.91 MB written).
+# Source: profiles/contract_planes_corr4-small_traffic.md (the kernel of this build).
+NCU_TRAFFIC_PER_LAUNCH = {"planes": 2.0073e9, "tree": 2.0014e9}
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -95,6 +98,25 @@ def time_calls(fn, reps, warm=2, stream=None):
     b.record(stream)
     b.synchronize()
     return a.elapsed_time(b) * 1e-3 / reps
+
+
+def tree_partials(N):
+    """(n, right) of the partial contractions in a dimension-tree sweep of an N-way
+    tensor: modes >= 2 at n = 1 (right), and for N = 4 modes 0, 1 at n = 2 (left)."""
+    return [(1, True), (2, False)] if N == 4 else [(1, True)]
+
+
+def partial_bytes(dims, C, n, right):
+    """Algorithmic bytes of one partial contraction on the planes: the tensor once
+    (4 B per entry over both planes), the factors on the contracted side, the output."""
+    I = 1
+    for d in dims:
+        I *= d
+    side = range(n + 1, len(dims)) if right else range(0, n)
+    rows = I
+    for k in side:
+        rows //= dims[k]
+    return 4.0 * I + 4.0 * C * sum(dims[k] for k in side) + 4.0 * rows * C
 
 
 def dist_env():
@@ -269,6 +291,19 @@ def main():
         prec = "planes" if args.precision == "best" else args.precision
         Xs = mtk.split_tensor(Xd)[0] if prec == "planes" else None
         ts = []
+        if Xs is not None and args.sweep == "tree":
+            # the two partial contractions of the dimension tree (n = 1 right, n = 2 left)
+            for n, right in tree_partials(N):
+                fn = lambda: mtk.partial_mttkrp_split(Xs, dims, U0, n, right)
+                if args.steps > 0:
+                    ts.append((f"{n}{'R' if right else 'L'}", time_calls(fn, args.steps, warm=args.warmup) * 1e6))
+                else:
+                    for _ in range(args.warmup):
+                        fn()
+            torch.cuda.synchronize()
+            print(json.dumps({"kernel_only": True, "workload": desc, "precision": prec, "tree_partials": True,
+                              "us": [[n, round(t, 1)] for n, t in ts]}), flush=True)
+            return 0
         for n in range(N):
             if Xs is not None:
                 fn = lambda: mtk.mttkrp(Xd, dims, U0, n, Xs=Xs)
@@ -380,6 +415,13 @@ def main():
         else:
             fn = lambda: mtk.mttkrp(Xd, dims, U0, n, precision=prec, algo=args.algo, out=out)
         per_mode.append(time_calls(fn, max(args.steps, 5), stream=stream))
+    # with the dimension tree the step's dominant kernel is the partial contraction on
+    # the planes (each call: prep, contraction, slab reduce), timed the same way
+    partials = []
+    if best_form == "tree":
+        for n, right in tree_partials(N):
+            fn = lambda: mtk.partial_mttkrp_split(als.Xs, dims, U0, n, right)
+            partials.append((n, right, time_calls(fn, max(args.steps, 5), stream=stream)))
     clocks = sampler.stop()
 
     t_tensor = torch.tensor([t_step], device=dev)
@@ -428,7 +470,20 @@ def main():
         cpu = cpu_baseline(X, dims, U, C)
 
     bytes_mode = [4.0 * I + 4.0 * C * (sum(dims) - dims[n]) + 4.0 * dims[n] * C for n in range(N)]
-    achieved = sum(bytes_mode) / sum(per_mode) / 1e9
+    tree_rows = []
+    if partials:
+        pbytes = [partial_bytes(dims, C, n, r) for n, r, _ in partials]
+        achieved = sum(pbytes) / sum(t for _, _, t in partials) / 1e9
+        kernel = ("planes partial contraction of the dimension tree (mtk_partial_mttkrp_split at "
+                  + ", ".join(f"n={n} {'right' if r else 'left'}" for n, r, _ in partials)
+                  + "; each call = prep + contraction + slab reduce)")
+        traffic = NCU_TRAFFIC_PER_LAUNCH.get("tree")
+        tree_rows = [{"n": n, "side": "right" if r else "left", "us": t * 1e6, "bytes": b,
+                      "frac": (b / hbm_peak / 1e9) / t} for (n, r, t), b in zip(partials, pbytes)]
+    else:
+        achieved = sum(bytes_mode) / sum(per_mode) / 1e9
+        kernel = "MTTKRP contraction (mtk_mttkrp per mode, incl. split reduce)"
+        traffic = NCU_TRAFFIC_PER_LAUNCH.get(prec)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -447,10 +502,11 @@ def main():
                                     "(inside every e2e step)") if planes else "not used",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(prec),
-                     "traffic_unit": "bytes per MTTKRP launch (ncu, scaled from the 200x200x30x40 capture)",
-                     "kernel": "MTTKRP contraction (mtk_mttkrp per mode, incl. split reduce)",
-                     "peak_kind": peak_kind},
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per launch of the contraction (ncu, scaled from the 200x200x30x40 "
+                                     "capture by the tensor entries)",
+                     "kernel": kernel, "peak_kind": peak_kind},
+        "tree_partials": tree_rows,
         "mttkrp_us_per_mode": [t * 1e6 for t in per_mode],
         "roofline_frac_per_mode": [(b / hbm_peak / 1e9) / t for b, t in zip(bytes_mode, per_mode)],
         "precision_forms": forms,

@@ -206,6 +206,23 @@ int mtk_partial_mttkrp(const float* X, const int64_t* dims, int N, const float* 
                        int n, int right, float* T, void* ws, size_t ws_bytes,
                        const mtk_opts* opts, void* stream);
 
+/* The same partial MTTKRP on the tensor's BF16 planes (Section 4.3, Algorithm 4, first
+ * step; the accuracy of mtk_mttkrp_split).  The partial KRP is not materialised: U is a
+ * host array of N device pointers to the factors (row-major dims[k] x C; only the
+ * factors on the contracted side are read: k > n for right = 1, k < n for right = 0),
+ * and the contraction forms it on chip.  T has the layout of mtk_partial_mttkrp.  This
+ * is the contraction that the dimension tree of mtk_cp_als_sweep_split runs (n = 1
+ * right, n = 2 left).  Requirements: right = 1 needs n < N-1, right = 0 needs n > 0
+ * (else MTK_EINVAL); C <= 64 and the shapes the planes kernel takes (right: I^L I_n a
+ * multiple of 8; left: I^L a multiple of 8), else MTK_EUNSUPPORTED (the workspace query
+ * then returns 0).  Xs: from mtk_split_tensor, 16-byte aligned.  opts: as for
+ * mtk_mttkrp_split.  ws: at least mtk_partial_mttkrp_split_workspace(...) bytes. */
+size_t mtk_partial_mttkrp_split_workspace(const int64_t* dims, int N, int C, int n, int right,
+                                          const mtk_opts* opts);
+int mtk_partial_mttkrp_split(const void* Xs, const int64_t* dims, int N, const float* const* U,
+                             int C, int n, int right, float* T, void* ws, size_t ws_bytes,
+                             const mtk_opts* opts, void* stream);
+
 /* Multi-TTV, the second step.  right = 1: M(i,c) = sum_l T[l + I^L i + I^L I_n c] K_L(l,c);
  * right = 0: M(i,c) = sum_r T[i + I_n r + I_n I^R c] K_R(r,c).  Ko: device, the other
  * partial KRP (K_L for right, K_R for left), row-major.  M: device I_n x C. */

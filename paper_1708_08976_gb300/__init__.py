@@ -6,9 +6,9 @@ The compute lives in ``lib/libmttkrp.so`` (CUDA kernels behind the C ABI of
 """
 from .api import (ALS, ALGOS, BatchedMTTKRP, mttkrp_batched, PRECISIONS, CPLoss, Workspace, cp_gradient, cp_loss, cp_residual,
                   default_workspace, gram, gram_hadamard_solve, khatri_rao, multi_ttv, mttkrp,
-                  norm2, partial_mttkrp, split_tensor)
+                  norm2, partial_mttkrp, partial_mttkrp_split, split_tensor)
 from ._lib import MtkError, load
 
 __all__ = ["ALS", "ALGOS", "BatchedMTTKRP", "mttkrp_batched", "PRECISIONS", "CPLoss", "Workspace", "cp_gradient", "cp_loss",
            "cp_residual", "default_workspace", "gram", "gram_hadamard_solve", "khatri_rao",
-           "multi_ttv", "mttkrp", "norm2", "partial_mttkrp", "split_tensor", "MtkError", "load"]
+           "multi_ttv", "mttkrp", "norm2", "partial_mttkrp", "partial_mttkrp_split", "split_tensor", "MtkError", "load"]

@@ -62,6 +62,8 @@ SIGNATURES = {
     "mtk_mttkrp_batched": (I32, [BATCH_P, I32, P, SZ, OPTS_P, P]),
     "mtk_partial_mttkrp_workspace": (SZ, [P, I32, I32, I32, I32, OPTS_P]),
     "mtk_partial_mttkrp": (I32, [P, P, I32, P, I32, I32, I32, P, P, SZ, OPTS_P, P]),
+    "mtk_partial_mttkrp_split_workspace": (SZ, [P, I32, I32, I32, I32, OPTS_P]),
+    "mtk_partial_mttkrp_split": (I32, [P, P, I32, P, I32, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_multi_ttv": (I32, [P, P, I32, P, I32, I32, I32, P, P]),
     "mtk_gram_workspace": (SZ, [I64, I32]),
     "mtk_gram": (I32, [P, I64, I32, P, P, SZ, P]),

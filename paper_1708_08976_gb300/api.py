@@ -235,6 +235,54 @@ def partial_mttkrp(X, dims, Kp, n, right: bool, *, precision="auto", splits=0, o
     return out
 
 
+def partial_mttkrp_split(Xs, dims, U, n, right: bool, *, splits=0, out=None, ws=None):
+    """First step of Algorithm 4 on the tensor's BF16 planes (mtk_partial_mttkrp_split).
+
+    U is the list of factors (entries on the side that is not contracted may be None);
+    the partial KRP is formed inside the contraction.  Returns T with the layout of
+    partial_mttkrp (flat, C slowest)."""
+    _req(Xs, torch.int16, "Xs")
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    side = range(n + 1, N) if right else range(0, n)
+    if len(side) == 0:
+        raise ValueError("no modes to contract on that side of n")
+    C = _rank([U[k] for k in side])
+    ptrs = [None] * N
+    for k in side:
+        _req(U[k], torch.float32, f"U[{k}]")
+        if tuple(U[k].shape) != (dims[k], C):
+            raise ValueError(f"U[{k}] must be {dims[k]} x {C}")
+        ptrs[k] = U[k].data_ptr()
+    IL = 1
+    for d in dims[:n]:
+        IL *= d
+    IR = 1
+    for d in dims[n + 1:]:
+        IR *= d
+    size = (IL * dims[n] if right else dims[n] * IR) * C
+    if out is None:
+        out = torch.empty(size, dtype=torch.float32, device=Xs.device)
+    _req(out, torch.float32, "out")
+    if out.numel() < size:
+        raise ValueError("out is too small")
+    lib = L.load()
+    if Xs.numel() * 2 < lib.mtk_split_bytes(IL * dims[n] * IR):
+        raise ValueError("Xs is too small for dims")
+    o = _opts("auto", "auto", splits)
+    d = L.dims_arr(dims)
+    r = 1 if right else 0
+    need = lib.mtk_partial_mttkrp_split_workspace(d, N, C, n, r, L.ctypes.byref(o))
+    if need == 0:
+        raise L.MtkError(L.MTK_EUNSUPPORTED, "mtk_partial_mttkrp_split_workspace")
+    ws = ws or default_workspace(Xs.device)
+    wp, wb = ws.ptr(need)
+    L.check(lib.mtk_partial_mttkrp_split(Xs.data_ptr(), d, N, L.ptr_arr(ptrs), C, n, r, out.data_ptr(), wp, wb,
+                                         L.ctypes.byref(o), _stream(Xs.device)),
+            "mtk_partial_mttkrp_split")
+    return out
+
+
 def multi_ttv(T, dims, Ko, n, right: bool, *, out=None):
     """Second step of Algorithm 4."""
     _req(T, torch.float32, "T")

@@ -413,12 +413,21 @@ int check_split_opts(const mtk_opts* raw, bool sweep = false) {
 // (Section 4.3, Algorithm 4's second step).  The tensor is read twice per sweep.
 bool tree_shape(const int64_t* dims, int N, int C) { return (N == 3 || N == 4) && C <= 64 && dims; }
 
+// First step of Algorithm 4 on the planes.  right = 1: the contraction over the modes
+// > n on the 3-way view (1, I^L I_n, I^R), T[l + I^L i + I^L I_n c]; right = 0: over the
+// modes < n on the view (I^L, I_n I^R, 1), T[i + I_n r + I_n I^R c].  The partial KRP
+// is formed on chip from the factors, as in a per-mode MTTKRP.
+bool partial_sides_ok(int N, int n, int right) { return right ? n < N - 1 : n > 0; }
+
+PlanesPlan partial_plan(const int64_t* dims, int N, int C, int n, int right, const mtk_opts& o) {
+    const View v = mode_view(dims, N, n);
+    if (right) return planes_plan(1, v.L * v.I, dims + n + 1, N - n - 1, C, 0, planes_ctas(o.splits));
+    return planes_plan(v.L, v.I * v.R, dims, n, C, n, planes_ctas(o.splits));
+}
+
+// the dimension tree's partials: right = modes >= 2 (n = 1), left = modes 0, 1 (n = 2)
 PlanesPlan tree_plan(const int64_t* dims, int N, int C, int right, const mtk_opts& o) {
-    const int64_t A = dims[0] * dims[1];
-    int64_t B = 1;
-    for (int k = 2; k < N; ++k) B *= dims[k];
-    if (right) return planes_plan(1, A, dims + 2, N - 2, C, 0, planes_ctas(o.splits));
-    return planes_plan(A, B, dims, 2, C, 2, planes_ctas(o.splits));
+    return partial_plan(dims, N, C, right ? 1 : 2, right, o);
 }
 
 bool tree_ok(const int64_t* dims, int N, int C, const mtk_opts& o) {
@@ -437,28 +446,37 @@ size_t tree_scratch(const int64_t* dims, int N, int C, const mtk_opts& o) {
 }
 
 // ws: status (unused) then the planes scratch; T: rows x C, C slowest
-int run_tree_partial(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int right, float* T,
-                     void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s) {
-    const PlanesPlan pl = tree_plan(dims, N, C, right, o);
+int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int n,
+                      int right, float* T, void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s) {
+    const PlanesPlan pl = partial_plan(dims, N, C, n, right, o);
     if (!pl.ok) return MTK_EUNSUPPORTED;
-    const int64_t A = dims[0] * dims[1];
-    int64_t B = 1;
-    for (int k = 2; k < N; ++k) B *= dims[k];
+    const View v = mode_view(dims, N, n);
     const float* fac[MTK_MAXN];
     int64_t frad[MTK_MAXN];
     int nf = 0;
-    for (int k = right ? 2 : 0; k < (right ? N : 2); ++k) {
+    for (int k = right ? n + 1 : 0; k < (right ? N : n); ++k) {
         fac[nf] = U[k];
         frad[nf] = dims[k];
         ++nf;
     }
     Carve cv{static_cast<char*>(ws), kStatusBytes, 0};
     void* scratch = cv.take(planes_scratch_bytes(pl));
-    cudaError_t e = right ? launch_contract_planes(Xs, split_pitch(A * B), 1, A, B, fac, frad, nf, C, pl, T, 1, A,
+    const int64_t rows = right ? v.L * v.I : v.I * v.R;
+    const int64_t pitch = split_pitch(v.L * v.I * v.R);
+    cudaError_t e = right ? launch_contract_planes(Xs, pitch, 1, rows, v.R, fac, frad, nf, C, pl, T, 1, rows,
                                                    scratch, status, s)
-                          : launch_contract_planes(Xs, split_pitch(A * B), A, B, 1, fac, frad, nf, C, pl, T, 1, B,
+                          : launch_contract_planes(Xs, pitch, v.L, rows, 1, fac, frad, nf, C, pl, T, 1, rows,
                                                    scratch, status, s);
     return e == cudaSuccess ? MTK_OK : MTK_ECUDA;
+}
+
+size_t partial_split_bytes(const PlanesPlan& pl) {
+    return align256(align256(kStatusBytes) + planes_scratch_bytes(pl));
+}
+
+int run_tree_partial(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int right, float* T,
+                     void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s) {
+    return run_partial_split(Xs, dims, N, U, C, right ? 1 : 2, right, T, ws, status, o, s);
 }
 
 int check_mttkrp_ptrs(const float* X, const float* const* U, int N, int n, const float* M,
@@ -613,6 +631,32 @@ int mtk_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N,
     mtk_opts o = defaults(opts);
     return do_mttkrp_split(Xs, X, dims, N, U, C, n, M, ws, ws_bytes, static_cast<uint32_t*>(ws), o,
                            (cudaStream_t)stream);
+}
+
+size_t mtk_partial_mttkrp_split_workspace(const int64_t* dims, int N, int C, int n, int right,
+                                          const mtk_opts* opts) {
+    if (check_shape(dims, N, C, n) != MTK_OK || !partial_sides_ok(N, n, right)) return 0;
+    if (check_split_opts(opts) != MTK_OK) return 0;
+    const PlanesPlan pl = partial_plan(dims, N, C, n, right, defaults(opts));
+    return pl.ok ? partial_split_bytes(pl) : 0;
+}
+
+int mtk_partial_mttkrp_split(const void* Xs, const int64_t* dims, int N, const float* const* U, int C,
+                             int n, int right, float* T, void* ws, size_t ws_bytes,
+                             const mtk_opts* opts, void* stream) {
+    int st = check_shape(dims, N, C, n);
+    if (st) return st;
+    if (!partial_sides_ok(N, n, right)) return MTK_EINVAL;
+    if (!Xs || !aligned16(Xs) || !U || !T || !aligned4(T) || !ws) return MTK_EINVAL;
+    for (int k = right ? n + 1 : 0; k < (right ? N : n); ++k)
+        if (!U[k] || !aligned4(U[k])) return MTK_EINVAL;
+    if (check_split_opts(opts) != MTK_OK) return MTK_EINVAL;
+    const mtk_opts o = defaults(opts);
+    const PlanesPlan pl = partial_plan(dims, N, C, n, right, o);
+    if (!pl.ok) return MTK_EUNSUPPORTED;
+    if (ws_bytes < partial_split_bytes(pl)) return MTK_EWORKSPACE;
+    return run_partial_split(Xs, dims, N, U, C, n, right, T, ws, static_cast<uint32_t*>(ws), o,
+                             (cudaStream_t)stream);
 }
 
 static int check_batch(const mtk_batch_problem* probs, int P) {

@@ -228,3 +228,95 @@ def test_als_sweep_dimension_tree(dims, C):
         assert err < 5e-5, (dims, k, err)
         assert rel_fro(Ut[k].double().cpu().numpy(), Up[k].double().cpu().numpy()) < 5e-5
     assert abs(tree.fit.item() - ref_fit) < 1e-5
+
+
+def partial_bound(Xr, dims, Ur, n, right, ref):
+    """The bf16x2 bound of bf16x2_bound, with the partial MTTKRP of the squared inputs
+    in place of the MTTKRP (the same sums, over one side of n only)."""
+    T2 = oracle.partial_mttkrp(Xr * Xr, dims, [u * u for u in Ur], n, right)
+    rho = np.sqrt(max(T2.sum(), 0.0)) / max(np.linalg.norm(ref), 1e-300)
+    return 3.0 * 2.0 ** -16 / np.sqrt(3.0) * rho + 2e-6
+
+
+PARTIAL_SHAPES = [
+    # (dims, C): every (n, side) with a contracted side that the planes kernel takes
+    ((24, 16, 20, 8), 8),         # the 4-way tree shape; I^L = 24 at n = 1 (left), 384 at n = 2
+    ((32, 24, 40), 12),           # 3-way; left at n = 2 is the mode-2 MTTKRP's view
+    ((40, 16, 24, 10), 25),       # C = 25 (two 16-column chunks)
+    ((8, 6, 5, 4, 3), 5),         # N = 5: several factors on each side
+    ((64, 48, 40), 33),           # C = 33 (three chunks); MN view of 64 rows (n = 0, right)
+    ((200, 200, 12, 5), 25),      # tall right view at n = 1: 40000 rows, many CTAs
+    ((5, 24, 40, 8), 8),          # I_0 = 5: n = 0 right and n = 1 left are not taken
+]
+
+
+@pytest.mark.parametrize("dims,C", PARTIAL_SHAPES)
+def test_partial_split_parity(dims, C):
+    """First step of Algorithm 4 on the planes (mtk_partial_mttkrp_split) against the
+    oracle's partial MTTKRP by its element-wise definition, for every mode and both
+    sides that the planes kernel takes; others must report EUNSUPPORTED."""
+    X, dims, U = synth.random_case(dims, C, seed=7 * sum(dims) + C)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    Xd = to_dev(X, torch)
+    Ud = factors_dev(U, torch)
+    Xs, _ = mtk.split_tensor(Xd)
+    N = len(dims)
+    ran = 0
+    for n in range(N):
+        for right in (True, False):
+            if (right and n == N - 1) or (not right and n == 0):
+                continue
+            IL = int(np.prod(dims[:n])) if n else 1
+            takes = (IL * dims[n]) % 8 == 0 if right else IL % 8 == 0
+            if not takes:
+                with pytest.raises(mtk.MtkError) as ei:
+                    mtk.partial_mttkrp_split(Xs, dims, Ud, n, right)
+                assert ei.value.status == L.MTK_EUNSUPPORTED
+                continue
+            got = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right)
+            torch.cuda.synchronize()
+            ref = oracle.partial_mttkrp(Xr, dims, Ur, n, right)
+            err = rel_fro(got.double().cpu().numpy(), ref.reshape(-1))
+            tol = partial_bound(Xr, dims, Ur, n, right, ref)
+            assert err < tol, (dims, C, n, right, err, tol)
+            ran += 1
+    assert ran >= 2
+
+
+def test_partial_split_factors_off_side_unused_and_repeatable():
+    """Only the factors on the contracted side are read (the others may be None), the
+    output is overwritten, and two calls give the same bits (fixed-order reduction)."""
+    X, dims, U = synth.random_case((24, 16, 20, 8), 8, seed=3)
+    Xd = to_dev(X, torch)
+    Ud = factors_dev(U, torch)
+    Xs, _ = mtk.split_tensor(Xd)
+    a = mtk.partial_mttkrp_split(Xs, dims, [None, None, Ud[2], Ud[3]], 1, True)
+    b = torch.full_like(a, float("nan"))
+    mtk.partial_mttkrp_split(Xs, dims, Ud, 1, True, out=b)
+    c = mtk.partial_mttkrp_split(Xs, dims, [Ud[0], Ud[1], None, None], 2, False)
+    d = mtk.partial_mttkrp_split(Xs, dims, Ud, 2, False)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert torch.equal(c, d)
+    assert mtk.default_workspace(Xd.device).status() == 0
+
+
+def test_corr4_tree_partials_full():
+    """The two partials of the dimension tree on the 200x200x300x40 workload in the
+    benchmark's launch configuration (modes >= 2 at n = 1, 40000 x 25; modes 0, 1 at
+    n = 2, 12000 x 25), whole outputs against the FP64 oracle."""
+    X, dims, U = synth.corr4()
+    X64 = X.astype(np.float64)
+    U64 = [u.astype(np.float64) for u in U]
+    Xd = torch.from_numpy(X).cuda()
+    Ud = [torch.from_numpy(u).cuda() for u in U]
+    Xs, _ = mtk.split_tensor(Xd)
+    del Xd
+    for n, right in ((1, True), (2, False)):
+        got = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right).double().cpu().numpy()
+        ref = oracle.partial_mttkrp(X64, dims, U64, n, right).reshape(-1)
+        err = rel_fro(got, ref)
+        assert err < 1e-5, (n, right, err)
+        tol = partial_bound(X64, dims, U64, n, right, ref)
+        assert err < tol, (n, right, err, tol)

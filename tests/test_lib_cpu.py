@@ -126,3 +126,46 @@ def test_split_and_batched_calls_rejected_before_launch():
     big = (L.MtkBatchProblem * (L.BATCH_MAXP + 1))(*[prob([4, 4, 4], 0, 4) for _ in range(L.BATCH_MAXP + 1)])
     assert lib.mtk_mttkrp_batched(big, L.BATCH_MAXP + 1, fake, 1 << 30, None, None) == L.MTK_EINVAL
     assert lib.mtk_mttkrp_batched(arr, 1, fake, 16, None, None) == L.MTK_EWORKSPACE
+
+
+def test_partial_split_rejected_before_launch():
+    """mtk_partial_mttkrp_split checks the side, the pointers, the options and the
+    workspace on the host; shapes the planes kernel does not take return
+    MTK_EUNSUPPORTED.  None of these calls reaches the device."""
+    lib = L.load()
+    fake = 0x10000
+    d = L.dims_arr([16, 24, 40, 8])
+    U = L.ptr_arr([fake, fake, fake, fake])
+    # a contracted side exists: right needs n < N-1, left needs n > 0
+    assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 8, 3, 1, None) == 0
+    assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 8, 0, 0, None) == 0
+    assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 8, 3, 1, fake, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 8, 0, 0, fake, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    for n, right in ((0, 1), (1, 1), (2, 1), (1, 0), (2, 0), (3, 0)):
+        need = lib.mtk_partial_mttkrp_split_workspace(d, 4, 8, n, right, None)
+        assert need >= 512, (n, right)
+        assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 8, n, right, fake, fake, need - 1, None,
+                                            None) == L.MTK_EWORKSPACE
+    # null or misaligned planes, null output, a missing factor on the contracted side
+    assert lib.mtk_partial_mttkrp_split(None, d, 4, U, 8, 1, 1, fake, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    assert lib.mtk_partial_mttkrp_split(fake + 8, d, 4, U, 8, 1, 1, fake, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 8, 1, 1, None, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    U_no3 = L.ptr_arr([fake, fake, fake, None])
+    assert lib.mtk_partial_mttkrp_split(fake, d, 4, U_no3, 8, 1, 1, fake, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    # the factors on the other side are not read (may be NULL)
+    U_left_only = L.ptr_arr([fake, None, None, None])
+    assert lib.mtk_partial_mttkrp_split(fake, d, 4, U_left_only, 8, 1, 0, fake, fake, 16, None,
+                                        None) == L.MTK_EWORKSPACE
+    # options other than AUTO/BF16X2 precision and AUTO/FUSED algorithm
+    for o in (L.opts(precision=L.PREC_FP32), L.opts(algo=L.ALGO_TWO_STEP)):
+        assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 8, 1, 1, ctypes.byref(o)) == 0
+        assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 8, 1, 1, fake, fake, 1 << 30, ctypes.byref(o),
+                                            None) == L.MTK_EINVAL
+    # shapes outside the planes kernel: C > 64; a left view with I^L not a multiple of 8
+    assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 65, 1, 1, None) == 0
+    assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 65, 1, 1, fake, fake, 1 << 30, None,
+                                        None) == L.MTK_EUNSUPPORTED
+    d_odd = L.dims_arr([5, 24, 40, 8])
+    assert lib.mtk_partial_mttkrp_split_workspace(d_odd, 4, 8, 1, 0, None) == 0
+    assert lib.mtk_partial_mttkrp_split(fake, d_odd, 4, U, 8, 1, 0, fake, fake, 1 << 30, None,
+                                        None) == L.MTK_EUNSUPPORTED
