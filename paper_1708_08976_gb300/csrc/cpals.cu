@@ -130,63 +130,6 @@ chol_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __
     }
 }
 
-// H^{-1} for C <= 64 by Gauss-Jordan elimination in place, FP64, one CTA (textbook
-// Gauss-Jordan inversion without pivoting, which is stable for symmetric positive
-// definite matrices).  Its pivots are the squares of the Cholesky diagonal, so H is
-// positive definite iff every pivot is > 0; a pivot <= 0 flags MTK_ENOTPD exactly as the
-// Cholesky factorisation would.  Each of the C steps is one reciprocal and C^2
-// independent updates over 256 threads, so the dependent chain is C steps long (the
-// FP64 pipe of this part is narrow; long serial chains, not flop counts, set the time).
-// Hbuf layout as chol_kernel: Hinv[C*C] at Hbuf + C*C + C.
-__global__ void __launch_bounds__(256)
-inv_gj_kernel(const __grid_constant__ GramList gl, int N, int C, int n, double* __restrict__ Hbuf,
-              int* __restrict__ flag, uint32_t* status) {
-    __shared__ double A[64 * 64];
-    __shared__ double prow[64], pcol[64];
-    __shared__ double rp;
-    __shared__ int bad;
-    const int t = threadIdx.x;
-    for (int e = t; e < C * C; e += blockDim.x) {
-        double h = 1.0;
-        for (int k = 0; k < N; ++k)
-            if (k != n) h *= gl.G[k][e];
-        A[e] = h;
-    }
-    if (t == 0) bad = 0;
-    __syncthreads();
-    for (int p = 0; p < C; ++p) {
-        if (t < C) {
-            prow[t] = A[p * C + t];
-            pcol[t] = A[t * C + p];
-        }
-        if (t == 0) {
-            const double d = A[p * C + p];
-            if (!(d > 0.0)) bad = 1;
-            rp = (d > 0.0) ? 1.0 / d : 0.0;
-        }
-        __syncthreads();
-        if (bad) break;
-        const double r = rp;
-        for (int e = t; e < C * C; e += blockDim.x) {
-            const int i = e / C, k = e - (e / C) * C;
-            double v;
-            if (i == p && k == p) v = r;
-            else if (i == p) v = prow[k] * r;
-            else if (k == p) v = -pcol[i] * r;
-            else v = A[e] - pcol[i] * prow[k] * r;
-            A[e] = v;
-        }
-        __syncthreads();
-    }
-    double* Hinv = Hbuf + (size_t)C * C + C;
-    if (!bad)
-        for (int e = t; e < C * C; e += blockDim.x) Hinv[e] = A[e];
-    if (t == 0) {
-        *flag = bad ? 0 : 1;
-        if (bad) set_status(status, MTK_ENOTPD);
-    }
-}
-
 // U_n(i, b) = sum_a M(i, a) Hinv(a, b), FP64 accumulation, one thread per output entry;
 // nothing is written when H was not positive definite
 __global__ void __launch_bounds__(256)
@@ -339,15 +282,12 @@ cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const
     GramList gl;
     for (int k = 0; k < MTK_MAXN; ++k) gl.G[k] = (k < N) ? G[k] : nullptr;
     const size_t hbytes = (size_t)C * C * sizeof(double);
-    if (C <= 64) {
-        inv_gj_kernel<<<1, 256, 0, s>>>(gl, N, C, n, Hbuf, flag, status);
-    } else {
-        const int chol_smem = hbytes <= 200 * 1024;
-        if (chol_smem) {
-            cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hbytes);
-        }
-        chol_kernel<<<1, 256, chol_smem ? hbytes : 0, s>>>(gl, N, C, n, Hbuf, flag, status, chol_smem);
+    // C <= 64 takes the one-launch update of als_update.cu; this path serves larger ranks
+    const int chol_smem = hbytes <= 200 * 1024;
+    if (chol_smem) {
+        cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hbytes);
     }
+    chol_kernel<<<1, 256, chol_smem ? hbytes : 0, s>>>(gl, N, C, n, Hbuf, flag, status, chol_smem);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
