@@ -32,12 +32,14 @@ METRIC = "Dense MTTKRP TFLOP/s & roofline %, mixed-precision vs FP32 at stated r
 
 # DRAM bytes (read + write) per launch of the planes contraction on the full
 # 200x200x300x40 workload, from ncu dram__bytes_read.sum + dram__bytes_write.sum on the
-# 200x200x30x40 case: reads scaled by the 10x larger tensor, writes by the output size.
-#   tree: mean of the two partials (n = 1 right: 192.77 MB read + 4.54 MB written;
-#         n = 2 left: 207.00 MB + 0.06 MB) -> 1.9323e9 and 2.0706e9 per full launch;
-#   planes: mean of the four per-mode launches (200.63 MB read, 0.91 MB written).
-# Source: profiles/contract_planes_corr4-small_traffic.md (the kernel of this build).
-NCU_TRAFFIC_PER_LAUNCH = {"planes": 2.0073e9, "tree": 2.0014e9}
+# 200x200x30x40 case: reads scaled by the 10x larger tensor; writes are the partial slabs
+# that the full-size plan writes (rows x C x 4 B per unit).
+#   tree: mean of the two partials (n = 1 right: 192.49 MB read, 6 slabs of 4.0 MB
+#         written at full size; n = 2 left: 206.89 MB read, 3.85 MB written) -> 1.9489e9
+#         and 2.0727e9 per full launch.
+#   planes (per-mode MTTKRPs): None, not captured since the last change to the kernel.
+# Source: profiles/contract_planes_corr4-small_traffic.md.
+NCU_TRAFFIC_PER_LAUNCH = {"planes": None, "tree": 2.0108e9}
 L2_BYTES = 129 * 1024 * 1024
 
 

@@ -27,7 +27,10 @@
 // warp 0 issues the tensor TMA loads into the A ring, warp 1 owns TMEM and one of its
 // lanes issues the MMAs, warp 2 issues the image slices into the B ring, and 4 warps per
 // MMA tile drain the accumulators (one TMEM lane, i.e. one row of M, per thread) and
-// write the result or a partial slab.  Every mbarrier wait is bounded (1 s of
+// write the result or a partial slab.  The work is a list of units (a tile of rows and a
+// slab of its stages); a CTA runs one unit, or, when the view has more units than SMs,
+// several back to back, each role carrying its ring slots, phases and accumulator
+// buffers over from one unit to the next.  Every mbarrier wait is bounded (1 s of
 // %globaltimer); on expiry the kernel sets MTK_ETIMEOUT, lets its own copies and MMAs
 // finish (again bounded), frees its TMEM and returns.
 #include <cuda.h>
@@ -98,6 +101,36 @@ struct PsParams {
     uint32_t* status;
 };
 
+// A unit of work: one tile of rows and one slab (a contiguous range of its stages).
+// Units are numbered tile-major: the first ntiles - 1 tiles have s_full slabs each, the
+// last one s_last.  A CTA takes units blockIdx.x, blockIdx.x + gridDim.x, ...; the grid
+// is at most one CTA per SM, so a view with more units than that runs them back to back
+// in each CTA with the rings, barriers and TMEM kept from one unit to the next.
+struct PsUnit {
+    int tile, sp, nst;
+    int64_t t0, i0;
+};
+
+__device__ __forceinline__ int ps_units(const PsParams& p) { return (p.ntiles - 1) * p.s_full + p.s_last; }
+
+__device__ __forceinline__ PsUnit ps_unit(const PsParams& p, int b) {
+    PsUnit u;
+    int S_t;
+    if (b < (p.ntiles - 1) * p.s_full) {
+        u.tile = b / p.s_full;
+        u.sp = b - u.tile * p.s_full;
+        S_t = p.s_full;
+    } else {
+        u.tile = p.ntiles - 1;
+        u.sp = b - (p.ntiles - 1) * p.s_full;
+        S_t = p.s_last;
+    }
+    u.t0 = p.stot * u.sp / S_t;
+    u.nst = (int)(p.stot * (u.sp + 1) / S_t - u.t0);
+    u.i0 = (int64_t)u.tile * p.BI;
+    return u;
+}
+
 template <int NCH, bool MN, int MT>
 __global__ void __launch_bounds__(96 + 128 * MT, 1)
 contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant__ CUtensorMap xmap) {
@@ -114,25 +147,9 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
     const uint32_t dsm_s = smem_u32(dsm);
     const int SA = p.sa, SB = p.sb, NB = p.nbuf;
 
-    // this CTA's tile of rows and its range of stages
-    int tile, sp, S_t;
-    {
-        const int b = (int)blockIdx.x;
-        if (b < (p.ntiles - 1) * p.s_full) {
-            tile = b / p.s_full;
-            sp = b % p.s_full;
-            S_t = p.s_full;
-        } else {
-            tile = p.ntiles - 1;
-            sp = b - (p.ntiles - 1) * p.s_full;
-            S_t = p.s_last;
-        }
-    }
-    const int64_t t0 = p.stot * sp / S_t, t1 = p.stot * (sp + 1) / S_t;
-    const int nst = (int)(t1 - t0);
+    const int nunits = ps_units(p);
     const int64_t I = p.I;
     const int U = p.U, BI = p.BI, spr = p.spr;
-    const int64_t i0 = (int64_t)tile * BI;
     const int64_t nruns = p.nruns;
 
     if (threadIdx.x == 0) {
@@ -165,12 +182,12 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
     if (warp == 0) {
         // ------------------------------------------------------------ tensor (A) producer
         if (lane == 0) {
-            int issued = 0;
+            int issued = 0;                                  // stages issued by this CTA
             bool ok = true;
             // position of the next stage: super-run sr, chunk j of the head (no divisions
             // in the loop); per packed run g present, its (lq, r) coordinates
-            int64_t sr = t0 / spr;
-            int j = (int)(t0 - sr * spr);
+            int64_t sr = 0;
+            int j = 0;
             int ng = 0;
             int glq[16], gr[16];
             auto set_groups = [&]() {
@@ -186,52 +203,58 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     }
                 }
             };
-            set_groups();
-            int nbox = 0;                                    // MN-major, U == 1: 64-row boxes present
-            if (MN && U == 1)
-                while (nbox < 2 * MT && i0 + 64 * nbox < I) ++nbox;
             int slot = 0;
             uint32_t ph = 1;                                 // parity of the empty phase to wait for
-            for (int s = 0; s < nst; ++s) {
-                if (s >= SA && !mbar_wait(smem_u32(&aempty[slot]), ph, &abort_flag, kPsWaitNs)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t st = dsm_s + (uint32_t)(slot * p.a_stage);
-                const uint32_t fb = smem_u32(&afull[slot]);
-                uint32_t bytes;
-                if (MN) bytes = (uint32_t)(2 * (U == 1 ? nbox : ng) * PS_MN_ATOM);
-                else bytes = (uint32_t)(2 * ng * BI * 128);
-                mbar_arrive_expect_tx(fb, bytes);
-                for (int g = 0; g < ng; ++g) {
+            for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
+                const PsUnit w = ps_unit(p, ub);
+                const int64_t i0 = w.i0;
+                sr = w.t0 / spr;
+                j = (int)(w.t0 - sr * spr);
+                set_groups();
+                int nbox = 0;                                    // MN-major, U == 1: 64-row boxes present
+                if (MN && U == 1)
+                    while (nbox < 2 * MT && i0 + 64 * nbox < I) ++nbox;
+                for (int s = 0; s < w.nst; ++s) {
+                    if (issued >= SA && !mbar_wait(smem_u32(&aempty[slot]), ph, &abort_flag, kPsWaitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = dsm_s + (uint32_t)(slot * p.a_stage);
+                    const uint32_t fb = smem_u32(&afull[slot]);
+                    uint32_t bytes;
+                    if (MN) bytes = (uint32_t)(2 * (U == 1 ? nbox : ng) * PS_MN_ATOM);
+                    else bytes = (uint32_t)(2 * ng * BI * 128);
+                    mbar_arrive_expect_tx(fb, bytes);
+                    for (int g = 0; g < ng; ++g) {
 #pragma unroll
-                    for (int pl = 0; pl < 2; ++pl) {
-                        const uint32_t dst = st + (uint32_t)(pl * p.plane_bytes);
-                        if (MN) {
-                            const int q = (int)(sr * U + g);
-                            if (U == 1) {
-                                for (int a = 0; a < nbox; ++a)
-                                    tma_load_4d(dst + (uint32_t)(a * PS_MN_ATOM), &xmap, (int)(i0 + 64 * a), 64 * j, q,
-                                                pl, fb);
+                        for (int pl = 0; pl < 2; ++pl) {
+                            const uint32_t dst = st + (uint32_t)(pl * p.plane_bytes);
+                            if (MN) {
+                                const int q = (int)(sr * U + g);
+                                if (U == 1) {
+                                    for (int a = 0; a < nbox; ++a)
+                                        tma_load_4d(dst + (uint32_t)(a * PS_MN_ATOM), &xmap, (int)(i0 + 64 * a), 64 * j, q,
+                                                    pl, fb);
+                                } else {
+                                    tma_load_4d(dst + (uint32_t)(g * PS_MN_ATOM), &xmap, 0, 64 * j, q, pl, fb);
+                                }
                             } else {
-                                tma_load_4d(dst + (uint32_t)(g * PS_MN_ATOM), &xmap, 0, 64 * j, q, pl, fb);
+                                const uint32_t d = dst + (uint32_t)(g * BI * 128);
+                                if (p.ldims == 5) tma_load_5d(d, &xmap, 64 * j, glq[g], (int)i0, gr[g], pl, fb);
+                                else tma_load_4d(d, &xmap, 64 * j, (int)i0, gr[g], pl, fb);
                             }
-                        } else {
-                            const uint32_t d = dst + (uint32_t)(g * BI * 128);
-                            if (p.ldims == 5) tma_load_5d(d, &xmap, 64 * j, glq[g], (int)i0, gr[g], pl, fb);
-                            else tma_load_4d(d, &xmap, 64 * j, (int)i0, gr[g], pl, fb);
                         }
                     }
-                }
-                ++issued;
-                if (++slot == SA) {
-                    slot = 0;
-                    ph ^= 1u;
-                }
-                if (++j == spr) {
-                    j = 0;
-                    ++sr;
-                    set_groups();
+                    ++issued;
+                    if (++slot == SA) {
+                        slot = 0;
+                        ph ^= 1u;
+                    }
+                    if (++j == spr) {
+                        j = 0;
+                        ++sr;
+                        set_groups();
+                    }
                 }
             }
             if (!ok) {
@@ -249,26 +272,29 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
     } else if (warp == 2) {
         // ------------------------------------------------------------ KRP image (B) producer
         if (lane == 0) {
-            int issued = 0;
+            int issued = 0;                                  // slices issued by this CTA
             bool ok = true;
-            int j = (int)(t0 % spr);
             int slot = 0;
             uint32_t ph = 1;
-            for (int s = 0; s < nst; ++s) {
-                if (s >= SB && !mbar_wait(smem_u32(&bempty[slot]), ph, &abort_flag, kPsWaitNs)) {
-                    ok = false;
-                    break;
+            for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
+                const PsUnit w = ps_unit(p, ub);
+                int j = (int)(w.t0 % spr);
+                for (int s = 0; s < w.nst; ++s) {
+                    if (issued >= SB && !mbar_wait(smem_u32(&bempty[slot]), ph, &abort_flag, kPsWaitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&bfull[slot]);
+                    mbar_arrive_expect_tx(fb, (uint32_t)p.b_bytes);
+                    bulk_copy_g2s(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage),
+                                  p.bimg + (int64_t)j * p.b_bytes, (uint32_t)p.b_bytes, fb);
+                    ++issued;
+                    if (++slot == SB) {
+                        slot = 0;
+                        ph ^= 1u;
+                    }
+                    if (++j == spr) j = 0;
                 }
-                const uint32_t fb = smem_u32(&bfull[slot]);
-                mbar_arrive_expect_tx(fb, (uint32_t)p.b_bytes);
-                bulk_copy_g2s(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage), p.bimg + (int64_t)j * p.b_bytes,
-                              (uint32_t)p.b_bytes, fb);
-                ++issued;
-                if (++slot == SB) {
-                    slot = 0;
-                    ph ^= 1u;
-                }
-                if (++j == spr) j = 0;
             }
             if (!ok) {
                 abort_flag = 1;
@@ -298,80 +324,84 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             // k-steps of the last chunk of a run that hold head rows (the rest is padding)
             const int64_t tail_rows = p.H - (int64_t)PS_BK * (spr - 1);
             const int kk_last = (int)((tail_rows + 15) / 16);
-            int g = 0, gs = 0;
-            int j = (int)(t0 % spr);
+            int g = 0, gs = 0;                               // accumulation groups (all units)
             int sa = 0, sb = 0, bi = 0;
             uint32_t pa = 0, pb = 0, pe = 1;
             uint64_t ad = adesc0, bd = bdesc0;
             bool ok = true;
             uint32_t dcol = tmem;
-            for (int s = 0; s < nst; ++s) {
-                if (!mbar_wait(smem_u32(&afull[sa]), pa, &abort_flag, kPsWaitNs) ||
-                    !mbar_wait(smem_u32(&bfull[sb]), pb, &abort_flag, kPsWaitNs)) {
-                    ok = false;
-                    break;
-                }
-                if (gs == 0) {
-                    if (g >= NB && !mbar_wait(smem_u32(&acce_bar[bi]), pe, &abort_flag, kPsWaitNs)) {
+            for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
+                const PsUnit w = ps_unit(p, ub);
+                const int nst = w.nst;
+                int j = (int)(w.t0 % spr);
+                for (int s = 0; s < nst; ++s) {
+                    if (!mbar_wait(smem_u32(&afull[sa]), pa, &abort_flag, kPsWaitNs) ||
+                        !mbar_wait(smem_u32(&bfull[sb]), pb, &abort_flag, kPsWaitNs)) {
                         ok = false;
                         break;
                     }
-                    dcol = tmem + (uint32_t)(bi * p.acc_cols);
-                }
-                tc_fence_after();
-                const int kk_n = (j == spr - 1) ? kk_last : PS_BK / 16;
-                // hi plane x all three KRP pieces; lo plane x the first two (the dropped
-                // lo * third-piece product is below 2^-24 of |x w|).  One MMA tile: the lo
-                // plane has its own accumulator (columns N .. N + 2 CP).
+                    if (gs == 0) {
+                        if (g >= NB && !mbar_wait(smem_u32(&acce_bar[bi]), pe, &abort_flag, kPsWaitNs)) {
+                            ok = false;
+                            break;
+                        }
+                        dcol = tmem + (uint32_t)(bi * p.acc_cols);
+                    }
+                    tc_fence_after();
+                    const int kk_n = (j == spr - 1) ? kk_last : PS_BK / 16;
+                    // hi plane x all three KRP pieces; lo plane x the first two (the dropped
+                    // lo * third-piece product is below 2^-24 of |x w|).  One MMA tile: the lo
+                    // plane has its own accumulator (columns N .. N + 2 CP).
 #pragma unroll
-                for (int kk = 0; kk < PS_BK / 16; ++kk) {
-                    if (kk < kk_n) {
-                        const uint64_t bk = bd + (uint64_t)(kk * 2);
-                        const uint32_t acc = (kk == 0 && gs == 0) ? 0u : 1u;
-                        if (MT == 1) {
-                            const uint64_t a0 = ad + (uint64_t)(kk * a_k16);
-                            mma_bf16(dcol, a0, bk, idh, acc);
-                            mma_bf16(dcol + ncol, a0 + plane16, bk, idl, acc);
-                        } else {
+                    for (int kk = 0; kk < PS_BK / 16; ++kk) {
+                        if (kk < kk_n) {
+                            const uint64_t bk = bd + (uint64_t)(kk * 2);
+                            const uint32_t acc = (kk == 0 && gs == 0) ? 0u : 1u;
+                            if (MT == 1) {
+                                const uint64_t a0 = ad + (uint64_t)(kk * a_k16);
+                                mma_bf16(dcol, a0, bk, idh, acc);
+                                mma_bf16(dcol + ncol, a0 + plane16, bk, idl, acc);
+                            } else {
 #pragma unroll
-                            for (int mt = 0; mt < MT; ++mt) {
-                                const uint64_t a0 = ad + (uint64_t)(kk * a_k16 + mt * (PS_TILE >> 4));
-                                mma_bf16(dcol + (uint32_t)mt * ncol, a0, bk, idh, acc);
-                            }
+                                for (int mt = 0; mt < MT; ++mt) {
+                                    const uint64_t a0 = ad + (uint64_t)(kk * a_k16 + mt * (PS_TILE >> 4));
+                                    mma_bf16(dcol + (uint32_t)mt * ncol, a0, bk, idh, acc);
+                                }
 #pragma unroll
-                            for (int mt = 0; mt < MT; ++mt) {
-                                const uint64_t a0 = ad + (uint64_t)(kk * a_k16 + mt * (PS_TILE >> 4)) + plane16;
-                                mma_bf16(dcol + (uint32_t)mt * ncol, a0, bk, idl, 1u);
+                                for (int mt = 0; mt < MT; ++mt) {
+                                    const uint64_t a0 = ad + (uint64_t)(kk * a_k16 + mt * (PS_TILE >> 4)) + plane16;
+                                    mma_bf16(dcol + (uint32_t)mt * ncol, a0, bk, idl, 1u);
+                                }
                             }
                         }
                     }
-                }
-                mma_commit(smem_u32(&aempty[sa]));
-                mma_commit(smem_u32(&bempty[sb]));
-                if (++sa == SA) {
-                    sa = 0;
-                    pa ^= 1u;
-                    ad = adesc0;
-                } else {
-                    ad += a_st16;
-                }
-                if (++sb == SB) {
-                    sb = 0;
-                    pb ^= 1u;
-                    bd = bdesc0;
-                } else {
-                    bd += b_st16;
-                }
-                ++gs;
-                const bool run_end = (++j == spr);
-                if (run_end) j = 0;
-                if (gs == PS_GROUP || run_end || s + 1 == nst) {
-                    mma_commit(smem_u32(&accf_bar[bi]));
-                    ++g;
-                    gs = 0;
-                    if (++bi == NB) {                // next round of the buffers: group g
-                        bi = 0;                          // waits for drain #(g / NB - 1)
-                        pe ^= 1u;
+                    mma_commit(smem_u32(&aempty[sa]));
+                    mma_commit(smem_u32(&bempty[sb]));
+                    if (++sa == SA) {
+                        sa = 0;
+                        pa ^= 1u;
+                        ad = adesc0;
+                    } else {
+                        ad += a_st16;
+                    }
+                    if (++sb == SB) {
+                        sb = 0;
+                        pb ^= 1u;
+                        bd = bdesc0;
+                    } else {
+                        bd += b_st16;
+                    }
+                    ++gs;
+                    const bool run_end = (++j == spr);
+                    if (run_end) j = 0;
+                    if (gs == PS_GROUP || run_end || s + 1 == nst) {
+                        mma_commit(smem_u32(&accf_bar[bi]));
+                        ++g;
+                        gs = 0;
+                        if (++bi == NB) {                // next round of the buffers: group g
+                            bi = 0;                          // waits for drain #(g / NB - 1)
+                            pe ^= 1u;
+                        }
                     }
                 }
             }
@@ -393,143 +423,148 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
         const int row = mt * 128 + sub * 32 + lane;  // row of the CTA tile = TMEM lane of tile mt
         const int myg = U > 1 ? row / BI : 0;
         const int myil = U > 1 ? row % BI : row;
-        const int64_t rows_here = (U > 1) ? I : ((I - i0) < BI ? (I - i0) : BI);
-        const bool rowvalid = myg < U && myil < rows_here;
         const int C = p.C, CP = p.CP;
         float acc[16 * NCH], qc[16 * NCH];
-#pragma unroll
-        for (int e = 0; e < 16 * NCH; ++e) {
-            acc[e] = 0.0f;
-            qc[e] = e < C ? 1.0f : 0.0f;
-        }
-        int64_t qcached = -1;
         int g = 0, gs = 0;
         int db = 0;                                          // accumulator buffer of group g
         uint32_t dph = 0;                                    // and the parity of its next fill
-        int64_t sr = t0 / spr;                               // super-run of the next stage
-        int j = (int)(t0 - sr * spr);
         bool ok = true;
-        for (int s = 0; s < nst; ++s) {
-            const int64_t sr_s = sr;
-            ++gs;
-            const bool run_end = (++j == spr);
-            if (run_end) {
-                j = 0;
-                ++sr;
-            }
-            if (!(gs == PS_GROUP || run_end || s + 1 == nst)) continue;
-            gs = 0;
-            const int b = db;
-            const int64_t q = sr_s * U + myg;
-            const bool live = rowvalid && q < nruns;
-            if (live && p.ntail > 0 && q != qcached) {
-                // Q(q, c) = prod_z tail_z(digit_z(q), c): one row of the table, or the
-                // product formed here (digits once, then the columns)
-                if (p.qtab) {
-                    const float4* qr = reinterpret_cast<const float4*>(p.qtab + q * CP);
+        for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
+            const PsUnit w = ps_unit(p, ub);
+            const int64_t i0 = w.i0;
+            const int nst = w.nst;
+            const int64_t rows_here = (U > 1) ? I : ((I - i0) < BI ? (I - i0) : BI);
+            const bool rowvalid = myg < U && myil < rows_here;
 #pragma unroll
-                    for (int e4 = 0; e4 < 4 * NCH; ++e4) {
-                        const float4 v = __ldg(qr + e4);
-                        qc[4 * e4] = v.x;
-                        qc[4 * e4 + 1] = v.y;
-                        qc[4 * e4 + 2] = v.z;
-                        qc[4 * e4 + 3] = v.w;
+            for (int e = 0; e < 16 * NCH; ++e) {
+                acc[e] = 0.0f;
+                qc[e] = e < C ? 1.0f : 0.0f;
+            }
+            int64_t qcached = -1;
+            int64_t sr = w.t0 / spr;                             // super-run of the next stage
+            int j = (int)(w.t0 - sr * spr);
+            for (int s = 0; s < nst; ++s) {
+                const int64_t sr_s = sr;
+                ++gs;
+                const bool run_end = (++j == spr);
+                if (run_end) {
+                    j = 0;
+                    ++sr;
+                }
+                if (!(gs == PS_GROUP || run_end || s + 1 == nst)) continue;
+                gs = 0;
+                const int b = db;
+                const int64_t q = sr_s * U + myg;
+                const bool live = rowvalid && q < nruns;
+                if (live && p.ntail > 0 && q != qcached) {
+                    // Q(q, c) = prod_z tail_z(digit_z(q), c): one row of the table, or the
+                    // product formed here (digits once, then the columns)
+                    if (p.qtab) {
+                        const float4* qr = reinterpret_cast<const float4*>(p.qtab + q * CP);
+#pragma unroll
+                        for (int e4 = 0; e4 < 4 * NCH; ++e4) {
+                            const float4 v = __ldg(qr + e4);
+                            qc[4 * e4] = v.x;
+                            qc[4 * e4 + 1] = v.y;
+                            qc[4 * e4 + 2] = v.z;
+                            qc[4 * e4 + 3] = v.w;
+                        }
+                    } else {
+                        const float* rowp[MTK_MAXN];
+                        int64_t rem = q;
+                        for (int z = 0; z < p.ntail; ++z) {
+                            const int64_t rad = p.tail_rad[z];
+                            const int64_t nq = rem / rad;
+                            rowp[z] = p.tail[z] + (rem - nq * rad) * C;
+                            rem = nq;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 16 * NCH; ++e) qc[e] = e < C ? __ldg(rowp[0] + e) : 0.0f;
+                        for (int z = 1; z < p.ntail; ++z) {
+#pragma unroll
+                            for (int e = 0; e < 16 * NCH; ++e)
+                                if (e < C) qc[e] *= __ldg(rowp[z] + e);
+                        }
+                    }
+                    qcached = q;
+                }
+                if (!mbar_wait(smem_u32(&accf_bar[b]), dph, &abort_flag, kPsWaitNs)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(b * p.acc_cols + mt * p.N);
+                if (MT == 1) {
+                    // hi accumulator (w0, w1, w2 at 0, CP, 2 CP) and lo accumulator (w0, w1 at
+                    // N, N + CP); summed smallest first
+#pragma unroll
+                    for (int m = 0; m < NCH; ++m) {
+                        float h0[16], h1[16], h2[16], l0[16], l1[16];
+                        tmem_ld16(ta + 16 * m, h0);
+                        tmem_ld16(ta + 16 * m + CP, h1);
+                        tmem_ld16(ta + 16 * m + 2 * CP, h2);
+                        tmem_ld16(ta + 16 * m + p.N, l0);
+                        tmem_ld16(ta + 16 * m + p.N + CP, l1);
+                        tmem_ld_wait();
+                        if (live) {
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const int e = 16 * m + jj;
+                                const float v = ((h2[jj] + l1[jj]) + (h1[jj] + l0[jj])) + h0[jj];
+                                acc[e] = fmaf(v, qc[e], acc[e]);
+                            }
+                        }
                     }
                 } else {
-                    const float* rowp[MTK_MAXN];
-                    int64_t rem = q;
-                    for (int z = 0; z < p.ntail; ++z) {
-                        const int64_t rad = p.tail_rad[z];
-                        const int64_t nq = rem / rad;
-                        rowp[z] = p.tail[z] + (rem - nq * rad) * C;
-                        rem = nq;
-                    }
 #pragma unroll
-                    for (int e = 0; e < 16 * NCH; ++e) qc[e] = e < C ? __ldg(rowp[0] + e) : 0.0f;
-                    for (int z = 1; z < p.ntail; ++z) {
+                    for (int m = 0; m < NCH; ++m) {
+                        float v0[16], v1[16], v2[16];
+                        tmem_ld16(ta + 16 * m, v0);
+                        tmem_ld16(ta + 16 * m + CP, v1);
+                        tmem_ld16(ta + 16 * m + 2 * CP, v2);
+                        tmem_ld_wait();
+                        if (live) {
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const int e = 16 * m + jj;
+                                acc[e] = fmaf((v2[jj] + v1[jj]) + v0[jj], qc[e], acc[e]);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
+                ++g;
+                if (++db == NB) {
+                    db = 0;
+                    dph ^= 1u;
+                }
+            }
+            if (ok && rowvalid) {
+                const int64_t i = i0 + myil;
+                if (p.nslab == 1) {
+#pragma unroll
+                    for (int e = 0; e < 16 * NCH; ++e)
+                        if (e < C) p.out[i * p.out_si + e * p.out_sc] = acc[e];
+                } else {
+                    float* slab = p.part + ((int64_t)w.sp * U + myg) * I * C;
+                    if (p.part_cm) {
 #pragma unroll
                         for (int e = 0; e < 16 * NCH; ++e)
-                            if (e < C) qc[e] *= __ldg(rowp[z] + e);
+                            if (e < C) slab[(int64_t)e * I + i] = acc[e];
+                    } else {
+                        float* dst = slab + i * C;
+#pragma unroll
+                        for (int e = 0; e < 16 * NCH; ++e)
+                            if (e < C) dst[e] = acc[e];
                     }
                 }
-                qcached = q;
-            }
-            if (!mbar_wait(smem_u32(&accf_bar[b]), dph, &abort_flag, kPsWaitNs)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(b * p.acc_cols + mt * p.N);
-            if (MT == 1) {
-                // hi accumulator (w0, w1, w2 at 0, CP, 2 CP) and lo accumulator (w0, w1 at
-                // N, N + CP); summed smallest first
-#pragma unroll
-                for (int m = 0; m < NCH; ++m) {
-                    float h0[16], h1[16], h2[16], l0[16], l1[16];
-                    tmem_ld16(ta + 16 * m, h0);
-                    tmem_ld16(ta + 16 * m + CP, h1);
-                    tmem_ld16(ta + 16 * m + 2 * CP, h2);
-                    tmem_ld16(ta + 16 * m + p.N, l0);
-                    tmem_ld16(ta + 16 * m + p.N + CP, l1);
-                    tmem_ld_wait();
-                    if (live) {
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) {
-                            const int e = 16 * m + jj;
-                            const float v = ((h2[jj] + l1[jj]) + (h1[jj] + l0[jj])) + h0[jj];
-                            acc[e] = fmaf(v, qc[e], acc[e]);
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < NCH; ++m) {
-                    float v0[16], v1[16], v2[16];
-                    tmem_ld16(ta + 16 * m, v0);
-                    tmem_ld16(ta + 16 * m + CP, v1);
-                    tmem_ld16(ta + 16 * m + 2 * CP, v2);
-                    tmem_ld_wait();
-                    if (live) {
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) {
-                            const int e = 16 * m + jj;
-                            acc[e] = fmaf((v2[jj] + v1[jj]) + v0[jj], qc[e], acc[e]);
-                        }
-                    }
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
-            ++g;
-            if (++db == NB) {
-                db = 0;
-                dph ^= 1u;
             }
         }
         if (!ok) {
             abort_flag = 1;
             set_status(p.status, MTK_ETIMEOUT);
-        }
-        if (ok && rowvalid) {
-            const int64_t i = i0 + myil;
-            if (p.nslab == 1) {
-#pragma unroll
-                for (int e = 0; e < 16 * NCH; ++e)
-                    if (e < C) p.out[i * p.out_si + e * p.out_sc] = acc[e];
-            } else {
-                float* slab = p.part + ((int64_t)sp * U + myg) * I * C;
-                if (p.part_cm) {
-#pragma unroll
-                    for (int e = 0; e < 16 * NCH; ++e)
-                        if (e < C) slab[(int64_t)e * I + i] = acc[e];
-                } else {
-                    float* dst = slab + i * C;
-#pragma unroll
-                    for (int e = 0; e < 16 * NCH; ++e)
-                        if (e < C) dst[e] = acc[e];
-                }
-            }
         }
         tc_fence_before();
     }
@@ -934,16 +969,16 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     int64_t smax = pl.stot / 4;
     if (smax < 1) smax = 1;
     if (T >= ctas) {
-        // more tiles than CTAs: T tiles run as ceil(T / ctas) waves of whole-tile CTAs.
-        // Splitting every tile's stages into s slabs makes the last wave's share of the
-        // time smaller; the cost in stage-times is waves(s) * (stot / s + ~4 stages of
-        // pipeline fill per CTA) plus the slab reduce (8 s I C bytes, ~5 MB per stage-time
-        // over the whole GPU)
+        // more tiles than CTAs: each of the ctas CTAs runs its units (tile, slab) back to
+        // back, with the rings and TMEM kept live, so a unit costs its stages plus about a
+        // quarter stage of drain.  Splitting every tile's stages into s slabs evens out the
+        // units per CTA; the cost in stage-times is ceil(T s / ctas) * (stot / s + 1/4)
+        // plus the slab reduce (8 s I C bytes, ~5 MB per stage-time over the whole GPU)
         int bs = 1;
         double bc = 0.0;
         for (int s = 1; s <= 16 && s <= smax; ++s) {
             const int64_t waves = ((int64_t)T * s + ctas - 1) / ctas;
-            const double c = (double)waves * ((double)pl.stot / s + 4.0) +
+            const double c = (double)waves * ((double)pl.stot / s + 0.25) +
                              (s > 1 ? 8.0 * s * (double)I * C / 5.0e6 : 0.0);
             if (s == 1 || c < bc * 0.98) {
                 bc = c;
@@ -963,7 +998,8 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
         pl.s_full = (int)sf;
         pl.s_last = (int)sl;
     }
-    pl.grid = (T - 1) * pl.s_full + pl.s_last;
+    pl.grid = (T - 1) * pl.s_full + pl.s_last;          // units; at most ctas CTAs run them
+    if (pl.grid > ctas) pl.grid = ctas;
     pl.nslab = (pl.s_full > pl.s_last ? pl.s_full : pl.s_last) * pl.U;
     pl.image_bytes = (size_t)pl.spr * pl.N * 128;
     // table of tail scales Q(q, c) when it is small

@@ -320,3 +320,25 @@ def test_corr4_tree_partials_full():
         assert err < 1e-5, (n, right, err)
         tol = partial_bound(X64, dims, U64, n, right, ref)
         assert err < tol, (n, right, err, tol)
+
+
+@pytest.mark.parametrize("splits", [1, 5, 7])
+def test_partial_split_units_back_to_back(splits):
+    """Views with more units (tile, slab) than CTAs: each CTA runs several units back to
+    back, with its rings, barrier phases and accumulator buffers carried over.  One CTA,
+    and CTA counts that do not divide the units, on an MN-major view (n = 1, right:
+    3072 rows, 256-row tiles) and a K-major one (n = 2, left: 320 rows)."""
+    X, dims, U = synth.random_case((64, 48, 40, 8), 16, seed=100 + splits)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    Xd = to_dev(X, torch)
+    Ud = factors_dev(U, torch)
+    Xs, _ = mtk.split_tensor(Xd)
+    for n, right in ((1, True), (2, False)):
+        got = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right, splits=splits)
+        ref = oracle.partial_mttkrp(Xr, dims, Ur, n, right)
+        err = rel_fro(got.double().cpu().numpy(), ref.reshape(-1))
+        tol = partial_bound(Xr, dims, Ur, n, right, ref)
+        assert err < tol, (splits, n, right, err, tol)
+        again = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right, splits=splits)
+        assert torch.equal(got, again)

@@ -140,3 +140,18 @@ def test_sweep_update_paths(dims, C):
     als2.sweep()
     for a, b in zip(Ud, Ue):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("dims,C,n", [((150, 120, 90), 80, 1), ((300, 260), 128, 0)])
+def test_solve_rank_above_64(dims, C, n):
+    """Ranks above 64 take the other solve path (FP64 Cholesky and explicit inverse in one
+    CTA, then a wide kernel applies it; the Gram of U_n by the chunked FP64 Gram kernels):
+    the same bounds against the oracle's textbook Cholesky solve."""
+    U, M = make_case(dims, C, n, seed=C + n)
+    Un, Gn, st = run_update(U, M, n)
+    assert st == 0
+    H = oracle.gram_hadamard(dims, [u.astype(np.float64) for u in U], n)
+    ref = oracle.chol_solve(oracle.cholesky(H), M.astype(np.float64))
+    assert rel_fro(Un.cpu().numpy(), ref) < 1e-6
+    ref_g = oracle.gram(Un.cpu().numpy())
+    np.testing.assert_allclose(Gn.cpu().numpy(), ref_g, rtol=1e-12, atol=1e-12 * np.abs(ref_g).max())
