@@ -121,6 +121,23 @@ def partial_bytes(dims, C, n, right):
     return 4.0 * I + 4.0 * C * sum(dims[k] for k in side) + 4.0 * rows * C
 
 
+def max_over_ranks(t, world, device):
+    """The job's time per step: the slowest rank's (an all-reduce MAX over the replicas of
+    the process group; the tensor lives on `device`, a GPU under NCCL, the CPU under gloo)."""
+    if world == 1:
+        return float(t)
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def job_value(flops_step, world, t_max):
+    """Whole-job TFLOP/s: every replica does flops_step per step, the job takes t_max."""
+    return world * flops_step / t_max / 1e12
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -426,11 +443,8 @@ def main():
             partials.append((n, right, time_calls(fn, max(args.steps, 5), stream=stream)))
     clocks = sampler.stop()
 
-    t_tensor = torch.tensor([t_step], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_tensor, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t_tensor.item())
-    value = world * flops_step / t_max / 1e12
+    t_max = max_over_ranks(t_step, world, dev)
+    value = job_value(flops_step, world, t_max)
 
     # e2e: host buffers, H2D of the tensor + factors and D2H of factors + fit inside the region
     e2e = None
