@@ -49,7 +49,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="corr4", choices=["corr4", "cube512", "corr4-small", "corr4-mid"])
+    ap.add_argument("--workload", default="corr4",
+                    choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth"],
+                    help="paper-synth: the paper's equal-dimension tensors (N = 3..6, ~7.3e8 entries, "
+                         "C = 25), every mode's MTTKRP timed and checked on sampled rows; prints its own line")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run every mode's MTTKRP W+K times (for profiler captures)")
     ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | planes | best")
@@ -284,6 +287,54 @@ def run_reference(args):
     return 0
 
 
+def run_paper_synth(args, mtk, torch, dev, hbm_peak):
+    """Every mode's MTTKRP of the paper's equal-dimension tensors (900^3, 165^4, 60^5, 30^6,
+    C = 25): the fused contraction on the BF16 planes where the planes kernel takes the
+    mode, else the FP32-input path at bf16x2 (tensor cores, or CUDA cores for shapes the
+    tensor-core kernel does not take).  Each result is checked against the FP64 oracle on
+    sampled rows; times are CUDA events over back-to-back calls (inputs > L2)."""
+    import oracle
+    from paper_1708_08976_gb300 import _lib as L
+    out = []
+    for N in (3, 4, 5, 6):
+        X, dims, U = synth.paper_equal(N)
+        C = U[0].shape[1]
+        I = X.size
+        U64 = [u.astype(np.float64) for u in U]
+        Xd = torch.from_numpy(X).to(dev)
+        Ud = [torch.from_numpy(u).to(dev) for u in U]
+        Xs, _ = mtk.split_tensor(Xd)
+        M = torch.empty((dims[0], C), dtype=torch.float32, device=dev)
+        g = np.random.default_rng(1000 + N)
+        modes = []
+        for n in range(N):
+            path = "planes"
+            fn = lambda: mtk.mttkrp(None, dims, Ud, n, Xs=Xs, out=M)
+            try:
+                fn()
+            except mtk.MtkError as e:
+                if e.status != L.MTK_EUNSUPPORTED:
+                    raise
+                path = "bf16x2 on the FP32 tensor"
+                fn = lambda: mtk.mttkrp(Xd, dims, Ud, n, precision="bf16x2", out=M)
+            t = time_calls(fn, max(args.steps, 3), warm=max(args.warmup, 1))
+            fn()
+            rows = np.unique(np.concatenate([[0, dims[n] - 1], g.integers(0, dims[n], 2)]))
+            ref = oracle.mttkrp_rows_f32(X, dims, U64, n, rows)
+            got = M[torch.as_tensor(rows, device=dev)].double().cpu().numpy()
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            b = 4.0 * I + 4.0 * C * (sum(dims) - dims[n]) + 4.0 * dims[n] * C
+            modes.append({"n": n, "path": path, "us": t * 1e6, "tflops": 2.0 * I * C / t / 1e12,
+                          "roofline_frac": (b / hbm_peak / 1e9) / t, "rel_err_sampled_rows": err})
+        out.append({"dims": list(dims), "entries": I, "rank": C, "modes": modes})
+        del Xd, Xs, Ud, M
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "paper-synth: equal-dimension tensors of the paper's synthetic sweep, "
+                      "entries uniform[-1,1), factors N(0,1)/sqrt(25)", "hbm_peak_gbs": hbm_peak,
+                      "tensors": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -299,6 +350,8 @@ def main():
     lib = mtk.load()
     hbm_peak, bf16_peak, peak_kind = peaks()
 
+    if args.workload == "paper-synth":
+        return run_paper_synth(args, mtk, torch, dev, hbm_peak)
     X, dims, U, desc = workload(args.workload)
     N = len(dims)
     C = U[0].shape[1]

@@ -169,3 +169,18 @@ def random_case(dims, C, seed, dtype=np.float64, dist="normal"):
         X = g.random(numel(dims))
         U = [g.random((int(d), C)) for d in dims]
     return X.astype(dtype), tuple(int(d) for d in dims), [u.astype(dtype) for u in U]
+
+
+# The paper's synthetic sweep: for N = 3..6 every mode has the same dimension, chosen so
+# that the tensor has about 750 million entries, and the rank is 25.  The entry values are
+# not stated there; these are uniform in [-1, 1) (FP32 draws), the factors N(0, 1) / sqrt(C).
+PAPER_EQUAL_DIMS = {3: 900, 4: 165, 5: 60, 6: 30}
+
+
+def paper_equal(N, C=25, seed=9):
+    dims = (PAPER_EQUAL_DIMS[N],) * N
+    X = rng(seed + N).random(numel(dims), dtype=np.float32)
+    X *= np.float32(2.0)
+    X -= np.float32(1.0)
+    U = normal_factors(dims, C, seed + 10 + N, np.float32, scale=1.0 / np.sqrt(C))
+    return X, dims, U
