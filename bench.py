@@ -3,13 +3,20 @@
 
 Workload (default): the correlation-shaped 4-way FP32 tensor 200x200x300x40
 (regions x regions x time windows x subjects, 480M entries, 1.92 GB), rank
-C = 25.  One step = one CP-ALS sweep through the C ABI (mtk_cp_als_sweep): for
-each of the 4 modes the MTTKRP, the FP64 Gram-Hadamard Cholesky solve and the
-Gram update, then the fit.  Metric = useful MTTKRP flops (4 modes x 2*I*C)
-per second of the whole sweep.
+C = 25.  One step = one CP-ALS sweep through the C ABI: for each of the 4 modes
+the MTTKRP, the FP64 factor update and the Gram of the new factor, then the fit.
+The tensor is split once into its two BF16 planes (timed apart, and inside every
+e2e step); the sweep runs on the planes either with per-mode MTTKRPs or with the
+dimension tree (two partial contractions shared by two modes each), and the
+faster form is reported.  Metric = useful MTTKRP flops (4 modes x 2*I*C) per
+second of the whole sweep.
 
-Prints one JSON line (rank 0).  See the repository's design doc for the
-roofline bookkeeping.
+Roofline: the dominant kernel is timed alone with CUDA events on its launch
+stream (the tree's partial contractions, or the per-mode MTTKRPs); achieved =
+its algorithmic bytes (the tensor once, the factors read, the output written)
+over that time, against the measured HBM copy bandwidth.
+
+Prints one JSON line (rank 0).
 """
 from __future__ import annotations
 
