@@ -1,0 +1,13 @@
+// contract_tc_px2_km.cu -- the tensor-core contraction kernel with 2 BF16 pieces per tensor
+// entry and a K-major tensor operand (modes n > 0), both staging paths, in a translation unit
+// of its own so that the kernel variants compile in parallel.
+#include "contract_tc_kernel.cuh"
+
+namespace mtk {
+
+template cudaError_t tc_launch<2, false, true>(const tcd::TcParams&, const CUtensorMap&, dim3, size_t,
+                                               cudaStream_t);
+template cudaError_t tc_launch<2, false, false>(const tcd::TcParams&, const CUtensorMap&, dim3, size_t,
+                                               cudaStream_t);
+
+}  // namespace mtk
