@@ -57,9 +57,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="corr4",
-                    choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth"],
+                    choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth", "krp"],
                     help="paper-synth: the paper's equal-dimension tensors (N = 3..6, ~7.3e8 entries, "
-                         "C = 25), every mode's MTTKRP timed and checked on sampled rows; prints its own line")
+                         "C = 25), every mode's MTTKRP timed and checked on sampled rows; krp: the "
+                         "Khatri-Rao product with and without reuse (Z = 2..4, ~2e7 rows, C = 25, 50); "
+                         "each prints its own line")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run every mode's MTTKRP W+K times (for profiler captures)")
     ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | planes | best")
@@ -294,6 +296,52 @@ def run_reference(args):
     return 0
 
 
+def run_krp(args, mtk, torch, dev, hbm_peak):
+    """The Khatri-Rao product of Z = 2, 3, 4 equal operands with about 2e7 output rows, at
+    C = 25 and 50, with the reuse of Algorithm 1 and without it (every row from scratch).
+    Both are bound by the HBM write of K: roofline time = (K bytes + operand bytes) over the
+    measured copy bandwidth.  Sampled rows are checked against the oracle's KRP of the
+    same operand rows (exact FP64 products, compared with the FP32 result)."""
+    import oracle
+    out = []
+    for Z in (2, 3, 4):
+        for C in (25, 50):
+            U = synth.krp_case(Z, C)
+            Ud = [torch.from_numpy(u).to(dev) for u in U]
+            J = 1
+            for u in U:
+                J *= u.shape[0]
+            K = torch.empty((J, C), dtype=torch.float32, device=dev)
+            nbytes = 4.0 * J * C + sum(4.0 * u.size for u in U)
+            row = {"Z": Z, "C": C, "rows": J, "bytes": nbytes}
+            g = np.random.default_rng(Z * 100 + C)
+            for reuse in (True, False):
+                fn = lambda: mtk.khatri_rao(Ud, reuse=reuse, out=K)
+                t = time_calls(fn, max(args.steps, 3), warm=max(args.warmup, 1))
+                fn()
+                js = np.unique(np.concatenate([[0, J - 1], g.integers(0, J, 6)]))
+                got = K[torch.as_tensor(js, device=dev)].double().cpu().numpy()
+                err = 0.0
+                for q, j in enumerate(js):
+                    rem, sel = int(j), []
+                    for u in reversed(U):                    # the last operand's index is fastest
+                        sel.append(u[rem % u.shape[0]: rem % u.shape[0] + 1])
+                        rem //= u.shape[0]
+                    ref = oracle.krp(sel[::-1])[0]
+                    err = max(err, float(np.max(np.abs(got[q] - ref) / np.maximum(np.abs(ref), 1e-30))))
+                key = "reuse" if reuse else "naive"
+                row[key] = {"us": t * 1e6, "gbs": nbytes / t / 1e9, "roofline_frac": nbytes / t / 1e9 / hbm_peak,
+                            "max_rel_err_sampled_rows": err}
+            row["reuse_speedup"] = row["naive"]["us"] / row["reuse"]["us"]
+            out.append(row)
+            del Ud, K
+            torch.cuda.empty_cache()
+    print(json.dumps({"workload": "krp: Z equal operands of uniform[0,1) FP32 entries, prod of rows ~2e7, "
+                      "C in {25, 50}; reuse (Algorithm 1) vs every row from scratch", "hbm_peak_gbs": hbm_peak,
+                      "cases": out}), flush=True)
+    return 0
+
+
 def run_paper_synth(args, mtk, torch, dev, hbm_peak):
     """Every mode's MTTKRP of the paper's equal-dimension tensors (900^3, 165^4, 60^5, 30^6,
     C = 25): the fused contraction on the BF16 planes where the planes kernel takes the
@@ -359,6 +407,8 @@ def main():
 
     if args.workload == "paper-synth":
         return run_paper_synth(args, mtk, torch, dev, hbm_peak)
+    if args.workload == "krp":
+        return run_krp(args, mtk, torch, dev, hbm_peak)
     X, dims, U, desc = workload(args.workload)
     N = len(dims)
     C = U[0].shape[1]

@@ -184,3 +184,13 @@ def paper_equal(N, C=25, seed=9):
     X -= np.float32(1.0)
     U = normal_factors(dims, C, seed + 10 + N, np.float32, scale=1.0 / np.sqrt(C))
     return X, dims, U
+
+
+# The paper's KRP experiment: Z = 2, 3 or 4 operands with equal row counts whose product
+# is about 2e7 output rows, C = 25 or 50, entries uniform in [0, 1).
+KRP_ROWS = {2: 4472, 3: 271, 4: 67}
+
+
+def krp_case(Z, C, seed=20):
+    g = rng(seed + 10 * Z + C)
+    return [g.random((KRP_ROWS[Z], C), dtype=np.float32) for _ in range(Z)]
