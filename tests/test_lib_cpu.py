@@ -169,3 +169,46 @@ def test_partial_split_rejected_before_launch():
     assert lib.mtk_partial_mttkrp_split_workspace(d_odd, 4, 8, 1, 0, None) == 0
     assert lib.mtk_partial_mttkrp_split(fake, d_odd, 4, U, 8, 1, 0, fake, fake, 1 << 30, None,
                                         None) == L.MTK_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("dims,C", [((200, 200, 300, 40), 25), ((24, 16, 20, 8), 8), ((32, 24, 40), 12),
+                                    ((40, 16, 24, 10), 25), ((200, 200, 12, 5), 25), ((64, 48, 40, 8), 64)])
+def test_sweep_workspace_covers_tree_partials(dims, C):
+    """The CP-ALS workspace query (every sweep form) is at least what the dimension tree
+    carves: each partial contraction's own workspace plus the partial tensors it keeps,
+    and at least every per-mode planes MTTKRP's workspace (host-side sizes, no launch)."""
+    lib = L.load()
+    N = len(dims)
+    d = L.dims_arr(list(dims))
+    o = L.opts(algo=L.ALGO_TWO_STEP)
+    ws = lib.mtk_cp_als_workspace(d, N, C, ctypes.byref(o))
+    assert ws > 0
+    parts = 4 * dims[0] * dims[1] * C + (4 * dims[2] * dims[3] * C if N == 4 else 0)
+    wr = lib.mtk_partial_mttkrp_split_workspace(d, N, C, 1, 1, None)
+    wl = lib.mtk_partial_mttkrp_split_workspace(d, N, C, 2, 0, None) if N == 4 else 0
+    assert wr > 0 and (N == 3 or wl > 0)
+    assert ws >= max(wr, wl) + parts
+    for n in range(N):
+        assert ws >= lib.mtk_mttkrp_split_workspace(d, N, C, n, None)
+
+
+def test_noalloc_scratch_covers_the_benchmark_shapes():
+    """The fixed scratch of mtk_mttkrp_noalloc (MTK_NOALLOC_SCRATCH_BYTES, 16 MiB) covers
+    the fused and two-step MTTKRPs of the 200x200x300x40 and 60x50x40 workloads in every
+    precision, and the fused ones of 512^3.  The two-step form of 512^3 at mode 1 keeps a
+    512 x 512 x 32 partial tensor (32 MiB): that call is one the fixed scratch refuses."""
+    lib = L.load()
+    limit = 16 << 20
+    for dims, C, algos in (((200, 200, 300, 40), 25, (L.ALGO_FUSED, L.ALGO_TWO_STEP)),
+                           ((60, 50, 40), 8, (L.ALGO_FUSED, L.ALGO_TWO_STEP)),
+                           ((512, 512, 512), 32, (L.ALGO_FUSED,))):
+        d = L.dims_arr(list(dims))
+        for algo in algos:
+            for prec in (L.PREC_FP32, L.PREC_BF16X2, L.PREC_BF16X3):
+                o = L.opts(algo=algo, precision=prec)
+                for n in range(len(dims)):
+                    need = lib.mtk_mttkrp_workspace(d, len(dims), C, n, ctypes.byref(o))
+                    assert 0 < need <= limit, (dims, algo, prec, n, need)
+    d = L.dims_arr([512, 512, 512])
+    o = L.opts(algo=L.ALGO_TWO_STEP, precision=L.PREC_FP32)
+    assert lib.mtk_mttkrp_workspace(d, 3, 32, 1, ctypes.byref(o)) > limit
