@@ -45,7 +45,6 @@ METRIC = "Dense MTTKRP TFLOP/s & roofline %, mixed-precision vs FP32 at stated r
 #         written at full size; n = 2 left: 206.89 MB read, 3.85 MB written) -> 1.9489e9
 #         and 2.0727e9 per full launch.
 #   planes (per-mode MTTKRPs): None, not captured since the last change to the kernel.
-# Source: profiles/contract_planes_corr4-small_traffic.md.
 NCU_TRAFFIC_PER_LAUNCH = {"planes": None, "tree": 2.0108e9}
 L2_BYTES = 129 * 1024 * 1024
 

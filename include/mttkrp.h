@@ -72,7 +72,15 @@ typedef struct {
     int algo;          /* MTK_ALGO_* */
     int precision;     /* MTK_PREC_* */
     int splits;        /* contraction splits across CTAs; 0 = automatic */
-    int reserved[5];   /* set to 0 */
+    int wait_us;       /* limit of each device-side wait of the tensor-core contraction
+                          kernels, in microseconds; 0 = 1 second.  A wait that runs out
+                          sets MTK_ETIMEOUT in the status word; the kernel then lets the
+                          copies and MMAs it has started finish and returns. */
+    int test_stall;    /* 0 in normal use.  1 (a test of the timeout path): the tensor-core
+                          contraction kernel first waits on a barrier that nothing
+                          completes, so that this wait runs out after wait_us and the call
+                          reports MTK_ETIMEOUT (the output is not valid then). */
+    int reserved[3];   /* set to 0 */
 } mtk_opts;            /* NULL = all defaults */
 
 /* status helpers --------------------------------------------------------- */
@@ -120,7 +128,9 @@ int mtk_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U
  * MTK_NOALLOC_SCRATCH_BYTES bytes inside the library; no cudaMalloc, cudaFree
  * or allocating library routine is called.
  *  - The first call on a device (the current device) looks up that device's
- *    copy of the array; make that first call before any stream capture.
+ *    copy of the array; make that first call before any stream capture.  The
+ *    lookup is repeated when the device's context has changed since (after
+ *    cudaDeviceReset the module, and so the array, is loaded again).
  *  - Every call on a device shares the one array, which keeps the previous
  *    call's contents (the status word is cleared at the start of each call).
  *    Calls whose work overlaps on the GPU (other streams, other host threads)
@@ -284,6 +294,12 @@ int mtk_cp_als_sweep_split(const void* Xs, const float* X, const int64_t* dims, 
  * fit = 1 - sqrt(max(0, r2)) / ||X||. */
 int mtk_cp_residual(const double* normX2, const float* M, const float* Um, int64_t Im,
                     const double* const* G, int N, int C, double* r2, double* fit, void* stream);
+
+/* The CP least-squares loss f = 0.5 ||X - [[U_0..U_{N-1}]]||^2 (Section 2.2's model),
+ * from the same identity as mtk_cp_residual: f = 0.5 r2.  loss: device float (the FP64
+ * value rounded once).  Other arguments as for mtk_cp_residual. */
+int mtk_cp_loss(const double* normX2, const float* M, const float* Um, int64_t Im,
+                const double* const* G, int N, int C, float* loss, void* stream);
 
 /* Gradient of f = 0.5 ||X - [[U]]||^2 with respect to U_n (MTTKRP is part of the
  * gradient, Section 2.2):  grad = scale * (U_n H_n - M_n), H_n = Hadamard_{k != n} G_k.

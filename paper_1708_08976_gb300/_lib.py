@@ -24,7 +24,8 @@ PREC_AUTO, PREC_FP32, PREC_BF16X2, PREC_BF16X3 = 0, 1, 2, 3
 
 
 class MtkOpts(ctypes.Structure):
-    _fields_ = [("algo", I32), ("precision", I32), ("splits", I32), ("reserved", I32 * 5)]
+    _fields_ = [("algo", I32), ("precision", I32), ("splits", I32), ("wait_us", I32), ("test_stall", I32),
+                ("reserved", I32 * 3)]
 
 
 OPTS_P = ctypes.POINTER(MtkOpts)
@@ -75,6 +76,7 @@ SIGNATURES = {
     "mtk_cp_als_sweep": (I32, [P, P, I32, P, I32, P, P, P, SZ, OPTS_P, P]),
     "mtk_cp_als_sweep_split": (I32, [P, P, P, I32, P, I32, P, P, P, SZ, OPTS_P, P]),
     "mtk_cp_residual": (I32, [P, P, P, I64, P, I32, I32, P, P, P]),
+    "mtk_cp_loss": (I32, [P, P, P, I64, P, I32, I32, P, P]),
     "mtk_cp_gradient": (I32, [P, P, P, I32, I32, I32, I64, P, P, P]),
 }
 
@@ -116,11 +118,13 @@ def check(st: int, what: str) -> None:
         raise MtkError(st, what)
 
 
-def opts(algo=ALGO_AUTO, precision=PREC_AUTO, splits=0):
+def opts(algo=ALGO_AUTO, precision=PREC_AUTO, splits=0, wait_us=0, test_stall=0):
     o = MtkOpts()
     o.algo = int(algo)
     o.precision = int(precision)
     o.splits = int(splits)
+    o.wait_us = int(wait_us)
+    o.test_stall = int(test_stall)
     return o
 
 

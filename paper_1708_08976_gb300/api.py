@@ -358,6 +358,18 @@ def cp_residual(normX2, M, Um, G, *, r2=None, fit=None):
     return r2, fit
 
 
+def cp_loss_value(normX2, M, Um, G, *, out=None):
+    """f = 0.5 ||X - [[U]]||^2 as an FP32 device scalar (mtk_cp_loss)."""
+    dev = M.device
+    if out is None:
+        out = torch.empty((), dtype=torch.float32, device=dev)
+    ptrs = [_req(g, torch.float64, "G").data_ptr() for g in G]
+    L.check(L.load().mtk_cp_loss(normX2.data_ptr(), _req(M, torch.float32, "M").data_ptr(),
+                                 _req(Um, torch.float32, "Um").data_ptr(), int(M.shape[0]), L.ptr_arr(ptrs),
+                                 len(G), int(M.shape[1]), out.data_ptr(), _stream(dev)), "mtk_cp_loss")
+    return out
+
+
 def cp_gradient(Un, Mn, G, n, *, scale=None, out=None):
     """scale * (U_n Hadamard_{k!=n}(G_k) - M_n)."""
     dev = Un.device
@@ -562,13 +574,13 @@ class CPLoss(torch.autograd.Function):
         G = [gram(u) for u in U]
         M = mttkrp(X, dims, list(U), N - 1, **opts)
         nx2 = norm2(X)
-        r2, _ = cp_residual(nx2, M, U[N - 1], G)
+        loss = cp_loss_value(nx2, M, U[N - 1], G)
         ctx.save_for_backward(X, *U)
         ctx.dims = dims
         ctx.opts = opts
         ctx.M_last = M
         ctx.G = G
-        return (0.5 * r2).to(torch.float32)
+        return loss
 
     @staticmethod
     def backward(ctx, go):

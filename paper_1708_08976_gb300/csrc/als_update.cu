@@ -8,6 +8,9 @@
 // CTA): a dependent FP64 FMA takes ~64 cycles, one warp issues at most one FP64
 // instruction per ~64 cycles however many of its lanes are active, the SM as a whole peaks
 // near one FP64 warp-instruction per ~17 cycles, and an FP64 reciprocal costs ~440 cycles.
+// Everything that does not need M runs before griddepcontrol.wait, i.e. (launched with
+// programmatic stream serialisation) while the kernel that writes M is still running; what
+// is left after M arrives is short and runs on the FP32 pipe.
 //  - H = L D L^T is factored in FP64 without a division on its C-step chain.  Step j
 //    replaces the trailing entries by 2^-e_j (d_j A(i,k) - A(i,j) A(k,j)), d_j the current
 //    pivot and e_j its binary exponent; the scaling is an exact exponent change.  After
@@ -17,17 +20,21 @@
 //    in parallel, after the elimination.  H is positive definite iff every pivot is > 0
 //    (the pivots are the squares of the Cholesky diagonal, up to the positive sigma_j);
 //    otherwise MTK_ENOTPD is raised and U_n is left as it is.
-//  - Each row of U_n solves L y = m, z = D^{-1} y, L^T u = z in FP64 (one warp per row,
-//    one column per lane, the solved entry broadcast by a shuffle).
-//  - Every CTA factors H itself (all of them obtain bitwise the same factor), so the
-//    update needs no second launch.  Launched with programmatic stream serialisation,
-//    the factorisation runs before griddepcontrol.wait, i.e. while the kernel that
-//    writes M is still running.
-//  - The Gram sums run on the FP32 pipe in double-FP32 arithmetic: exact products
-//    (p = a*b, q = fma(a, b, -p)) and two-sum accumulation (Knuth, TAOCP vol. 2,
+//  - W = L^{-1} by column elimination (C - 1 steps of independent FMAs, one barrier
+//    each), then H^{-1} = W^T D^{-1} W, all in FP64.  H^{-1} is kept in shared memory as
+//    pairs of FP32 numbers (hi + lo, 48 significant bits).
+//  - After M arrives, each row is U_n(i, :) = M(i, :) H^{-1}: every product of an FP32
+//    entry of M and an FP32 half of H^{-1} formed exactly, the C of them summed in
+//    double-FP32 (about 2^-44 relative), then rounded to FP32 (one warp per row, one
+//    column per lane).
+//  - Every CTA factors H itself (all of them obtain bitwise the same factor and inverse),
+//    so the update needs no second launch.
+//  - The Gram of the new U_n runs on the FP32 pipe in double-FP32 arithmetic: exact
+//    products (p = a*b, q = fma(a, b, -p)) and two-sum accumulation (Knuth, TAOCP vol. 2,
 //    4.2.2; Dekker 1971), about 2^-44 relative.  The per-CTA partials are added in a
 //    fixed order by a two-level ticket reduction (groups of 8 CTAs, then the groups) and
-//    rounded once to FP64, so results do not depend on scheduling.
+//    rounded once to FP64, so results do not depend on scheduling; the last CTA writes
+//    G_n, which the next mode's update reads as it is.
 #include <string.h>
 
 #include "mtk_internal.cuh"
@@ -42,7 +49,10 @@ constexpr int kUpdRows = 4;                                   // rows per pass: 
 constexpr int kUpdMaxC = 64;
 constexpr int kMaxPairs = kUpdMaxC * (kUpdMaxC + 1) / 2;      // 2080
 constexpr int kPairsPerThread = (kMaxPairs + kUpdThreads - 1) / kUpdThreads;
-constexpr int kUpdMaxCtas = 304;
+constexpr int kUpdMaxCtas = 128;
+constexpr int kAppThreads = 256;                              // the factor update: 8 warps
+constexpr int kAppRows = kAppThreads / 32;                    // rows per pass: one per warp
+constexpr int kAppPairs = (kMaxPairs + kAppThreads - 1) / kAppThreads;
 constexpr int kGroup = 8;                                     // CTAs per first-level group
 constexpr int kGramRows = 16;                                 // rows staged per pass (Grams)
 constexpr int kGramMaxCtas = 64;                              // per factor
@@ -184,82 +194,68 @@ __device__ __forceinline__ int pair_index(int a, int b, int C) {
 }
 
 struct UpdParams {
-    const double* G[MTK_MAXN];   // Grams of the factors (entries n and, with pprev, nprev not read)
+    const double* G[MTK_MAXN];   // Grams of the factors (entry n not read)
     int N, C, n;
     const float* M;              // In x C
     int64_t In;
     float* Un;                   // In x C, overwritten (left as it is when H is not pd)
-    int64_t rows;                // rows per CTA, a multiple of kUpdRows
-    int gmode;                   // 0: no Gram of U_n; 1: partial Grams only; 2: G_n (and the fit)
-    float2* part;                // [grid][npairs] this CTA's partial Gram (gmode >= 1)
-    const float2* pprev;         // the previous update's partials (or null): G_nprev is reduced
-    int Pprev, nprev;            // from them here, and written to Gprev by CTA 0
-    double* Gprev;
-    double* Gn;                  // gmode 2: the Gram of the new U_n
-    float2* gsum;                // gmode 2: [groups][npairs]
-    double* dots;                // gmode 2 with fit: [grid] partial <M, U_n>
-    unsigned int* tk;            // gmode 2: tickets, zero on entry and on exit
-    const double* normX2;        // gmode 2: the fit (else null)
+    int64_t rows;                // rows per CTA, a multiple of kAppRows
+    int gram;                    // 1: the Gram of U_n is reduced here and written to Gn
+    double* Gn;
+    float2* part;                // [grid][npairs] this CTA's partial Gram
+    float2* gsum;                // [groups][npairs]
+    double* dots;                // [grid] partial <M, U_n> (with the fit)
+    unsigned int* tk;            // tickets, zero on entry and on exit
+    const double* normX2;        // with gram: the fit (else null)
     double* fit;
     double* r2;
     uint32_t* status;
 };
 
-// dynamic shared memory: A[C*C] doubles, then fin and fprev, C(C+1)/2 float2 each
-__global__ void __launch_bounds__(kUpdThreads)
+// dynamic shared memory: A[C*C], W[C*C] (doubles), then H^{-1}[C*C] and fin[npairs]
+// (float2 pairs)
+__global__ void __launch_bounds__(kAppThreads)
 als_update_kernel(const __grid_constant__ UpdParams p) {
     extern __shared__ double dsm[];
     __shared__ double dinv[kUpdMaxC], rcp[kUpdMaxC];
-    __shared__ double red[kUpdThreads / 32];
+    __shared__ double red[kAppThreads / 32];
     __shared__ int tri[kMaxPairs];
-    __shared__ float ur[kUpdRows][kUpdMaxC];
+    __shared__ float ur[kAppRows][kUpdMaxC];
     __shared__ int flag;
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int C = p.C, N = p.N, n = p.n;
     const int npairs = C * (C + 1) / 2;
     double* A = dsm;
-    float2* fin = reinterpret_cast<float2*>(dsm + C * C);
-    float2* fprev = fin + npairs;
+    double* W = A + C * C;
+    float2* Hv = reinterpret_cast<float2*>(W + C * C);
+    float2* fin = Hv + C * C;
 
     build_pairs(tri, C);
-    __syncthreads();
-    // ---- G of the previous mode from its update's partials (written before the kernel
-    // that precedes this one started)
-    const bool prev = p.pprev != nullptr;
-    if (prev) {
-        sum_rows(p.pprev, p.Pprev, npairs, fprev);
-        __syncthreads();
-        if (blockIdx.x == 0) write_gram(fprev, tri, npairs, C, p.Gprev);
-    }
-    // ---- H = Hadamard_{k != n} G_k; the loads of one factor are issued together
-    for (int e0 = t; e0 < C * C; e0 += 8 * kUpdThreads) {
-        double h[8];
+    // ---- H = Hadamard_{k != n} G_k (the loads of one factor issued together); W = I
+    for (int e0 = t; e0 < C * C; e0 += 4 * kAppThreads) {
+        double h[4];
         bool first = true;
         for (int k = 0; k < N; ++k) {
             if (k == n) continue;
-            double g[8];
+            double g[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = e0 + q * kUpdThreads;
-                if (e < C * C) {
-                    if (prev && k == p.nprev) {
-                        const float2 v = fprev[pair_index(e / C, e % C, C)];
-                        g[q] = (double)v.x + (double)v.y;
-                    } else {
-                        g[q] = p.G[k][e];
-                    }
-                } else {
-                    g[q] = 0.0;
-                }
+            for (int q = 0; q < 4; ++q) {
+                const int e = e0 + q * kAppThreads;
+                g[q] = e < C * C ? p.G[k][e] : 0.0;
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) h[q] = first ? g[q] : h[q] * g[q];
+            for (int q = 0; q < 4; ++q) h[q] = first ? g[q] : h[q] * g[q];
             first = false;
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (e0 + q * kUpdThreads < C * C) A[e0 + q * kUpdThreads] = h[q];
+        for (int q = 0; q < 4; ++q) {
+            const int e = e0 + q * kAppThreads;
+            if (e < C * C) {
+                A[e] = h[q];
+                W[e] = (e / C == e % C) ? 1.0 : 0.0;
+            }
+        }
     }
     __syncthreads();
 
@@ -275,8 +271,7 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
         const int ej = ed - 1023;
         const int m = C - 1 - j;
         const int cnt = m * (m + 1) / 2;
-#pragma unroll 3
-        for (int x = t; x < cnt; x += kUpdThreads) {
+        for (int x = t; x < cnt; x += kAppThreads) {
             const int i = tri[x] >> 8, k = tri[x] & 255;
             const double v = A[i * C + j] * A[k * C + j];
             A[i * C + k] = scale_exp2(fma(d, A[i * C + k], -v), ej);
@@ -306,15 +301,39 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
         if (warp == 1) excl *= red[0];
         if (t < C) dinv[t] = excl * r_own;
         __syncthreads();
-        // L(i, k) = A(i, k) / d_k for i > k, kept in both triangles: A[k][i] = A[i][k] = L(i, k)
-#pragma unroll 4
-        for (int x = t; x < npairs; x += kUpdThreads) {
+        // L(i, k) = A(i, k) / d_k for i > k (lower triangle of A)
+        for (int x = t; x < npairs; x += kAppThreads) {
             const int i = tri[x] >> 8, k = tri[x] & 255;
-            if (i > k) {
-                const double l = A[i * C + k] * rcp[k];
-                A[i * C + k] = l;
-                A[k * C + i] = l;
+            if (i > k) A[i * C + k] *= rcp[k];
+        }
+        __syncthreads();
+        // W = L^{-1} (unit lower triangular), column k eliminated at step k: rows i > k,
+        // columns c <= k, W(i, c) -= L(i, k) W(k, c); row k is final at step k
+        for (int k = 0; k + 1 < C; ++k) {
+            const int w = k + 1, cnt = (C - 1 - k) * w;
+            for (int x = t; x < cnt; x += kAppThreads) {
+                const int q = x / w;
+                const int i = k + 1 + q, c = x - q * w;
+                W[i * C + c] = fma(-A[i * C + k], W[k * C + c], W[i * C + c]);
             }
+            __syncthreads();
+        }
+        // H^{-1} = W^T D^{-1} W: (a, b), a >= b, sums over k >= a; kept as FP32 (hi, lo)
+        // pairs, both triangles, row-major [k][c]
+        for (int x = t; x < npairs; x += kAppThreads) {
+            const int a = tri[x] >> 8, b = tri[x] & 255;
+            double s0 = 0.0, s1 = 0.0;
+            int k = a;
+            for (; k + 1 < C; k += 2) {
+                s0 = fma(W[k * C + a] * dinv[k], W[k * C + b], s0);
+                s1 = fma(W[(k + 1) * C + a] * dinv[k + 1], W[(k + 1) * C + b], s1);
+            }
+            if (k < C) s0 = fma(W[k * C + a] * dinv[k], W[k * C + b], s0);
+            const double h = s0 + s1;
+            const float hh = (float)h;
+            const float2 v = make_float2(hh, (float)(h - (double)hh));
+            Hv[a * C + b] = v;
+            Hv[b * C + a] = v;
         }
         __syncthreads();
     }
@@ -322,16 +341,16 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
     // ---- M is written by the previous kernel
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
-    const bool gram = p.gmode >= 1;
-    const bool fit = p.gmode == 2 && p.normX2 != nullptr;
+    const bool gram = p.gram != 0;
+    const bool fit = gram && p.normX2 != nullptr;
     const int64_t r0 = (int64_t)blockIdx.x * p.rows;
     const int64_t r1 = (r0 + p.rows < p.In) ? r0 + p.rows : p.In;
-    float gh[kPairsPerThread], gl[kPairsPerThread];
+    float gh[kAppPairs], gl[kAppPairs];
 #pragma unroll
-    for (int q = 0; q < kPairsPerThread; ++q) gh[q] = gl[q] = 0.0f;
+    for (int q = 0; q < kAppPairs; ++q) gh[q] = gl[q] = 0.0f;
     double dot = 0.0;
     const int j0 = lane, j1 = lane + 32;
-    for (int64_t rb = r0; rb < r1; rb += kUpdRows) {
+    for (int64_t rb = r0; rb < r1; rb += kAppRows) {
         const int64_t i = rb + warp;
         float u0 = 0.0f, u1 = 0.0f;
         if (i < r1) {
@@ -340,33 +359,24 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
             const float m0 = j0 < C ? mrow[j0] : 0.0f;
             const float m1 = j1 < C ? mrow[j1] : 0.0f;
             if (!bad) {
-                double s0 = (double)m0, s1 = (double)m1;
-                if (C <= 32) {
-                    for (int k = 0; k < C; ++k) {             // L y = m
-                        const double y = __shfl_sync(0xffffffffu, s0, k);
-                        if (j0 > k && j0 < C) s0 = fma(-A[k * C + j0], y, s0);
+                // U_n(i, :) = M(i, :) H^{-1}: products of an FP32 entry and an FP32 pair,
+                // each formed exactly, summed in double-FP32 (about 2^-44 relative)
+                float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+                for (int k = 0; k < C; ++k) {
+                    const float mk = __shfl_sync(0xffffffffu, k < 32 ? m0 : m1, k & 31);
+                    if (j0 < C) {
+                        const float2 w = Hv[k * C + j0];
+                        df_madd(h0, l0, mk, w.x);
+                        l0 = fmaf(mk, w.y, l0);
                     }
-                    s0 *= dinv[j0 < C ? j0 : 0];              // z = D^{-1} y
-                    for (int k = C - 1; k >= 0; --k) {        // L^T u = z
-                        const double y = __shfl_sync(0xffffffffu, s0, k);
-                        if (j0 < k) s0 = fma(-A[k * C + j0], y, s0);
-                    }
-                } else {
-                    for (int k = 0; k < C; ++k) {
-                        const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
-                        if (j0 > k) s0 = fma(-A[k * C + j0], y, s0);
-                        if (j1 > k && j1 < C) s1 = fma(-A[k * C + j1], y, s1);
-                    }
-                    s0 *= dinv[j0];
-                    if (j1 < C) s1 *= dinv[j1];
-                    for (int k = C - 1; k >= 0; --k) {
-                        const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
-                        if (j0 < k) s0 = fma(-A[k * C + j0], y, s0);
-                        if (j1 < k) s1 = fma(-A[k * C + j1], y, s1);
+                    if (j1 < C) {
+                        const float2 w = Hv[k * C + j1];
+                        df_madd(h1, l1, mk, w.x);
+                        l1 = fmaf(mk, w.y, l1);
                     }
                 }
-                u0 = (float)s0;
-                u1 = (float)s1;
+                u0 = __fadd_rn(h0, l0);
+                u1 = __fadd_rn(h1, l1);
                 if (j0 < C) urow[j0] = u0;
                 if (j1 < C) urow[j1] = u1;
             } else {
@@ -382,10 +392,10 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
         if (j0 < C) ur[warp][j0] = u0;
         if (j1 < C) ur[warp][j1] = u1;
         __syncthreads();
-        const int nr = (r1 - rb) < kUpdRows ? (int)(r1 - rb) : kUpdRows;
+        const int nr = (r1 - rb) < kAppRows ? (int)(r1 - rb) : kAppRows;
 #pragma unroll
-        for (int q = 0; q < kPairsPerThread; ++q) {
-            const int x = t + q * kUpdThreads;
+        for (int q = 0; q < kAppPairs; ++q) {
+            const int x = t + q * kAppThreads;
             if (x < npairs) {
                 const int a = tri[x] >> 8, b = tri[x] & 255;
                 for (int r = 0; r < nr; ++r) df_madd(gh[q], gl[q], ur[r][a], ur[r][b]);
@@ -395,37 +405,39 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
     }
     if (!gram) return;
 
-    // ---- partial Gram (and partial <M, U_n>) of this CTA
+    // ---- partial Gram (and partial <M, U_n>) of this CTA, then the fixed-order reduction
     float2* prow = p.part + (size_t)blockIdx.x * npairs;
 #pragma unroll
-    for (int q = 0; q < kPairsPerThread; ++q) {
-        const int x = t + q * kUpdThreads;
+    for (int q = 0; q < kAppPairs; ++q) {
+        const int x = t + q * kAppThreads;
         if (x < npairs) {
             df_renorm(gh[q], gl[q]);
             prow[x] = make_float2(gh[q], gl[q]);
         }
     }
-    if (p.gmode == 1) return;
     if (fit) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
         if (lane == 0) red[warp] = dot;
         __syncthreads();
-        if (t == 0) p.dots[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+        if (t == 0) {
+            double sd = 0.0;
+            for (int w = 0; w < kAppThreads / 32; ++w) sd += red[w];
+            p.dots[blockIdx.x] = sd;
+        }
     }
     if (!ticket_reduce(p.part, p.gsum, fin, p.tk + kTicketUpd, (int)blockIdx.x, (int)gridDim.x, npairs, &flag))
         return;
     write_gram(fin, tri, npairs, C, p.Gn);
     if (!fit) return;
-    // ---- fit: y2 = sum_ab prod_k G_k(a, b) with the new G_n (fin) and, when it was reduced
-    // here, the previous mode's G (fprev; CTA 0's global copy may not be written yet);
-    // <M, U_n> from the partials
+    // ---- fit: y2 = sum_ab prod_k G_k(a, b) with the new G_n (fin); <M, U_n> from the
+    // partials
     double v = 0.0;
-    for (int e0 = t; e0 < C * C; e0 += 8 * kUpdThreads) {
-        double h[8];
+    for (int e0 = t; e0 < C * C; e0 += 4 * kAppThreads) {
+        double h[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = e0 + q * kUpdThreads;
+        for (int q = 0; q < 4; ++q) {
+            const int e = e0 + q * kAppThreads;
             if (e < C * C) {
                 const float2 w = fin[pair_index(e / C, e % C, C)];
                 h[q] = (double)w.x + (double)w.y;
@@ -435,27 +447,20 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
         }
         for (int k = 0; k < N; ++k) {
             if (k == n) continue;
-            double g[8];
+            double g[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = e0 + q * kUpdThreads;
-                if (e >= C * C) {
-                    g[q] = 0.0;
-                } else if (prev && k == p.nprev) {
-                    const float2 w = fprev[pair_index(e / C, e % C, C)];
-                    g[q] = (double)w.x + (double)w.y;
-                } else {
-                    g[q] = p.G[k][e];
-                }
+            for (int q = 0; q < 4; ++q) {
+                const int e = e0 + q * kAppThreads;
+                g[q] = e < C * C ? p.G[k][e] : 0.0;
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) h[q] *= g[q];
+            for (int q = 0; q < 4; ++q) h[q] *= g[q];
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v += h[q];
+        for (int q = 0; q < 4; ++q) v += h[q];
     }
     double ds = 0.0;
-    for (int b = t; b < (int)gridDim.x; b += kUpdThreads) ds += __ldcg(p.dots + b);
+    for (int b = t; b < (int)gridDim.x; b += kAppThreads) ds += __ldcg(p.dots + b);
     v -= 2.0 * ds;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -464,7 +469,9 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
     __syncthreads();
     if (t == 0) {
         const double nx2 = *p.normX2;
-        const double r2 = nx2 + ((red[0] + red[1]) + (red[2] + red[3]));
+        double y = 0.0;
+        for (int w = 0; w < kAppThreads / 32; ++w) y += red[w];
+        const double r2 = nx2 + y;
         if (p.r2) *p.r2 = r2;
         if (p.fit) *p.fit = 1.0 - sqrt(r2 > 0.0 ? r2 : 0.0) / sqrt(nx2);
     }
@@ -546,10 +553,10 @@ bool als_update_supported(int C) { return C >= 1 && C <= kUpdMaxC; }
 size_t als_ticket_bytes() { return 2048; }
 
 int als_update_ctas(int64_t In, int64_t* rows) {
-    int64_t P = (In + kUpdRows - 1) / kUpdRows;
-    int64_t r = kUpdRows;
+    int64_t P = (In + kAppRows - 1) / kAppRows;
+    int64_t r = kAppRows;
     if (P > kUpdMaxCtas) {
-        r = ((In + kUpdMaxCtas - 1) / kUpdMaxCtas + kUpdRows - 1) / kUpdRows * kUpdRows;
+        r = ((In + kUpdMaxCtas - 1) / kUpdMaxCtas + kAppRows - 1) / kAppRows * kAppRows;
         P = (In + r - 1) / r;
     }
     if (rows) *rows = r;
@@ -565,10 +572,10 @@ int als_update_max_ctas(const int64_t* dims, int N) {
     return P;
 }
 
-// two partial buffers (consecutive updates alternate), the ticket groups' sums, the dots
+// the per-CTA partial Grams, the ticket groups' sums, the partial dots
 size_t als_update_scratch_bytes(int Pmax, int C) {
     const int ng = (Pmax + kGroup - 1) / kGroup;
-    return 2 * rup((size_t)Pmax * pair_bytes(C), 256) + rup((size_t)ng * pair_bytes(C), 256) +
+    return rup((size_t)Pmax * pair_bytes(C), 256) + rup((size_t)ng * pair_bytes(C), 256) +
            rup((size_t)Pmax * sizeof(double), 256);
 }
 
@@ -589,34 +596,32 @@ cudaError_t launch_als_update(const AlsUpdateArgs& a, cudaStream_t s) {
     p.In = a.In;
     p.Un = a.Un;
     const int P = als_update_ctas(a.In, &p.rows);
-    if (P > a.Pmax || (a.prevP > a.Pmax)) return cudaErrorInvalidValue;
-    const size_t pb = rup((size_t)a.Pmax * pair_bytes(a.C), 256);
+    if (P > a.Pmax) return cudaErrorInvalidValue;
     const int ng = (a.Pmax + kGroup - 1) / kGroup;
     char* w = static_cast<char*>(a.scratch);
-    float2* buf[2] = {reinterpret_cast<float2*>(w), reinterpret_cast<float2*>(w + pb)};
-    p.gmode = a.gmode;
-    p.part = buf[a.parity & 1];
-    if (a.prevP > 0) {
-        p.pprev = buf[(a.parity & 1) ^ 1];
-        p.Pprev = a.prevP;
-        p.nprev = a.nprev;
-        p.Gprev = a.Gprev;
-    }
+    p.gram = a.Gn ? 1 : 0;
     p.Gn = a.Gn;
-    p.gsum = reinterpret_cast<float2*>(w + 2 * pb);
-    p.dots = reinterpret_cast<double*>(w + 2 * pb + rup((size_t)ng * pair_bytes(a.C), 256));
+    p.part = reinterpret_cast<float2*>(w);
+    w += rup((size_t)a.Pmax * pair_bytes(a.C), 256);
+    p.gsum = reinterpret_cast<float2*>(w);
+    w += rup((size_t)ng * pair_bytes(a.C), 256);
+    p.dots = reinterpret_cast<double*>(w);
     p.tk = a.tickets;
-    p.normX2 = a.gmode == 2 ? a.normX2 : nullptr;
+    p.normX2 = a.Gn ? a.normX2 : nullptr;
     p.fit = a.fit;
     p.r2 = a.r2;
     p.status = a.status;
-    const size_t smem = (size_t)a.C * a.C * sizeof(double) + 2 * pair_bytes(a.C);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(als_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = 2 * (size_t)a.C * a.C * sizeof(double) + (size_t)a.C * a.C * sizeof(float2) +
+                        pair_bytes(a.C);
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(als_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)P);
-    cfg.blockDim = dim3(kUpdThreads);
+    cfg.blockDim = dim3(kAppThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points declared in include/mttkrp.h: argument
 // checks, workspace layout and the choice of kernels.  No device memory is
 // allocated here; every buffer comes from the caller.
+#include <cuda.h>
 #include <string.h>
 
 #include "mtk_internal.cuh"
@@ -17,6 +18,19 @@ using namespace mtk;
 namespace mtk {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+// With no device to ask (a workspace query on a host without a GPU) the count of the
+// GB300 the library is built for stands in, so that host-side sizes match that GPU's.
+int num_sms() {
+    constexpr int kGb300Sms = 152;
+    static int n = []() {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return kGb300Sms;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return kGb300Sms;
+        return v;
+    }();
+    return n;
+}
 }  // namespace mtk
 
 namespace {
@@ -27,6 +41,37 @@ constexpr int kSimtBI = 64;
 constexpr int kNoAllocMaxDevices = 64;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Identity of the CUDA context current on this thread (0 if none or unavailable):
+// cuCtxGetCurrent + cuCtxGetId, reached through the runtime.  Context ids are never
+// reused within a process, so an id that changes means the module (and its static
+// device arrays) was loaded again, e.g. after cudaDeviceReset.
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrentFn)(CUcontext*);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+    static GetCurrentFn get_current = []() {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (GetCurrentFn) nullptr;
+        return reinterpret_cast<GetCurrentFn>(p);
+    }();
+    static GetIdFn get_id = []() {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (GetIdFn) nullptr;
+        return reinterpret_cast<GetIdFn>(p);
+    }();
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 struct Carve {                    // bump allocator over a caller workspace
     char* base;
@@ -49,6 +94,11 @@ mtk_opts defaults(const mtk_opts* o) {
 }
 
 bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
+// limit of the contraction kernels' abortable device waits (0: the kernels' 1 s default)
+unsigned long long wait_limit_ns(const mtk_opts& o) {
+    return o.wait_us > 0 ? (unsigned long long)o.wait_us * 1000ull : 0ull;
+}
 
 int check_shape(const int64_t* dims, int N, int C, int n) {
     if (!dims || N < 2 || N > MTK_MAXN || C < 1 || C > MTK_MAXC || n < 0 || n >= N)
@@ -95,7 +145,7 @@ ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int split
     const int64_t quantum = pl.tc ? kTcBK : 1;              // split boundaries
     int64_t S = splits;
     if (S <= 0) {
-        const int64_t target = 152 * (pl.tc ? 2 : 4);       // CTAs resident per wave
+        const int64_t target = (int64_t)num_sms() * (pl.tc ? 2 : 4);       // CTAs resident per wave
         const int64_t tiles = (int64_t)pl.i_tiles * pl.c_blocks;
         S = target / tiles;
         const int64_t maxS = (K + 4 * kTcBK - 1) / (4 * kTcBK);   // >= 4 stages per split
@@ -294,6 +344,8 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
     p.X = X;
     p.C = C;
     p.status = status;
+    p.wait_ns = wait_limit_ns(o);
+    p.stall = o.test_stall;
     if (ly.algo == MTK_ALGO_FUSED || ly.algo == MTK_ALGO_MATERIALIZED) {
         p.L = v.L; p.I = v.I; p.R = v.R; p.K = v.L * v.R;
         FactorList fl = mode_factors(U, dims, N, n);
@@ -388,7 +440,7 @@ int do_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, 
     void* scratch = cv.take(planes_scratch_bytes(pl));
     const int64_t NX = v.L * v.I * v.R;
     if (launch_contract_planes(Xs, split_pitch(NX), v.L, v.I, v.R, fl.f, fl.rad, fl.Z, C, pl, M, C, 1,
-                               scratch, status, s) != cudaSuccess)
+                               scratch, status, s, wait_limit_ns(o), o.test_stall) != cudaSuccess)
         return MTK_ECUDA;
     return MTK_OK;
 }
@@ -464,9 +516,9 @@ int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* c
     const int64_t rows = right ? v.L * v.I : v.I * v.R;
     const int64_t pitch = split_pitch(v.L * v.I * v.R);
     cudaError_t e = right ? launch_contract_planes(Xs, pitch, 1, rows, v.R, fac, frad, nf, C, pl, T, 1, rows,
-                                                   scratch, status, s)
+                                                   scratch, status, s, wait_limit_ns(o), o.test_stall)
                           : launch_contract_planes(Xs, pitch, v.L, rows, 1, fac, frad, nf, C, pl, T, 1, rows,
-                                                   scratch, status, s);
+                                                   scratch, status, s, wait_limit_ns(o), o.test_stall);
     return e == cudaSuccess ? MTK_OK : MTK_ECUDA;
 }
 
@@ -572,18 +624,22 @@ int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* 
     mtk_opts o = defaults(opts);
     if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
     if (mttkrp_layout(dims, N, C, n, o).total > MTK_NOALLOC_SCRATCH_BYTES) return MTK_EWORKSPACE;
-    // set-up, once per device, with that device current
+    // set-up, once per device (and again whenever that device's context is new, e.g.
+    // after cudaDeviceReset), with that device current: the device address of the array
     static std::mutex mu;
     static void* dev_scratch[kNoAllocMaxDevices];
+    static unsigned long long dev_ctx[kNoAllocMaxDevices];
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return MTK_ECUDA;
     void* ws;
     {
         std::lock_guard<std::mutex> lock(mu);
-        if (!dev_scratch[dev]) {
+        const unsigned long long id = current_context_id();
+        if (!dev_scratch[dev] || id == 0 || id != dev_ctx[dev]) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MTK_ECUDA;
             dev_scratch[dev] = p;
+            dev_ctx[dev] = current_context_id();   // the lookup made the context current
         }
         ws = dev_scratch[dev];
     }
@@ -798,7 +854,6 @@ int mtk_gram_hadamard_solve(const double* const* G, int N, int C, int n, const f
         a.M = M;
         a.In = In;
         a.Un = Un;
-        a.gmode = Gn ? 2 : 0;
         a.Gn = Gn;
         a.scratch = scratch;
         a.Pmax = als_update_ctas(In, nullptr);
@@ -981,9 +1036,9 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
         }
         if (st) return st;
         if (fused) {
-            // U_n in one launch that may overlap the kernel before it.  Its Gram leaves as
-            // per-CTA partials that the next mode's update reduces (before it waits for its
-            // M); the last mode forms G_n itself, with the fit.
+            // U_n in one launch whose factorisation of H (and H^{-1}) overlaps the kernel
+            // before it; the launch also reduces the Gram of the new U_n into G_n, which
+            // the next update reads, and the last mode's computes the fit.
             AlsUpdateArgs ua;
             memset(&ua, 0, sizeof(ua));
             ua.G = G;
@@ -994,19 +1049,12 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
             ua.In = dims[n];
             ua.Un = U[n];
             const bool last = n == N - 1;
-            ua.gmode = last ? (fit ? 2 : 0) : 1;
             ua.Gn = const_cast<double*>(G[n]);
             ua.scratch = upd;
             ua.Pmax = als_update_max_ctas(dims, N);
-            ua.parity = n & 1;
-            if (n > 0) {
-                ua.prevP = als_update_ctas(dims[n - 1], nullptr);
-                ua.nprev = n - 1;
-                ua.Gprev = const_cast<double*>(G[n - 1]);
-            }
             ua.tickets = tick;
-            ua.normX2 = normX2;
-            ua.fit = fit;
+            ua.normX2 = last ? normX2 : nullptr;
+            ua.fit = last ? fit : nullptr;
             ua.status = status;
             ua.programmatic = true;
             if (launch_als_update(ua, s) != cudaSuccess) return MTK_ECUDA;
@@ -1048,6 +1096,17 @@ int mtk_cp_residual(const double* normX2, const float* M, const float* Um, int64
     for (int k = 0; k < N; ++k)
         if (!G[k]) return MTK_EINVAL;
     if (launch_residual(normX2, M, Um, Im, G, N, C, r2, fit, (cudaStream_t)stream) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+int mtk_cp_loss(const double* normX2, const float* M, const float* Um, int64_t Im,
+                const double* const* G, int N, int C, float* loss, void* stream) {
+    if (!normX2 || !M || !Um || !G || !loss || N < 2 || N > MTK_MAXN || C < 1 || C > MTK_MAXC || Im < 1)
+        return MTK_EINVAL;
+    for (int k = 0; k < N; ++k)
+        if (!G[k]) return MTK_EINVAL;
+    if (launch_residual(normX2, M, Um, Im, G, N, C, nullptr, nullptr, (cudaStream_t)stream, loss) != cudaSuccess)
         return MTK_ECUDA;
     return MTK_OK;
 }

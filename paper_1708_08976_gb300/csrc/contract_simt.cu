@@ -230,7 +230,7 @@ cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, floa
                                 int64_t si, int64_t sc, cudaStream_t s) {
     const int64_t n = I * C;
     int blocks = (int)((n + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > num_sms() * 8) blocks = num_sms() * 8;
     if (blocks < 1) blocks = 1;
     split_reduce_kernel<<<blocks, 256, 0, s>>>(part, S, I, C, out, si, sc);
     note_launches(1);

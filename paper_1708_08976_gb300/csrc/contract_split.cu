@@ -31,8 +31,10 @@
 // slab of its stages); a CTA runs one unit, or, when the view has more units than SMs,
 // several back to back, each role carrying its ring slots, phases and accumulator
 // buffers over from one unit to the next.  Every mbarrier wait is bounded (1 s of
-// %globaltimer); on expiry the kernel sets MTK_ETIMEOUT, lets its own copies and MMAs
-// finish (again bounded), frees its TMEM and returns.
+// %globaltimer by default, or the caller's limit); on expiry the kernel sets MTK_ETIMEOUT
+// and every role stops.  The producers then wait for their last copies to land and the
+// MMA issuer for its last MMAs (waits of 1 s that an abort does not shorten) before the
+// CTA frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -48,13 +50,29 @@ using namespace tc;
 
 constexpr int PS_BK = 64;                    // k per stage
 constexpr int PS_M = 128;                    // MMA M
-constexpr int PS_GROUP = 2;                  // stages per accumulation chain
+#ifndef MTK_PS_GROUP
+#define MTK_PS_GROUP 2
+#endif
+#ifndef MTK_PS_LO_SEP
+#define MTK_PS_LO_SEP 1
+#endif
+#ifndef MTK_PS_MT2_FILL
+#define MTK_PS_MT2_FILL 0.75
+#endif
+constexpr int PS_GROUP = MTK_PS_GROUP;       // stages per accumulation chain (at most)
+// one MMA tile: the lo plane accumulates into accumulator columns of its own (1) or into
+// the hi plane's first two pieces (0)
+constexpr bool PS_LO_SEP = MTK_PS_LO_SEP != 0;
 constexpr int PS_MAX_A = 8;
 constexpr int PS_MAX_B = 6;
 constexpr int PS_MAX_BUF = 4;
 constexpr int PS_TILE = PS_M * 128;          // one plane of a 128 x 64 BF16 tile (16 KB)
 constexpr int PS_MN_ATOM = 64 * 128;         // MN-major: 64 k rows x 64 i (8 KB)
 constexpr unsigned long long kPsWaitNs = 1000000000ull;
+// smallest B ring of a one-MMA-tile CTA (the A ring takes the rest of the budget)
+#ifndef MTK_PS_SB_MIN1
+#define MTK_PS_SB_MIN1 3
+#endif
 
 // L2 promotion of the tensor-map loads (0 none, 1 64 B, 2 128 B, 3 256 B), per operand
 // orientation.
@@ -99,6 +117,8 @@ struct PsParams {
     float* part;            // partial slabs when nslab > 1: [slab][I][C], or [slab][C][I] (part_cm)
     int part_cm;            // slabs in the output's column-major layout (out_si == 1)
     uint32_t* status;
+    unsigned long long wait_ns;   // limit of every wait that an abort can end
+    int stall;              // test hook: the MMA issuer first waits on a barrier that nothing completes
 };
 
 // A unit of work: one tile of rows and one slab (a contiguous range of its stages).
@@ -138,7 +158,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
     __shared__ __align__(8) uint64_t afull[PS_MAX_A], aempty[PS_MAX_A];
     __shared__ __align__(8) uint64_t bfull[PS_MAX_B], bempty[PS_MAX_B];
     __shared__ __align__(8) uint64_t accf_bar[PS_MAX_BUF], acce_bar[PS_MAX_BUF];
-    __shared__ __align__(8) uint64_t fin_bar;
+    __shared__ __align__(8) uint64_t fin_bar, stall_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -166,6 +186,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             mbar_init(smem_u32(&acce_bar[b]), 4 * MT);
         }
         mbar_init(smem_u32(&fin_bar), 1);
+        mbar_init(smem_u32(&stall_bar), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -215,7 +236,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 if (MN && U == 1)
                     while (nbox < 2 * MT && i0 + 64 * nbox < I) ++nbox;
                 for (int s = 0; s < w.nst; ++s) {
-                    if (issued >= SA && !mbar_wait(smem_u32(&aempty[slot]), ph, &abort_flag, kPsWaitNs)) {
+                    if (issued >= SA && !mbar_wait(smem_u32(&aempty[slot]), ph, &abort_flag, p.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -260,12 +281,13 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             if (!ok) {
                 abort_flag = 1;
                 set_status(p.status, MTK_ETIMEOUT);
-                // let the copies already issued land before the CTA leaves
-                const int first = issued > SA ? issued - SA : 0;
-                for (int s = first; s < issued; ++s) {
-                    volatile int never = 0;
-                    (void)mbar_wait(smem_u32(&afull[s % SA]), (uint32_t)((s / SA) & 1), &never, kPsWaitNs);
-                }
+            }
+            // let the copies already issued land before the CTA leaves (also when another
+            // role aborted after this one had issued its last stage; consumed phases return
+            // at once)
+            for (int s = issued > SA ? issued - SA : 0; s < issued; ++s) {
+                volatile int never = 0;
+                (void)mbar_wait(smem_u32(&afull[s % SA]), (uint32_t)((s / SA) & 1), &never, kPsWaitNs);
             }
         }
         __syncwarp();
@@ -280,7 +302,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 const PsUnit w = ps_unit(p, ub);
                 int j = (int)(w.t0 % spr);
                 for (int s = 0; s < w.nst; ++s) {
-                    if (issued >= SB && !mbar_wait(smem_u32(&bempty[slot]), ph, &abort_flag, kPsWaitNs)) {
+                    if (issued >= SB && !mbar_wait(smem_u32(&bempty[slot]), ph, &abort_flag, p.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -299,11 +321,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             if (!ok) {
                 abort_flag = 1;
                 set_status(p.status, MTK_ETIMEOUT);
-                const int first = issued > SB ? issued - SB : 0;
-                for (int s = first; s < issued; ++s) {
-                    volatile int never = 0;
-                    (void)mbar_wait(smem_u32(&bfull[s % SB]), (uint32_t)((s / SB) & 1), &never, kPsWaitNs);
-                }
+            }
+            for (int s = issued > SB ? issued - SB : 0; s < issued; ++s) {
+                volatile int never = 0;
+                (void)mbar_wait(smem_u32(&bfull[s % SB]), (uint32_t)((s / SB) & 1), &never, kPsWaitNs);
             }
         }
         __syncwarp();
@@ -329,19 +350,20 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             uint32_t pa = 0, pb = 0, pe = 1;
             uint64_t ad = adesc0, bd = bdesc0;
             bool ok = true;
+            if (p.stall && !mbar_wait(smem_u32(&stall_bar), 0u, &abort_flag, p.wait_ns)) ok = false;
             uint32_t dcol = tmem;
             for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
                 const PsUnit w = ps_unit(p, ub);
                 const int nst = w.nst;
                 int j = (int)(w.t0 % spr);
                 for (int s = 0; s < nst; ++s) {
-                    if (!mbar_wait(smem_u32(&afull[sa]), pa, &abort_flag, kPsWaitNs) ||
-                        !mbar_wait(smem_u32(&bfull[sb]), pb, &abort_flag, kPsWaitNs)) {
+                    if (!mbar_wait(smem_u32(&afull[sa]), pa, &abort_flag, p.wait_ns) ||
+                        !mbar_wait(smem_u32(&bfull[sb]), pb, &abort_flag, p.wait_ns)) {
                         ok = false;
                         break;
                     }
                     if (gs == 0) {
-                        if (g >= NB && !mbar_wait(smem_u32(&acce_bar[bi]), pe, &abort_flag, kPsWaitNs)) {
+                        if (g >= NB && !mbar_wait(smem_u32(&acce_bar[bi]), pe, &abort_flag, p.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -357,7 +379,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                         if (kk < kk_n) {
                             const uint64_t bk = bd + (uint64_t)(kk * 2);
                             const uint32_t acc = (kk == 0 && gs == 0) ? 0u : 1u;
-                            if (MT == 1) {
+                            if (MT == 1 && PS_LO_SEP) {
                                 const uint64_t a0 = ad + (uint64_t)(kk * a_k16);
                                 mma_bf16(dcol, a0, bk, idh, acc);
                                 mma_bf16(dcol + ncol, a0 + plane16, bk, idl, acc);
@@ -433,7 +455,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             const PsUnit w = ps_unit(p, ub);
             const int64_t i0 = w.i0;
             const int nst = w.nst;
-            const int64_t rows_here = (U > 1) ? I : ((I - i0) < BI ? (I - i0) : BI);
+            const int64_t rows_here = (I - i0) < BI ? (I - i0) : BI;
             const bool rowvalid = myg < U && myil < rows_here;
 #pragma unroll
             for (int e = 0; e < 16 * NCH; ++e) {
@@ -488,13 +510,13 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     }
                     qcached = q;
                 }
-                if (!mbar_wait(smem_u32(&accf_bar[b]), dph, &abort_flag, kPsWaitNs)) {
+                if (!mbar_wait(smem_u32(&accf_bar[b]), dph, &abort_flag, p.wait_ns)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t ta = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(b * p.acc_cols + mt * p.N);
-                if (MT == 1) {
+                if (MT == 1 && PS_LO_SEP) {
                     // hi accumulator (w0, w1, w2 at 0, CP, 2 CP) and lo accumulator (w0, w1 at
                     // N, N + CP); summed smallest first
 #pragma unroll
@@ -674,8 +696,11 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
 template <int Q>
 __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI,
                                                              int U, int ntiles, int s_full, int s_last,
-                                                             float* __restrict__ out, int colmajor, int vec) {
+                                                             float* __restrict__ out, int colmajor, int vec,
+                                                             const uint32_t* status) {
     allow_dependent_launch();
+    // a contraction that timed out left its slabs incomplete: the output stays as it was
+    if (status && (*reinterpret_cast<const volatile uint32_t*>(status) & (1u << MTK_ETIMEOUT))) return;
     __shared__ float red[32][32 * Q];
     const int W = (int)(blockDim.x >> 5);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -683,7 +708,7 @@ __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __rest
     const int64_t f0 = ((int64_t)blockIdx.x * 32 + lane) * Q;
     auto slabs = [&](int64_t f) {
         const int64_t i = colmajor ? f % I : f / C;
-        const int64_t tile = U > 1 ? 0 : i / BI;
+        const int64_t tile = i / BI;
         return (tile < ntiles - 1 ? s_full : s_last) * U;
     };
     float v[Q];
@@ -847,16 +872,6 @@ cudaError_t launch_planes_variant(const PsParams& p, const CUtensorMap& map, int
     return cudaGetLastError();
 }
 
-int num_sms() {
-    static int n = []() {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return 152;
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 152;
-        return v;
-    }();
-    return n;
-}
-
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
@@ -927,40 +942,53 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     pl.Lq = mn ? 1 : L / H;
     if (H > lim || pl.nruns > lim || I > lim || (!mn && (K / L) > lim)) return pl;
     pl.mn = mn ? 1 : 0;
-    // rows: small I_n packs U runs into one 128-row MMA tile; otherwise a CTA takes up to
-    // 256 rows of i (two 128-row MMA tiles), so that its loads cover more of each row of
-    // the tensor and each image slice serves more rows, when such tiles are at least 3/4
-    // full; else tiles of up to 128 rows
-    const int64_t t2 = (I + 2 * PS_M - 1) / (2 * PS_M);
-    const bool two = I > 64 && (double)I >= 0.75 * (double)(t2 * 2 * PS_M);
-    if (I <= 64) {
-        pl.MT = 1;
-        pl.ntiles = 1;
-        if (mn) {
-            pl.U = (int)(pl.nruns < 2 ? pl.nruns : 2);
+    // Rows of a CTA tile: up to 256 (two 128-row MMA tiles).  Each stage has a fixed cost
+    // besides its bytes, so the tiling carries as many rows per stage as it can: BI rows of
+    // i per run group and, when BI <= 128, U run groups of the head (different runs q,
+    // the same rows) packed one above the other; each packed group is a partial slab of
+    // its own.  K-major: the fewest i-tiles of at most 256 rows when they are at least 3/4
+    // full; otherwise the number of i-tiles that maximises U * BI, preferring fewer tiles
+    // (each packed group adds partial slabs) unless the rows grow by more than an eighth.
+    // MN-major (i is the contiguous index, loaded in 64-row boxes): tiles of 256 rows, or
+    // of 128 when I_n <= 128, and up to four packed 64-row groups when I_n <= 64.
+    if (mn) {
+        if (I <= 64) {
             pl.BI = 64;
+            pl.U = (int)(pl.nruns < 4 ? pl.nruns : 4);
+            pl.MT = pl.U > 2 ? 2 : 1;
+            pl.ntiles = 1;
         } else {
-            pl.BI = (int)round_up(I, 8);
-            int64_t u = PS_M / pl.BI;
-            if (u > pl.nruns) u = pl.nruns;
-            pl.U = (int)u;
+            pl.U = 1;
+            pl.MT = I > PS_M ? 2 : 1;
+            pl.BI = PS_M * pl.MT;
+            pl.ntiles = (int)((I + pl.BI - 1) / pl.BI);
         }
     } else {
-        pl.U = 1;
-        pl.MT = two ? 2 : 1;
-        // more tiles than CTAs (a tall view such as a partial MTTKRP): the tile height
-        // with the fewer waves of tile-sized work (a 256-row tile costs two 128-row ones)
-        if (pl.MT == 2) {
-            const int64_t t2w = (I + 2 * PS_M - 1) / (2 * PS_M), t1w = (I + PS_M - 1) / PS_M;
-            if (t2w > ctas && ((t1w + ctas - 1) / ctas) < 2 * ((t2w + ctas - 1) / ctas)) pl.MT = 1;
+        const int64_t t0 = (I + 2 * PS_M - 1) / (2 * PS_M);
+        int64_t best_bi = round_up((I + t0 - 1) / t0, 8), best_u = 1;
+        if (best_bi <= PS_M) {
+            best_u = (2 * PS_M) / best_bi;
+            if (best_u > pl.nruns) best_u = pl.nruns;
         }
-        const int cap = PS_M * pl.MT;
-        if (mn) {
-            pl.BI = cap;
-        } else {
-            const int64_t t = (I + cap - 1) / cap;
-            pl.BI = (int)round_up((I + t - 1) / t, 8);
+        int64_t best_rows = best_u * best_bi;
+        if (best_rows * 4 < 3 * 2 * PS_M) {
+            for (int64_t t = t0 + 1; t <= t0 + 64 && t <= (I + 7) / 8; ++t) {
+                const int64_t bi = round_up((I + t - 1) / t, 8);
+                int64_t u = 1;
+                if (bi <= PS_M) {
+                    u = (2 * PS_M) / bi;
+                    if (u > pl.nruns) u = pl.nruns;
+                }
+                if (u * bi * 8 > best_rows * 9) {
+                    best_rows = u * bi;
+                    best_bi = bi;
+                    best_u = u;
+                }
+            }
         }
+        pl.BI = (int)best_bi;
+        pl.U = (int)best_u;
+        pl.MT = best_rows > PS_M ? 2 : 1;
         pl.ntiles = (int)((I + pl.BI - 1) / pl.BI);
     }
     pl.stot = ((pl.nruns + pl.U - 1) / pl.U) * pl.spr;
@@ -1020,7 +1048,8 @@ int planes_ctas(int splits) { return splits > 0 ? splits : num_sms(); }
 cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int64_t I, int64_t R,
                                    const float* const* fac, const int64_t* frad, int nfac, int C,
                                    const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
-                                   void* scratch, uint32_t* status, cudaStream_t s) {
+                                   void* scratch, uint32_t* status, cudaStream_t s,
+                                   unsigned long long wait_ns, int stall) {
     char* sc = static_cast<char*>(scratch);
     uint8_t* image = reinterpret_cast<uint8_t*>(sc);
     float* qtab = pl.qtab_bytes ? reinterpret_cast<float*>(sc + round_up((int64_t)pl.image_bytes, 256)) : nullptr;
@@ -1051,7 +1080,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     {
         const int64_t items = (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * pl.CP : 0);
         int64_t blocks = (items + 255) / 256;
-        if (blocks > 152 * 8) blocks = 152 * 8;
+        if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         planes_prep_kernel<<<(int)blocks, 256, 0, s>>>(pa);
         note_launches(1);
         cudaError_t e = cudaGetLastError();
@@ -1108,27 +1137,31 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     p.C = C;
     p.CP = pl.CP;
     p.N = pl.N;
-    p.plane_bytes = pl.MT * PS_TILE;
+    // A stage: both planes of the tile.  K-major planes hold only the rows they load
+    // (U * BI, a multiple of 8: whole 1024-byte swizzle atoms); the MMAs still read
+    // MT x 128 rows from each plane base, and the rows beyond the tile (the next plane or
+    // stage, or the B ring after the last stage) only feed accumulator rows that are never
+    // drained.
+    const int tile_rows = pl.U > 1 ? pl.U * pl.BI : pl.BI;
+    p.plane_bytes = !pl.mn ? (int)round_up(tile_rows, 8) * 128 : pl.MT * PS_TILE;
     p.a_stage = 2 * p.plane_bytes;
     p.b_bytes = pl.N * 128;
     p.b_stage = (int)round_up(p.b_bytes, 1024);
-    // shared memory: A ring (tensor tiles, HBM latency) as deep as fits next to a
-    // shallower B ring (image slices, L2 latency)
-    // (one MMA tile: both rings equally deep, so the image slices are requested as early
-    // as the tensor tiles; two tiles: 3 + 2 stages fill the budget)
+    // shared memory: the A ring (tensor tiles, HBM latency) as deep as fits next to the
+    // shallowest useful B ring (image slices, L2 latency), then the rest to the B ring
     const int budget = 225 * 1024;
-    if (pl.MT == 1) {
-        p.sb = budget / (p.a_stage + p.b_stage);
-        if (p.sb > PS_MAX_B) p.sb = PS_MAX_B;
-    } else {
-        p.sb = 2;
-    }
-    p.sa = (budget - p.sb * p.b_stage) / p.a_stage;
+    const int sb_min = pl.MT == 1 ? MTK_PS_SB_MIN1 : 2;
+    p.sa = (budget - sb_min * p.b_stage) / p.a_stage;
     if (p.sa > PS_MAX_A) p.sa = PS_MAX_A;
+    p.sb = (budget - p.sa * p.a_stage) / p.b_stage;
+    if (p.sb > PS_MAX_B) p.sb = PS_MAX_B;
     if (p.sa < 2 || p.sb < 2) return cudaErrorInvalidConfiguration;
+    // the over-read of the last stage's lo plane (MT x 128 rows from its base) stays
+    // inside the B ring
+    if (pl.MT * PS_TILE - p.plane_bytes > p.sb * p.b_stage) return cudaErrorInvalidConfiguration;
     p.b_base = p.sa * p.a_stage;
-    p.lo_sep = pl.MT == 1 ? 1 : 0;
-    p.acc_cols = pl.MT == 1 ? pl.N + 2 * pl.CP : pl.MT * pl.N;
+    p.lo_sep = (pl.MT == 1 && PS_LO_SEP) ? 1 : 0;
+    p.acc_cols = p.lo_sep ? pl.N + 2 * pl.CP : pl.MT * pl.N;
     p.nbuf = 512 / p.acc_cols;
     if (p.nbuf > PS_MAX_BUF) p.nbuf = PS_MAX_BUF;
     if (p.nbuf < 1) return cudaErrorInvalidConfiguration;
@@ -1157,6 +1190,8 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     if (!((out_si == C && out_sc == 1) || (out_si == 1 && out_sc == I))) return cudaErrorInvalidValue;
     p.part_cm = (out_si == 1 && C > 1) ? 1 : 0;
     p.status = status;
+    p.wait_ns = wait_ns ? wait_ns : kPsWaitNs;
+    p.stall = stall;
     const size_t smem = (size_t)p.sa * p.a_stage + (size_t)p.sb * p.b_stage + 1024;
     const int nch = pl.CP / 16;
     cudaError_t e;
@@ -1183,11 +1218,11 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
         if (n >= 65536) {
             const int W = pl.nslab < 8 ? pl.nslab : 8;
             planes_reduce_kernel<4><<<(unsigned)((n + 127) / 128), 32 * W, 0, s>>>(
-                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, vec);
+                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, vec, status);
         } else {
             const int W = pl.nslab < 32 ? pl.nslab : 32;
             planes_reduce_kernel<1><<<(unsigned)((n + 31) / 32), 32 * W, 0, s>>>(
-                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, 0);
+                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, 0, status);
         }
         note_launches(1);
         e = cudaGetLastError();

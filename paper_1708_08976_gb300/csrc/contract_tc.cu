@@ -38,8 +38,13 @@
 // holding registers), split it, store the pieces, and drain the accumulator; one
 // thread of the last warp issues tcgen05.mma.
 //
-// Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel sets
-// MTK_ETIMEOUT in the status word, stops, frees its TMEM and returns.
+// Every mbarrier wait is bounded (1 s of %globaltimer by default, or the caller's limit);
+// on expiry the kernel sets MTK_ETIMEOUT in the status word and every role stops.  Before
+// the CTA frees its TMEM and leaves, each role waits (with a 1 s limit that an abort does
+// not shorten) for the asynchronous work it started: the TMA producer for its last tile
+// loads, the converter warp that issues the B-image copies for those copies, and the MMA
+// issuer for its MMAs (one final commit).  Nothing then lands in shared memory or TMEM
+// after the CTA has exited.
 #include "contract_tc_kernel.cuh"
 
 namespace mtk {
@@ -234,6 +239,8 @@ cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* ima
     TcParams tp;
     memset(&tp, 0, sizeof(tp));
     tp.p = p;
+    tp.wait_ns = p.wait_ns ? p.wait_ns : kWaitNs;
+    tp.stall = p.stall;
     tp.bimg = static_cast<const uint8_t*>(image);
     tp.ntail = p.nfac - pl.head;
     for (int z = pl.head; z < p.nfac; ++z) {
@@ -285,7 +292,7 @@ cudaError_t launch_contract_tc(const ContractParams& p, int precision, void* ima
     ia.img = static_cast<uint8_t*>(image);
     const int64_t items = (pl.rad0p / 8) * pl.CP;
     int64_t blocks = (items + 255) / 256;
-    int grid_img = (int)(blocks < 152 * 8 ? blocks : 152 * 8);
+    int grid_img = (int)(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
     tc_image_kernel<<<grid_img, 256, 0, s>>>(ia);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
@@ -326,7 +333,7 @@ cudaError_t launch_tc_image(const float* const* fac, const int64_t* frad, int he
     ia.img = static_cast<uint8_t*>(image);
     const int64_t items = (rad0p / 8) * CP;
     const int64_t blocks = (items + 255) / 256;
-    const int grid = (int)(blocks < 152 * 8 ? blocks : 152 * 8);
+    const int grid = (int)(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
     tc_image_kernel<<<grid, 256, 0, s>>>(ia);
     note_launches(1);
     return cudaGetLastError();

@@ -52,6 +52,8 @@ struct TcParams {
     int kwide;              // TMA, K-major: one 64-k box per row set (contiguous runs), else octet boxes
     int stage_bytes, b_off, b_bytes, stg_off, tmem_cols;
     uint32_t idesc;
+    unsigned long long wait_ns;   // limit of every wait that an abort can end (kWaitNs by default)
+    int stall;              // test hook: the MMA issuer first waits on a barrier that nothing completes
 };
 
 }  // namespace tcd
@@ -126,8 +128,10 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
     __shared__ __align__(8) uint64_t xempty_bar[MAX_STAGING];
     __shared__ __align__(8) uint64_t accf_bar[2];
     __shared__ __align__(8) uint64_t acce_bar[2];
+    __shared__ __align__(8) uint64_t fin_bar, stall_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    __shared__ int b_issued;                 // stages whose B-image copy has been issued
 
     const ContractParams& p = tp.p;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -161,7 +165,10 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
             mbar_init(smem_u32(&xfull_bar[x]), 1);
             mbar_init(smem_u32(&xempty_bar[x]), CONV_WARPS);
         }
+        mbar_init(smem_u32(&fin_bar), 1);
+        mbar_init(smem_u32(&stall_bar), 1);
         abort_flag = 0;
+        b_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // zero the tensor pieces of every stage once: rows beyond the packed tile are never
@@ -191,16 +198,17 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
             int g = 0;
             bool first = true, ok = true;
             uint32_t b = 0;
-            for (int s = 0; s < nst; ++s) {
+            if (tp.stall && !mbar_wait(smem_u32(&stall_bar), 0u, &abort_flag, tp.wait_ns)) ok = false;
+            for (int s = 0; ok && s < nst; ++s) {
                 const int slot = s % ST;
-                if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((s / ST) & 1), &abort_flag, kWaitNs)) {
+                if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((s / ST) & 1), &abort_flag, tp.wait_ns)) {
                     ok = false;
                     break;
                 }
                 if (first) {
                     b = (uint32_t)(g & 1);
                     if (g >= 2 && !mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)(((g >> 1) - 1) & 1), &abort_flag,
-                                             kWaitNs)) {
+                                             tp.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -230,6 +238,11 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
                 abort_flag = 1;
                 set_status(p.status, MTK_ETIMEOUT);
             }
+            // every MMA issued by this thread (and the barrier arrivals of its commits) has
+            // completed once fin_bar flips; this wait ignores the abort flag
+            mma_commit(smem_u32(&fin_bar));
+            volatile int never = 0;
+            (void)mbar_wait(smem_u32(&fin_bar), 0u, &never, kWaitNs);
         }
         __syncwarp();
     } else if (warp == CONV_WARPS + 1) {
@@ -249,14 +262,16 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
                         xr = k0 / L;
                     }
                 }
+                int issued = 0;
                 for (int s = 0; s < nst; ++s) {
                     const int slot = s % tp.P;
                     if (s >= tp.P &&
-                        !mbar_wait(smem_u32(&xempty_bar[slot]), (uint32_t)(((s / tp.P) - 1) & 1), &abort_flag, kWaitNs)) {
+                        !mbar_wait(smem_u32(&xempty_bar[slot]), (uint32_t)(((s / tp.P) - 1) & 1), &abort_flag, tp.wait_ns)) {
                         abort_flag = 1;
                         set_status(p.status, MTK_ETIMEOUT);
                         break;
                     }
+                    ++issued;
                     const uint32_t fb = smem_u32(&xfull_bar[slot]);
                     const uint32_t dst = stg0 + (uint32_t)slot * stg_bytes;
                     mbar_arrive_expect_tx(fb, bytes);
@@ -303,6 +318,12 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
                     }
                     ld_d0 += TC_BK;
                     if (ld_d0 == rad0p) { ld_d0 = 0; ++ld_qg; }
+                }
+                // the loads of the last P stages may still be in flight when another role has
+                // aborted: let them land before the CTA leaves (consumed phases return at once)
+                for (int s = issued > tp.P ? issued - tp.P : 0; s < issued; ++s) {
+                    volatile int never = 0;
+                    (void)mbar_wait(smem_u32(&xfull_bar[s % tp.P]), (uint32_t)((s / tp.P) & 1), &never, kWaitNs);
                 }
             }
         }
@@ -473,7 +494,7 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
             float4 v[2 * RPT];
             if constexpr (TMA) {
                 // the producer's boxes for stage s have landed
-                if (!mbar_wait(smem_u32(&xfull_bar[pslot]), (uint32_t)((s / tp.P) & 1), &abort_flag, kWaitNs)) {
+                if (!mbar_wait(smem_u32(&xfull_bar[pslot]), (uint32_t)((s / tp.P) & 1), &abort_flag, tp.wait_ns)) {
                     abort_flag = 1;
                     set_status(p.status, MTK_ETIMEOUT);
                     return false;
@@ -507,7 +528,7 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
                 }
             }
             if (s >= ST) {
-                if (!mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)(((s / ST) - 1) & 1), &abort_flag, kWaitNs)) {
+                if (!mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)(((s / ST) - 1) & 1), &abort_flag, tp.wait_ns)) {
                     abort_flag = 1;
                     set_status(p.status, MTK_ETIMEOUT);
                     return false;
@@ -519,6 +540,7 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
                 mbar_expect_tx(fb, (uint32_t)tp.b_bytes);
                 bulk_copy_g2s(smem_u32(st + tp.b_off), tp.bimg + (int64_t)pr_sir * tp.b_bytes,
                               (uint32_t)tp.b_bytes, fb);
+                *reinterpret_cast<volatile int*>(&b_issued) = s + 1;
             }
             if constexpr (TMA) {
 #pragma unroll
@@ -566,7 +588,7 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
         int64_t q_cached = -1;
         auto drain = [&](int g, int64_t qg) -> bool {
             const int b = g & 1;
-            if (!mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((g >> 1) & 1), &abort_flag, kWaitNs)) {
+            if (!mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((g >> 1) & 1), &abort_flag, tp.wait_ns)) {
                 abort_flag = 1;
                 set_status(p.status, MTK_ETIMEOUT);
                 return false;
@@ -615,8 +637,10 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
                 else asm volatile("cp.async.commit_group;" ::: "memory");
             }
         }
+        int arrived = 0;                                 // stages this warp has arrived on
         for (int s = 0; s < nst; ++s) {
             if (!produce(s)) { ok = false; break; }
+            ++arrived;
             const bool last = ((pr_sir + 1) % GROUP == 0) || (pr_sir + 1 == spr) || (s == nst - 1);
             const int64_t qg_s = pr_qg;
             if (++pr_sir == spr) { pr_sir = 0; ++pr_qg; }
@@ -630,6 +654,23 @@ contract_tc_kernel(const __grid_constant__ TcParams tp, const __grid_constant__ 
         }
         if (ok && pending) ok = drain(pend_g, pend_qg);
         asm volatile("cp.async.wait_all;" ::: "memory");
+        // Abort: the B-image copies already issued must land before the CTA leaves.  Each
+        // completes a full barrier that also counts one arrival per converter warp, so every
+        // warp first arrives for the issued stages it has not reached (at most ST of them,
+        // each the current phase of its slot: stage s was issued only after stage s - ST had
+        // been consumed), then the issuing thread waits for those phases.
+        asm volatile("bar.sync 1, %0;" ::"r"(CONV_THREADS) : "memory");
+        if (*reinterpret_cast<volatile int*>(&abort_flag)) {
+            const int nb = *reinterpret_cast<volatile int*>(&b_issued);
+            if (lane == 0)
+                for (int s = arrived; s < nb; ++s) mbar_arrive(smem_u32(&full_bar[s % ST]));
+            if (warp == 0 && lane == 0) {
+                for (int s = nb > ST ? nb - ST : 0; s < nb; ++s) {
+                    volatile int never = 0;
+                    (void)mbar_wait(smem_u32(&full_bar[s % ST]), (uint32_t)((s / ST) & 1), &never, kWaitNs);
+                }
+            }
+        }
 
         // ------------------------------------------------------------ epilogue
         // packed run offsets become separate partial slabs: slab = sp * U + u

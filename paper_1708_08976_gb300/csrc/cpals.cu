@@ -198,11 +198,12 @@ __global__ void sum_chunks_kernel(const double* __restrict__ part, int n, double
 }
 
 // r2 = ||X||^2 - 2 <M, U> + sum_{a,b} prod_k G_k(a,b)  (= ||X - [[U]]||^2 when M is the
-// MTTKRP of the mode U belongs to), fit = 1 - sqrt(max(0, r2)) / ||X||
+// MTTKRP of the mode U belongs to), fit = 1 - sqrt(max(0, r2)) / ||X||, and the loss
+// 0.5 r2 rounded to FP32
 __global__ void __launch_bounds__(256)
 residual_kernel(const double* __restrict__ normX2, const float* __restrict__ M,
                 const float* __restrict__ U, int64_t I, const __grid_constant__ GramList gl, int N,
-                int C, double* r2_out, double* fit) {
+                int C, double* r2_out, double* fit, float* loss) {
     __shared__ double red[256];
     double inner = 0.0;
     for (int64_t e = threadIdx.x; e < I * C; e += blockDim.x) inner += (double)M[e] * (double)U[e];
@@ -223,6 +224,7 @@ residual_kernel(const double* __restrict__ normX2, const float* __restrict__ M,
         const double r2 = nx2 + red[0];
         if (r2_out) *r2_out = r2;
         if (fit) *fit = 1.0 - sqrt(r2 > 0.0 ? r2 : 0.0) / sqrt(nx2);
+        if (loss) *loss = (float)(0.5 * r2);
     }
 }
 
@@ -294,7 +296,7 @@ cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const
     const double* Hinv = Hbuf + (size_t)C * C + C;
     const size_t smem = C <= 64 ? hbytes : 0;
     int64_t blocks = (In * C + 255) / 256;
-    int grid = (int)(blocks < 152 * 4 ? blocks : 152 * 4);
+    int grid = (int)(blocks < num_sms() * 4 ? blocks : num_sms() * 4);
     apply_inverse_kernel<<<grid, 256, smem, s>>>(Hinv, flag, M, In, C, Un);
     note_launches(1);
     return cudaGetLastError();
@@ -313,10 +315,10 @@ cudaError_t launch_norm2(const float* X, int64_t I, double* part, int nchunks, d
 
 cudaError_t launch_residual(const double* normX2, const float* M, const float* U, int64_t I,
                             const double* const* G, int N, int C, double* r2, double* fit,
-                            cudaStream_t s) {
+                            cudaStream_t s, float* loss) {
     GramList gl;
     for (int k = 0; k < MTK_MAXN; ++k) gl.G[k] = (k < N) ? G[k] : nullptr;
-    residual_kernel<<<1, 256, 0, s>>>(normX2, M, U, I, gl, N, C, r2, fit);
+    residual_kernel<<<1, 256, 0, s>>>(normX2, M, U, I, gl, N, C, r2, fit, loss);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -328,7 +330,7 @@ cudaError_t launch_gradient(const float* U, const float* M, const double* const*
     const size_t smem = (size_t)C * C * sizeof(double);
     cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int64_t blocks = (In * C + 255) / 256;
-    int grid = (int)(blocks < 152 * 4 ? blocks : 152 * 4);
+    int grid = (int)(blocks < num_sms() * 4 ? blocks : num_sms() * 4);
     gradient_kernel<<<grid, 256, smem, s>>>(U, M, gl, N, C, n, In, scale, grad);
     note_launches(1);
     return cudaGetLastError();

@@ -53,10 +53,14 @@ struct ContractParams {
     int64_t out_si, out_sc;
     float* part;           // S x I x C partials when S > 1
     uint32_t* status;
+    unsigned long long wait_ns;   // limit of the tensor-core kernels' abortable waits (0: 1 s)
+    int stall;             // test hook: one wait that nothing completes (the kernel times out)
 };
 
 // host-side count of kernel launches issued by the library (monotonic, atomic)
 void note_launches(int n);
+// streaming multiprocessors of the current device (queried once per process)
+int num_sms();
 
 // ---- launchers (host side), defined in the .cu files -------------------------
 cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,
@@ -106,10 +110,12 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
 size_t planes_scratch_bytes(const PlanesPlan& pl);   // image + Q table + partials
 int planes_ctas(int splits);           // CTAs of one launch (0 = one per SM)
 // scratch: planes_scratch_bytes(pl) bytes, 256-byte aligned
+// wait_ns: limit of the kernel's abortable waits (0: 1 s); stall: the timeout test hook
 cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int64_t I, int64_t R,
                                    const float* const* fac, const int64_t* frad, int nfac, int C,
                                    const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
-                                   void* scratch, uint32_t* status, cudaStream_t s);
+                                   void* scratch, uint32_t* status, cudaStream_t s,
+                                   unsigned long long wait_ns = 0, int stall = 0);
 
 // ---- batched MTTKRPs in one persistent launch (batched.cu) --------------------------
 typedef mtk_batch_problem BatchedProblem;
@@ -135,29 +141,26 @@ cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const
 cudaError_t launch_norm2(const float* X, int64_t I, double* part, int nchunks, double* out,
                          cudaStream_t s);
 int norm2_chunks(int64_t I);
+// loss (may be NULL): 0.5 r2 as FP32
 cudaError_t launch_residual(const double* normX2, const float* M, const float* U, int64_t I,
                             const double* const* G, int N, int C, double* r2, double* fit,
-                            cudaStream_t s);
+                            cudaStream_t s, float* loss = nullptr);
 // factor update of a CP-ALS step in one launch (als_update.cu), C <= 64: U_n = M H^{-1}
-// (FP64 L D L^T of H = Hadamard_{k != n} G_k) and the Gram of the new U_n:
-//   gmode 0: none; 1: per-CTA partials only, in buffer `parity` of the scratch, reduced by
-//   the next update (prevP = this launch's CTA count, nprev = n, the other parity), whose
-//   CTA 0 writes G_nprev to Gprev; 2: G_n written to Gn, and the fit when normX2 is given.
-// Tickets (gmode 2): als_ticket_bytes() of zeros, left at zero.  programmatic: launched with
-// programmatic stream serialisation (the factorisation may run while the previous kernel
-// of the stream runs; M is read after that kernel completed).
+// with H = Hadamard_{k != n} G_k (FP64 L D L^T and H^{-1}, formed before the kernel waits
+// for M), and with Gn given the Gram of the new U_n, reduced in a fixed order and written
+// to Gn, then with normX2 (and fit / r2) the fit.  Tickets: als_ticket_bytes() of zeros,
+// left at zero.  programmatic: launched with programmatic stream serialisation (H and its
+// inverse are formed while the previous kernel of the stream runs; M is read after that
+// kernel completed).
 struct AlsUpdateArgs {
     const double* const* G;
     int N, C, n;
     const float* M;
     int64_t In;
     float* Un;
-    int gmode;
     double* Gn;
     void* scratch;
-    int Pmax, parity;
-    int prevP, nprev;
-    double* Gprev;
+    int Pmax;
     unsigned int* tickets;
     const double* normX2;
     double* fit;

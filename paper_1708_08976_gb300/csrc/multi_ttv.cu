@@ -69,12 +69,12 @@ cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, co
     if (right) {
         const int64_t nw = I * C;
         int64_t blocks = (nw + 7) / 8;
-        int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+        int grid = (int)(blocks < num_sms() * 16 ? blocks : num_sms() * 16);
         multi_ttv_right_kernel<<<grid, 256, 0, s>>>(T, L, I, Ko, C, M);
         note_launches(1);
     } else {
         const int64_t blocks = (I + 31) / 32 * C;
-        int grid = (int)(blocks < 152 * 8 ? blocks : 152 * 8);
+        int grid = (int)(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
         multi_ttv_left_kernel<<<grid, 256, 0, s>>>(T, I, R, Ko, C, M);
         note_launches(1);
     }

@@ -101,6 +101,49 @@ def test_khatri_rao(Z, reuse):
         np.testing.assert_allclose(got, ref, rtol=4e-7, atol=1e-30)
 
 
+KRP_SHAPES = [
+    ((7, 5, 3, 2, 3), 3),         # Z = 5: the generic naive kernel
+    ((3, 2, 2, 3, 2, 5), 5),      # Z = 6
+    ((4099,), 25),                # Z = 1 (a copy): several tiles, a ragged last group
+    ((1, 4097), 7),               # a one-row operand first
+    ((37, 113, 5), 50),           # C = 50: two 16-byte words per lane in some rows
+    ((300, 301), 1),              # C = 1: four rows per 16-byte word
+    ((2, 3), 33),                 # C > 32: lanes take two words
+    ((61, 1, 59), 25),            # a one-row operand inside
+]
+
+
+@pytest.mark.parametrize("rows,C", KRP_SHAPES)
+@pytest.mark.parametrize("reuse", [True, False])
+def test_khatri_rao_shapes(rows, C, reuse):
+    """Row rule of Section 2.1 (oracle, no reuse) against both kernels: tiles of rows,
+    groups of four rows written as 16-byte words, ragged last groups, Z up to 6."""
+    g = np.random.default_rng(sum(rows) + C)
+    U = [g.standard_normal((r, C)) for r in rows]
+    Ur = f32_round(U)
+    ref = oracle.krp(Ur)
+    got = mtk.khatri_rao(factors_dev(U, torch), reuse=reuse).cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, ref, rtol=4e-7, atol=1e-30)
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_khatri_rao_unaligned_output(reuse):
+    """An output that starts 4 bytes past a 16-byte boundary takes the scalar stores;
+    the floats around it are left as they were."""
+    g = np.random.default_rng(77)
+    rows, C = (45, 23), 25
+    U = [g.standard_normal((r, C)) for r in rows]
+    ref = oracle.krp(f32_round(U))
+    J = rows[0] * rows[1]
+    buf = torch.full((J * C + 2,), 7.0, dtype=torch.float32, device="cuda")
+    out = buf[1:1 + J * C].view(J, C)
+    assert out.data_ptr() % 16 != 0
+    mtk.khatri_rao(factors_dev(U, torch), reuse=reuse, out=out)
+    got = buf.cpu().numpy()
+    assert got[0] == 7.0 and got[-1] == 7.0
+    np.testing.assert_allclose(got[1:-1].reshape(J, C).astype(np.float64), ref, rtol=4e-7, atol=1e-30)
+
+
 def test_khatri_rao_hand_example():
     import json, os
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")))
