@@ -66,6 +66,7 @@ constexpr bool PS_LO_SEP = MTK_PS_LO_SEP != 0;
 constexpr int PS_MAX_A = 8;
 constexpr int PS_MAX_B = 6;
 constexpr int PS_MAX_BUF = 4;
+constexpr int PS_MAX_U = 32;                 // packed run groups per tile (256 rows / 8)
 constexpr int PS_TILE = PS_M * 128;          // one plane of a 128 x 64 BF16 tile (16 KB)
 constexpr int PS_MN_ATOM = 64 * 128;         // MN-major: 64 k rows x 64 i (8 KB)
 constexpr unsigned long long kPsWaitNs = 1000000000ull;
@@ -99,7 +100,14 @@ struct PsParams {
     int64_t H;              // head rows (the last chunk of a run holds H - 64 (spr - 1) of them)
     int spr;                // stages per run (H padded to a multiple of 64, / 64)
     int U, BI, MT;          // packed runs, rows per run group (tile rows), 128-row MMA tiles
-    int ldims;              // K-major tensor map rank: 5 (h, lq, i, r, plane) or 4 (h, i, r, plane)
+    int P;                  // K-major: row classes i mod P, P = 8 / gcd(I^L, 8) (1: aligned rows)
+    int64_t Ic;             // rows per class, I / P
+    int ntc;                // tiles per class (ntiles = P * ntc)
+    int64_t L;              // I^L (K-major)
+    int nsh;                // head images: 1, or 8 shifted ones when run starts are not 16-byte aligned
+    int box_mode;           // packed runs (U > 1): 0 one TMA box per run group; 1 one box for all U
+                            // groups, runs along r (rows grouped by run); 2 one box, runs along lq
+                            // (rows interleaved: tile row m = U i + u)
     int C, CP, N;           // N = 3 CP columns of the hi-plane accumulator
     int lo_sep;             // the lo plane accumulates into its own 2 CP columns (one MMA tile)
     int acc_cols;           // TMEM columns per accumulator buffer
@@ -127,8 +135,8 @@ struct PsParams {
 // is at most one CTA per SM, so a view with more units than that runs them back to back
 // in each CTA with the rings, barriers and TMEM kept from one unit to the next.
 struct PsUnit {
-    int tile, sp, nst;
-    int64_t t0, i0;
+    int tile, sp, nst, rho;
+    int64_t t0, i0;         // first stage; first row of the tile within its class (rows rho + P (i0 + m))
 };
 
 __device__ __forceinline__ int ps_units(const PsParams& p) { return (p.ntiles - 1) * p.s_full + p.s_last; }
@@ -147,7 +155,8 @@ __device__ __forceinline__ PsUnit ps_unit(const PsParams& p, int b) {
     }
     u.t0 = p.stot * u.sp / S_t;
     u.nst = (int)(p.stot * (u.sp + 1) / S_t - u.t0);
-    u.i0 = (int64_t)u.tile * p.BI;
+    u.rho = u.tile / p.ntc;
+    u.i0 = (int64_t)(u.tile - u.rho * p.ntc) * p.BI;
     return u;
 }
 
@@ -210,7 +219,13 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             int64_t sr = 0;
             int j = 0;
             int ng = 0;
-            int glq[16], gr[16];
+            // K-major: group g of the super-run loads rows rho + P (i0 + m) of run q = (lq, r)
+            // as rows y = i0 + m + Ic r of the super-row view, from column x = H lq + I^L rho
+            // + 64 j - delta, delta = (H lq + I^L rho) mod 8 (the image of the stage is the
+            // head shifted by delta, so x is a multiple of 8: a 16-byte aligned start)
+            int gx[PS_MAX_U], gy[PS_MAX_U];
+            int rho = 0;
+            int64_t i0 = 0;
             auto set_groups = [&]() {
                 ng = 0;
                 while (ng < U && sr * U + ng < nruns) ++ng;
@@ -219,8 +234,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     for (int g = 0; g < ng; ++g) {
                         const uint32_t q = (uint32_t)(sr * U + g);
                         const uint32_t r = q / Lq;
-                        glq[g] = (int)(q - r * Lq);
-                        gr[g] = (int)r;
+                        const int64_t base = p.H * (int64_t)(q - r * Lq) + p.L * rho;
+                        const int64_t dlt = p.nsh > 1 ? (base & 7) : 0;
+                        gx[g] = (int)(base - dlt);
+                        gy[g] = (int)(i0 + p.Ic * (int64_t)r);
                     }
                 }
             };
@@ -228,7 +245,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             uint32_t ph = 1;                                 // parity of the empty phase to wait for
             for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
                 const PsUnit w = ps_unit(p, ub);
-                const int64_t i0 = w.i0;
+                i0 = w.i0;
+                rho = w.rho;
                 sr = w.t0 / spr;
                 j = (int)(w.t0 - sr * spr);
                 set_groups();
@@ -243,10 +261,30 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     const uint32_t st = dsm_s + (uint32_t)(slot * p.a_stage);
                     const uint32_t fb = smem_u32(&afull[slot]);
                     uint32_t bytes;
-                    if (MN) bytes = (uint32_t)(2 * (U == 1 ? nbox : ng) * PS_MN_ATOM);
-                    else bytes = (uint32_t)(2 * ng * BI * 128);
+                    if (MN) bytes = (uint32_t)(2 * (U == 1 ? nbox : (p.box_mode ? U : ng)) * PS_MN_ATOM);
+                    else bytes = (uint32_t)(2 * (p.box_mode ? U : ng) * BI * 128);
                     mbar_arrive_expect_tx(fb, bytes);
-                    for (int g = 0; g < ng; ++g) {
+                    if (p.box_mode) {
+                        // one box holds every packed run of the super-run (a run beyond the
+                        // last reads the zero fill)
+                        const int q0 = (int)(sr * U);
+#pragma unroll
+                        for (int pl = 0; pl < 2; ++pl) {
+                            const uint32_t dst = st + (uint32_t)(pl * p.plane_bytes);
+                            if (MN) {
+                                tma_load_4d(dst, &xmap, 0, 64 * j, q0, pl, fb);
+                            } else if (p.box_mode == 1) {
+                                // one run per row (q = r): the class offset and its shift
+                                const int64_t base = p.L * rho;
+                                const int x0 = (int)(base - (p.nsh > 1 ? (base & 7) : 0));
+                                tma_load_4d(dst, &xmap, x0 + 64 * j, (int)i0, q0, pl, fb);
+                            } else {
+                                const int r = q0 / (int)p.Lq;
+                                tma_load_5d(dst, &xmap, 64 * j, q0 - r * (int)p.Lq, (int)i0, r, pl, fb);
+                            }
+                        }
+                    }
+                    for (int g = 0; !p.box_mode && g < ng; ++g) {
 #pragma unroll
                         for (int pl = 0; pl < 2; ++pl) {
                             const uint32_t dst = st + (uint32_t)(pl * p.plane_bytes);
@@ -260,9 +298,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                                     tma_load_4d(dst + (uint32_t)(g * PS_MN_ATOM), &xmap, 0, 64 * j, q, pl, fb);
                                 }
                             } else {
-                                const uint32_t d = dst + (uint32_t)(g * BI * 128);
-                                if (p.ldims == 5) tma_load_5d(d, &xmap, 64 * j, glq[g], (int)i0, gr[g], pl, fb);
-                                else tma_load_4d(d, &xmap, 64 * j, (int)i0, gr[g], pl, fb);
+                                tma_load_3d(dst + (uint32_t)(g * BI * 128), &xmap, gx[g] + 64 * j, gy[g], pl, fb);
                             }
                         }
                     }
@@ -300,7 +336,16 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             uint32_t ph = 1;
             for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
                 const PsUnit w = ps_unit(p, ub);
-                int j = (int)(w.t0 % spr);
+                int64_t sr = w.t0 / spr;
+                int j = (int)(w.t0 - sr * spr);
+                // first slice of the super-run's image: the head shifted by the run's delta
+                // (every packed run of a super-run has the same delta)
+                auto image_base = [&]() -> int64_t {
+                    if (p.nsh == 1) return 0;
+                    const int64_t lq = (sr * U) % p.Lq;
+                    return ((p.H * lq + p.L * w.rho) & 7) * (int64_t)spr;
+                };
+                int64_t ib = image_base();
                 for (int s = 0; s < w.nst; ++s) {
                     if (issued >= SB && !mbar_wait(smem_u32(&bempty[slot]), ph, &abort_flag, p.wait_ns)) {
                         ok = false;
@@ -309,13 +354,17 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     const uint32_t fb = smem_u32(&bfull[slot]);
                     mbar_arrive_expect_tx(fb, (uint32_t)p.b_bytes);
                     bulk_copy_g2s(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage),
-                                  p.bimg + (int64_t)j * p.b_bytes, (uint32_t)p.b_bytes, fb);
+                                  p.bimg + (ib + j) * p.b_bytes, (uint32_t)p.b_bytes, fb);
                     ++issued;
                     if (++slot == SB) {
                         slot = 0;
                         ph ^= 1u;
                     }
-                    if (++j == spr) j = 0;
+                    if (++j == spr) {
+                        j = 0;
+                        ++sr;
+                        ib = image_base();
+                    }
                 }
             }
             if (!ok) {
@@ -343,7 +392,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             const uint32_t idh = p.idesc_hi, idl = p.idesc_lo;
             const uint32_t ncol = (uint32_t)p.N;
             // k-steps of the last chunk of a run that hold head rows (the rest is padding)
-            const int64_t tail_rows = p.H - (int64_t)PS_BK * (spr - 1);
+            // (with shifted images the real rows of a chunk depend on the shift: all k-steps)
+            const int64_t tail_rows = p.nsh > 1 ? PS_BK : p.H - (int64_t)PS_BK * (spr - 1);
             const int kk_last = (int)((tail_rows + 15) / 16);
             int g = 0, gs = 0;                               // accumulation groups (all units)
             int sa = 0, sb = 0, bi = 0;
@@ -443,8 +493,9 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
         const int sub = warp & 3;                    // TMEM sub-partition of this warp
         const int mt = dw >> 2;                      // MMA tile
         const int row = mt * 128 + sub * 32 + lane;  // row of the CTA tile = TMEM lane of tile mt
-        const int myg = U > 1 ? row / BI : 0;
-        const int myil = U > 1 ? row % BI : row;
+        const bool ilv = p.box_mode == 2;
+        const int myg = U > 1 ? (ilv ? row % U : row / BI) : 0;
+        const int myil = U > 1 ? (ilv ? row / U : row % BI) : row;
         const int C = p.C, CP = p.CP;
         float acc[16 * NCH], qc[16 * NCH];
         int g = 0, gs = 0;
@@ -455,7 +506,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             const PsUnit w = ps_unit(p, ub);
             const int64_t i0 = w.i0;
             const int nst = w.nst;
-            const int64_t rows_here = (I - i0) < BI ? (I - i0) : BI;
+            const int64_t rows_here = (p.Ic - i0) < BI ? (p.Ic - i0) : BI;
             const bool rowvalid = myg < U && myil < rows_here;
 #pragma unroll
             for (int e = 0; e < 16 * NCH; ++e) {
@@ -564,7 +615,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 }
             }
             if (ok && rowvalid) {
-                const int64_t i = i0 + myil;
+                const int64_t i = w.rho + (int64_t)p.P * (i0 + myil);
                 if (p.nslab == 1) {
 #pragma unroll
                     for (int e = 0; e < 16 * NCH; ++e)
@@ -598,9 +649,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
 }
 
 // ---- per-call preparation: the B image of the head and the table of tail scales ----
-// Image slice j (one 64-k stage) is the 128-byte-swizzled K-major shared-memory image of
-// the N = 3 CP rows n = piece * CP + c, row n holding piece `piece` of Hd(64 j + d, c),
-// d = 0..63 (zero beyond the head's H rows and for c >= C).  Pieces: w0 = bf16_rn(w),
+// Image slice (sh, j) (one 64-k stage) is the 128-byte-swizzled K-major shared-memory
+// image of the N = 3 CP rows n = piece * CP + c, row n holding piece `piece` of
+// Hd(64 j - sh + d, c), d = 0..63 (zero outside the head's H rows and for c >= C); shift
+// sh = 0 only, or sh = 0..7 (slices sh * spr + j) when runs start at any element.  Pieces: w0 = bf16_rn(w),
 // w1 = bf16_rn(w - w0), w2 = bf16_rn(w - w0 - w1).  Q(q, c) = prod over the tail
 // factors of their rows at the digits of q (first tail factor fastest), 0 for c >= C.
 struct PrepArgs {
@@ -608,6 +660,7 @@ struct PrepArgs {
     const float* fac[MTK_MAXN];
     int64_t frad[MTK_MAXN];
     int64_t H, Hp;
+    int nsh;
     uint8_t* img;
     int ntail;
     const float* tail[MTK_MAXN];
@@ -624,15 +677,19 @@ __device__ __forceinline__ void split3(float w, __nv_bfloat16& a, __nv_bfloat16&
 }
 
 __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant__ PrepArgs a) {
-    const int64_t n_img = (a.Hp / 8) * a.CP;
+    const int64_t octs = a.Hp / 8;                         // octets of one shifted image
+    const int64_t n_img = a.nsh * octs * a.CP;
     const int64_t n_q = a.qtab ? a.nruns * a.CP : 0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_img + n_q;
          it += (int64_t)gridDim.x * blockDim.x) {
         if (it < n_img) {
             const int c = (int)(it % a.CP);
-            const int64_t k0 = (it / a.CP) * 8;             // first head row of this octet
+            const int64_t ro = it / a.CP;
+            const int sh = (int)(ro / octs);
+            const int64_t k0 = (ro - (int64_t)sh * octs) * 8;   // first position of this octet
+            const int64_t h0 = k0 - sh;                         // its head row (may be < 0)
             int64_t dig[MTK_MAXN];
-            int64_t rem = k0;
+            int64_t rem = h0 < 0 ? 0 : h0;
             for (int z = 0; z < a.head; ++z) {
                 const int64_t nq = rem / a.frad[z];
                 dig[z] = rem - nq * a.frad[z];
@@ -641,18 +698,21 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
             __nv_bfloat16 pc[3][8];
 #pragma unroll
             for (int d = 0; d < 8; ++d) {
+                const int64_t h = h0 + d;
                 float w = 0.0f;
-                if (k0 + d < a.H && c < a.C) {
+                if (h >= 0 && h < a.H && c < a.C) {
                     w = 1.0f;
                     for (int z = 0; z < a.head; ++z) w *= __ldg(a.fac[z] + dig[z] * a.C + c);
                 }
                 split3(w, pc[0][d], pc[1][d], pc[2][d]);
-                for (int z = 0; z < a.head; ++z) {           // next row: mixed-radix increment
-                    if (++dig[z] < a.frad[z]) break;
-                    dig[z] = 0;
+                if (h >= 0) {
+                    for (int z = 0; z < a.head; ++z) {       // next row: mixed-radix increment
+                        if (++dig[z] < a.frad[z]) break;
+                        dig[z] = 0;
+                    }
                 }
             }
-            const int64_t slice = k0 / PS_BK;
+            const int64_t slice = (int64_t)sh * (a.Hp / PS_BK) + k0 / PS_BK;
             const int oct = (int)((k0 % PS_BK) / 8);
             uint8_t* base = a.img + slice * (int64_t)(a.N * 128);
 #pragma unroll
@@ -695,8 +755,8 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
 // and up to 32 warps, so that enough loads are in flight.
 template <int Q>
 __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI,
-                                                             int U, int ntiles, int s_full, int s_last,
-                                                             float* __restrict__ out, int colmajor, int vec,
+                                                             int U, int ntiles, int s_full, int s_last, int P,
+                                                             int ntc, float* __restrict__ out, int colmajor, int vec,
                                                              const uint32_t* status) {
     allow_dependent_launch();
     // a contraction that timed out left its slabs incomplete: the output stays as it was
@@ -708,7 +768,7 @@ __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __rest
     const int64_t f0 = ((int64_t)blockIdx.x * 32 + lane) * Q;
     auto slabs = [&](int64_t f) {
         const int64_t i = colmajor ? f % I : f / C;
-        const int64_t tile = i / BI;
+        const int64_t tile = (i % P) * ntc + (i / P) / BI;        // row i = rho + P t
         return (tile < ntiles - 1 ? s_full : s_last) * U;
     };
     float v[Q];
@@ -905,31 +965,42 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     if (C < 1 || C > 64 || nfac < 1) return pl;
     const int64_t lim = ((int64_t)1 << 31) - 1;
     const bool mn = (L == 1);
+    // K-major rows (i, r) start at element I^L (i + I_n r).  When I^L is not a multiple of
+    // 8 they are not 16-byte aligned; rows in one class i mod P (P = 8 / gcd(I^L, 8)) are
+    // I^L P elements apart, a multiple of 8, so a class is loaded as rows of the view with
+    // that pitch ("super-rows" of P rows).  That view covers every r-slice alike when P
+    // divides I_n (taken); otherwise not (yet).
+    int P = 1;
     if (mn) {
         if (I % 8 != 0) return pl;
     } else {
-        if (L % 8 != 0 || n_left < 1) return pl;
+        if (n_left < 1) return pl;
+        P = (L % 8 == 0) ? 1 : (L % 4 == 0) ? 2 : (L % 2 == 0) ? 4 : 8;
+        if (I % P != 0) return pl;
+        if (P * L > lim) return pl;                    // columns of the super-row view are int
     }
     int64_t K = 1;
     for (int z = 0; z < nfac; ++z) K *= frad[z];
     pl.CP = (C + 15) & ~15;
     pl.N = 3 * pl.CP;
-    // head: a prefix of the factor list (K-major: within the modes left of n).  The
-    // first prefix with >= 64 rows and <= 1/32 padding, else the least padding; its
-    // image must stay L2-resident and, when further left modes follow it, its rows must
-    // be a multiple of 8 (16-byte stride of the plane's tensor map).
+    // head: a prefix of the factor list (K-major: within the modes left of n).  A run of
+    // the head starts at an element whose alignment may vary (class offset I^L rho, run
+    // offset H lq): then the image is kept for all 8 shifts, and each stage takes the one
+    // that moves its first element to a 16-byte boundary.  The first prefix with >= 64
+    // rows and <= 1/32 padding, else the least padding, among those whose images stay
+    // L2-resident.
     const int mmax = mn ? nfac : n_left;
     int best = -1;
     double best_waste = 2.0;
     int64_t prod = 1;
     for (int m = 1; m <= mmax; ++m) {
         prod *= frad[m - 1];
-        const int64_t padded = round_up(prod, PS_BK);
-        const size_t img = (size_t)(padded / PS_BK) * pl.N * 128;
+        const int nsh = (mn || (P == 1 && (L / prod == 1 || prod % 8 == 0))) ? 1 : 8;
+        const int64_t padded = round_up(prod + (nsh > 1 ? 7 : 0), PS_BK);
+        const size_t img = (size_t)nsh * (size_t)(padded / PS_BK) * pl.N * 128;
         if (img > ((size_t)32 << 20)) break;
-        if (!mn && m < n_left && prod % 8 != 0) continue;
         const double waste = (double)(padded - prod) / (double)padded;
-        if (prod >= PS_BK && (padded - prod) * 32 <= prod) { best = m; break; }
+        if (prod >= PS_BK && (padded - prod) * 32 <= padded) { best = m; break; }
         if (waste < best_waste) { best_waste = waste; best = m; }
     }
     if (best < 0) return pl;
@@ -937,11 +1008,18 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     for (int z = 0; z < best; ++z) H *= frad[z];
     pl.head = best;
     pl.H = H;
-    pl.spr = (int)(round_up(H, PS_BK) / PS_BK);
-    pl.nruns = K / H;
     pl.Lq = mn ? 1 : L / H;
-    if (H > lim || pl.nruns > lim || I > lim || (!mn && (K / L) > lim)) return pl;
+    pl.nsh = (mn || (P == 1 && (pl.Lq == 1 || H % 8 == 0))) ? 1 : 8;
+    pl.spr = (int)(round_up(H + (pl.nsh > 1 ? 7 : 0), PS_BK) / PS_BK);
+    pl.nruns = K / H;
+    pl.P = P;
+    pl.Ic = I / P;
+    if (H > lim || pl.nruns > lim || I > lim || (!mn && (K / L) > lim) || (!mn && pl.Ic * (K / L) > lim)) return pl;
     pl.mn = mn ? 1 : 0;
+    // packed runs share the stage's image: with shifted images only when every run of a
+    // class has the same shift (I^L rho mod 8: one run per class row, or H a multiple of 8)
+    const int64_t maxU = (pl.nsh > 1 && !(pl.Lq == 1 || H % 8 == 0)) ? 1 : pl.nruns;
+    const int64_t Ic = pl.Ic;
     // Rows of a CTA tile: up to 256 (two 128-row MMA tiles).  Each stage has a fixed cost
     // besides its bytes, so the tiling carries as many rows per stage as it can: BI rows of
     // i per run group and, when BI <= 128, U run groups of the head (different runs q,
@@ -957,6 +1035,7 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
             pl.U = (int)(pl.nruns < 4 ? pl.nruns : 4);
             pl.MT = pl.U > 2 ? 2 : 1;
             pl.ntiles = 1;
+            pl.box_mode = pl.U > 1 ? 1 : 0;           // the runs' 64-row boxes in one load
         } else {
             pl.U = 1;
             pl.MT = I > PS_M ? 2 : 1;
@@ -964,20 +1043,20 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
             pl.ntiles = (int)((I + pl.BI - 1) / pl.BI);
         }
     } else {
-        const int64_t t0 = (I + 2 * PS_M - 1) / (2 * PS_M);
-        int64_t best_bi = round_up((I + t0 - 1) / t0, 8), best_u = 1;
+        const int64_t t0 = (Ic + 2 * PS_M - 1) / (2 * PS_M);
+        int64_t best_bi = round_up((Ic + t0 - 1) / t0, 8), best_u = 1;
         if (best_bi <= PS_M) {
             best_u = (2 * PS_M) / best_bi;
-            if (best_u > pl.nruns) best_u = pl.nruns;
+            if (best_u > maxU) best_u = maxU;
         }
         int64_t best_rows = best_u * best_bi;
         if (best_rows * 4 < 3 * 2 * PS_M) {
-            for (int64_t t = t0 + 1; t <= t0 + 64 && t <= (I + 7) / 8; ++t) {
-                const int64_t bi = round_up((I + t - 1) / t, 8);
+            for (int64_t t = t0 + 1; t <= t0 + 64 && t <= (Ic + 7) / 8; ++t) {
+                const int64_t bi = round_up((Ic + t - 1) / t, 8);
                 int64_t u = 1;
                 if (bi <= PS_M) {
                     u = (2 * PS_M) / bi;
-                    if (u > pl.nruns) u = pl.nruns;
+                    if (u > maxU) u = maxU;
                 }
                 if (u * bi * 8 > best_rows * 9) {
                     best_rows = u * bi;
@@ -986,11 +1065,30 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
                 }
             }
         }
+        // packed runs in one TMA box when they lie at one stride: consecutive r (one run per
+        // row) or consecutive lq of the same r (a head of a multiple of 8 rows, U dividing
+        // the runs per row; U is lowered to a divisor when that keeps at least half of it)
+        if (best_u > 1 && pl.Lq == 1) {
+            pl.box_mode = 1;
+        } else if (best_u > 1 && P == 1 && pl.nsh == 1) {
+            if (H % 8 == 0) {
+                int64_t u = best_u;
+                while (u > 1 && pl.Lq % u != 0) --u;
+                if (2 * u >= best_u) {
+                    best_u = u;
+                    best_rows = u * best_bi;
+                    pl.box_mode = 2;
+                }
+            }
+        }
         pl.BI = (int)best_bi;
         pl.U = (int)best_u;
+        if (pl.U > PS_MAX_U) return pl;
         pl.MT = best_rows > PS_M ? 2 : 1;
-        pl.ntiles = (int)((I + pl.BI - 1) / pl.BI);
+        pl.ntc = (int)((Ic + pl.BI - 1) / pl.BI);
+        pl.ntiles = P * pl.ntc;
     }
+    if (mn) pl.ntc = pl.ntiles;
     pl.stot = ((pl.nruns + pl.U - 1) / pl.U) * pl.spr;
     // CTAs per tile, proportional to the rows each tile reads; at least 4 stages each
     const int T = pl.ntiles;
@@ -1029,7 +1127,7 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     pl.grid = (T - 1) * pl.s_full + pl.s_last;          // units; at most ctas CTAs run them
     if (pl.grid > ctas) pl.grid = ctas;
     pl.nslab = (pl.s_full > pl.s_last ? pl.s_full : pl.s_last) * pl.U;
-    pl.image_bytes = (size_t)pl.spr * pl.N * 128;
+    pl.image_bytes = (size_t)pl.nsh * pl.spr * pl.N * 128;
     // table of tail scales Q(q, c) when it is small
     const size_t qbytes = (size_t)pl.nruns * pl.CP * sizeof(float);
     pl.qtab_bytes = (nfac > best && qbytes <= ((size_t)32 << 20)) ? qbytes : 0;
@@ -1069,6 +1167,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     }
     pa.H = pl.H;
     pa.Hp = (int64_t)pl.spr * PS_BK;
+    pa.nsh = pl.nsh;
     pa.img = image;
     pa.ntail = nfac - pl.head;
     for (int z = pl.head; z < nfac; ++z) {
@@ -1078,7 +1177,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     pa.nruns = pl.nruns;
     pa.qtab = qtab;
     {
-        const int64_t items = (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * pl.CP : 0);
+        const int64_t items = pl.nsh * (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * pl.CP : 0);
         int64_t blocks = (items + 255) / 256;
         if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         planes_prep_kernel<<<(int)blocks, 256, 0, s>>>(pa);
@@ -1094,28 +1193,40 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     memset(&map, 0, sizeof(map));
     CUresult r;
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    int ldims = 4;
     if (pl.mn) {
         const cuuint64_t dims[4] = {(cuuint64_t)I, (cuuint64_t)pl.H, (cuuint64_t)pl.nruns, 2};
         const cuuint64_t strides[3] = {(cuuint64_t)I * 2, (cuuint64_t)I * pl.H * 2, (cuuint64_t)pitch * 2};
-        const cuuint32_t box[4] = {64, 64, 1, 1};
+        const cuuint32_t box[4] = {64, 64, (cuuint32_t)(pl.box_mode ? pl.U : 1), 1};
         r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Xs), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_MN_PROMO),
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    } else if (pl.Lq > 1) {
-        ldims = 5;
+    } else if (pl.box_mode == 1) {
+        // packed runs along r (one run per row): (super-row column, class row, r, plane),
+        // box (64, BI, U)
+        const cuuint64_t dims[4] = {(cuuint64_t)(pl.P * L), (cuuint64_t)pl.Ic, (cuuint64_t)R, 2};
+        const cuuint64_t strides[3] = {(cuuint64_t)(pl.P * L) * 2, (cuuint64_t)L * I * 2, (cuuint64_t)pitch * 2};
+        const cuuint32_t box[4] = {64, (cuuint32_t)pl.BI, (cuuint32_t)pl.U, 1};
+        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Xs), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else if (pl.box_mode == 2) {
+        // packed runs along lq: (h, lq, i, r, plane), box (64, U, BI)
         const cuuint64_t dims[5] = {(cuuint64_t)pl.H, (cuuint64_t)pl.Lq, (cuuint64_t)I, (cuuint64_t)R, 2};
         const cuuint64_t strides[4] = {(cuuint64_t)pl.H * 2, (cuuint64_t)L * 2, (cuuint64_t)L * I * 2,
                                        (cuuint64_t)pitch * 2};
-        const cuuint32_t box[5] = {64, 1, (cuuint32_t)pl.BI, 1, 1};
+        const cuuint32_t box[5] = {64, (cuuint32_t)pl.U, (cuuint32_t)pl.BI, 1, 1};
         r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(Xs), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
-        const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)I, (cuuint64_t)R, 2};
-        const cuuint64_t strides[3] = {(cuuint64_t)L * 2, (cuuint64_t)L * I * 2, (cuuint64_t)pitch * 2};
-        const cuuint32_t box[4] = {64, (cuuint32_t)pl.BI, 1, 1};
-        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Xs), dims, strides, box, es,
+        // K-major: super-rows of P consecutive rows (i, r) (I^L P elements, a multiple of 8),
+        // one column per element of the super-row; both planes
+        const int64_t Sw = pl.P * L;
+        const int64_t Y = (I / pl.P) * R;
+        const cuuint64_t dims[3] = {(cuuint64_t)Sw, (cuuint64_t)Y, 2};
+        const cuuint64_t strides[2] = {(cuuint64_t)Sw * 2, (cuuint64_t)pitch * 2};
+        const cuuint32_t box[3] = {64, (cuuint32_t)pl.BI, 1};
+        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(Xs), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
@@ -1133,7 +1244,12 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     p.U = pl.U;
     p.BI = pl.BI;
     p.MT = pl.MT;
-    p.ldims = ldims;
+    p.P = pl.P;
+    p.Ic = pl.Ic;
+    p.ntc = pl.ntc;
+    p.L = L;
+    p.nsh = pl.nsh;
+    p.box_mode = pl.box_mode;
     p.C = C;
     p.CP = pl.CP;
     p.N = pl.N;
@@ -1218,11 +1334,11 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
         if (n >= 65536) {
             const int W = pl.nslab < 8 ? pl.nslab : 8;
             planes_reduce_kernel<4><<<(unsigned)((n + 127) / 128), 32 * W, 0, s>>>(
-                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, vec, status);
+                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, pl.P, pl.ntc, out, p.part_cm, vec, status);
         } else {
             const int W = pl.nslab < 32 ? pl.nslab : 32;
             planes_reduce_kernel<1><<<(unsigned)((n + 31) / 32), 32 * W, 0, s>>>(
-                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, out, p.part_cm, 0, status);
+                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, pl.P, pl.ntc, out, p.part_cm, 0, status);
         }
         note_launches(1);
         e = cudaGetLastError();

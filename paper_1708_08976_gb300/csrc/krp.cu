@@ -5,24 +5,24 @@
 // J_{Z-1} rows that share one "prefix" (a_0..a_{Z-2}) form one contiguous run
 // of J_{Z-1}*C floats.
 //
-// Parallel variant (Section 4.1.2): each CTA owns a tile of consecutive rows.  It
-// first forms, once per tile, the prefix products P(p, :) = U_0(a_0,:) * ... *
-// U_{Z-2}(a_{Z-2},:) of the prefixes the tile touches and keeps them in shared
-// memory (the partial Hadamard products that Algorithm 1 keeps in its matrix P),
-// then streams the tile's rows as K(j, :) = P(p, :) * U_{Z-1}(a_{Z-1}, :): one
-// multiply per output entry, the prefix work amortised over the J_{Z-1} rows that
-// share it.
+// Parallel variant (Section 4.1.2): every warp owns a contiguous range of rows and
+// writes them four at a time (4 C floats, a whole number of 16-byte words): lane q
+// stores word q of each group of four rows with one 16-byte store.  The row and column
+// of each of the lane's four floats are therefore fixed, and from one group to the next
+// the lane's rows move by 4: their last-operand index advances by a counter, and the
+// prefix product P(p, c) = U_0(a_0, c) * ... * U_{Z-2}(a_{Z-2}, c) that Algorithm 1
+// keeps is held in a register per float, formed again only when the float's row enters
+// a new prefix (every J_{Z-1} rows).  Each entry then costs one load of U_{Z-1} and one
+// multiply: the prefix work is shared by the J_{Z-1} rows of a run.  The kernel is bound
+// by the HBM write of K.
 //
-// The kernel is bound by the HBM write of K.  A warp writes four consecutive rows
-// (4 C floats, a whole number of 16-byte words) per step: lane q stores word q of the
-// four rows with one 16-byte store, so every store instruction covers one contiguous
-// run of the output.  Which row and column each of the lane's four floats belongs to
-// is fixed for the lane; the rows' (prefix, last index) pairs advance by counters, so
-// the streaming loop has no integer division.  An output that is not 16-byte aligned
-// takes the same loop with scalar stores.
+// The naive comparator (Section 5.2) walks the same rows but forms every entry from all
+// Z operands (Z loads and Z - 1 multiplies per entry), its digits (a_0..a_{Z-1})
+// advanced by mixed-radix increments.
 //
-// The naive comparator (Section 5.2) runs the same loop but forms every entry from
-// all Z operands (Z - 1 multiplies per entry, no shared prefix products).
+// Lanes take 16-byte words q = lane and q = lane + 32 of each group (C <= 64); wider
+// outputs and outputs that are not 16-byte aligned take the generic loop (scalar
+// stores, digits per float).
 #include "mtk_internal.cuh"
 
 namespace mtk {
@@ -30,212 +30,146 @@ namespace {
 
 constexpr int kKrpThreads = 256;
 constexpr int kKrpWarps = kKrpThreads / 32;
-constexpr int kKrpTileFloats = 16384;      // output floats per tile (64 KB)
-constexpr int kKrpMaxTileRows = 4096;
 
 struct KrpArgs {
     int Z, C;
     const float* U[MTK_MAXN];
     int64_t rows[MTK_MAXN];
     int64_t J;        // total rows
-    int64_t RT;       // rows per tile, a multiple of 4
     float* K;
-    int vec;          // K is 16-byte aligned: 16-byte stores
 };
 
-// The (row, column) of float i of 16-byte word q inside a group of four rows (4 C floats
-// = C words), packed as row << 16 | column.
-__device__ __forceinline__ int word_float(int q, int i, int C) {
-    const int e = 4 * q + i;
-    const int r = e / C;
-    return (r << 16) | (e - r * C);
+// groups of four rows [g0, g1) of warp w of nw in all: a balanced split
+__device__ __forceinline__ void warp_groups(int64_t J, int64_t w, int64_t nw, int64_t& g0, int64_t& g1) {
+    const int64_t G = (J + 3) / 4;
+    g0 = G * w / nw;
+    g1 = G * (w + 1) / nw;
 }
 
-// Row cursor: row jb as (pb, tb) = (jb / Jl, jb % Jl), advanced by a constant number
-// of rows S = qS * Jl + rS without division.
-struct Cursor {
-    int64_t pb, tb;
-};
-__device__ __forceinline__ void cursor_advance(Cursor& c, int64_t qS, int64_t rS, int64_t Jl) {
-    c.pb += qS;
-    c.tb += rS;
-    if (c.tb >= Jl) {
-        c.tb -= Jl;
-        ++c.pb;
-    }
-}
-// (p, t) of row jb + r, 0 <= r < 4
-__device__ __forceinline__ void cursor_row(const Cursor& c, int r, int64_t Jl, int64_t& p, int64_t& t) {
-    p = c.pb;
-    t = c.tb + r;
-    while (t >= Jl) {
-        t -= Jl;
-        ++p;
+// digits of row j over the operands (last operand fastest), each kept as its row's
+// offset d * C into the operand (every operand has rows * C < 2^31 on this path)
+template <int ZM>
+__device__ __forceinline__ void row_offsets(const KrpArgs& a, int Z, int64_t j, int* o) {
+#pragma unroll
+    for (int z = ZM - 1; z >= 0; --z) {
+        if (z >= Z) continue;
+        const int64_t q = j / a.rows[z];
+        o[z] = (int)(j - q * a.rows[z]) * a.C;
+        j = q;
     }
 }
 
-// dynamic shared memory: the tile's prefix products, [prefixes][C]
-__global__ void __launch_bounds__(kKrpThreads) krp_reuse_kernel(const __grid_constant__ KrpArgs a) {
-    extern __shared__ float P[];
-    const int C = a.C, Z = a.Z;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t Jl = a.rows[Z - 1];                  // rows of the last operand
-    const int64_t Jp2 = (Z >= 2) ? a.rows[Z - 2] : 1;  // rows of the second-to-last operand
-    const float* Ul = a.U[Z - 1];
-    const int64_t ntiles = (a.J + a.RT - 1) / a.RT;
-    const int64_t S = 4 * kKrpWarps;                   // rows per step of a warp
-    const int64_t qS = S / Jl, rS = S % Jl;
-    int rc0[4];                                        // this lane's word q = lane
+// P(p, c) from the prefix rows' offsets o[0..Z-2]
+template <int ZM>
+__device__ __forceinline__ float prefix_value(const KrpArgs& a, int Z, const int* o, int c) {
+    float v = 1.0f;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) rc0[i] = word_float(lane, i, C);
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t j0 = tile * a.RT;
-        const int64_t j1 = (j0 + a.RT < a.J) ? j0 + a.RT : a.J;
-        const int64_t p0 = j0 / Jl, p1 = (j1 - 1) / Jl;
-        const int np = (int)(p1 - p0 + 1);
-        __syncthreads();
-        // prefix products: P(p) = Q(p / Jp2) * U_{Z-2}(p % Jp2), Q the product of operands
-        // 0..Z-3 at the digits of p / Jp2 (operand Z-3 fastest)
-        for (int e = threadIdx.x; e < np * C; e += kKrpThreads) {
-            const int pl = e / C, c = e - pl * C;
-            const int64_t pg = p0 + pl;
-            float v = 1.0f;
-            if (Z >= 2) {
-                int64_t q = pg / Jp2;
-                v = __ldg(a.U[Z - 2] + (pg - q * Jp2) * C + c);
-                for (int z = Z - 3; z >= 0; --z) {
-                    const int64_t nq = q / a.rows[z];
-                    v *= __ldg(a.U[z] + (q - nq * a.rows[z]) * C + c);
-                    q = nq;
-                }
-            }
-            P[e] = v;
-        }
-        __syncthreads();
-        // stream the tile: warp w takes the groups of four rows w, w + 8, ...
-        Cursor cur;
-        {
-            const int64_t jb = j0 + 4 * warp;
-            cur.pb = jb / Jl;
-            cur.tb = jb - cur.pb * Jl;
-        }
-        for (int64_t jb = j0 + 4 * warp; jb < j1; jb += S) {
-            const int64_t nr = (j1 - jb) < 4 ? (j1 - jb) : 4;    // rows of this group
-            float* dst = a.K + jb * C;
-            for (int q = lane; q < C; q += 32) {
-                float v[4];
-                int ri[4];
+    for (int z = 0; z < ZM - 1; ++z)
+        if (z < Z - 1) v *= __ldg(a.U[z] + o[z] + c);
+    return v;
+}
+
+// the last operand's digit wrapped: carry into the prefix digits (mixed radix)
+template <int ZM>
+__device__ __forceinline__ void prefix_carry(const KrpArgs& a, int Z, int* o) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int rc = q == lane ? rc0[i] : word_float(q, i, C);
-                    ri[i] = rc >> 16;
-                    const int ci = rc & 0xFFFF;
-                    v[i] = 0.0f;
-                    if (ri[i] < nr) {
-                        int64_t p, t;
-                        cursor_row(cur, ri[i], Jl, p, t);
-                        v[i] = P[(int)(p - p0) * C + ci] * __ldg(Ul + t * C + ci);
-                    }
-                }
-                if (a.vec && nr == 4) {
-                    *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(v[0], v[1], v[2], v[3]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (ri[i] < nr) dst[4 * q + i] = v[i];
-                }
-            }
-            cursor_advance(cur, qS, rS, Jl);
-        }
+    for (int z = ZM - 2; z >= 0; --z) {
+        if (z >= Z - 1) continue;
+        o[z] += a.C;
+        if (o[z] < (int)a.rows[z] * a.C) break;
+        o[z] = 0;
     }
 }
 
-// Naive comparator: every entry from all Z operands.  The row's digits (a_0..a_{Z-1})
-// advance with the group by mixed-radix addition of the step's digits.
-template <int ZT>
-__global__ void __launch_bounds__(kKrpThreads) krp_naive_kernel(const __grid_constant__ KrpArgs a) {
-    const int C = a.C;
+// Fast path: C <= 64, K 16-byte aligned.  REUSE: Algorithm 1; else the naive comparator.
+template <int ZT, bool REUSE>
+__global__ void __launch_bounds__(kKrpThreads) krp_words_kernel(const __grid_constant__ KrpArgs a) {
     constexpr int ZM = ZT > 0 ? ZT : MTK_MAXN;
     const int Z = ZT > 0 ? ZT : a.Z;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t S = 4 * (int64_t)kKrpWarps * gridDim.x;  // rows per step of a warp
-    int64_t sd[ZM], d[ZM];
-    {
-        int64_t s = S, j = 4 * ((int64_t)blockIdx.x * kKrpWarps + warp);
+    const int C = a.C;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * kKrpWarps + (threadIdx.x >> 5);
+    int64_t g0, g1;
+    warp_groups(a.J, w, (int64_t)gridDim.x * kKrpWarps, g0, g1);
+    if (g0 >= g1) return;
+    const int64_t Jl = a.rows[Z - 1];
+    const float* Ul = a.U[Z - 1];
+    for (int q = lane; q < C; q += 32) {
+        // the lane's four floats of word q: row offset ri (0..3) and column ci in a group
+        int ri[4], ci[4];
+        int o[4][ZM];               // offsets of the float's row in every operand (d * C)
+        float pv[4];                // REUSE: P(prefix, ci)
 #pragma unroll
-        for (int z = ZM - 1; z >= 0; --z) {
-            if (z >= Z) continue;
-            const int64_t r = a.rows[z];
-            sd[z] = s % r;
-            s /= r;
-            d[z] = j % r;
-            j /= r;
+        for (int e = 0; e < 4; ++e) {
+            const int f = 4 * q + e;
+            ri[e] = f / C;
+            ci[e] = f - ri[e] * C;
+            row_offsets<ZM>(a, Z, 4 * g0 + ri[e], o[e]);
+            pv[e] = REUSE ? prefix_value<ZM>(a, Z, o[e], ci[e]) : 1.0f;
         }
-    }
-    int rc0[4];                                        // this lane's word q = lane
-#pragma unroll
-    for (int i = 0; i < 4; ++i) rc0[i] = word_float(lane, i, C);
-    for (int64_t jb = 4 * ((int64_t)blockIdx.x * kKrpWarps + warp); jb < a.J; jb += S) {
-        const int64_t nr = (a.J - jb) < 4 ? (a.J - jb) : 4;
-        float* dst = a.K + jb * C;
-        for (int q = lane; q < C; q += 32) {
+        const int JlC = (int)Jl * C, step = 4 * C;
+        float* dst = a.K + 4 * g0 * C + 4 * q;
+        for (int64_t g = g0; g < g1; ++g) {
             float v[4];
-            int ri[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int rc = q == lane ? rc0[i] : word_float(q, i, C);
-                ri[i] = rc >> 16;
-                const int ci = rc & 0xFFFF;
-                v[i] = 0.0f;
-                if (ri[i] < nr) {
-                    // digits of row jb + ri: add ri to the last digit, carry upwards
-                    int64_t e[ZM];
-                    int64_t carry = ri[i];
+            for (int e = 0; e < 4; ++e) {
+                if (REUSE) {
+                    v[e] = pv[e] * __ldg(Ul + o[e][Z - 1] + ci[e]);
+                } else {
+                    float prod = __ldg(Ul + o[e][Z - 1] + ci[e]);
 #pragma unroll
-                    for (int z = ZM - 1; z >= 0; --z) {
-                        if (z >= Z) continue;
-                        int64_t x = d[z] + carry;
-                        carry = 0;
-                        while (x >= a.rows[z]) {
-                            x -= a.rows[z];
-                            ++carry;
-                        }
-                        e[z] = x;
-                    }
-                    float prod = 1.0f;
-#pragma unroll
-                    for (int z = 0; z < ZM; ++z)
-                        if (z < Z) prod *= __ldg(a.U[z] + e[z] * C + ci);
-                    v[i] = prod;
+                    for (int z = 0; z < ZM - 1; ++z)
+                        if (z < Z - 1) prod *= __ldg(a.U[z] + o[e][z] + ci[e]);
+                    v[e] = prod;
                 }
             }
-            if (a.vec && nr == 4) {
-                *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(v[0], v[1], v[2], v[3]);
+            if (4 * g + 3 < a.J) {
+                *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
             } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (ri[i] < nr) dst[4 * q + i] = v[i];
+                for (int e = 0; e < 4; ++e)
+                    if (4 * g + ri[e] < a.J) dst[e] = v[e];
             }
-        }
-        // next group: d += sd (mixed radix, every digit of sd below its radix)
-        int64_t carry = 0;
+            dst += 4 * C;
+            // next group: every row moves by 4
 #pragma unroll
-        for (int z = ZM - 1; z >= 0; --z) {
-            if (z >= Z) continue;
-            int64_t x = d[z] + sd[z] + carry;
-            carry = 0;
-            if (x >= a.rows[z]) {
-                x -= a.rows[z];
-                carry = 1;
+            for (int e = 0; e < 4; ++e) {
+                int& ol = o[e][Z - 1];
+                ol += step;
+                if (ol >= JlC) {
+                    do {
+                        ol -= JlC;
+                        prefix_carry<ZM>(a, Z, o[e]);
+                    } while (ol >= JlC);
+                    if (REUSE && g + 1 < g1) pv[e] = prefix_value<ZM>(a, Z, o[e], ci[e]);
+                }
             }
-            d[z] = x;
         }
     }
 }
 
+// Generic loop: any C and alignment; one float per thread step, digits per float (the
+// same products for both forms).
+__global__ void __launch_bounds__(kKrpThreads) krp_generic_kernel(const __grid_constant__ KrpArgs a) {
+    const int64_t n = a.J * a.C;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = e / a.C;
+        const int c = (int)(e - j * a.C);
+        float v = 1.0f;
+        for (int z = a.Z - 1; z >= 0; --z) {
+            const int64_t q = j / a.rows[z];
+            v *= __ldg(a.U[z] + (j - q * a.rows[z]) * a.C + c);
+            j = q;
+        }
+        a.K[e] = v;
+    }
+}
+
 template <int ZT>
-void naive_launch(const KrpArgs& a, int grid, cudaStream_t s) {
-    krp_naive_kernel<ZT><<<grid, kKrpThreads, 0, s>>>(a);
+void words_launch(const KrpArgs& a, bool reuse, int grid, cudaStream_t s) {
+    if (reuse) krp_words_kernel<ZT, true><<<grid, kKrpThreads, 0, s>>>(a);
+    else krp_words_kernel<ZT, false><<<grid, kKrpThreads, 0, s>>>(a);
 }
 
 }  // namespace
@@ -249,40 +183,31 @@ cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C,
     for (int z = 0; z < MTK_MAXN; ++z) { a.U[z] = nullptr; a.rows[z] = 1; }
     for (int z = 0; z < Z; ++z) { a.U[z] = U[z]; a.rows[z] = rows[z]; a.J *= rows[z]; }
     a.K = K;
-    a.vec = (reinterpret_cast<uintptr_t>(K) & 15) == 0 ? 1 : 0;
     if (a.J == 0) return cudaSuccess;
-    int64_t RT = (kKrpTileFloats / C) & ~(int64_t)3;
-    if (RT < 4) RT = 4;
-    if (RT > kKrpMaxTileRows) RT = kKrpMaxTileRows;
-    a.RT = RT;
-    if (reuse) {
-        // a tile of RT rows touches at most RT / J_{Z-1} + 2 prefixes
-        const int64_t Jl = rows[Z - 1];
-        int64_t np = RT / Jl + 2;
-        if (np > RT) np = RT;
-        const size_t smem = (size_t)np * C * sizeof(float);
-        if (smem > 48 * 1024) {
-            const cudaError_t e =
-                cudaFuncSetAttribute(krp_reuse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        const int64_t ntiles = (a.J + RT - 1) / RT;
-        const int grid = (int)(ntiles < num_sms() * 4 ? ntiles : num_sms() * 4);
-        krp_reuse_kernel<<<grid, kKrpThreads, smem, s>>>(a);
-        note_launches(1);
-    } else {
+    bool fast = (reinterpret_cast<uintptr_t>(K) & 15) == 0 && C <= 64;
+    for (int z = 0; z < Z; ++z)
+        if (rows[z] * C + 4 * (int64_t)C >= ((int64_t)1 << 31)) fast = false;
+    if (fast) {
+        // warps: up to 64 per SM, each with at least 16 groups of four rows
         const int64_t groups = (a.J + 3) / 4;
-        const int64_t blocks = (groups + kKrpWarps - 1) / kKrpWarps;
-        const int grid = (int)(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
+        int64_t warps = (groups + 15) / 16;
+        const int64_t cap = (int64_t)num_sms() * 64;
+        if (warps > cap) warps = cap;
+        const int grid = (int)((warps + kKrpWarps - 1) / kKrpWarps);
         switch (Z) {
-            case 1: naive_launch<1>(a, grid, s); break;
-            case 2: naive_launch<2>(a, grid, s); break;
-            case 3: naive_launch<3>(a, grid, s); break;
-            case 4: naive_launch<4>(a, grid, s); break;
-            default: naive_launch<0>(a, grid, s); break;
+            case 1: words_launch<1>(a, reuse != 0, grid, s); break;
+            case 2: words_launch<2>(a, reuse != 0, grid, s); break;
+            case 3: words_launch<3>(a, reuse != 0, grid, s); break;
+            case 4: words_launch<4>(a, reuse != 0, grid, s); break;
+            default: words_launch<0>(a, reuse != 0, grid, s); break;
         }
-        note_launches(1);
+    } else {
+        const int64_t n = a.J * C;
+        int64_t blocks = (n + kKrpThreads - 1) / kKrpThreads;
+        const int grid = (int)(blocks < num_sms() * 16 ? blocks : num_sms() * 16);
+        krp_generic_kernel<<<grid, kKrpThreads, 0, s>>>(a);
     }
+    note_launches(1);
     return cudaGetLastError();
 }
 

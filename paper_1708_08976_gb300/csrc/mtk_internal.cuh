@@ -100,10 +100,13 @@ int split_chunks(int64_t NX);          // FP64 partials of ||X||^2 written by th
 cudaError_t launch_split_planes(const float* X, int64_t NX, void* Xs, double* part, double* normX2,
                                 cudaStream_t s);
 // Plan of the planes contraction for view (L, I, R) and the mode's factor list; ok = 0
-// when the shape is not taken (C > 64, I^L or I_n not a multiple of 8, ...).
+// when the shape is not taken (C > 64; MN-major: I_n not a multiple of 8; K-major:
+// P = 8 / gcd(I^L, 8) not dividing I_n, ...).
 struct PlanesPlan {
     int ok, mn, head, spr, U, BI, MT, CP, N, ntiles, s_full, s_last, nslab, grid;
-    int64_t H, nruns, Lq, stot;
+    int P, ntc, nsh;          // K-major row classes, tiles per class, head image shifts
+    int box_mode;             // packed runs: one TMA box per group (0) or for all (1: along r, 2: along lq)
+    int64_t H, nruns, Lq, stot, Ic;
     size_t image_bytes, qtab_bytes, part_bytes;
 };
 PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int C, int n_left, int ctas);

@@ -10,10 +10,13 @@ mtk_mttkrp_split, mtk_cp_als_sweep_split) against the FP64 oracle.
   accumulation.
 The shapes cover each branch of the planes kernel: K-major CTA tiles of up to 128 rows or
 of up to 256 rows as two MMA tiles (one or several per mode, ragged last tile), K-major with the head inside the modes left of n
-(5-D tensor map), runs packed into the MMA rows for I_n <= 64, MN-major (mode 0) with
+(several runs per row), K-major rows in classes i mod P when I^L is not a multiple of 8
+(shifted head images), runs packed into the MMA rows for small I_n, MN-major (mode 0) with
 one to four 64-row boxes per CTA or packed runs, ranks C = 1..64 (one to four 16-column chunks), N = 2..5,
 heads shorter than one 64-k stage, several tail factors, and explicit CTA counts.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -94,6 +97,38 @@ SHAPES = [
 ]
 
 
+# K-major modes whose I^L is not a multiple of 8: the rows of one class i mod P (P = 8 /
+# gcd(I^L, 8)) are loaded as rows of the super-row view, and every stage takes the head
+# image shifted so that its first element sits on a 16-byte boundary.  (dims, C, modes
+# the planes kernel must take without the FP32 tensor)
+CLASS_SHAPES = [
+    ((12, 6, 10), 8, (1, 2)),          # I^L = 12: P = 2; mode 2 I^L = 72 with shifted runs or one run
+    ((20, 10, 7, 8), 25, (1, 2, 3)),   # P = 2, two classes of 5 rows, packed runs under one shift
+    ((6, 4, 10, 5), 12, (1, 2, 3)),    # I^L = 6: P = 4 classes of one row
+    ((5, 8, 9), 8, (1, 2)),            # I^L = 5: P = 8 classes of one row each
+    ((3, 16, 11, 2), 16, (1, 2, 3)),   # I^L = 3: P = 8, two rows per class
+    ((100, 3000, 3), 25, (1, 2)),      # mode 1: P = 2, 1500 rows per class (6 tiles); mode 2: head
+                                       # of 100 rows (the 300000-row one exceeds the image budget),
+                                       # 3000 runs per row at alternating shifts 0, 4
+    ((30, 30, 4, 6), 33, (2, 3)),      # mode 2: I^L = 900, P = 2; C = 33 (three chunks)
+]
+
+
+@pytest.mark.parametrize("dims,C,modes", CLASS_SHAPES)
+def test_mttkrp_split_row_classes(dims, C, modes):
+    """The planes kernel on K-major modes with unaligned rows or runs, against the
+    oracle, without the FP32 tensor to fall back to."""
+    X, dims, U = synth.random_case(dims, C, seed=13 * sum(dims) + C)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    for n in modes:
+        ref = oracle.mttkrp(Xr, dims, Ur, n)
+        got = run_split(X, dims, U, n, C, with_x=False)
+        err = rel_fro(got, ref)
+        tol = bf16x2_bound(Xr, dims, Ur, n, ref)
+        assert err < tol, (dims, C, n, err, tol)
+
+
 @pytest.mark.parametrize("dims,C", SHAPES)
 def test_mttkrp_split_parity(dims, C):
     X, dims, U = synth.random_case(dims, C, seed=11 * sum(dims) + C)
@@ -116,18 +151,18 @@ def test_mttkrp_split_without_fp32_tensor():
         ref = oracle.mttkrp(Xr, dims, Ur, n)
         got = run_split(X, dims, U, n, 8, with_x=False)
         assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, n, ref)
-    X, dims, U = synth.tiny3()                       # mode 1 has I^L = 60 (not a multiple of 8)
+    X, dims, U = synth.tiny3()                       # mode 0 has I_0 = 60 (not a multiple of 8)
     Xd = to_dev(X, torch)
     Xs, _ = mtk.split_tensor(Xd)
     with pytest.raises(mtk.MtkError) as ei:
-        mtk.mttkrp(None, dims, factors_dev(U, torch), 1, Xs=Xs)
+        mtk.mttkrp(None, dims, factors_dev(U, torch), 0, Xs=Xs)
     assert ei.value.status == L.MTK_EUNSUPPORTED
     # with the FP32 tensor the same call runs the FP32-input tensor-core path
     Xr = X.astype(np.float32).astype(np.float64)
     Ur = f32_round(U)
-    ref = oracle.mttkrp(Xr, dims, Ur, 1)
-    got = run_split(X, dims, U, 1, 8)
-    assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, 1, ref)
+    ref = oracle.mttkrp(Xr, dims, Ur, 0)
+    got = run_split(X, dims, U, 0, 8)
+    assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, 0, ref)
 
 
 @pytest.mark.parametrize("splits", [1, 3, 500])
@@ -246,7 +281,8 @@ PARTIAL_SHAPES = [
     ((8, 6, 5, 4, 3), 5),         # N = 5: several factors on each side
     ((64, 48, 40), 33),           # C = 33 (three chunks); MN view of 64 rows (n = 0, right)
     ((200, 200, 12, 5), 25),      # tall right view at n = 1: 40000 rows, many CTAs
-    ((5, 24, 40, 8), 8),          # I_0 = 5: n = 0 right and n = 1 left are not taken
+    ((5, 24, 40, 8), 8),          # I_0 = 5: n = 0 right is not taken; n = 1 left: I^L = 5, 8 row classes
+    ((6, 5, 8, 3), 8),            # left views with I^L = 6 and 30 (P = 4 classes); right n = 0, 1 not taken
 ]
 
 
@@ -268,7 +304,10 @@ def test_partial_split_parity(dims, C):
             if (right and n == N - 1) or (not right and n == 0):
                 continue
             IL = int(np.prod(dims[:n])) if n else 1
-            takes = (IL * dims[n]) % 8 == 0 if right else IL % 8 == 0
+            IR = int(np.prod(dims[n + 1:]))
+            # right: the MN-major view (1, I^L I_n, I^R) needs I^L I_n a multiple of 8; left:
+            # the K-major view (I^L, I_n I^R, 1) needs P = 8 / gcd(I^L, 8) to divide its rows
+            takes = (IL * dims[n]) % 8 == 0 if right else (dims[n] * IR) % (8 // math.gcd(IL, 8)) == 0
             if not takes:
                 with pytest.raises(mtk.MtkError) as ei:
                     mtk.partial_mttkrp_split(Xs, dims, Ud, n, right)

@@ -161,11 +161,12 @@ def test_partial_split_rejected_before_launch():
         assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 8, 1, 1, ctypes.byref(o)) == 0
         assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 8, 1, 1, fake, fake, 1 << 30, ctypes.byref(o),
                                             None) == L.MTK_EINVAL
-    # shapes outside the planes kernel: C > 64; a left view with I^L not a multiple of 8
+    # shapes outside the planes kernel: C > 64; a left view whose rows do not split into
+    # the classes i mod P of its I^L (I^L = 6: P = 4, 5 x 3 x 3 = 45 rows)
     assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 65, 1, 1, None) == 0
     assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 65, 1, 1, fake, fake, 1 << 30, None,
                                         None) == L.MTK_EUNSUPPORTED
-    d_odd = L.dims_arr([5, 24, 40, 8])
+    d_odd = L.dims_arr([6, 5, 3, 3])
     assert lib.mtk_partial_mttkrp_split_workspace(d_odd, 4, 8, 1, 0, None) == 0
     assert lib.mtk_partial_mttkrp_split(fake, d_odd, 4, U, 8, 1, 0, fake, fake, 1 << 30, None,
                                         None) == L.MTK_EUNSUPPORTED
