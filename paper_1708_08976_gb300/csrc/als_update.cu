@@ -152,10 +152,36 @@ __device__ void sum_rows(const float2* __restrict__ src, int cnt, int npairs, fl
 // the group to arrive adds the group's rows into gsum[g]; the last group to finish adds
 // the groups into fin (npairs entries, may be shared memory).  Returns 1 in that one CTA.
 // tk[0] counts finished groups, tk[1 + g] the arrivals in group g; both are left at zero.
+// dst[x] = sum over rows b = 0..cnt-1 (cnt <= 32) of src[b][x], all rows of a thread's
+// entries loaded at once (one trip to L2)
+__device__ void sum_rows32(const float2* __restrict__ src, int cnt, int npairs, float2* __restrict__ dst) {
+    for (int x = threadIdx.x; x < npairs; x += blockDim.x) {
+        float2 v[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) v[b] = b < cnt ? __ldcg(src + (size_t)b * npairs + x) : make_float2(0.0f, 0.0f);
+        float h = 0.0f, l = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 32; ++b)
+            if (b < cnt) df_add(h, l, v[b].x, v[b].y);
+        dst[x] = make_float2(h, l);
+    }
+}
+
 __device__ int ticket_reduce(float2* part, float2* gsum, float2* fin, unsigned int* tk, int idx, int cnt,
                              int npairs, int* flag) {
     __threadfence();
     __syncthreads();
+    if (cnt <= 32) {
+        // one level: the last CTA to arrive adds every row, in row order
+        if (threadIdx.x == 0) *flag = (atomicAdd(&tk[0], 1u) == (unsigned)(cnt - 1)) ? 1 : 0;
+        __syncthreads();
+        if (!*flag) return 0;
+        __threadfence();
+        sum_rows32(part, cnt, npairs, fin);
+        if (threadIdx.x == 0) tk[0] = 0u;
+        __syncthreads();
+        return 1;
+    }
     const int g = idx / kGroup, ng = (cnt + kGroup - 1) / kGroup;
     const int members = (cnt - kGroup * g) < kGroup ? (cnt - kGroup * g) : kGroup;
     if (threadIdx.x == 0) *flag = (atomicAdd(&tk[1 + g], 1u) == (unsigned)(members - 1)) ? 1 : 0;
@@ -210,10 +236,157 @@ struct UpdParams {
     double* fit;
     double* r2;
     uint32_t* status;
+    const float2* hinv;          // H^{-1} formed by als_factor_kernel (C x C pairs), then its not-pd
+                                 // flag (an int at hinv + C*C); null: H is factored here
 };
 
-// dynamic shared memory: A[C*C], W[C*C] (doubles), then H^{-1}[C*C] and fin[npairs]
-// (float2 pairs)
+// ---- the factorisation, on shared memory, by all threads of the CTA ------------------------
+// A = H = Hadamard_{k != n} G_k (the loads of one factor issued together)
+__device__ void form_h(const double* const* G, int N, int n, int C, double* A) {
+    for (int e0 = threadIdx.x; e0 < C * C; e0 += 4 * blockDim.x) {
+        double h[4];
+        bool first = true;
+        for (int k = 0; k < N; ++k) {
+            if (k == n) continue;
+            double g[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = e0 + q * (int)blockDim.x;
+                g[q] = e < C * C ? G[k][e] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h[q] = first ? g[q] : h[q] * g[q];
+            first = false;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = e0 + q * (int)blockDim.x;
+            if (e < C * C) A[e] = h[q];
+        }
+    }
+    __syncthreads();
+}
+
+// Division-free L D L^T of A (lower triangle), one barrier per step.  Returns true when H
+// is not positive definite (the same answer in every thread).  Otherwise L is left in both
+// triangles of A (A[i][k] = A[k][i] = L(i, k), i > k) and dinv[k] = D_k^{-1}.
+__device__ bool ldl(double* A, int C, const int* tri, double* dinv, double* rcp, double* red) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nt = blockDim.x;
+    for (int j = 0; j < C; ++j) {
+        const double d = A[j * C + j];
+        const int ed = (int)((__double_as_longlong(d) >> 52) & 0x7FF);
+        if (!(d > 0.0) || ed == 0 || ed == 0x7FF) return true;
+        const int ej = ed - 1023;
+        const int m = C - 1 - j;
+        const int cnt = m * (m + 1) / 2;
+        for (int x = t; x < cnt; x += nt) {
+            const int i = tri[x] >> 8, k = tri[x] & 255;
+            const double v = A[i * C + j] * A[k * C + j];
+            A[i * C + k] = scale_exp2(fma(d, A[i * C + k], -v), ej);
+        }
+        __syncthreads();
+    }
+    // sigma_j = prod_{m<j} mant(d_m) (exclusive scan), D_j^{-1} = sigma_j / d_j
+    double s_own = 1.0, r_own = 0.0;
+    if (t < C) {
+        const double d = A[t * C + t];
+        s_own = __longlong_as_double((__double_as_longlong(d) & 0x000FFFFFFFFFFFFFLL) | (1023LL << 52));
+        r_own = 1.0 / d;
+        rcp[t] = r_own;
+    }
+    double incl = s_own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl *= y;
+    }
+    if (t == 31) red[0] = incl;
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 1.0;
+    __syncthreads();
+    if (warp == 1) excl *= red[0];
+    if (t < C) dinv[t] = excl * r_own;
+    __syncthreads();
+    const int npairs = C * (C + 1) / 2;
+    for (int x = t; x < npairs; x += nt) {
+        const int i = tri[x] >> 8, k = tri[x] & 255;
+        if (i > k) {
+            const double l = A[i * C + k] * rcp[k];
+            A[i * C + k] = l;
+            A[k * C + i] = l;
+        }
+    }
+    __syncthreads();
+    return false;
+}
+
+// H^{-1} = W^T D^{-1} W with W = L^{-1} (column elimination, C - 1 steps of independent
+// FMAs, one barrier each), kept as FP32 pairs (hi + lo, 48 significant bits), both
+// triangles, row-major [k][c].  W: C x C doubles of scratch.
+__device__ void ldl_inverse(const double* A, double* W, const double* dinv, const int* tri, float2* Hv, int C) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int e = t; e < C * C; e += nt) W[e] = (e / C == e % C) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k + 1 < C; ++k) {
+        const int w = k + 1, cnt = (C - 1 - k) * w;
+        for (int x = t; x < cnt; x += nt) {
+            const int q = x / w;
+            const int i = k + 1 + q, c = x - q * w;
+            W[i * C + c] = fma(-A[i * C + k], W[k * C + c], W[i * C + c]);
+        }
+        __syncthreads();
+    }
+    const int npairs = C * (C + 1) / 2;
+    for (int x = t; x < npairs; x += nt) {
+        const int a = tri[x] >> 8, b = tri[x] & 255;
+        double s0 = 0.0, s1 = 0.0;
+        int k = a;
+        for (; k + 1 < C; k += 2) {
+            s0 = fma(W[k * C + a] * dinv[k], W[k * C + b], s0);
+            s1 = fma(W[(k + 1) * C + a] * dinv[k + 1], W[(k + 1) * C + b], s1);
+        }
+        if (k < C) s0 = fma(W[k * C + a] * dinv[k], W[k * C + b], s0);
+        const double h = s0 + s1;
+        const float hh = (float)h;
+        const float2 v = make_float2(hh, (float)(h - (double)hh));
+        Hv[a * C + b] = v;
+        Hv[b * C + a] = v;
+    }
+    __syncthreads();
+}
+
+// ---- H^{-1} alone, one CTA (launched ahead of a long kernel that it may overlap) -------
+struct FactorParams {
+    const double* G[MTK_MAXN];
+    int N, C, n;
+    float2* hinv;                // C x C pairs, then the not-pd flag (int)
+    uint32_t* status;
+};
+
+// dynamic shared memory: A[C*C], W[C*C] (doubles), Hv[C*C] (float2)
+__global__ void __launch_bounds__(kAppThreads) als_factor_kernel(const __grid_constant__ FactorParams p) {
+    // the next kernel of the stream (launched with programmatic serialisation) may start now
+    allow_dependent_launch();
+    extern __shared__ double dsm[];
+    __shared__ double dinv[kUpdMaxC], rcp[kUpdMaxC];
+    __shared__ double red[kAppThreads / 32];
+    __shared__ int tri[kMaxPairs];
+    const int C = p.C;
+    double* A = dsm;
+    double* W = A + C * C;
+    float2* Hv = reinterpret_cast<float2*>(W + C * C);
+    build_pairs(tri, C);
+    form_h(p.G, p.N, p.n, C, A);
+    const bool bad = ldl(A, C, tri, dinv, rcp, red);
+    if (!bad) ldl_inverse(A, W, dinv, tri, Hv, C);
+    for (int e = threadIdx.x; e < C * C && !bad; e += blockDim.x) p.hinv[e] = Hv[e];
+    if (threadIdx.x == 0) *reinterpret_cast<int*>(p.hinv + C * C) = bad ? 1 : 0;
+    if (bad && threadIdx.x == 0) set_status(p.status, MTK_ENOTPD);
+}
+
+// ---- the update ------------------------------------------------------------------------------
+// dynamic shared memory: A[C*C] (doubles), Hv[C*C] and fin[npairs] (float2)
 __global__ void __launch_bounds__(kAppThreads)
 als_update_kernel(const __grid_constant__ UpdParams p) {
     extern __shared__ double dsm[];
@@ -227,119 +400,25 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
     const int C = p.C, N = p.N, n = p.n;
     const int npairs = C * (C + 1) / 2;
     double* A = dsm;
-    double* W = A + C * C;
-    float2* Hv = reinterpret_cast<float2*>(W + C * C);
+    float2* Hv = reinterpret_cast<float2*>(A + C * C);
     float2* fin = Hv + C * C;
 
     build_pairs(tri, C);
-    // ---- H = Hadamard_{k != n} G_k (the loads of one factor issued together); W = I
-    for (int e0 = t; e0 < C * C; e0 += 4 * kAppThreads) {
-        double h[4];
-        bool first = true;
-        for (int k = 0; k < N; ++k) {
-            if (k == n) continue;
-            double g[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = e0 + q * kAppThreads;
-                g[q] = e < C * C ? p.G[k][e] : 0.0;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) h[q] = first ? g[q] : h[q] * g[q];
-            first = false;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = e0 + q * kAppThreads;
-            if (e < C * C) {
-                A[e] = h[q];
-                W[e] = (e / C == e % C) ? 1.0 : 0.0;
-            }
-        }
+    // ---- the inverse from als_factor_kernel, or L D L^T here (before M is ready)
+    const bool pre = p.hinv != nullptr;
+    bool bad;
+    if (pre) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        bad = *reinterpret_cast<const volatile int*>(p.hinv + C * C) != 0;
+        for (int e = t; e < C * C && !bad; e += kAppThreads) Hv[e] = p.hinv[e];
+        __syncthreads();
+    } else {
+        form_h(p.G, N, n, C, A);
+        bad = ldl(A, C, tri, dinv, rcp, red);
+        if (bad && blockIdx.x == 0 && t == 0) set_status(p.status, MTK_ENOTPD);
+        // ---- M is written by the previous kernel
+        asm volatile("griddepcontrol.wait;" ::: "memory");
     }
-    __syncthreads();
-
-    // ---- division-free L D L^T (lower triangle), one barrier per step
-    bool bad = false;
-    for (int j = 0; j < C; ++j) {
-        const double d = A[j * C + j];
-        const int ed = (int)((__double_as_longlong(d) >> 52) & 0x7FF);
-        if (!(d > 0.0) || ed == 0 || ed == 0x7FF) {     // same value in every thread
-            bad = true;
-            break;
-        }
-        const int ej = ed - 1023;
-        const int m = C - 1 - j;
-        const int cnt = m * (m + 1) / 2;
-        for (int x = t; x < cnt; x += kAppThreads) {
-            const int i = tri[x] >> 8, k = tri[x] & 255;
-            const double v = A[i * C + j] * A[k * C + j];
-            A[i * C + k] = scale_exp2(fma(d, A[i * C + k], -v), ej);
-        }
-        __syncthreads();
-    }
-    if (bad && blockIdx.x == 0 && t == 0) set_status(p.status, MTK_ENOTPD);
-    if (!bad) {
-        // sigma_j = prod_{m<j} mant(d_m) (exclusive scan), D_j^{-1} = sigma_j / d_j
-        double s_own = 1.0, r_own = 0.0;
-        if (t < C) {
-            const double d = A[t * C + t];
-            s_own = __longlong_as_double((__double_as_longlong(d) & 0x000FFFFFFFFFFFFFLL) | (1023LL << 52));
-            r_own = 1.0 / d;
-            rcp[t] = r_own;
-        }
-        double incl = s_own;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl *= y;
-        }
-        if (t == 31) red[0] = incl;
-        double excl = __shfl_up_sync(0xffffffffu, incl, 1);
-        if (lane == 0) excl = 1.0;
-        __syncthreads();
-        if (warp == 1) excl *= red[0];
-        if (t < C) dinv[t] = excl * r_own;
-        __syncthreads();
-        // L(i, k) = A(i, k) / d_k for i > k (lower triangle of A)
-        for (int x = t; x < npairs; x += kAppThreads) {
-            const int i = tri[x] >> 8, k = tri[x] & 255;
-            if (i > k) A[i * C + k] *= rcp[k];
-        }
-        __syncthreads();
-        // W = L^{-1} (unit lower triangular), column k eliminated at step k: rows i > k,
-        // columns c <= k, W(i, c) -= L(i, k) W(k, c); row k is final at step k
-        for (int k = 0; k + 1 < C; ++k) {
-            const int w = k + 1, cnt = (C - 1 - k) * w;
-            for (int x = t; x < cnt; x += kAppThreads) {
-                const int q = x / w;
-                const int i = k + 1 + q, c = x - q * w;
-                W[i * C + c] = fma(-A[i * C + k], W[k * C + c], W[i * C + c]);
-            }
-            __syncthreads();
-        }
-        // H^{-1} = W^T D^{-1} W: (a, b), a >= b, sums over k >= a; kept as FP32 (hi, lo)
-        // pairs, both triangles, row-major [k][c]
-        for (int x = t; x < npairs; x += kAppThreads) {
-            const int a = tri[x] >> 8, b = tri[x] & 255;
-            double s0 = 0.0, s1 = 0.0;
-            int k = a;
-            for (; k + 1 < C; k += 2) {
-                s0 = fma(W[k * C + a] * dinv[k], W[k * C + b], s0);
-                s1 = fma(W[(k + 1) * C + a] * dinv[k + 1], W[(k + 1) * C + b], s1);
-            }
-            if (k < C) s0 = fma(W[k * C + a] * dinv[k], W[k * C + b], s0);
-            const double h = s0 + s1;
-            const float hh = (float)h;
-            const float2 v = make_float2(hh, (float)(h - (double)hh));
-            Hv[a * C + b] = v;
-            Hv[b * C + a] = v;
-        }
-        __syncthreads();
-    }
-
-    // ---- M is written by the previous kernel
-    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const bool gram = p.gram != 0;
     const bool fit = gram && p.normX2 != nullptr;
@@ -358,7 +437,7 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
             float* urow = p.Un + i * C;
             const float m0 = j0 < C ? mrow[j0] : 0.0f;
             const float m1 = j1 < C ? mrow[j1] : 0.0f;
-            if (!bad) {
+            if (!bad && pre) {
                 // U_n(i, :) = M(i, :) H^{-1}: products of an FP32 entry and an FP32 pair,
                 // each formed exactly, summed in double-FP32 (about 2^-44 relative)
                 float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
@@ -377,6 +456,26 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
                 }
                 u0 = __fadd_rn(h0, l0);
                 u1 = __fadd_rn(h1, l1);
+            } else if (!bad) {
+                // L y = m, z = D^{-1} y, L^T u = z in FP64, one column per lane, the solved
+                // entry broadcast by a shuffle
+                double s0 = (double)m0, s1 = (double)m1;
+                for (int k = 0; k < C; ++k) {
+                    const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
+                    if (j0 > k && j0 < C) s0 = fma(-A[k * C + j0], y, s0);
+                    if (j1 > k && j1 < C) s1 = fma(-A[k * C + j1], y, s1);
+                }
+                if (j0 < C) s0 *= dinv[j0];
+                if (j1 < C) s1 *= dinv[j1];
+                for (int k = C - 1; k >= 0; --k) {
+                    const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
+                    if (j0 < k) s0 = fma(-A[k * C + j0], y, s0);
+                    if (j1 < k && j1 < C) s1 = fma(-A[k * C + j1], y, s1);
+                }
+                u0 = (float)s0;
+                u1 = (float)s1;
+            }
+            if (!bad) {
                 if (j0 < C) urow[j0] = u0;
                 if (j1 < C) urow[j1] = u1;
             } else {
@@ -611,8 +710,8 @@ cudaError_t launch_als_update(const AlsUpdateArgs& a, cudaStream_t s) {
     p.fit = a.fit;
     p.r2 = a.r2;
     p.status = a.status;
-    const size_t smem = 2 * (size_t)a.C * a.C * sizeof(double) + (size_t)a.C * a.C * sizeof(float2) +
-                        pair_bytes(a.C);
+    p.hinv = static_cast<const float2*>(a.hinv);
+    const size_t smem = (size_t)a.C * a.C * sizeof(double) + (size_t)a.C * a.C * sizeof(float2) + pair_bytes(a.C);
     if (smem > 48 * 1024) {
         const cudaError_t e =
             cudaFuncSetAttribute(als_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -632,6 +731,29 @@ cudaError_t launch_als_update(const AlsUpdateArgs& a, cudaStream_t s) {
     const cudaError_t e = cudaLaunchKernelEx(&cfg, als_update_kernel, p);
     note_launches(1);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+size_t als_hinv_bytes(int C) { return rup((size_t)C * C * sizeof(float2) + sizeof(int), 256); }
+
+cudaError_t launch_als_factor(const double* const* G, int N, int C, int n, void* hinv, uint32_t* status,
+                              cudaStream_t s) {
+    FactorParams p;
+    memset(&p, 0, sizeof(p));
+    for (int k = 0; k < N && k < MTK_MAXN; ++k) p.G[k] = G[k];
+    p.N = N;
+    p.C = C;
+    p.n = n;
+    p.hinv = static_cast<float2*>(hinv);
+    p.status = status;
+    const size_t smem = 2 * (size_t)C * C * sizeof(double) + (size_t)C * C * sizeof(float2);
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(als_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    als_factor_kernel<<<1, kAppThreads, smem, s>>>(p);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gram_all(const float* const* U, const int64_t* I, int N, int C, double* const* G,

@@ -404,10 +404,17 @@ int do_mttkrp(const float* X, const int64_t* dims, int N, const float* const* U,
 }
 
 // --- MTTKRP on a tensor split into BF16 planes ------------------------------------
-PlanesPlan planes_for(const int64_t* dims, int N, int C, int n, const mtk_opts& o) {
+// CTAs of a planes contraction: the caller's count, else one per SM less `reserve` (a CP-ALS
+// sweep leaves one SM to the factorisation it overlaps with the contraction)
+int planes_ctas_for(const mtk_opts& o, int reserve) {
+    const int c = planes_ctas(o.splits);
+    return (o.splits > 0 || c - reserve < 1) ? c : c - reserve;
+}
+
+PlanesPlan planes_for(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve = 0) {
     const View v = mode_view(dims, N, n);
     const FactorList fl = mode_factors(nullptr, dims, N, n);
-    return planes_plan(v.L, v.I, fl.rad, fl.Z, C, n, planes_ctas(o.splits));
+    return planes_plan(v.L, v.I, fl.rad, fl.Z, C, n, planes_ctas_for(o, reserve));
 }
 
 mtk_opts fallback_opts(const mtk_opts& o) {
@@ -419,29 +426,34 @@ mtk_opts fallback_opts(const mtk_opts& o) {
 
 // workspace of one MTTKRP on the planes: the planes kernel's scratch when it takes the
 // shape, else that of the FP32-tensor path it falls back to
-size_t split_mttkrp_bytes(const int64_t* dims, int N, int C, int n, const mtk_opts& o) {
-    const PlanesPlan pl = planes_for(dims, N, C, n, o);
+size_t split_mttkrp_bytes(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve = 0) {
+    const PlanesPlan pl = planes_for(dims, N, C, n, o, reserve);
     if (!pl.ok) return mttkrp_layout(dims, N, C, n, fallback_opts(o)).total;
     return align256(align256(kStatusBytes) + planes_scratch_bytes(pl));
 }
 
+// hook (may be null): a factorisation to run alongside the planes contraction; *hooked
+// (may be null) tells whether it ran (not when the shape falls back to the FP32 tensor)
 int do_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, const float* const* U,
                     int C, int n, float* M, void* ws, size_t ws_bytes, uint32_t* status,
-                    const mtk_opts& o, cudaStream_t s) {
-    const PlanesPlan pl = planes_for(dims, N, C, n, o);
+                    const mtk_opts& o, cudaStream_t s, const FactorHook* hook = nullptr, int reserve = 0,
+                    bool* hooked = nullptr) {
+    if (hooked) *hooked = false;
+    const PlanesPlan pl = planes_for(dims, N, C, n, o, reserve);
     if (!pl.ok) {
         if (!X) return MTK_EUNSUPPORTED;
         return do_mttkrp(X, dims, N, U, C, n, M, ws, ws_bytes, status, fallback_opts(o), s);
     }
-    if (ws_bytes < split_mttkrp_bytes(dims, N, C, n, o)) return MTK_EWORKSPACE;
+    if (ws_bytes < split_mttkrp_bytes(dims, N, C, n, o, reserve)) return MTK_EWORKSPACE;
     const View v = mode_view(dims, N, n);
     const FactorList fl = mode_factors(U, dims, N, n);
     Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
     void* scratch = cv.take(planes_scratch_bytes(pl));
     const int64_t NX = v.L * v.I * v.R;
     if (launch_contract_planes(Xs, split_pitch(NX), v.L, v.I, v.R, fl.f, fl.rad, fl.Z, C, pl, M, C, 1,
-                               scratch, status, s, wait_limit_ns(o), o.test_stall) != cudaSuccess)
+                               scratch, status, s, wait_limit_ns(o), o.test_stall, hook) != cudaSuccess)
         return MTK_ECUDA;
+    if (hooked) *hooked = hook != nullptr;
     return MTK_OK;
 }
 
@@ -471,27 +483,28 @@ bool tree_shape(const int64_t* dims, int N, int C) { return (N == 3 || N == 4) &
 // is formed on chip from the factors, as in a per-mode MTTKRP.
 bool partial_sides_ok(int N, int n, int right) { return right ? n < N - 1 : n > 0; }
 
-PlanesPlan partial_plan(const int64_t* dims, int N, int C, int n, int right, const mtk_opts& o) {
+PlanesPlan partial_plan(const int64_t* dims, int N, int C, int n, int right, const mtk_opts& o, int reserve = 0) {
     const View v = mode_view(dims, N, n);
-    if (right) return planes_plan(1, v.L * v.I, dims + n + 1, N - n - 1, C, 0, planes_ctas(o.splits));
-    return planes_plan(v.L, v.I * v.R, dims, n, C, n, planes_ctas(o.splits));
+    const int ctas = planes_ctas_for(o, reserve);
+    if (right) return planes_plan(1, v.L * v.I, dims + n + 1, N - n - 1, C, 0, ctas);
+    return planes_plan(v.L, v.I * v.R, dims, n, C, n, ctas);
 }
 
 // the dimension tree's partials: right = modes >= 2 (n = 1), left = modes 0, 1 (n = 2)
-PlanesPlan tree_plan(const int64_t* dims, int N, int C, int right, const mtk_opts& o) {
-    return partial_plan(dims, N, C, right ? 1 : 2, right, o);
+PlanesPlan tree_plan(const int64_t* dims, int N, int C, int right, const mtk_opts& o, int reserve = 0) {
+    return partial_plan(dims, N, C, right ? 1 : 2, right, o, reserve);
 }
 
-bool tree_ok(const int64_t* dims, int N, int C, const mtk_opts& o) {
+bool tree_ok(const int64_t* dims, int N, int C, const mtk_opts& o, int reserve = 0) {
     if (!tree_shape(dims, N, C)) return false;
-    if (!tree_plan(dims, N, C, 1, o).ok) return false;
-    return N == 3 || tree_plan(dims, N, C, 0, o).ok;
+    if (!tree_plan(dims, N, C, 1, o, reserve).ok) return false;
+    return N == 3 || tree_plan(dims, N, C, 0, o, reserve).ok;
 }
 
-size_t tree_scratch(const int64_t* dims, int N, int C, const mtk_opts& o) {
-    size_t a = planes_scratch_bytes(tree_plan(dims, N, C, 1, o));
+size_t tree_scratch(const int64_t* dims, int N, int C, const mtk_opts& o, int reserve = 0) {
+    size_t a = planes_scratch_bytes(tree_plan(dims, N, C, 1, o, reserve));
     if (N == 4) {
-        const size_t b = planes_scratch_bytes(tree_plan(dims, N, C, 0, o));
+        const size_t b = planes_scratch_bytes(tree_plan(dims, N, C, 0, o, reserve));
         if (b > a) a = b;
     }
     return align256(align256(kStatusBytes) + a);
@@ -499,8 +512,9 @@ size_t tree_scratch(const int64_t* dims, int N, int C, const mtk_opts& o) {
 
 // ws: status (unused) then the planes scratch; T: rows x C, C slowest
 int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int n,
-                      int right, float* T, void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s) {
-    const PlanesPlan pl = partial_plan(dims, N, C, n, right, o);
+                      int right, float* T, void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s,
+                      const FactorHook* hook = nullptr, int reserve = 0) {
+    const PlanesPlan pl = partial_plan(dims, N, C, n, right, o, reserve);
     if (!pl.ok) return MTK_EUNSUPPORTED;
     const View v = mode_view(dims, N, n);
     const float* fac[MTK_MAXN];
@@ -516,9 +530,9 @@ int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* c
     const int64_t rows = right ? v.L * v.I : v.I * v.R;
     const int64_t pitch = split_pitch(v.L * v.I * v.R);
     cudaError_t e = right ? launch_contract_planes(Xs, pitch, 1, rows, v.R, fac, frad, nf, C, pl, T, 1, rows,
-                                                   scratch, status, s, wait_limit_ns(o), o.test_stall)
+                                                   scratch, status, s, wait_limit_ns(o), o.test_stall, hook)
                           : launch_contract_planes(Xs, pitch, v.L, rows, 1, fac, frad, nf, C, pl, T, 1, rows,
-                                                   scratch, status, s, wait_limit_ns(o), o.test_stall);
+                                                   scratch, status, s, wait_limit_ns(o), o.test_stall, hook);
     return e == cudaSuccess ? MTK_OK : MTK_ECUDA;
 }
 
@@ -527,8 +541,9 @@ size_t partial_split_bytes(const PlanesPlan& pl) {
 }
 
 int run_tree_partial(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int right, float* T,
-                     void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s) {
-    return run_partial_split(Xs, dims, N, U, C, right ? 1 : 2, right, T, ws, status, o, s);
+                     void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s, const FactorHook* hook,
+                     int reserve) {
+    return run_partial_split(Xs, dims, N, U, C, right ? 1 : 2, right, T, ws, status, o, s, hook, reserve);
 }
 
 int check_mttkrp_ptrs(const float* X, const float* const* U, int N, int n, const float* M,
@@ -893,8 +908,9 @@ int mtk_norm2(const float* X, int64_t I, double* out, void* ws, size_t ws_bytes,
 // --- CP-ALS sweep ----------------------------------------------------------------
 namespace {
 struct AlsLayout {
-    size_t mbuf, gbufs, gpart, hbuf, flag, upd, tick, mt, tree, total;
+    size_t mbuf, gbufs, gpart, hbuf, flag, upd, tick, hinv, mt, tree, total;
     int maxIn;
+    int reserve;                // SMs the planes contractions leave to an overlapped factorisation
 };
 
 // split = 1: the MTTKRPs read the tensor's BF16 planes (mtk_cp_als_sweep_split);
@@ -904,11 +920,14 @@ AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o, int s
     memset(&a, 0, sizeof(a));
     int64_t maxIn = 0, maxChunks = 1;
     size_t mt = 0;
+    // on the planes, a mode's factorisation H_n^{-1} runs alongside its contraction on an SM
+    // the contraction leaves free (one-launch updates only)
+    a.reserve = (split && als_update_supported(C)) ? 1 : 0;
     for (int k = 0; k < N; ++k) {
         if (dims[k] > maxIn) maxIn = dims[k];
         const int ch = gram_chunks(dims[k]);
         if (ch > maxChunks) maxChunks = ch;
-        const size_t w = split ? split_mttkrp_bytes(dims, N, C, k, o) : mttkrp_layout(dims, N, C, k, o).total;
+        const size_t w = split ? split_mttkrp_bytes(dims, N, C, k, o, a.reserve) : mttkrp_layout(dims, N, C, k, o).total;
         if (w > mt) mt = w;
     }
     a.maxIn = (int)maxIn;
@@ -924,11 +943,13 @@ AlsLayout als_layout(const int64_t* dims, int N, int C, const mtk_opts& o, int s
         const size_t b = als_update_scratch_bytes(als_update_max_ctas(dims, N), C);
         a.upd = u > b ? u : b;
         a.tick = als_ticket_bytes();
+        if (a.reserve) a.hinv = als_hinv_bytes(C);
     }
     cv.take(a.upd);
     cv.take(a.tick);
+    cv.take(a.hinv);
     if (split == 2) {                                   // dimension tree: partials T_R, T_L
-        const size_t ts = tree_scratch(dims, N, C, o);
+        const size_t ts = tree_scratch(dims, N, C, o, a.reserve);
         if (ts > mt) mt = ts;
         a.tree = (size_t)(dims[0] * dims[1] + (N == 4 ? dims[2] * dims[3] : 0)) * C * sizeof(float);
     }
@@ -975,8 +996,9 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
     mtk_opts o = defaults(opts);
     if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
     if (Xs && check_split_opts(opts, true) != MTK_OK) return MTK_EINVAL;
-    const bool tree = Xs && o.algo == MTK_ALGO_TWO_STEP && tree_ok(dims, N, C, o);
-    const AlsLayout a = als_layout(dims, N, C, o, tree ? 2 : (Xs ? 1 : 0));
+    const int split_form = Xs ? 1 : 0;
+    const bool tree = Xs && o.algo == MTK_ALGO_TWO_STEP && tree_ok(dims, N, C, o, als_layout(dims, N, C, o, split_form).reserve);
+    const AlsLayout a = als_layout(dims, N, C, o, tree ? 2 : split_form);
     if (ws_bytes < a.total) return MTK_EWORKSPACE;
     const mtk_opts om = [&]() {                         // per-mode MTTKRPs of a split sweep
         mtk_opts q = o;
@@ -993,6 +1015,7 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
     int* flag = static_cast<int*>(cv.take(a.flag));
     void* upd = cv.take(a.upd);
     unsigned int* tick = static_cast<unsigned int*>(cv.take(a.tick));
+    void* hinv = cv.take(a.hinv);
     char* mws = static_cast<char*>(cv.take(a.mt));
     const double* G[MTK_MAXN];
     for (int k = 0; k < N; ++k) G[k] = Gall + (size_t)k * C * C;
@@ -1014,10 +1037,15 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
     float* TL = tree && N == 4 ? TR + (size_t)dims[0] * dims[1] * C : nullptr;
     for (int n = 0; n < N; ++n) {
         int st = MTK_OK;
+        // H_n^{-1} formed alongside this mode's planes contraction (when it has one of its own)
+        FactorHook hk{G, N, C, n, hinv, status};
+        const FactorHook* hook = a.reserve ? &hk : nullptr;
+        bool hooked = false;
         if (tree && n < 2) {
             // modes 0 and 1 from the right partial (computed once, with U_2.. as they are)
             if (n == 0) {
-                st = run_tree_partial(Xs, dims, N, U, C, 1, TR, mws, status, om, s);
+                st = run_tree_partial(Xs, dims, N, U, C, 1, TR, mws, status, om, s, hook, a.reserve);
+                hooked = hook != nullptr;
                 if (!st && launch_multi_ttv(TR, 1, dims[0], dims[1], U[1], C, 0, M, s) != cudaSuccess) st = MTK_ECUDA;
             } else if (launch_multi_ttv(TR, dims[0], dims[1], 1, U[0], C, 1, M, s) != cudaSuccess) {
                 st = MTK_ECUDA;
@@ -1025,13 +1053,14 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
         } else if (tree && N == 4) {
             // modes 2 and 3 from the left partial (with the updated U_0, U_1)
             if (n == 2) {
-                st = run_tree_partial(Xs, dims, N, U, C, 0, TL, mws, status, om, s);
+                st = run_tree_partial(Xs, dims, N, U, C, 0, TL, mws, status, om, s, hook, a.reserve);
+                hooked = hook != nullptr;
                 if (!st && launch_multi_ttv(TL, 1, dims[2], dims[3], U[3], C, 0, M, s) != cudaSuccess) st = MTK_ECUDA;
             } else if (launch_multi_ttv(TL, dims[2], dims[3], 1, U[2], C, 1, M, s) != cudaSuccess) {
                 st = MTK_ECUDA;
             }
         } else {
-            st = Xs ? do_mttkrp_split(Xs, X, dims, N, U, C, n, M, mws, a.mt, status, om, s)
+            st = Xs ? do_mttkrp_split(Xs, X, dims, N, U, C, n, M, mws, a.mt, status, om, s, hook, a.reserve, &hooked)
                     : do_mttkrp(X, dims, N, U, C, n, M, mws, a.mt, status, o, s);
         }
         if (st) return st;
@@ -1057,6 +1086,7 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
             ua.fit = last ? fit : nullptr;
             ua.status = status;
             ua.programmatic = true;
+            ua.hinv = hooked ? hinv : nullptr;
             if (launch_als_update(ua, s) != cudaSuccess) return MTK_ECUDA;
             continue;
         }

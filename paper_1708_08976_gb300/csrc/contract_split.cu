@@ -56,8 +56,10 @@ constexpr int PS_M = 128;                    // MMA M
 #ifndef MTK_PS_LO_SEP
 #define MTK_PS_LO_SEP 1
 #endif
-#ifndef MTK_PS_MT2_FILL
-#define MTK_PS_MT2_FILL 0.75
+// head: the first prefix with at least 64 rows whose padding is at most 1/MTK_PS_HEAD_PAD
+// of its padded rows
+#ifndef MTK_PS_HEAD_PAD
+#define MTK_PS_HEAD_PAD 32
 #endif
 constexpr int PS_GROUP = MTK_PS_GROUP;       // stages per accumulation chain (at most)
 // one MMA tile: the lo plane accumulates into accumulator columns of its own (1) or into
@@ -75,6 +77,12 @@ constexpr unsigned long long kPsWaitNs = 1000000000ull;
 #define MTK_PS_SB_MIN1 3
 #endif
 
+// L2 eviction hints: tensor tiles are read once (evict first), the head image is read by
+// every stage of every CTA (evict last), so that the streaming tensor does not push the
+// image out of L2.
+#ifndef MTK_PS_L2_HINTS
+#define MTK_PS_L2_HINTS 1
+#endif
 // L2 promotion of the tensor-map loads (0 none, 1 64 B, 2 128 B, 3 256 B), per operand
 // orientation.
 #ifndef MTK_PS_KM_PROMO
@@ -115,6 +123,9 @@ struct PsParams {
     uint32_t idesc_hi, idesc_lo;
     int a_stage, plane_bytes, b_bytes, b_stage, b_base;
     int ntiles, s_full, s_last, nslab;
+    int sk;                 // stream-K: CTA c takes stages [c tot / G, (c + 1) tot / G) of the flattened
+    int64_t sk_tot;         // (tile, stage) space (tot = ntiles * stot, G = gridDim.x); a tile split
+                            // between CTAs leaves one partial slab per piece
     const uint8_t* bimg;
     const float* qtab;      // Q(q, c) as [nruns][CP], or null (products formed in the drain)
     int ntail;
@@ -137,9 +148,36 @@ struct PsParams {
 struct PsUnit {
     int tile, sp, nst, rho;
     int64_t t0, i0;         // first stage; first row of the tile within its class (rows rho + P (i0 + m))
+    bool direct;            // the unit is the whole tile: the result goes straight to the output
 };
 
 __device__ __forceinline__ int ps_units(const PsParams& p) { return (p.ntiles - 1) * p.s_full + p.s_last; }
+
+// stream-K: the CTA that holds flattened stage s
+__host__ __device__ __forceinline__ int64_t sk_cta(int64_t s, int64_t tot, int64_t G) { return ((s + 1) * G - 1) / tot; }
+
+// The units of this CTA, in order: classic, units blockIdx.x, blockIdx.x + gridDim.x, ...;
+// stream-K, the tiles its stage range touches.
+struct PsIter {
+    int64_t s0, s1;
+    int tfirst, nk;
+};
+__device__ __forceinline__ PsIter ps_iter(const PsParams& p) {
+    PsIter it;
+    it.s0 = it.s1 = 0;
+    it.tfirst = 0;
+    const int64_t c = blockIdx.x, G = gridDim.x;
+    if (!p.sk) {
+        const int nu = ps_units(p);
+        it.nk = c < nu ? (int)((nu - c + G - 1) / G) : 0;
+    } else {
+        it.s0 = c * p.sk_tot / G;
+        it.s1 = (c + 1) * p.sk_tot / G;
+        it.tfirst = (int)(it.s0 / p.stot);
+        it.nk = it.s1 > it.s0 ? (int)((it.s1 - 1) / p.stot) - it.tfirst + 1 : 0;
+    }
+    return it;
+}
 
 __device__ __forceinline__ PsUnit ps_unit(const PsParams& p, int b) {
     PsUnit u;
@@ -155,6 +193,23 @@ __device__ __forceinline__ PsUnit ps_unit(const PsParams& p, int b) {
     }
     u.t0 = p.stot * u.sp / S_t;
     u.nst = (int)(p.stot * (u.sp + 1) / S_t - u.t0);
+    u.rho = u.tile / p.ntc;
+    u.i0 = (int64_t)(u.tile - u.rho * p.ntc) * p.BI;
+    u.direct = p.nslab == 1;
+    return u;
+}
+
+__device__ __forceinline__ PsUnit ps_unit_k(const PsParams& p, const PsIter& it, int k) {
+    if (!p.sk) return ps_unit(p, (int)blockIdx.x + k * (int)gridDim.x);
+    PsUnit u;
+    u.tile = it.tfirst + k;
+    const int64_t ts = (int64_t)u.tile * p.stot;
+    const int64_t a = it.s0 > ts ? it.s0 : ts;
+    const int64_t b = it.s1 < ts + p.stot ? it.s1 : ts + p.stot;
+    u.t0 = a - ts;
+    u.nst = (int)(b - a);
+    u.direct = (a == ts && b == ts + p.stot) && p.U == 1;   // packed runs always leave slabs
+    u.sp = (int)((int64_t)blockIdx.x - sk_cta(ts, p.sk_tot, gridDim.x));      // piece of the tile
     u.rho = u.tile / p.ntc;
     u.i0 = (int64_t)(u.tile - u.rho * p.ntc) * p.BI;
     return u;
@@ -176,7 +231,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
     const uint32_t dsm_s = smem_u32(dsm);
     const int SA = p.sa, SB = p.sb, NB = p.nbuf;
 
-    const int nunits = ps_units(p);
+    const PsIter pit = ps_iter(p);
     const int64_t I = p.I;
     const int U = p.U, BI = p.BI, spr = p.spr;
     const int64_t nruns = p.nruns;
@@ -243,8 +298,9 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             };
             int slot = 0;
             uint32_t ph = 1;                                 // parity of the empty phase to wait for
-            for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
-                const PsUnit w = ps_unit(p, ub);
+            const uint64_t pol_a = MTK_PS_L2_HINTS ? policy_evict_first() : policy_evict_normal();
+            for (int uk = 0; ok && uk < pit.nk; ++uk) {
+                const PsUnit w = ps_unit_k(p, pit, uk);
                 i0 = w.i0;
                 rho = w.rho;
                 sr = w.t0 / spr;
@@ -272,15 +328,15 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                         for (int pl = 0; pl < 2; ++pl) {
                             const uint32_t dst = st + (uint32_t)(pl * p.plane_bytes);
                             if (MN) {
-                                tma_load_4d(dst, &xmap, 0, 64 * j, q0, pl, fb);
+                                tma_load_4d_hint(dst, &xmap, 0, 64 * j, q0, pl, fb, pol_a);
                             } else if (p.box_mode == 1) {
                                 // one run per row (q = r): the class offset and its shift
                                 const int64_t base = p.L * rho;
                                 const int x0 = (int)(base - (p.nsh > 1 ? (base & 7) : 0));
-                                tma_load_4d(dst, &xmap, x0 + 64 * j, (int)i0, q0, pl, fb);
+                                tma_load_4d_hint(dst, &xmap, x0 + 64 * j, (int)i0, q0, pl, fb, pol_a);
                             } else {
                                 const int r = q0 / (int)p.Lq;
-                                tma_load_5d(dst, &xmap, 64 * j, q0 - r * (int)p.Lq, (int)i0, r, pl, fb);
+                                tma_load_5d_hint(dst, &xmap, 64 * j, q0 - r * (int)p.Lq, (int)i0, r, pl, fb, pol_a);
                             }
                         }
                     }
@@ -292,13 +348,14 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                                 const int q = (int)(sr * U + g);
                                 if (U == 1) {
                                     for (int a = 0; a < nbox; ++a)
-                                        tma_load_4d(dst + (uint32_t)(a * PS_MN_ATOM), &xmap, (int)(i0 + 64 * a), 64 * j, q,
-                                                    pl, fb);
+                                        tma_load_4d_hint(dst + (uint32_t)(a * PS_MN_ATOM), &xmap, (int)(i0 + 64 * a),
+                                                         64 * j, q, pl, fb, pol_a);
                                 } else {
-                                    tma_load_4d(dst + (uint32_t)(g * PS_MN_ATOM), &xmap, 0, 64 * j, q, pl, fb);
+                                    tma_load_4d_hint(dst + (uint32_t)(g * PS_MN_ATOM), &xmap, 0, 64 * j, q, pl, fb, pol_a);
                                 }
                             } else {
-                                tma_load_3d(dst + (uint32_t)(g * BI * 128), &xmap, gx[g] + 64 * j, gy[g], pl, fb);
+                                tma_load_3d_hint(dst + (uint32_t)(g * BI * 128), &xmap, gx[g] + 64 * j, gy[g], pl, fb,
+                                                 pol_a);
                             }
                         }
                     }
@@ -334,8 +391,9 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             bool ok = true;
             int slot = 0;
             uint32_t ph = 1;
-            for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
-                const PsUnit w = ps_unit(p, ub);
+            const uint64_t pol_b = MTK_PS_L2_HINTS ? policy_evict_last() : policy_evict_normal();
+            for (int uk = 0; ok && uk < pit.nk; ++uk) {
+                const PsUnit w = ps_unit_k(p, pit, uk);
                 int64_t sr = w.t0 / spr;
                 int j = (int)(w.t0 - sr * spr);
                 // first slice of the super-run's image: the head shifted by the run's delta
@@ -353,8 +411,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     }
                     const uint32_t fb = smem_u32(&bfull[slot]);
                     mbar_arrive_expect_tx(fb, (uint32_t)p.b_bytes);
-                    bulk_copy_g2s(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage),
-                                  p.bimg + (ib + j) * p.b_bytes, (uint32_t)p.b_bytes, fb);
+                    bulk_copy_g2s_hint(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage),
+                                       p.bimg + (ib + j) * p.b_bytes, (uint32_t)p.b_bytes, fb, pol_b);
                     ++issued;
                     if (++slot == SB) {
                         slot = 0;
@@ -402,8 +460,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             bool ok = true;
             if (p.stall && !mbar_wait(smem_u32(&stall_bar), 0u, &abort_flag, p.wait_ns)) ok = false;
             uint32_t dcol = tmem;
-            for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
-                const PsUnit w = ps_unit(p, ub);
+            for (int uk = 0; ok && uk < pit.nk; ++uk) {
+                const PsUnit w = ps_unit_k(p, pit, uk);
                 const int nst = w.nst;
                 int j = (int)(w.t0 % spr);
                 for (int s = 0; s < nst; ++s) {
@@ -502,8 +560,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
         int db = 0;                                          // accumulator buffer of group g
         uint32_t dph = 0;                                    // and the parity of its next fill
         bool ok = true;
-        for (int ub = (int)blockIdx.x; ok && ub < nunits; ub += (int)gridDim.x) {
-            const PsUnit w = ps_unit(p, ub);
+        for (int uk = 0; ok && uk < pit.nk; ++uk) {
+            const PsUnit w = ps_unit_k(p, pit, uk);
             const int64_t i0 = w.i0;
             const int nst = w.nst;
             const int64_t rows_here = (p.Ic - i0) < BI ? (p.Ic - i0) : BI;
@@ -616,7 +674,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             }
             if (ok && rowvalid) {
                 const int64_t i = w.rho + (int64_t)p.P * (i0 + myil);
-                if (p.nslab == 1) {
+                if (w.direct) {
 #pragma unroll
                     for (int e = 0; e < 16 * NCH; ++e)
                         if (e < C) p.out[i * p.out_si + e * p.out_sc] = acc[e];
@@ -646,6 +704,9 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
     }
+    // launched after a factorisation it may overlap: complete only after it (a no-op for
+    // an ordinary launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---- per-call preparation: the B image of the head and the table of tail scales ----
@@ -753,11 +814,73 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
 // are added in warp order, so the result does not depend on scheduling.  Many outputs
 // and few slabs (a tall partial MTTKRP): Q = 4, W <= 8; few outputs and many slabs: Q = 1
 // and up to 32 warps, so that enough loads are in flight.
+struct ReduceShape {
+    int64_t I;
+    int C, BI, U, ntiles, s_full, s_last, P, ntc;
+    int sk;                 // stream-K: slabs of a tile = its pieces (0: a whole-tile unit wrote it)
+    int64_t stot, tot, G;
+};
+
+// slabs that hold pieces of output f (0: its tile was written whole, nothing to add)
+__device__ __forceinline__ int reduce_slabs(const ReduceShape& rs, int64_t f, int colmajor) {
+    const int64_t i = colmajor ? f % rs.I : f / rs.C;
+    const int64_t tile = (i % rs.P) * rs.ntc + (i / rs.P) / rs.BI;        // row i = rho + P t
+    if (rs.sk) {
+        const int64_t np = sk_cta((tile + 1) * rs.stot - 1, rs.tot, rs.G) - sk_cta(tile * rs.stot, rs.tot, rs.G) + 1;
+        return (np > 1 || rs.U > 1) ? (int)np * rs.U : 0;
+    }
+    return (tile < rs.ntiles - 1 ? rs.s_full : rs.s_last) * rs.U;
+}
+
+// Few slabs (<= 8) and many outputs: a thread takes 4 consecutive outputs (one 16-byte
+// word), loads all of their slabs at once and adds them in slab order.
+constexpr int kFewSlabs = 8;
+__global__ void __launch_bounds__(256) planes_reduce_few_kernel(const float* __restrict__ part, const ReduceShape rs,
+                                                               float* __restrict__ out, int colmajor, int vec,
+                                                               const uint32_t* status) {
+    allow_dependent_launch();
+    if (status && (*reinterpret_cast<const volatile uint32_t*>(status) & (1u << MTK_ETIMEOUT))) return;
+    const int64_t n = rs.I * rs.C;
+    const int64_t ng = (n + 3) / 4;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f0 = 4 * g;
+        int ns[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ns[j] = f0 + j < n ? reduce_slabs(rs, f0 + j, colmajor) : 0;
+        if (vec && f0 + 3 < n && ns[0] > 0 && ns[1] == ns[0] && ns[2] == ns[0] && ns[3] == ns[0]) {
+            float4 x[kFewSlabs];
+#pragma unroll
+            for (int sl = 0; sl < kFewSlabs; ++sl)
+                if (sl < ns[0]) x[sl] = __ldg(reinterpret_cast<const float4*>(part + (int64_t)sl * n + f0));
+            float4 a = x[0];
+#pragma unroll
+            for (int sl = 1; sl < kFewSlabs; ++sl) {
+                if (sl < ns[0]) {
+                    a.x += x[sl].x;
+                    a.y += x[sl].y;
+                    a.z += x[sl].z;
+                    a.w += x[sl].w;
+                }
+            }
+            *reinterpret_cast<float4*>(out + f0) = a;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (ns[j] == 0) continue;
+                float a = 0.0f;
+                for (int sl = 0; sl < ns[j]; ++sl) a += __ldg(part + (int64_t)sl * n + f0 + j);
+                out[f0 + j] = a;
+            }
+        }
+    }
+}
+
 template <int Q>
-__global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __restrict__ part, int64_t I, int C, int BI,
-                                                             int U, int ntiles, int s_full, int s_last, int P,
-                                                             int ntc, float* __restrict__ out, int colmajor, int vec,
+__global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __restrict__ part, const ReduceShape rs,
+                                                             float* __restrict__ out, int colmajor, int vec,
                                                              const uint32_t* status) {
+    const int64_t I = rs.I;
+    const int C = rs.C;
     allow_dependent_launch();
     // a contraction that timed out left its slabs incomplete: the output stays as it was
     if (status && (*reinterpret_cast<const volatile uint32_t*>(status) & (1u << MTK_ETIMEOUT))) return;
@@ -766,18 +889,18 @@ __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __rest
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = I * C;
     const int64_t f0 = ((int64_t)blockIdx.x * 32 + lane) * Q;
-    auto slabs = [&](int64_t f) {
-        const int64_t i = colmajor ? f % I : f / C;
-        const int64_t tile = (i % P) * ntc + (i / P) / BI;        // row i = rho + P t
-        return (tile < ntiles - 1 ? s_full : s_last) * U;
-    };
+    auto slabs = [&](int64_t f) -> int { return reduce_slabs(rs, f, colmajor); };
     float v[Q];
+    int nsj[Q];
 #pragma unroll
-    for (int j = 0; j < Q; ++j) v[j] = 0.0f;
+    for (int j = 0; j < Q; ++j) {
+        v[j] = 0.0f;
+        nsj[j] = f0 + j < n ? slabs(f0 + j) : 0;
+    }
     bool v4 = false;
     if (f0 < n) {
-        const int ns = slabs(f0);
-        if (Q == 4) v4 = vec && f0 + 3 < n && slabs(f0 + 1) == ns && slabs(f0 + 2) == ns && slabs(f0 + 3) == ns;
+        const int ns = nsj[0];
+        if (Q == 4) v4 = vec && f0 + 3 < n && ns > 0 && nsj[1 % Q] == ns && nsj[2 % Q] == ns && nsj[3 % Q] == ns;
         if (v4) {
             for (int sl = w; sl < ns; sl += W) {
                 const float4 x = __ldg(reinterpret_cast<const float4*>(part + (int64_t)sl * n + f0));
@@ -791,7 +914,7 @@ __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __rest
             for (int j = 0; j < Q; ++j) {
                 const int64_t f = f0 + j;
                 if (f < n) {
-                    const int nj = j == 0 ? ns : slabs(f);
+                    const int nj = nsj[j];
                     float a = 0.0f;
                     for (int sl = w; sl < nj; sl += W) a += __ldg(part + (int64_t)sl * n + f);
                     v[j] = a;
@@ -814,7 +937,7 @@ __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __rest
         } else {
 #pragma unroll
             for (int j = 0; j < Q; ++j)
-                if (f0 + j < n) out[f0 + j] = t[j];
+                if (f0 + j < n && nsj[j] > 0) out[f0 + j] = t[j];
         }
     }
 }
@@ -914,22 +1037,35 @@ __global__ void sum_partials_kernel(const double* __restrict__ part, int n, doub
 
 // block: warp 0 tensor producer, warp 1 MMA issuer (TMEM owner), warp 2 image producer,
 // then four drain warps per 128-row MMA tile
-template <int NCH, bool MN>
-cudaError_t launch_planes_variant(const PsParams& p, const CUtensorMap& map, int grid, size_t smem, cudaStream_t s) {
-    cudaError_t e;
-    if (p.MT == 2) {
-        e = cudaFuncSetAttribute(contract_planes_kernel<NCH, MN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        contract_planes_kernel<NCH, MN, 2><<<grid, 96 + 128 * 2, smem, s>>>(p, map);
-    } else {
-        e = cudaFuncSetAttribute(contract_planes_kernel<NCH, MN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        contract_planes_kernel<NCH, MN, 1><<<grid, 96 + 128, smem, s>>>(p, map);
-    }
+// pdl: launched with programmatic stream serialisation (it may start while the kernel
+// before it, a factorisation, still runs)
+template <int NCH, bool MN, int MT>
+cudaError_t launch_planes_mt(const PsParams& p, const CUtensorMap& map, int grid, size_t smem, cudaStream_t s,
+                             bool pdl) {
+    cudaError_t e = cudaFuncSetAttribute(contract_planes_kernel<NCH, MN, MT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(96 + 128 * MT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, contract_planes_kernel<NCH, MN, MT>, p, map);
     note_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int NCH, bool MN>
+cudaError_t launch_planes_variant(const PsParams& p, const CUtensorMap& map, int grid, size_t smem, cudaStream_t s,
+                                  bool pdl) {
+    return p.MT == 2 ? launch_planes_mt<NCH, MN, 2>(p, map, grid, smem, s, pdl)
+                     : launch_planes_mt<NCH, MN, 1>(p, map, grid, smem, s, pdl);
 }
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -1000,7 +1136,7 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
         const size_t img = (size_t)nsh * (size_t)(padded / PS_BK) * pl.N * 128;
         if (img > ((size_t)32 << 20)) break;
         const double waste = (double)(padded - prod) / (double)padded;
-        if (prod >= PS_BK && (padded - prod) * 32 <= padded) { best = m; break; }
+        if (prod >= PS_BK && (padded - prod) * MTK_PS_HEAD_PAD <= padded) { best = m; break; }
         if (waste < best_waste) { best_waste = waste; best = m; }
     }
     if (best < 0) return pl;
@@ -1095,23 +1231,17 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     int64_t smax = pl.stot / 4;
     if (smax < 1) smax = 1;
     if (T >= ctas) {
-        // more tiles than CTAs: each of the ctas CTAs runs its units (tile, slab) back to
-        // back, with the rings and TMEM kept live, so a unit costs its stages plus about a
-        // quarter stage of drain.  Splitting every tile's stages into s slabs evens out the
-        // units per CTA; the cost in stage-times is ceil(T s / ctas) * (stot / s + 1/4)
-        // plus the slab reduce (8 s I C bytes, ~5 MB per stage-time over the whole GPU)
-        int bs = 1;
-        double bc = 0.0;
-        for (int s = 1; s <= 16 && s <= smax; ++s) {
-            const int64_t waves = ((int64_t)T * s + ctas - 1) / ctas;
-            const double c = (double)waves * ((double)pl.stot / s + 0.25) +
-                             (s > 1 ? 8.0 * s * (double)I * C / 5.0e6 : 0.0);
-            if (s == 1 || c < bc * 0.98) {
-                bc = c;
-                bs = s;
-            }
-        }
-        pl.s_full = pl.s_last = bs;
+        // more tiles than CTAs (a tall view such as a partial MTTKRP): stream-K.  CTA c takes
+        // the stages [c tot / G, (c + 1) tot / G) of the flattened (tile, stage) space (tot =
+        // T stot, G = ctas), so every CTA has the same work to within one stage; it runs the
+        // tiles its range touches back to back with the rings and TMEM kept live.  A tile
+        // that one CTA covers whole goes straight to the output; the pieces of a tile split
+        // between CTAs are partial slabs, at most ceil(stot / (tot / G)) + 1 of them.
+        const int64_t tot = (int64_t)T * pl.stot;
+        const int64_t per = tot / ctas;
+        const int64_t kmax = (pl.stot + per - 1) / per + 1;
+        pl.sk = 1;
+        pl.s_full = pl.s_last = (int)kmax;
     } else if (T == 1) {
         pl.s_full = pl.s_last = (int)(ctas < smax ? ctas : smax);
     } else {
@@ -1125,7 +1255,7 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
         pl.s_last = (int)sl;
     }
     pl.grid = (T - 1) * pl.s_full + pl.s_last;          // units; at most ctas CTAs run them
-    if (pl.grid > ctas) pl.grid = ctas;
+    if (pl.grid > ctas || pl.sk) pl.grid = ctas;
     pl.nslab = (pl.s_full > pl.s_last ? pl.s_full : pl.s_last) * pl.U;
     pl.image_bytes = (size_t)pl.nsh * pl.spr * pl.N * 128;
     // table of tail scales Q(q, c) when it is small
@@ -1147,7 +1277,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
                                    const float* const* fac, const int64_t* frad, int nfac, int C,
                                    const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
                                    void* scratch, uint32_t* status, cudaStream_t s,
-                                   unsigned long long wait_ns, int stall) {
+                                   unsigned long long wait_ns, int stall, const FactorHook* hook) {
     char* sc = static_cast<char*>(scratch);
     uint8_t* image = reinterpret_cast<uint8_t*>(sc);
     float* qtab = pl.qtab_bytes ? reinterpret_cast<float*>(sc + round_up((int64_t)pl.image_bytes, 256)) : nullptr;
@@ -1183,6 +1313,10 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
         planes_prep_kernel<<<(int)blocks, 256, 0, s>>>(pa);
         note_launches(1);
         cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (hook) {
+        const cudaError_t e = launch_als_factor(hook->G, hook->N, hook->C, hook->n, hook->hinv, hook->status, s);
         if (e != cudaSuccess) return e;
     }
 
@@ -1290,6 +1424,8 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     p.s_full = pl.s_full;
     p.s_last = pl.s_last;
     p.nslab = pl.nslab;
+    p.sk = pl.sk;
+    p.sk_tot = (int64_t)pl.ntiles * pl.stot;
     p.bimg = image;
     p.qtab = qtab;
     p.ntail = nfac - pl.head;
@@ -1313,32 +1449,49 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     cudaError_t e;
     if (pl.mn) {
         switch (nch) {
-            case 1: e = launch_planes_variant<1, true>(p, map, pl.grid, smem, s); break;
-            case 2: e = launch_planes_variant<2, true>(p, map, pl.grid, smem, s); break;
-            case 3: e = launch_planes_variant<3, true>(p, map, pl.grid, smem, s); break;
-            default: e = launch_planes_variant<4, true>(p, map, pl.grid, smem, s); break;
+            case 1: e = launch_planes_variant<1, true>(p, map, pl.grid, smem, s, hook != nullptr); break;
+            case 2: e = launch_planes_variant<2, true>(p, map, pl.grid, smem, s, hook != nullptr); break;
+            case 3: e = launch_planes_variant<3, true>(p, map, pl.grid, smem, s, hook != nullptr); break;
+            default: e = launch_planes_variant<4, true>(p, map, pl.grid, smem, s, hook != nullptr); break;
         }
     } else {
         switch (nch) {
-            case 1: e = launch_planes_variant<1, false>(p, map, pl.grid, smem, s); break;
-            case 2: e = launch_planes_variant<2, false>(p, map, pl.grid, smem, s); break;
-            case 3: e = launch_planes_variant<3, false>(p, map, pl.grid, smem, s); break;
-            default: e = launch_planes_variant<4, false>(p, map, pl.grid, smem, s); break;
+            case 1: e = launch_planes_variant<1, false>(p, map, pl.grid, smem, s, hook != nullptr); break;
+            case 2: e = launch_planes_variant<2, false>(p, map, pl.grid, smem, s, hook != nullptr); break;
+            case 3: e = launch_planes_variant<3, false>(p, map, pl.grid, smem, s, hook != nullptr); break;
+            default: e = launch_planes_variant<4, false>(p, map, pl.grid, smem, s, hook != nullptr); break;
         }
     }
     if (e != cudaSuccess) return e;
     if (pl.nslab > 1) {
         const int64_t n = I * C;
+        ReduceShape rs;
+        rs.I = I;
+        rs.C = C;
+        rs.BI = pl.BI;
+        rs.U = pl.U;
+        rs.ntiles = pl.ntiles;
+        rs.s_full = pl.s_full;
+        rs.s_last = pl.s_last;
+        rs.P = pl.P;
+        rs.ntc = pl.ntc;
+        rs.sk = pl.sk;
+        rs.stot = pl.stot;
+        rs.tot = (int64_t)pl.ntiles * pl.stot;
+        rs.G = pl.grid;
         const int vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
                         ((reinterpret_cast<uintptr_t>(part) & 15) == 0);
-        if (n >= 65536) {
+        if (n >= 65536 && pl.nslab <= kFewSlabs) {
+            const int64_t ng = (n + 3) / 4;
+            int64_t blocks = (ng + 255) / 256;
+            if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+            planes_reduce_few_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, rs, out, p.part_cm, vec, status);
+        } else if (n >= 65536) {
             const int W = pl.nslab < 8 ? pl.nslab : 8;
-            planes_reduce_kernel<4><<<(unsigned)((n + 127) / 128), 32 * W, 0, s>>>(
-                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, pl.P, pl.ntc, out, p.part_cm, vec, status);
+            planes_reduce_kernel<4><<<(unsigned)((n + 127) / 128), 32 * W, 0, s>>>(part, rs, out, p.part_cm, vec, status);
         } else {
             const int W = pl.nslab < 32 ? pl.nslab : 32;
-            planes_reduce_kernel<1><<<(unsigned)((n + 31) / 32), 32 * W, 0, s>>>(
-                part, I, C, pl.BI, pl.U, pl.ntiles, pl.s_full, pl.s_last, pl.P, pl.ntc, out, p.part_cm, 0, status);
+            planes_reduce_kernel<1><<<(unsigned)((n + 31) / 32), 32 * W, 0, s>>>(part, rs, out, p.part_cm, 0, status);
         }
         note_launches(1);
         e = cudaGetLastError();

@@ -106,6 +106,7 @@ struct PlanesPlan {
     int ok, mn, head, spr, U, BI, MT, CP, N, ntiles, s_full, s_last, nslab, grid;
     int P, ntc, nsh;          // K-major row classes, tiles per class, head image shifts
     int box_mode;             // packed runs: one TMA box per group (0) or for all (1: along r, 2: along lq)
+    int sk;                   // stream-K over the (tile, stage) space (tall views)
     int64_t H, nruns, Lq, stot, Ic;
     size_t image_bytes, qtab_bytes, part_bytes;
 };
@@ -113,12 +114,23 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
 size_t planes_scratch_bytes(const PlanesPlan& pl);   // image + Q table + partials
 int planes_ctas(int splits);           // CTAs of one launch (0 = one per SM)
 // scratch: planes_scratch_bytes(pl) bytes, 256-byte aligned
+// A factorisation to overlap with a planes contraction: H_n^{-1} of a CP-ALS update
+// (launch_als_factor), launched between the contraction's prep and the contraction, which
+// then starts at once (programmatic stream serialisation) on the SMs the plan left free and
+// completes only after the factorisation has.
+struct FactorHook {
+    const double* const* G;
+    int N, C, n;
+    void* hinv;
+    uint32_t* status;
+};
 // wait_ns: limit of the kernel's abortable waits (0: 1 s); stall: the timeout test hook
 cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int64_t I, int64_t R,
                                    const float* const* fac, const int64_t* frad, int nfac, int C,
                                    const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
                                    void* scratch, uint32_t* status, cudaStream_t s,
-                                   unsigned long long wait_ns = 0, int stall = 0);
+                                   unsigned long long wait_ns = 0, int stall = 0,
+                                   const FactorHook* hook = nullptr);
 
 // ---- batched MTTKRPs in one persistent launch (batched.cu) --------------------------
 typedef mtk_batch_problem BatchedProblem;
@@ -170,8 +182,15 @@ struct AlsUpdateArgs {
     double* r2;
     uint32_t* status;
     bool programmatic;
+    const void* hinv;          // H^{-1} from launch_als_factor (null: factored in the update)
 };
 bool als_update_supported(int C);
+// H_n^{-1} (and its not-positive-definite flag) for a later update, in one CTA that
+// triggers the next kernel of the stream at once (so a long kernel launched after it with
+// programmatic stream serialisation can run meanwhile).  hinv: als_hinv_bytes(C) bytes.
+size_t als_hinv_bytes(int C);
+cudaError_t launch_als_factor(const double* const* G, int N, int C, int n, void* hinv, uint32_t* status,
+                              cudaStream_t s);
 size_t als_ticket_bytes();
 int als_update_ctas(int64_t In, int64_t* rows);
 int als_update_max_ctas(const int64_t* dims, int N);

@@ -177,7 +177,10 @@ def test_partial_split_rejected_before_launch():
 def test_sweep_workspace_covers_tree_partials(dims, C):
     """The CP-ALS workspace query (every sweep form) is at least what the dimension tree
     carves: each partial contraction's own workspace plus the partial tensors it keeps,
-    and at least every per-mode planes MTTKRP's workspace (host-side sizes, no launch)."""
+    and at least every per-mode planes MTTKRP's workspace (host-side sizes, no launch).
+    A sweep runs its planes contractions on one CTA per SM but one (151 on the 152-SM
+    GB300 the host-side sizes assume): that SM takes the factorisation overlapped with
+    the contraction."""
     lib = L.load()
     N = len(dims)
     d = L.dims_arr(list(dims))
@@ -185,12 +188,13 @@ def test_sweep_workspace_covers_tree_partials(dims, C):
     ws = lib.mtk_cp_als_workspace(d, N, C, ctypes.byref(o))
     assert ws > 0
     parts = 4 * dims[0] * dims[1] * C + (4 * dims[2] * dims[3] * C if N == 4 else 0)
-    wr = lib.mtk_partial_mttkrp_split_workspace(d, N, C, 1, 1, None)
-    wl = lib.mtk_partial_mttkrp_split_workspace(d, N, C, 2, 0, None) if N == 4 else 0
+    so = L.opts(splits=151)
+    wr = lib.mtk_partial_mttkrp_split_workspace(d, N, C, 1, 1, ctypes.byref(so))
+    wl = lib.mtk_partial_mttkrp_split_workspace(d, N, C, 2, 0, ctypes.byref(so)) if N == 4 else 0
     assert wr > 0 and (N == 3 or wl > 0)
     assert ws >= max(wr, wl) + parts
     for n in range(N):
-        assert ws >= lib.mtk_mttkrp_split_workspace(d, N, C, n, None)
+        assert ws >= lib.mtk_mttkrp_split_workspace(d, N, C, n, ctypes.byref(so))
 
 
 def test_noalloc_scratch_covers_the_benchmark_shapes():
