@@ -56,10 +56,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="corr4",
-                    choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth", "krp"],
+                    choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth", "krp", "corr4-sym"],
                     help="paper-synth: the paper's equal-dimension tensors (N = 3..6, ~7.3e8 entries, "
                          "C = 25), every mode's MTTKRP timed and checked on sampled rows; krp: the "
                          "Khatri-Rao product with and without reuse (Z = 2..4, ~2e7 rows, C = 25, 50); "
+                         "corr4-sym: corr4 stored packed in its symmetric modes 0/1, every mode's MTTKRP "
+                         "from the packed planes, and a CP-ALS sweep of the packed 3-way tensor; "
                          "each prints its own line")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run every mode's MTTKRP W+K times (for profiler captures)")
@@ -95,6 +97,22 @@ def workload(name):
         X, dims, U = synth.cube512()
         desc = "cube512: 512^3 FP32 N(0,1), rank C=32, factors N(0,1)/sqrt(32)"
     return X, tuple(dims), U, desc
+
+
+def ffma_peak(mtk, torch):
+    """The device's FP32 FMA throughput (TFLOP/s) from the library's FMA probe: the best
+    of three CUDA-event timings of one launch (8 CTAs of 256 threads per SM, 8 independent
+    chains per thread)."""
+    mtk.ffma_probe(8, 256)
+    best = 0.0
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        flops = mtk.ffma_probe(8, 65536)
+        b.record()
+        b.synchronize()
+        best = max(best, flops / (a.elapsed_time(b) * 1e-3) / 1e12)
+    return best
 
 
 def time_calls(fn, reps, warm=2, stream=None):
@@ -357,7 +375,7 @@ def run_paper_synth(args, mtk, torch, dev, hbm_peak):
         U64 = [u.astype(np.float64) for u in U]
         Xd = torch.from_numpy(X).to(dev)
         Ud = [torch.from_numpy(u).to(dev) for u in U]
-        Xs, _ = mtk.split_tensor(Xd)
+        Xs, _ = mtk.split_tensor(Xd, dims)
         M = torch.empty((dims[0], C), dtype=torch.float32, device=dev)
         g = np.random.default_rng(1000 + N)
         modes = []
@@ -389,6 +407,98 @@ def run_paper_synth(args, mtk, torch, dev, hbm_peak):
     return 0
 
 
+def run_sym(args, mtk, torch, dev, hbm_peak):
+    """corr4 (200x200x300x40, exactly symmetric in modes 0/1) stored packed: the 20,100
+    entries a >= b of each 200 x 200 slice (20,104 rows with padding), about half the
+    bytes.  Every mode's MTTKRP of the full tensor is computed from the BF16 planes of the
+    packed tensor (mtk_mttkrp_sym_split) and checked on sampled rows against the FP64
+    oracle on the full tensor; the same MTTKRPs on the full tensor's planes are timed
+    beside it.  Roofline: the packed planes (4 B per packed entry) + factors + output over
+    the measured copy bandwidth.  Then the paper's 3-D variant: the 19,900 entries a > b
+    as one mode of a 3-way tensor (19,904 x 300 x 40 with padding), one CP-ALS sweep on
+    its planes (C = 25)."""
+    import oracle
+    from paper_1708_08976_gb300 import _lib as L
+    lib = L.load()
+    X, dims, U = synth.corr4()
+    N, C, I = len(dims), U[0].shape[1], X.size
+    U64 = [u.astype(np.float64) for u in U]
+    Xd = torch.from_numpy(X).to(dev)
+    Ud = [torch.from_numpy(u).to(dev) for u in U]
+    Xs, _ = mtk.split_tensor(Xd, dims)
+    Xp = mtk.pack_symmetric(Xd, dims)
+    Pp = lib.mtk_sym_packed_rows(dims[0], 1)
+    rest = I // (dims[0] * dims[1])
+    Xps, _ = mtk.split_tensor(Xp, mtk.sym_packed_dims(dims))
+    del Xp
+    torch.cuda.synchronize()
+    pack_us = time_calls(lambda: mtk.pack_symmetric(Xd, dims), 3) * 1e6
+    M = torch.empty((max(dims), C), dtype=torch.float32, device=dev)
+    g = np.random.default_rng(77)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    modes = []
+    l0 = lib.mtk_launch_count()
+    reps = max(args.steps, 5)
+    for n in range(N):
+        out = M[: dims[n]]
+        fn_sym = lambda: mtk.mttkrp_sym(Xps, dims, Ud, n, out=out)
+        fn_full = lambda: mtk.mttkrp(None, dims, Ud, n, Xs=Xs, out=out)
+        t_full = time_calls(fn_full, reps, warm=max(args.warmup, 1))
+        t_sym = time_calls(fn_sym, reps, warm=max(args.warmup, 1))
+        fn_sym()
+        rows = np.unique(np.concatenate([[0, dims[n] - 1], g.integers(0, dims[n], 6)]))
+        ref = oracle.mttkrp_rows_f32(X, dims, U64, n, rows)
+        got = out[torch.as_tensor(rows, device=dev)].double().cpu().numpy()
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        b = 4.0 * Pp * rest + 4.0 * C * (sum(dims) - dims[n]) + 4.0 * dims[n] * C
+        modes.append({"n": n, "us_packed": t_sym * 1e6, "us_full_planes": t_full * 1e6,
+                      "speedup_vs_full": t_full / t_sym, "bytes_packed": b,
+                      "roofline_frac": (b / hbm_peak / 1e9) / t_sym, "rel_err_sampled_rows": err})
+    launches = lib.mtk_launch_count() - l0
+    # the paper's 3-D variant: CP-ALS on the packed 3-way tensor without the diagonal
+    Xp3 = mtk.pack_symmetric(Xd, dims, diag=False)
+    del Xd, Xs, Xps
+    torch.cuda.empty_cache()
+    d3 = (lib.mtk_sym_packed_rows(dims[0], 0), dims[2], dims[3])
+    U3 = [torch.from_numpy(u).to(dev) for u in synth.uniform_factors(d3, C, 5, np.float32)]
+    als = mtk.ALS(Xp3, d3, U3, presplit=True)
+    for _ in range(max(args.warmup, 3)):
+        als.sweep()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        als.sweep()
+    e1.record()
+    torch.cuda.synchronize()
+    sweep3_ms = e0.elapsed_time(e1) / args.steps
+    clocks = sampler.stop()
+    t_step = sum(m["us_packed"] for m in modes) * 1e-6
+    bsum = sum(m["bytes_packed"] for m in modes)
+    achieved = bsum / t_step / 1e9
+    print(json.dumps({
+        "metric": "Dense MTTKRP of a tensor symmetric in modes 0/1 from packed storage, every mode",
+        "value": N * 2.0 * I * C / t_step / 1e12, "unit": "TFLOP/s (full-tensor MTTKRP flops 2 I C per mode)",
+        "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "dtype": "bf16x2 split products (packed tensor pre-split into BF16 hi/lo planes), f32 accumulate",
+        "data": "synthetic",
+        "config": {"workload": "corr4-sym: corr4 (200x200x300x40, exactly symmetric in modes 0/1) packed as "
+                               f"{Pp} x 300 x 40 (a >= b), rank C=25", "dims": list(dims), "packed_rows": Pp,
+                   "step": "the 4 MTTKRPs of the full tensor from the packed planes", "pack_us": pack_us,
+                   "l2": "packed planes (0.96 GB) larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "mtk_mttkrp_sym_split per mode (pair products or triangle walk + planes contraction)"},
+        "modes": modes,
+        "paper_3d_variant": {"dims": list(d3), "packed_rows_without_diagonal": dims[0] * (dims[0] - 1) // 2,
+                             "sweep_ms": sweep3_ms, "fit": float(als.fit.item()),
+                             "tflops": 3 * 2.0 * d3[0] * d3[1] * d3[2] * C / (sweep3_ms * 1e-3) / 1e12},
+        "clocks": clocks, "gpu_launches": int(launches)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -408,6 +518,8 @@ def main():
         return run_paper_synth(args, mtk, torch, dev, hbm_peak)
     if args.workload == "krp":
         return run_krp(args, mtk, torch, dev, hbm_peak)
+    if args.workload == "corr4-sym":
+        return run_sym(args, mtk, torch, dev, hbm_peak)
     X, dims, U, desc = workload(args.workload)
     N = len(dims)
     C = U[0].shape[1]
@@ -417,7 +529,7 @@ def main():
     U0 = [torch.from_numpy(u).to(dev) for u in U]
     if args.kernel_only:
         prec = "planes" if args.precision == "best" else args.precision
-        Xs = mtk.split_tensor(Xd)[0] if prec == "planes" else None
+        Xs = mtk.split_tensor(Xd, dims)[0] if prec == "planes" else None
         ts = []
         if Xs is not None and args.sweep == "tree":
             # the two partial contractions of the dimension tree (n = 1 right, n = 2 left)
@@ -452,10 +564,11 @@ def main():
     Ud64 = [u.astype(np.float64) for u in U]
     g = np.random.default_rng(123)
     forms = {}
+    ffma = ffma_peak(mtk, torch)
     # the tensor split once into its BF16 planes (with ||X||^2 from the same pass)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     torch.cuda.synchronize()
-    split_us = time_calls(lambda: mtk.split_tensor(Xd, out=Xs), 3) * 1e6
+    split_us = time_calls(lambda: mtk.split_tensor(Xd, dims, out=Xs), 3) * 1e6
 
     def call(prec, n, out=None):
         if prec == "planes":
@@ -474,6 +587,14 @@ def main():
                 times.append(time_calls(lambda: call(prec, n, out=M), 5))
             forms[prec] = {"rel_err_per_mode": errs, "mttkrp_us_per_mode": [t * 1e6 for t in times],
                            "tflops_per_mode": [2.0 * I * C / t / 1e12 for t in times]}
+            if prec == "fp32":
+                # the plain-FP32 form runs on the CUDA cores (one FFMA per multiply-add): its
+                # ceiling is the measured FMA throughput, or the HBM read of the tensor
+                forms[prec]["ffma_peak_tflops"] = ffma
+                forms[prec]["ffma_frac_per_mode"] = [2.0 * I * C / t / 1e12 / ffma for t in times]
+                forms[prec]["hbm_frac_per_mode"] = [
+                    (4.0 * I + 4.0 * C * (sum(dims) - dims[n]) + 4.0 * dims[n] * C) / t / 1e9 / hbm_peak
+                    for n, t in enumerate(times)]
         except mtk.MtkError as e:
             forms[prec] = {"unavailable": str(e)}
     if args.precision == "best":

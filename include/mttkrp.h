@@ -149,33 +149,93 @@ int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* 
 /* Tensor stored as two BF16 planes (Section 2.2: CP-ALS runs an MTTKRP for every mode
  * of every sweep on the same tensor, so the tensor can be prepared once) ----------
  * The split: hi = bf16_rn(x), lo = bf16_rn(x - hi) for every entry x (two-piece split
- * of Henry, Tang and Heinecke, ARITH 2019; |x - hi - lo| <= 2^-16 |x|).  Xs holds hi at
- * entries [0, I) and lo at [pitch, pitch + I), pitch = mtk_split_pitch(I), both in the
- * natural linearization, as 16-bit BF16 words: mtk_split_bytes(I) bytes in all, the
- * size of the FP32 tensor rounded up to 64 entries per plane.  Xs: device, 16-byte
- * aligned, caller-owned.  normX2 (device double, may be NULL) receives ||X||^2 from
- * the same pass (exact squares, compensated FP32 sums of 64 entries added in FP64,
- * fixed order).  ws: at least mtk_split_workspace(I) bytes. */
-int64_t mtk_split_pitch(int64_t I);
-size_t mtk_split_bytes(int64_t I);
-size_t mtk_split_workspace(int64_t I);
-int mtk_split_tensor(const float* X, int64_t I, void* Xs, double* normX2, void* ws, size_t ws_bytes,
-                     void* stream);
+ * of Henry, Tang and Heinecke, ARITH 2019; |x - hi - lo| <= 2^-16 |x|).  The planes keep
+ * the natural linearization with mode 0 padded to I0p = mtk_split_rows0(dims[0]), the
+ * next multiple of 8: entry (i0, i1, ..., i_{N-1}) sits at i0 + I0p (i1 + I1 (i2 + ...)),
+ * and the entries with i0 >= I0 are zero.  Every row of every mode's matricization then
+ * starts on a 16-byte boundary, which the tensor-core loads need.  Xs holds hi at entries
+ * [0, NXp) and lo at [pitch, pitch + NXp), NXp = I0p prod(dims[1..N-1]),
+ * pitch = mtk_split_pitch(dims, N) (NXp rounded up to 64), as 16-bit BF16 words:
+ * mtk_split_bytes(dims, N) bytes in all, the size of the FP32 tensor when I0 is a
+ * multiple of 8.  Xs: device, 16-byte aligned, caller-owned.  normX2 (device double, may
+ * be NULL) receives ||X||^2 from the same pass (exact squares, compensated FP32 sums of 64
+ * entries added in FP64, fixed order).  ws: at least mtk_split_workspace(dims, N) bytes.
+ * Bad dims (N outside 1..8, a dim < 1, more than 2^46 padded entries): the size queries
+ * return 0 and the split MTK_EINVAL. */
+int64_t mtk_split_rows0(int64_t I0);
+int64_t mtk_split_pitch(const int64_t* dims, int N);
+size_t mtk_split_bytes(const int64_t* dims, int N);
+size_t mtk_split_workspace(const int64_t* dims, int N);
+int mtk_split_tensor(const float* X, const int64_t* dims, int N, void* Xs, double* normX2, void* ws,
+                     size_t ws_bytes, void* stream);
 
 /* MTTKRP on the planes (the same operation as mtk_mttkrp, tensor entries carried as
  * hi + lo, KRP entries as three BF16 pieces, all six cross products on tcgen05 with
  * FP32 accumulation: the accuracy of MTK_PREC_BF16X2).  The tensor is read through TMA
  * straight into the tensor-core operand, 4 bytes per entry.  Xs: from
  * mtk_split_tensor for a tensor with these dims.  X (device, may be NULL): the FP32
- * tensor, used only for shapes the planes kernel does not take (C > 64, I^L or I_n not
- * a multiple of 8, ...), which then run mtk_mttkrp with MTK_PREC_BF16X2; with X NULL
- * such shapes return MTK_EUNSUPPORTED.  opts: algo AUTO or FUSED, precision AUTO or
+ * tensor, used only for shapes the planes kernel does not take (C > 64, a head KRP
+ * image above 32 MB, index ranges above 2^31), which then run mtk_mttkrp with
+ * MTK_PREC_BF16X2; with X NULL such shapes return MTK_EUNSUPPORTED.  opts: algo AUTO or FUSED, precision AUTO or
  * BF16X2, splits = CTAs of the launch (0: one per SM); else MTK_EINVAL.  ws: at least
  * mtk_mttkrp_split_workspace(...) bytes. */
 size_t mtk_mttkrp_split_workspace(const int64_t* dims, int N, int C, int n, const mtk_opts* opts);
 int mtk_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, const float* const* U,
                      int C, int n, float* M, void* ws, size_t ws_bytes, const mtk_opts* opts,
                      void* stream);
+
+/* Every mode's MTTKRP with the same factors, on the planes (the gradient of the CP loss,
+ * Section 2.2, needs all N of them).  M[n] (device, I_n x C row-major) receives the
+ * mode-n MTTKRP for n = 0..N-1.  For N = 3, 4 and opts->algo AUTO or TWO_STEP this runs
+ * the dimension tree of Algorithm 4: the partial contraction over modes >= 2 (one pass over
+ * the tensor) and multi-TTVs give M[0] and M[1]; the contraction over modes 0, 1 (N = 4) or
+ * the mode-2 MTTKRP (N = 3) gives the rest, so the tensor is read twice instead of N
+ * times.  FUSED, or other N: N planes MTTKRPs.  Xs: from mtk_split_tensor; every mode must
+ * be one the planes kernel takes (else MTK_EUNSUPPORTED and a workspace query of 0).
+ * opts: precision AUTO or BF16X2; algo AUTO, FUSED or TWO_STEP.  ws: at least
+ * mtk_mttkrp_all_split_workspace(...) bytes. */
+size_t mtk_mttkrp_all_split_workspace(const int64_t* dims, int N, int C, const mtk_opts* opts);
+int mtk_mttkrp_all_split(const void* Xs, const int64_t* dims, int N, const float* const* U, int C,
+                         float* const* M, void* ws, size_t ws_bytes, const mtk_opts* opts, void* stream);
+
+/* FP32 FMA throughput probe: the ceiling of the plain-FP32 contraction ------------------
+ * mtk_ffma_probe launches ctas_per_sm CTAs per SM of 256 threads, each thread running 8
+ * independent FMA chains of `iters` steps, and stores one float per thread into `out`
+ * (device, mtk_ffma_probe_out_floats(ctas_per_sm) floats).  *flops (host, may be null)
+ * receives the floating-point operations it performs (2 per FMA).  The caller times the
+ * launch (CUDA events on `stream`): flops / time is the device's FP32 FMA throughput.
+ * ctas_per_sm in [1, 64], iters in [1, 2^24], else MTK_EINVAL. */
+int64_t mtk_ffma_probe_out_floats(int ctas_per_sm);
+int mtk_ffma_probe(int ctas_per_sm, int iters, float* out, double* flops, void* stream);
+
+/* Tensors symmetric in modes 0 and 1, stored packed (Section 5.3.3: the fMRI tensor's
+ * pair of region modes kept as one mode of the entries of one triangle) ----------------
+ * dims[0] = dims[1] = n0; r is the flat index of modes 2..N-1 (natural order).
+ * diag = 1: the entry X(a, b, r) with a >= b is kept at Xp[p + Pp r], p = a (a + 1) / 2 + b
+ * (n0 (n0 + 1) / 2 rows).  diag = 0 (the paper's layout: 200 regions -> 19,900 rows): only
+ * a > b, p = a (a - 1) / 2 + b (n0 (n0 - 1) / 2 rows), and the tensor is taken to be zero
+ * on its diagonal a = b.  Pp = mtk_sym_packed_rows(n0, diag) is the row count rounded up to
+ * a multiple of 8; the padding rows hold zeros.  The packed tensor has about half the
+ * entries of the full one.
+ * mtk_pack_symmetric: Xp (device, Pp * prod(dims[2..N-1]) floats) from the full tensor X
+ * (device, natural order); only the entries with a >= b (a > b) are read: the tensor is
+ * taken to be symmetric in modes 0, 1.  N >= 3, dims[0] == dims[1], diag 0 or 1, else
+ * MTK_EINVAL.
+ * mtk_mttkrp_sym_split: the mode-n MTTKRP of the full tensor (the same M as mtk_mttkrp on it,
+ * with its diagonal zeroed for diag = 0) from the BF16 planes of its packed form
+ * (mtk_split_tensor of Xp, mtk_split_bytes of Pp * prod(dims[2..]) entries).  Modes n >= 2
+ * run the planes MTTKRP of the packed tensor with a first factor
+ * W(p(a, b), c) = U_0(a, c) U_1(b, c) + U_0(b, c) U_1(a, c) (a > b), U_0(a, c) U_1(a, c)
+ * (a = b); modes 0 and 1 run its mode-0 MTTKRP V and then
+ * M(a, c) = sum_b V(p(max(a, b), min(a, b)), c) U_other(b, c) (b != a for diag = 0).
+ * dims: the full tensor's; U as for mtk_mttkrp (U[n] may be null); opts as for
+ * mtk_mttkrp_split; shapes the planes kernel does not take give MTK_EUNSUPPORTED (the
+ * workspace query then returns 0).  ws: at least mtk_mttkrp_sym_split_workspace(...) bytes. */
+int64_t mtk_sym_packed_rows(int64_t n0, int diag);
+int mtk_pack_symmetric(const float* X, const int64_t* dims, int N, int diag, float* Xp, void* stream);
+size_t mtk_mttkrp_sym_split_workspace(const int64_t* dims, int N, int diag, int C, int n, const mtk_opts* opts);
+int mtk_mttkrp_sym_split(const void* Xps, const int64_t* dims, int N, int diag, const float* const* U, int C, int n,
+                         float* M, void* ws, size_t ws_bytes, const mtk_opts* opts, void* stream);
 
 /* Batched MTTKRPs (Section 2.2) in one persistent launch ---------------------
  * P independent problems, each one mode-n MTTKRP of its own tensor, all computed by one

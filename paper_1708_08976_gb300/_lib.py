@@ -53,12 +53,21 @@ SIGNATURES = {
     "mtk_mttkrp_workspace": (SZ, [P, I32, I32, I32, OPTS_P]),
     "mtk_mttkrp": (I32, [P, P, I32, P, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_mttkrp_noalloc": (I32, [P, P, I32, P, I32, I32, P, OPTS_P, U32P, P]),
-    "mtk_split_pitch": (I64, [I64]),
-    "mtk_split_bytes": (SZ, [I64]),
-    "mtk_split_workspace": (SZ, [I64]),
-    "mtk_split_tensor": (I32, [P, I64, P, P, P, SZ, P]),
+    "mtk_split_rows0": (I64, [I64]),
+    "mtk_split_pitch": (I64, [P, I32]),
+    "mtk_split_bytes": (SZ, [P, I32]),
+    "mtk_split_workspace": (SZ, [P, I32]),
+    "mtk_split_tensor": (I32, [P, P, I32, P, P, P, SZ, P]),
     "mtk_mttkrp_split_workspace": (SZ, [P, I32, I32, I32, OPTS_P]),
     "mtk_mttkrp_split": (I32, [P, P, P, I32, P, I32, I32, P, P, SZ, OPTS_P, P]),
+    "mtk_mttkrp_all_split_workspace": (SZ, [P, I32, I32, OPTS_P]),
+    "mtk_mttkrp_all_split": (I32, [P, P, I32, P, I32, P, P, SZ, OPTS_P, P]),
+    "mtk_ffma_probe_out_floats": (I64, [I32]),
+    "mtk_ffma_probe": (I32, [I32, I32, P, P, P]),
+    "mtk_sym_packed_rows": (I64, [I64, I32]),
+    "mtk_pack_symmetric": (I32, [P, P, I32, I32, P, P]),
+    "mtk_mttkrp_sym_split_workspace": (SZ, [P, I32, I32, I32, I32, OPTS_P]),
+    "mtk_mttkrp_sym_split": (I32, [P, P, I32, I32, P, I32, I32, P, P, SZ, OPTS_P, P]),
     "mtk_mttkrp_batched_workspace": (SZ, [BATCH_P, I32, OPTS_P]),
     "mtk_mttkrp_batched": (I32, [BATCH_P, I32, P, SZ, OPTS_P, P]),
     "mtk_partial_mttkrp_workspace": (SZ, [P, I32, I32, I32, I32, OPTS_P]),

@@ -102,15 +102,25 @@ def _rank(U, skip=None):
     raise ValueError("no factor matrix given")
 
 
-def split_tensor(X: torch.Tensor, *, out: Optional[torch.Tensor] = None,
+def split_tensor(X: torch.Tensor, dims: Sequence[int], *, out: Optional[torch.Tensor] = None,
                  normX2: Optional[torch.Tensor] = None, ws: Optional[Workspace] = None):
-    """Split an FP32 tensor into its two BF16 planes (hi, lo) for mtk_mttkrp_split.
-    Returns (Xs, normX2): Xs an int16 tensor holding the planes' 16-bit words, normX2 a
-    device FP64 scalar with ||X||^2 from the same pass."""
+    """Split an FP32 tensor (natural order, dims) into its two BF16 planes (hi, lo) for
+    mtk_mttkrp_split, mode 0 padded to a multiple of 8.  Returns (Xs, normX2): Xs an int16
+    tensor holding the planes' 16-bit words, normX2 a device FP64 scalar with ||X||^2 from
+    the same pass."""
     _req(X, torch.float32, "X")
     lib = L.load()
-    I = X.numel()
-    nwords = lib.mtk_split_bytes(I) // 2
+    dims = [int(d) for d in dims]
+    d = L.dims_arr(dims)
+    nb = lib.mtk_split_bytes(d, len(dims))
+    if nb == 0:
+        raise ValueError(f"invalid dims {dims}")
+    n = 1
+    for v in dims:
+        n *= v
+    if X.numel() < n:
+        raise ValueError("X is smaller than dims")
+    nwords = nb // 2
     if out is None:
         out = torch.empty(nwords, dtype=torch.int16, device=X.device)
     _req(out, torch.int16, "out")
@@ -119,9 +129,9 @@ def split_tensor(X: torch.Tensor, *, out: Optional[torch.Tensor] = None,
     if normX2 is None:
         normX2 = torch.empty((), dtype=torch.float64, device=X.device)
     ws = ws or default_workspace(X.device)
-    wp, wb = ws.ptr(lib.mtk_split_workspace(I))
-    L.check(lib.mtk_split_tensor(X.data_ptr(), I, out.data_ptr(), normX2.data_ptr(), wp, wb, _stream(X.device)),
-            "mtk_split_tensor")
+    wp, wb = ws.ptr(lib.mtk_split_workspace(d, len(dims)))
+    L.check(lib.mtk_split_tensor(X.data_ptr(), d, len(dims), out.data_ptr(), normX2.data_ptr(), wp, wb,
+                                 _stream(X.device)), "mtk_split_tensor")
     return out, normX2
 
 
@@ -164,11 +174,8 @@ def _mttkrp_split(Xs, X, dims, U, n, *, algo, precision, splits, out, ws):
     N = len(dims)
     C = _rank(U, skip=n)
     ptrs = _factor_ptrs(U, dims, C, skip=n)
-    NX = 1
-    for d in dims:
-        NX *= d
     lib = L.load()
-    if Xs.numel() * 2 < lib.mtk_split_bytes(NX):
+    if Xs.numel() * 2 < lib.mtk_split_bytes(L.dims_arr(dims), N):
         raise ValueError("Xs is too small for dims")
     if out is None:
         out = torch.empty((dims[n], C), dtype=torch.float32, device=Xs.device)
@@ -184,6 +191,77 @@ def _mttkrp_split(Xs, X, dims, U, n, *, algo, precision, splits, out, ws):
                                  n, out.data_ptr(), wp, wb, L.ctypes.byref(o), _stream(Xs.device)),
             "mtk_mttkrp_split")
     return out
+
+
+def pack_symmetric(X: torch.Tensor, dims: Sequence[int], *, diag: bool = True,
+                   out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """The packed form of a tensor symmetric in modes 0 and 1 (mtk_pack_symmetric): the
+    entries with i_0 >= i_1 (diag) or i_0 > i_1 (not diag), flat, Pp * prod(dims[2:]) floats."""
+    _req(X, torch.float32, "X")
+    dims = [int(d) for d in dims]
+    lib = L.load()
+    rest = 1
+    for d in dims[2:]:
+        rest *= d
+    n = lib.mtk_sym_packed_rows(dims[0], int(diag)) * rest
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=X.device)
+    _req(out, torch.float32, "out")
+    if out.numel() < n:
+        raise ValueError(f"the packed tensor needs {n} floats")
+    L.check(lib.mtk_pack_symmetric(X.data_ptr(), L.dims_arr(dims), len(dims), int(diag), out.data_ptr(),
+                                   _stream(X.device)), "mtk_pack_symmetric")
+    return out
+
+
+def sym_packed_dims(dims: Sequence[int], *, diag: bool = True):
+    """Dims of the packed tensor: [Pp] + dims[2:], Pp = mtk_sym_packed_rows(dims[0], diag)
+    (what split_tensor takes for pack_symmetric's output)."""
+    dims = [int(d) for d in dims]
+    return [L.load().mtk_sym_packed_rows(dims[0], int(diag))] + dims[2:]
+
+
+def mttkrp_sym(Xps: torch.Tensor, dims: Sequence[int], U: Sequence[Optional[torch.Tensor]], n: int, *,
+               diag: bool = True, splits=0, out: Optional[torch.Tensor] = None,
+               ws: Optional[Workspace] = None) -> torch.Tensor:
+    """Mode-n MTTKRP of a tensor symmetric in modes 0 and 1, from the BF16 planes of its
+    packed form (split_tensor of pack_symmetric's output with sym_packed_dims, same diag);
+    dims are the full
+    tensor's.  Without diag the tensor's diagonal i_0 = i_1 counts as zero."""
+    _req(Xps, torch.int16, "Xps")
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    C = _rank(U, skip=n)
+    ptrs = _factor_ptrs(U, dims, C, skip=n)
+    if out is None:
+        out = torch.empty((dims[n], C), dtype=torch.float32, device=Xps.device)
+    _req(out, torch.float32, "out")
+    o = _opts("auto", "auto", splits)
+    lib = L.load()
+    d = L.dims_arr(dims)
+    need = lib.mtk_mttkrp_sym_split_workspace(d, N, int(diag), C, n, L.ctypes.byref(o))
+    if need == 0:
+        raise L.MtkError(L.MTK_EUNSUPPORTED, "mtk_mttkrp_sym_split_workspace")
+    ws = ws or default_workspace(Xps.device)
+    wp, wb = ws.ptr(need)
+    L.check(lib.mtk_mttkrp_sym_split(Xps.data_ptr(), d, N, int(diag), L.ptr_arr(ptrs), C, n, out.data_ptr(), wp, wb,
+                                     L.ctypes.byref(o), _stream(Xps.device)), "mtk_mttkrp_sym_split")
+    return out
+
+
+def ffma_probe(ctas_per_sm: int = 8, iters: int = 4096, *, device=None,
+               out: Optional[torch.Tensor] = None) -> float:
+    """Launch the FP32 FMA throughput probe (mtk_ffma_probe) on the current stream and
+    return the floating-point operations it performs; the caller times it."""
+    dev = torch.device(device if device is not None else "cuda")
+    lib = L.load()
+    n = lib.mtk_ffma_probe_out_floats(ctas_per_sm)
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+    flops = L.ctypes.c_double(0.0)
+    L.check(lib.mtk_ffma_probe(ctas_per_sm, iters, out.data_ptr(), L.ctypes.byref(flops), _stream(dev)),
+            "mtk_ffma_probe")
+    return flops.value
 
 
 def khatri_rao(U: Sequence[torch.Tensor], *, reuse: bool = True,
@@ -267,7 +345,7 @@ def partial_mttkrp_split(Xs, dims, U, n, right: bool, *, splits=0, out=None, ws=
     if out.numel() < size:
         raise ValueError("out is too small")
     lib = L.load()
-    if Xs.numel() * 2 < lib.mtk_split_bytes(IL * dims[n] * IR):
+    if Xs.numel() * 2 < lib.mtk_split_bytes(L.dims_arr(dims), N):
         raise ValueError("Xs is too small for dims")
     o = _opts("auto", "auto", splits)
     d = L.dims_arr(dims)
@@ -368,6 +446,33 @@ def cp_loss_value(normX2, M, Um, G, *, out=None):
                                  _req(Um, torch.float32, "Um").data_ptr(), int(M.shape[0]), L.ptr_arr(ptrs),
                                  len(G), int(M.shape[1]), out.data_ptr(), _stream(dev)), "mtk_cp_loss")
     return out
+
+
+def mttkrp_all(Xs: torch.Tensor, dims: Sequence[int], U: Sequence[torch.Tensor], *, algo="auto",
+               out: Optional[Sequence[torch.Tensor]] = None, ws: Optional[Workspace] = None):
+    """Every mode's MTTKRP with the same factors, on the tensor's BF16 planes
+    (mtk_mttkrp_all_split): the dimension tree for N = 3, 4 unless algo is "fused".
+    Returns the list [M_0, ..., M_{N-1}]."""
+    _req(Xs, torch.int16, "Xs")
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    C = _rank(U)
+    ptrs = _factor_ptrs(U, dims, C)
+    if out is None:
+        out = [torch.empty((d, C), dtype=torch.float32, device=Xs.device) for d in dims]
+    for m in out:
+        _req(m, torch.float32, "M")
+    o = _opts(algo, "auto", 0)
+    lib = L.load()
+    d = L.dims_arr(dims)
+    need = lib.mtk_mttkrp_all_split_workspace(d, N, C, L.ctypes.byref(o))
+    if need == 0:
+        raise L.MtkError(L.MTK_EUNSUPPORTED, "mtk_mttkrp_all_split_workspace")
+    ws = ws or default_workspace(Xs.device)
+    wp, wb = ws.ptr(need)
+    L.check(lib.mtk_mttkrp_all_split(Xs.data_ptr(), d, N, L.ptr_arr(ptrs), C, L.ptr_arr([m.data_ptr() for m in out]),
+                                     wp, wb, L.ctypes.byref(o), _stream(Xs.device)), "mtk_mttkrp_all_split")
+    return list(out)
 
 
 def cp_gradient(Un, Mn, G, n, *, scale=None, out=None):
@@ -530,7 +635,7 @@ class ALS:
         self.need = need
         self.Xs = None
         if self.presplit:
-            self.Xs, self.normX2 = split_tensor(X, ws=Workspace(X.device))
+            self.Xs, self.normX2 = split_tensor(X, self.dims, ws=Workspace(X.device))
         else:
             self.normX2 = norm2(X, ws=Workspace(X.device))
         self.fit = torch.zeros((), dtype=torch.float64, device=X.device)
@@ -539,7 +644,7 @@ class ALS:
     def resplit(self) -> None:
         """Re-split X (after its contents changed) and refresh ||X||^2."""
         if self.presplit:
-            split_tensor(self.X, out=self.Xs, normX2=self.normX2, ws=Workspace(self.X.device))
+            split_tensor(self.X, self.dims, out=self.Xs, normX2=self.normX2, ws=Workspace(self.X.device))
         else:
             norm2(self.X, out=self.normX2, ws=Workspace(self.X.device))
 
@@ -561,10 +666,21 @@ class ALS:
         return self.ws.status()
 
 
+def _per_mode(opts):
+    """mttkrp options of one mode: on the planes the algorithm is the fused one (the
+    dimension tree, algo "two_step", belongs to mttkrp_all)."""
+    if opts.get("Xs") is not None and opts.get("algo") == "two_step":
+        return {k: v for k, v in opts.items() if k != "algo"}
+    return opts
+
+
 class CPLoss(torch.autograd.Function):
     """f(U_0..U_{N-1}) = 0.5 ||X - [[U_0..U_{N-1}]]||^2 with a hand-written backward:
     df/dU_n = U_n Hadamard_{k!=n}(U_k^T U_k) - MTTKRP(X, n), for every mode n.
-    X is treated as a constant.  Usage: CPLoss.apply(X, dims, opts_dict, *U)."""
+    X is treated as a constant.  Usage: CPLoss.apply(X, dims, opts_dict, *U).
+    With opts["Xs"] (the planes of X from split_tensor) every MTTKRP runs on the planes,
+    and the backward takes all N of them from mttkrp_all: the dimension tree for N = 3, 4
+    (two passes over the tensor instead of N)."""
 
     @staticmethod
     def forward(ctx, X, dims, opts, *U):
@@ -572,7 +688,8 @@ class CPLoss(torch.autograd.Function):
         N = len(dims)
         opts = dict(opts or {})
         G = [gram(u) for u in U]
-        M = mttkrp(X, dims, list(U), N - 1, **opts)
+        Xs = opts.get("Xs")
+        M = mttkrp(None if Xs is not None else X, dims, list(U), N - 1, **_per_mode(opts))
         nx2 = norm2(X)
         loss = cp_loss_value(nx2, M, U[N - 1], G)
         ctx.save_for_backward(X, *U)
@@ -588,15 +705,26 @@ class CPLoss(torch.autograd.Function):
         dims, opts, G = ctx.dims, ctx.opts, ctx.G
         N = len(dims)
         scale = go.detach().to(torch.float32).contiguous()
+        Xs = opts.get("Xs")
+        want = [ctx.needs_input_grad[3 + n] for n in range(N)]
+        Ms = None
+        if Xs is not None and sum(want[:N - 1]) > 1:
+            Ms = mttkrp_all(Xs, dims, list(U), algo=opts.get("algo", "auto"))
         grads = []
         for n in range(N):
-            if not ctx.needs_input_grad[3 + n]:
+            if not want[n]:
                 grads.append(None)
                 continue
-            M = ctx.M_last if n == N - 1 else mttkrp(X, dims, list(U), n, **opts)
+            if Ms is not None:
+                M = Ms[n]
+            else:
+                M = ctx.M_last if n == N - 1 else mttkrp(None if Xs is not None else X, dims, list(U), n,
+                                                         **_per_mode(opts))
             grads.append(cp_gradient(U[n], M, G, n, scale=scale))
         return (None, None, None, *grads)
 
 
 def cp_loss(X, dims, U, **opts):
+    """0.5 ||X - [[U]]||^2 as an autograd scalar (CPLoss); opts go to mttkrp (Xs: the
+    planes, which also route the backward through mttkrp_all)."""
     return CPLoss.apply(X, list(dims), opts, *U)

@@ -142,10 +142,10 @@ ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int split
     const int BI = pl.tc ? BI_tc : kSimtBI;
     pl.i_tiles = (int)((I + BI - 1) / BI);
     pl.c_blocks = pl.tc ? 1 : (C + 31) / 32;
-    const int64_t quantum = pl.tc ? kTcBK : 1;              // split boundaries
+    const int64_t quantum = pl.tc ? kTcBK : kBK;            // split boundaries: whole stages
     int64_t S = splits;
     if (S <= 0) {
-        const int64_t target = (int64_t)num_sms() * (pl.tc ? 2 : 4);       // CTAs resident per wave
+        const int64_t target = (int64_t)num_sms() * 2;                    // CTAs resident per wave
         const int64_t tiles = (int64_t)pl.i_tiles * pl.c_blocks;
         S = target / tiles;
         const int64_t maxS = (K + 4 * kTcBK - 1) / (4 * kTcBK);   // >= 4 stages per split
@@ -411,10 +411,21 @@ int planes_ctas_for(const mtk_opts& o, int reserve) {
     return (o.splits > 0 || c - reserve < 1) ? c : c - reserve;
 }
 
+// The planes keep mode 0 padded to a multiple of 8 (planes_dims): every view below is of
+// the padded tensor.  Its first factor U_0 has only I_0 rows (the head image takes the
+// padding rows as zero), and mode 0's output keeps only rows i_0 < I_0.
 PlanesPlan planes_for(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve = 0) {
-    const View v = mode_view(dims, N, n);
-    const FactorList fl = mode_factors(nullptr, dims, N, n);
+    int64_t pd[MTK_MAXN];
+    planes_dims(dims, N, pd);
+    const View v = mode_view(pd, N, n);
+    const FactorList fl = mode_factors(nullptr, pd, N, n);
     return planes_plan(v.L, v.I, fl.rad, fl.Z, C, n, planes_ctas_for(o, reserve));
+}
+
+int64_t planes_entries(const int64_t* dims, int N) {
+    int64_t e = planes_rows0(dims[0]);
+    for (int k = 1; k < N; ++k) e *= dims[k];
+    return e;
 }
 
 mtk_opts fallback_opts(const mtk_opts& o) {
@@ -445,13 +456,18 @@ int do_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, 
         return do_mttkrp(X, dims, N, U, C, n, M, ws, ws_bytes, status, fallback_opts(o), s);
     }
     if (ws_bytes < split_mttkrp_bytes(dims, N, C, n, o, reserve)) return MTK_EWORKSPACE;
-    const View v = mode_view(dims, N, n);
-    const FactorList fl = mode_factors(U, dims, N, n);
+    int64_t pd[MTK_MAXN];
+    planes_dims(dims, N, pd);
+    const View v = mode_view(pd, N, n);
+    const FactorList fl = mode_factors(U, pd, N, n);
     Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
     void* scratch = cv.take(planes_scratch_bytes(pl));
-    const int64_t NX = v.L * v.I * v.R;
-    if (launch_contract_planes(Xs, split_pitch(NX), v.L, v.I, v.R, fl.f, fl.rad, fl.Z, C, pl, M, C, 1,
-                               scratch, status, s, wait_limit_ns(o), o.test_stall, hook) != cudaSuccess)
+    // the factor list starts with U_0 for n >= 1; mode 0's rows beyond I_0 are padding
+    const int64_t f0_rows = n >= 1 ? dims[0] : fl.rad[0];
+    const int64_t opad = n == 0 ? pd[0] : 0;
+    if (launch_contract_planes(Xs, split_pitch(planes_entries(dims, N)), v.L, v.I, v.R, fl.f, fl.rad, fl.Z, C,
+                               pl, M, C, 1, scratch, status, s, wait_limit_ns(o), o.test_stall, hook, f0_rows,
+                               opad, dims[0]) != cudaSuccess)
         return MTK_ECUDA;
     if (hooked) *hooked = hook != nullptr;
     return MTK_OK;
@@ -484,10 +500,12 @@ bool tree_shape(const int64_t* dims, int N, int C) { return (N == 3 || N == 4) &
 bool partial_sides_ok(int N, int n, int right) { return right ? n < N - 1 : n > 0; }
 
 PlanesPlan partial_plan(const int64_t* dims, int N, int C, int n, int right, const mtk_opts& o, int reserve = 0) {
-    const View v = mode_view(dims, N, n);
+    int64_t pd[MTK_MAXN];
+    planes_dims(dims, N, pd);
+    const View v = mode_view(pd, N, n);
     const int ctas = planes_ctas_for(o, reserve);
-    if (right) return planes_plan(1, v.L * v.I, dims + n + 1, N - n - 1, C, 0, ctas);
-    return planes_plan(v.L, v.I * v.R, dims, n, C, n, ctas);
+    if (right) return planes_plan(1, v.L * v.I, pd + n + 1, N - n - 1, C, 0, ctas);
+    return planes_plan(v.L, v.I * v.R, pd, n, C, n, ctas);
 }
 
 // the dimension tree's partials: right = modes >= 2 (n = 1), left = modes 0, 1 (n = 2)
@@ -516,23 +534,33 @@ int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* c
                       const FactorHook* hook = nullptr, int reserve = 0) {
     const PlanesPlan pl = partial_plan(dims, N, C, n, right, o, reserve);
     if (!pl.ok) return MTK_EUNSUPPORTED;
-    const View v = mode_view(dims, N, n);
+    int64_t pd[MTK_MAXN];
+    planes_dims(dims, N, pd);
+    const View v = mode_view(pd, N, n);
     const float* fac[MTK_MAXN];
     int64_t frad[MTK_MAXN];
     int nf = 0;
     for (int k = right ? n + 1 : 0; k < (right ? N : n); ++k) {
         fac[nf] = U[k];
-        frad[nf] = dims[k];
+        frad[nf] = pd[k];
         ++nf;
     }
     Carve cv{static_cast<char*>(ws), kStatusBytes, 0};
     void* scratch = cv.take(planes_scratch_bytes(pl));
-    const int64_t rows = right ? v.L * v.I : v.I * v.R;
-    const int64_t pitch = split_pitch(v.L * v.I * v.R);
-    cudaError_t e = right ? launch_contract_planes(Xs, pitch, 1, rows, v.R, fac, frad, nf, C, pl, T, 1, rows,
-                                                   scratch, status, s, wait_limit_ns(o), o.test_stall, hook)
-                          : launch_contract_planes(Xs, pitch, v.L, rows, 1, fac, frad, nf, C, pl, T, 1, rows,
-                                                   scratch, status, s, wait_limit_ns(o), o.test_stall, hook);
+    const int64_t pitch = split_pitch(planes_entries(dims, N));
+    cudaError_t e;
+    if (right) {
+        // rows (i_0 .. i_n) of the padded view; the output drops the padding rows of mode 0
+        const int64_t rows = v.L * v.I;
+        const int64_t out_rows = rows / pd[0] * dims[0];
+        e = launch_contract_planes(Xs, pitch, 1, rows, v.R, fac, frad, nf, C, pl, T, 1, out_rows, scratch, status,
+                                   s, wait_limit_ns(o), o.test_stall, hook, frad[0], pd[0], dims[0]);
+    } else {
+        // the factors start with U_0, whose padding rows the head image takes as zero
+        const int64_t rows = v.I * v.R;
+        e = launch_contract_planes(Xs, pitch, v.L, rows, 1, fac, frad, nf, C, pl, T, 1, rows, scratch, status, s,
+                                   wait_limit_ns(o), o.test_stall, hook, dims[0], 0, 0);
+    }
     return e == cudaSuccess ? MTK_OK : MTK_ECUDA;
 }
 
@@ -665,21 +693,44 @@ int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* 
     return mtk_read_status(ws, stream, status_bits);
 }
 
-int64_t mtk_split_pitch(int64_t I) { return I < 1 ? 0 : split_pitch(I); }
+namespace {
+bool split_dims_ok(const int64_t* dims, int N) {
+    if (!dims || N < 1 || N > MTK_MAXN) return false;
+    int64_t e = 1;
+    for (int k = 0; k < N; ++k) {
+        if (dims[k] < 1 || dims[k] > ((int64_t)1 << 40)) return false;
+        const int64_t d = k == 0 ? planes_rows0(dims[0]) : dims[k];
+        if (e > ((int64_t)1 << 46) / d) return false;
+        e *= d;
+    }
+    return true;
+}
+}  // namespace
 
-size_t mtk_split_bytes(int64_t I) { return I < 1 ? 0 : (size_t)(2 * split_pitch(I)) * 2; }
+int64_t mtk_split_rows0(int64_t I0) { return I0 < 1 ? 0 : planes_rows0(I0); }
 
-size_t mtk_split_workspace(int64_t I) {
-    if (I < 1) return 0;
-    return align256(kStatusBytes) + align256((size_t)split_chunks(I) * sizeof(double));
+int64_t mtk_split_pitch(const int64_t* dims, int N) {
+    return split_dims_ok(dims, N) ? split_pitch(planes_entries(dims, N)) : 0;
 }
 
-int mtk_split_tensor(const float* X, int64_t I, void* Xs, double* normX2, void* ws, size_t ws_bytes,
-                     void* stream) {
-    if (!X || !Xs || !ws || I < 1 || !aligned4(X) || !aligned16(Xs)) return MTK_EINVAL;
-    if (ws_bytes < mtk_split_workspace(I)) return MTK_EWORKSPACE;
+size_t mtk_split_bytes(const int64_t* dims, int N) {
+    return split_dims_ok(dims, N) ? (size_t)(2 * split_pitch(planes_entries(dims, N))) * 2 : 0;
+}
+
+size_t mtk_split_workspace(const int64_t* dims, int N) {
+    if (!split_dims_ok(dims, N)) return 0;
+    return align256(kStatusBytes) + align256((size_t)split_chunks(planes_entries(dims, N)) * sizeof(double));
+}
+
+int mtk_split_tensor(const float* X, const int64_t* dims, int N, void* Xs, double* normX2, void* ws,
+                     size_t ws_bytes, void* stream) {
+    if (!X || !Xs || !ws || !split_dims_ok(dims, N) || !aligned4(X) || !aligned16(Xs)) return MTK_EINVAL;
+    if (ws_bytes < mtk_split_workspace(dims, N)) return MTK_EWORKSPACE;
     double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + align256(kStatusBytes));
-    if (launch_split_planes(X, I, Xs, part, normX2, (cudaStream_t)stream) != cudaSuccess) return MTK_ECUDA;
+    int64_t rest = 1;
+    for (int k = 1; k < N; ++k) rest *= dims[k];
+    if (launch_split_planes(X, dims[0], rest, Xs, part, normX2, (cudaStream_t)stream) != cudaSuccess)
+        return MTK_ECUDA;
     return MTK_OK;
 }
 
@@ -728,6 +779,185 @@ int mtk_partial_mttkrp_split(const void* Xs, const int64_t* dims, int N, const f
     if (ws_bytes < partial_split_bytes(pl)) return MTK_EWORKSPACE;
     return run_partial_split(Xs, dims, N, U, C, n, right, T, ws, static_cast<uint32_t*>(ws), o,
                              (cudaStream_t)stream);
+}
+
+// ---- every mode's MTTKRP with the same factors (the gradient of the CP loss) ----------------
+namespace {
+// the dimension tree takes N = 3, 4 with both partials on the planes kernel; the
+// workspace: status, the partials T_R (I_0 I_1 C) and T_L (I_2 I_3 C, N = 4), then the
+// larger of the partial contractions' scratch and (N = 3) the mode-2 MTTKRP's
+bool all_tree(const int64_t* dims, int N, int C, const mtk_opts& o) {
+    return o.algo != MTK_ALGO_FUSED && tree_ok(dims, N, C, o);
+}
+size_t all_split_bytes(const int64_t* dims, int N, int C, const mtk_opts& o) {
+    if (all_tree(dims, N, C, o)) {
+        size_t t = (size_t)dims[0] * dims[1] * C * sizeof(float);
+        if (N == 4) t += (size_t)dims[2] * dims[3] * C * sizeof(float);
+        size_t inner = tree_scratch(dims, N, C, o);
+        if (N == 3) {
+            const size_t m2 = split_mttkrp_bytes(dims, N, C, 2, o);
+            if (m2 > inner) inner = m2;
+        }
+        return align256(kStatusBytes) + align256(t) + inner;
+    }
+    size_t w = 0;
+    for (int n = 0; n < N; ++n) {
+        const size_t b = split_mttkrp_bytes(dims, N, C, n, o);
+        if (b > w) w = b;
+    }
+    return w;
+}
+mtk_opts all_opts(const mtk_opts& o) {
+    mtk_opts q = o;
+    q.algo = MTK_ALGO_FUSED;
+    return q;
+}
+}  // namespace
+
+size_t mtk_mttkrp_all_split_workspace(const int64_t* dims, int N, int C, const mtk_opts* opts) {
+    for (int n = 0; n < N; ++n)
+        if (check_shape(dims, N, C, n) != MTK_OK) return 0;
+    if (check_split_opts(opts, true) != MTK_OK) return 0;
+    const mtk_opts o = defaults(opts);
+    for (int n = 0; n < N; ++n)
+        if (!planes_for(dims, N, C, n, all_opts(o)).ok) return 0;
+    return all_split_bytes(dims, N, C, o);
+}
+
+int mtk_mttkrp_all_split(const void* Xs, const int64_t* dims, int N, const float* const* U, int C,
+                         float* const* M, void* ws, size_t ws_bytes, const mtk_opts* opts, void* stream) {
+    for (int n = 0; n < N; ++n) {
+        const int st = check_shape(dims, N, C, n);
+        if (st) return st;
+    }
+    if (!Xs || !aligned16(Xs) || !U || !M || !ws) return MTK_EINVAL;
+    for (int k = 0; k < N; ++k)
+        if (!U[k] || !aligned4(U[k]) || !M[k] || !aligned4(M[k])) return MTK_EINVAL;
+    if (check_split_opts(opts, true) != MTK_OK) return MTK_EINVAL;
+    const mtk_opts o = defaults(opts);
+    const mtk_opts om = all_opts(o);
+    for (int n = 0; n < N; ++n)
+        if (!planes_for(dims, N, C, n, om).ok) return MTK_EUNSUPPORTED;
+    if (ws_bytes < all_split_bytes(dims, N, C, o)) return MTK_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* status = static_cast<uint32_t*>(ws);
+    if (!all_tree(dims, N, C, o)) {
+        for (int n = 0; n < N; ++n) {
+            const int st = do_mttkrp_split(Xs, nullptr, dims, N, U, C, n, M[n], ws, ws_bytes, status, om, s);
+            if (st) return st;
+        }
+        return MTK_OK;
+    }
+    Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+    float* TR = static_cast<float*>(cv.take((size_t)dims[0] * dims[1] * C * sizeof(float) +
+                                            (N == 4 ? (size_t)dims[2] * dims[3] * C * sizeof(float) : 0)));
+    float* TL = N == 4 ? TR + (size_t)dims[0] * dims[1] * C : nullptr;
+    // the inner calls carve their scratch after the status word of this block
+    char* inner = static_cast<char*>(cv.take(0)) - kStatusBytes;
+    const size_t inner_bytes = ws_bytes - (size_t)(inner - static_cast<char*>(ws));
+    // modes 0, 1 from the contraction over modes >= 2 (Algorithm 4: partial, then multi-TTV)
+    int st = run_tree_partial(Xs, dims, N, U, C, 1, TR, inner, status, om, s, nullptr, 0);
+    if (st) return st;
+    if (launch_multi_ttv(TR, 1, dims[0], dims[1], U[1], C, 0, M[0], s) != cudaSuccess ||
+        launch_multi_ttv(TR, dims[0], dims[1], 1, U[0], C, 1, M[1], s) != cudaSuccess)
+        return MTK_ECUDA;
+    if (N == 3) return do_mttkrp_split(Xs, nullptr, dims, N, U, C, 2, M[2], inner, inner_bytes, status, om, s);
+    // modes 2, 3 from the contraction over modes 0, 1
+    st = run_tree_partial(Xs, dims, N, U, C, 0, TL, inner, status, om, s, nullptr, 0);
+    if (st) return st;
+    if (launch_multi_ttv(TL, 1, dims[2], dims[3], U[3], C, 0, M[2], s) != cudaSuccess ||
+        launch_multi_ttv(TL, dims[2], dims[3], 1, U[2], C, 1, M[3], s) != cudaSuccess)
+        return MTK_ECUDA;
+    return MTK_OK;
+}
+
+// ---- FP32 FMA throughput probe ---------------------------------------------------------------
+int64_t mtk_ffma_probe_out_floats(int ctas_per_sm) {
+    if (ctas_per_sm < 1 || ctas_per_sm > 64) return 0;
+    return (int64_t)num_sms() * ctas_per_sm * ffma_probe_threads();
+}
+
+int mtk_ffma_probe(int ctas_per_sm, int iters, float* out, double* flops, void* stream) {
+    if (ctas_per_sm < 1 || ctas_per_sm > 64 || iters < 1 || iters > (1 << 24) || !out || !aligned4(out))
+        return MTK_EINVAL;
+    const int blocks = num_sms() * ctas_per_sm;
+    if (flops) *flops = 2.0 * 8.0 * (double)iters * (double)blocks * ffma_probe_threads();
+    if (launch_ffma_probe(blocks, iters, out, (cudaStream_t)stream) != cudaSuccess) return MTK_ECUDA;
+    return MTK_OK;
+}
+
+// ---- tensors symmetric in modes 0 and 1, packed ------------------------------------------
+namespace {
+// the packed tensor's dims (Pp, dims[2], ..., dims[N-1]) and its mode for full mode n
+int sym_packed_dims(const int64_t* dims, int N, int diag, int64_t* pd) {
+    pd[0] = sym_packed_rows(dims[0], diag);
+    for (int k = 2; k < N; ++k) pd[k - 1] = dims[k];
+    return N - 1;
+}
+bool sym_shape_ok(const int64_t* dims, int N, int diag, int C, int n) {
+    return check_shape(dims, N, C, n) == MTK_OK && N >= 3 && dims[0] == dims[1] && (diag == 0 || diag == 1);
+}
+// status, then W or V (Pp x C), then the packed MTTKRP's workspace
+size_t sym_bytes(const int64_t* dims, int N, int diag, int C, int n, const mtk_opts& o) {
+    int64_t pd[MTK_MAXN];
+    const int Np = sym_packed_dims(dims, N, diag, pd);
+    const int np = n >= 2 ? n - 1 : 0;
+    if (!planes_for(pd, Np, C, np, o).ok) return 0;
+    return align256(kStatusBytes) + align256((size_t)pd[0] * C * sizeof(float)) +
+           split_mttkrp_bytes(pd, Np, C, np, o);
+}
+}  // namespace
+
+int64_t mtk_sym_packed_rows(int64_t n0, int diag) {
+    return n0 < 1 || (diag != 0 && diag != 1) ? 0 : sym_packed_rows(n0, diag);
+}
+
+int mtk_pack_symmetric(const float* X, const int64_t* dims, int N, int diag, float* Xp, void* stream) {
+    if (!X || !Xp || !aligned4(X) || !aligned4(Xp) || !sym_shape_ok(dims, N, diag, 1, 0)) return MTK_EINVAL;
+    int64_t rest = 1;
+    for (int k = 2; k < N; ++k) rest *= dims[k];
+    if (launch_sym_pack(X, dims[0], diag, rest, Xp, (cudaStream_t)stream) != cudaSuccess) return MTK_ECUDA;
+    return MTK_OK;
+}
+
+size_t mtk_mttkrp_sym_split_workspace(const int64_t* dims, int N, int diag, int C, int n, const mtk_opts* opts) {
+    if (!sym_shape_ok(dims, N, diag, C, n) || check_split_opts(opts) != MTK_OK) return 0;
+    return sym_bytes(dims, N, diag, C, n, defaults(opts));
+}
+
+int mtk_mttkrp_sym_split(const void* Xps, const int64_t* dims, int N, int diag, const float* const* U, int C, int n,
+                         float* M, void* ws, size_t ws_bytes, const mtk_opts* opts, void* stream) {
+    if (!sym_shape_ok(dims, N, diag, C, n)) return MTK_EINVAL;
+    if (!Xps || !aligned16(Xps)) return MTK_EINVAL;
+    int st = check_mttkrp_ptrs(static_cast<const float*>(Xps), U, N, n, M, ws);
+    if (st) return st;
+    if (n < 2 && !U[1 - n]) return MTK_EINVAL;
+    if (check_split_opts(opts) != MTK_OK) return MTK_EINVAL;
+    const mtk_opts o = defaults(opts);
+    const size_t need = sym_bytes(dims, N, diag, C, n, o);
+    if (need == 0) return MTK_EUNSUPPORTED;
+    if (ws_bytes < need) return MTK_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t pd[MTK_MAXN];
+    const int Np = sym_packed_dims(dims, N, diag, pd);
+    Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+    float* buf = static_cast<float*>(cv.take((size_t)pd[0] * C * sizeof(float)));
+    const size_t inner_bytes = split_mttkrp_bytes(pd, Np, C, n >= 2 ? n - 1 : 0, o);
+    void* inner = cv.take(inner_bytes);
+    uint32_t* status = static_cast<uint32_t*>(ws);
+    const float* Up[MTK_MAXN];
+    for (int k = 2; k < N; ++k) Up[k - 1] = U[k];
+    if (n >= 2) {
+        // W, the symmetrised pair products, as the packed mode's factor
+        if (launch_sym_pair(U[0], U[1], dims[0], diag, C, buf, s) != cudaSuccess) return MTK_ECUDA;
+        Up[0] = buf;
+        return do_mttkrp_split(Xps, nullptr, pd, Np, Up, C, n - 1, M, inner, inner_bytes, status, o, s);
+    }
+    Up[0] = nullptr;
+    st = do_mttkrp_split(Xps, nullptr, pd, Np, Up, C, 0, buf, inner, inner_bytes, status, o, s);
+    if (st) return st;
+    if (launch_sym_ttv(buf, U[1 - n], dims[0], diag, C, M, s) != cudaSuccess) return MTK_ECUDA;
+    return MTK_OK;
 }
 
 static int check_batch(const mtk_batch_problem* probs, int P) {

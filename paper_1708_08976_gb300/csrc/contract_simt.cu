@@ -10,11 +10,19 @@
 //
 // Decomposition: grid = (i-tiles of 64, contraction splits S, column blocks of
 // 32).  Each CTA owns a contiguous k-range (the private partial result of
-// Algorithm 3), stages X tiles with 4-byte cp.async (zero-filled outside the
-// tensor) through a 3-deep ring, and accumulates an 8 x 4 register tile per
-// thread; four k-groups per CTA are summed in shared memory in fixed order.
-// Partials of the S splits are summed in split order by split_reduce_kernel
+// Algorithm 3), stages X tiles through a 3-deep cp.async ring (16-byte copies when
+// the rows allow it, else 4-byte ones; zero-filled outside the tensor) and generates
+// the matching 32 x 32 block of W in shared memory.  Its 256 threads are 8 k-groups
+// (one per warp, four k of every 32-k stage each) x 16 row groups x 2 column groups:
+// a thread accumulates a 4 x 16 register tile, reading per k one 16-byte word of X
+// (or a word of four k) and four broadcast words of W, so 20 shared loads feed 256
+// FMAs per stage.  The eight k-groups are summed in shared memory in a fixed tree
+// order; partials of the S splits are summed in split order by split_reduce_kernel
 // (the parallel reduction of Algorithm 3), so results are deterministic.
+//
+// Layouts of an X stage: rows of i with k contiguous ([i][k]) when the view has
+// I^L > 1 (consecutive k are consecutive l in the tensor), columns of i ([k][i]) when
+// I^L = 1 (consecutive i are contiguous).
 #include "mtk_internal.cuh"
 
 namespace mtk {
@@ -22,19 +30,23 @@ namespace {
 
 constexpr int BK = 32;        // k per stage
 constexpr int BI = 64;        // i per CTA tile
-constexpr int NKG = 4;        // k-groups per CTA
+constexpr int CB = 32;        // columns per CTA (a column block)
+constexpr int NKG = 8;        // k-groups per CTA (one warp each)
+constexpr int THREADS = 256;
 constexpr int STAGES = 3;
-constexpr int XP = BI + 4;    // padded row pitch of the X stage (floats)
-constexpr int WP = 32 + 4;    // padded row pitch of the W stage
+constexpr int XPK = BK + 4;   // [i][k] stage: row pitch (floats)
+constexpr int XPM = BI + 4;   // [k][i] stage: row pitch
+constexpr int WP = CB + 4;    // W stage row pitch
+constexpr int RP = CB + 4;    // reduction row pitch
+constexpr int XSTAGE = (BI * XPK > BK * XPM) ? BI * XPK : BK * XPM;
 
 struct __align__(16) SimtSmem {
     union {
         struct {
-            float xs[STAGES][BK][XP];
+            float xs[STAGES][XSTAGE];
             float ws[2][BK][WP];
-            float qs[2][32];
         } pipe;
-        float red[NKG][BI][32];
+        float red[NKG / 2][BI][RP];
     };
 };
 
@@ -42,6 +54,11 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool v
     unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     int sz = valid ? 4 : 0;
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
+    unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    int sz = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gmem), "r"(sz));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -59,22 +76,23 @@ __device__ __forceinline__ float tail_product(const KrpOperand& W, int64_t q, in
     return p;
 }
 
-__global__ void __launch_bounds__(256)
+// KM: X stage [i][k] (I^L > 1); else [k][i] (I^L = 1).  VEC: 16-byte copies (KM: I^L a
+// multiple of 4; else I_n a multiple of 4; the tensor 16-byte aligned, split starts at
+// multiples of BK).
+template <bool KM, bool VEC>
+__global__ void __launch_bounds__(THREADS, 2)
 contract_simt_kernel(const __grid_constant__ ContractParams p) {
     __shared__ SimtSmem sm;
-    const int nCg = blockDim.x / 32;             // column groups of 4
-    const int Cb = nCg * 4;                      // columns handled (>= real columns)
-    const int t = threadIdx.x, nth = blockDim.x;
-    const int tc = t % nCg, ti = (t / nCg) % 8, kg = t / (nCg * 8);
+    const int t = threadIdx.x;
+    const int cg = t & 1, ig = (t >> 1) & 15, kg = t >> 5;
     const int64_t i0 = (int64_t)blockIdx.x * BI;
     const int sp = blockIdx.y;
-    const int c0 = blockIdx.z * 32;
+    const int c0 = blockIdx.z * CB;
     const int C = p.C;
     const int64_t L = p.L, I = p.I;
     const int64_t kb = (int64_t)sp * p.kchunk;
     const int64_t ke = (kb + p.kchunk < p.K) ? kb + p.kchunk : p.K;
     const int nst = (int)((ke - kb + BK - 1) / BK);
-    const bool kfast = L > 1;
     const KrpOperand& W = p.W;
 
     // uniform trackers of the stage start: (l, r) for X, (d0, q) for W
@@ -84,121 +102,196 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int64_t qtot = p.K / W.rad0;           // number of q values (rows of Q)
 
     auto issue_x = [&](int s) {
-        float* dst = &sm.pipe.xs[s % STAGES][0][0];
+        float* dst = sm.pipe.xs[s % STAGES];
         const int64_t ks = kb + (int64_t)s * BK;
-        for (int e = t; e < BK * BI; e += nth) {
-            int kk, ii;
-            if (kfast) { kk = e % BK; ii = e / BK; } else { ii = e % BI; kk = e / BI; }
-            const int64_t k = ks + kk, i = i0 + ii;
-            const bool valid = (k < ke) && (i < I);
-            int64_t off = 0;
-            if (valid) {
-                if (L == 1) {
-                    off = k * I;
+        if (VEC) {
+            // 512 words of four floats: KM (ii, k4) with the four k in one row of the
+            // tensor (I^L % 4 == 0); else (kk, i4) with four consecutive i
+            for (int e = t; e < BI * BK / 4; e += THREADS) {
+                if (KM) {
+                    const int ii = e >> 3, k4 = e & 7;
+                    const int64_t k = ks + 4 * k4, i = i0 + ii;
+                    const bool valid = (k < ke) && (i < I);
+                    int64_t off = 0;
+                    if (valid) {
+                        int64_t l = xl + 4 * k4, r = xr;
+                        while (l >= L) { l -= L; ++r; }
+                        off = l + L * i + L * I * r;
+                    }
+                    cp_async16(dst + ii * XPK + 4 * k4, p.X + off, valid);
                 } else {
-                    int64_t l = xl + kk, r = xr;
-                    while (l >= L) { l -= L; ++r; }
-                    off = l + L * I * r;
+                    const int kk = e >> 4, i4 = e & 15;
+                    const int64_t k = ks + kk, i = i0 + 4 * i4;
+                    const bool valid = (k < ke) && (i < I);
+                    cp_async16(dst + kk * XPM + 4 * i4, p.X + (valid ? k * I + i : 0), valid);
                 }
-                off += L * i;
             }
-            cp_async4(dst + kk * XP + ii, p.X + off, valid);
+        } else {
+            for (int e = t; e < BK * BI; e += THREADS) {
+                int kk, ii;
+                if (KM) { kk = e % BK; ii = e / BK; } else { ii = e % BI; kk = e / BI; }
+                const int64_t k = ks + kk, i = i0 + ii;
+                const bool valid = (k < ke) && (i < I);
+                int64_t off = 0;
+                if (valid) {
+                    if (L == 1) {
+                        off = k * I;
+                    } else {
+                        int64_t l = xl + kk, r = xr;
+                        while (l >= L) { l -= L; ++r; }
+                        off = l + L * I * r;
+                    }
+                    off += L * i;
+                }
+                cp_async4(KM ? dst + ii * XPK + kk : dst + kk * XPM + ii, p.X + off, valid);
+            }
         }
         cp_async_commit();
         if (L > 1) { xl += BK; while (xl >= L) { xl -= L; ++xr; } }
     };
 
-    // W stage s into ws[s & 1]; needs Q rows for wq, wq+1 in qs
-    auto gen_w = [&](int s) {
-        float* dst = &sm.pipe.ws[s & 1][0][0];
+    // W stage s into ws[s & 1].  Thread t forms column cc = t % 32 of rows kk = t / 32 + 8 m
+    // (m = 0..3).  The factor entries of the next stage are loaded into registers before
+    // the current stage's FMAs and multiplied by the tail scale Q(q, cc) and stored after
+    // them, so their L2 latency is hidden.  The head has >= BK rows whenever there is a
+    // tail, so a stage spans at most two q; the thread keeps Q(q, cc) for the stage's
+    // first q and the next in registers, formed again only when q moves.
+    const int wcc = t & (CB - 1), wk0 = t / CB;
+    const int wc = c0 + wcc;
+    float wraw[4];
+    float q0 = 1.0f, q1 = 1.0f;
+    auto load_w = [&](int s) {
         const int64_t ks = kb + (int64_t)s * BK;
-        for (int e = t; e < BK * Cb; e += nth) {
-            const int kk = e / Cb, cc = e % Cb;
-            const int c = c0 + cc;
+        if (W.ntail > 0 && wq != qcached) {
+            q0 = (wc < C && wq < qtot) ? tail_product(W, wq, wc, C) : 0.0f;
+            q1 = (wc < C && wq + 1 < qtot) ? tail_product(W, wq + 1, wc, C) : 0.0f;
+            qcached = wq;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int kk = wk0 + (THREADS / CB) * m;
             float w = 0.0f;
-            if (ks + kk < ke && c < C) {
+            if (ks + kk < ke && wc < C) {
                 int64_t d = wd + kk;
-                int which = 0;
-                if (W.ntail > 0 && d >= W.rad0) { d -= W.rad0; which = 1; }
-                w = __ldg(W.f0 + d * C + c);
-                if (W.ntail > 0) w *= sm.pipe.qs[which][cc];
+                if (W.ntail > 0 && d >= W.rad0) d -= W.rad0;
+                w = __ldg(W.f0 + d * C + wc);
             }
-            dst[kk * WP + cc] = w;
+            wraw[m] = w;
+        }
+    };
+    auto store_w = [&](int s) {
+        float* dst = &sm.pipe.ws[s & 1][0][0];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int kk = wk0 + (THREADS / CB) * m;
+            float w = wraw[m];
+            if (W.ntail > 0) w *= (wd + kk >= W.rad0) ? q1 : q0;
+            dst[kk * WP + wcc] = w;
         }
     };
     auto advance_w = [&]() {
         wd += BK;
         while (wd >= W.rad0) { wd -= W.rad0; ++wq; }
     };
-    // refresh the cached Q rows if the stage's q changed (uniform branch)
-    auto refresh_q = [&]() {
-        if (W.ntail > 0 && wq != qcached) {
-            __syncthreads();
-            for (int e = t; e < 2 * 32; e += nth) {
-                const int which = e / 32, cc = e % 32, c = c0 + cc;
-                sm.pipe.qs[which][cc] = (c < C && wq + which < qtot) ? tail_product(W, wq + which, c, C) : 0.0f;
-            }
-            qcached = wq;
-            __syncthreads();
-        }
-    };
 
-    float acc[8][4];
+    float acc[4][16];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+        for (int b = 0; b < 16; ++b) acc[a][b] = 0.0f;
 
     for (int s = 0; s < STAGES - 1; ++s) {
         if (s < nst) issue_x(s); else cp_async_commit();
     }
-    if (nst > 0) { refresh_q(); gen_w(0); }
+    if (nst > 0) {
+        load_w(0);
+        store_w(0);
+    }
 
     for (int s = 0; s < nst; ++s) {
         cp_async_wait<STAGES - 2>();
         __syncthreads();
         if (s + STAGES - 1 < nst) issue_x(s + STAGES - 1); else cp_async_commit();
-
-        const float* xs = &sm.pipe.xs[s % STAGES][0][0];
-        const float* ws = &sm.pipe.ws[s & 1][0][0];
-#pragma unroll
-        for (int j = 0; j < BK / NKG; ++j) {
-            const int kk = kg + NKG * j;
-            const float4 xa = *reinterpret_cast<const float4*>(xs + kk * XP + ti * 8);
-            const float4 xb = *reinterpret_cast<const float4*>(xs + kk * XP + ti * 8 + 4);
-            const float4 w = *reinterpret_cast<const float4*>(ws + kk * WP + tc * 4);
-            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-            const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], wv[b], acc[a][b]);
-        }
-        if (s + 1 < nst) {
+        // the next stage's factor entries, in flight during this stage's FMAs
+        const bool more = s + 1 < nst;
+        if (more) {
             advance_w();
-            refresh_q();
-            gen_w(s + 1);
+            load_w(s + 1);
         }
+
+        const float* xs = sm.pipe.xs[s % STAGES];
+        const float* ws = &sm.pipe.ws[s & 1][0][0];
+        float xv[4][4];                  // [row a][k j]
+        if (KM) {
+            // rows ig + 16 a (16 consecutive rows per load: conflict-free words)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float4 v = *reinterpret_cast<const float4*>(xs + (ig + 16 * a) * XPK + 4 * kg);
+                xv[a][0] = v.x; xv[a][1] = v.y; xv[a][2] = v.z; xv[a][3] = v.w;
+            }
+        } else {
+            // rows 4 ig .. 4 ig + 3
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 v = *reinterpret_cast<const float4*>(xs + (4 * kg + j) * XPM + 4 * ig);
+                xv[0][j] = v.x; xv[1][j] = v.y; xv[2][j] = v.z; xv[3][j] = v.w;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float* wr = ws + (4 * kg + j) * WP + 16 * cg;
+            float wv[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = *reinterpret_cast<const float4*>(wr + 4 * q);
+                wv[4 * q] = v.x; wv[4 * q + 1] = v.y; wv[4 * q + 2] = v.z; wv[4 * q + 3] = v.w;
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 16; ++b) acc[a][b] = fmaf(xv[a][j], wv[b], acc[a][b]);
+        }
+        if (more) store_w(s + 1);
     }
     cp_async_wait<0>();
     __syncthreads();
 
-    // fixed-order reduction over the k-groups
+    // fixed-order reduction over the k-groups: (g, g + 4), then (g, g + 2), then (0, 1)
+    auto row_of = [&](int a) { return KM ? ig + 16 * a : 4 * ig + a; };
+    for (int half = NKG / 2; half >= 1; half >>= 1) {
+        if (kg >= half && kg < 2 * half) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) sm.red[kg][ti * 8 + a][tc * 4 + b] = acc[a][b];
-    __syncthreads();
-    for (int e = t; e < BI * Cb; e += nth) {
-        const int ii = e / Cb, cc = e % Cb;
-        const int64_t i = i0 + ii;
-        const int c = c0 + cc;
-        if (i >= I || c >= C) continue;
-        float v = sm.red[0][ii][cc];
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<float4*>(&sm.red[kg - half][row_of(a)][16 * cg + 4 * q]) =
+                        make_float4(acc[a][4 * q], acc[a][4 * q + 1], acc[a][4 * q + 2], acc[a][4 * q + 3]);
+        }
+        __syncthreads();
+        if (kg < half) {
 #pragma unroll
-        for (int g = 1; g < NKG; ++g) v += sm.red[g][ii][cc];
-        if (p.S == 1) p.out[i * p.out_si + c * p.out_sc] = v;
-        else p.part[((int64_t)sp * I + i) * C + c] = v;
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = *reinterpret_cast<const float4*>(&sm.red[kg][row_of(a)][16 * cg + 4 * q]);
+                    acc[a][4 * q] += v.x; acc[a][4 * q + 1] += v.y; acc[a][4 * q + 2] += v.z; acc[a][4 * q + 3] += v.w;
+                }
+        }
+        __syncthreads();
+    }
+    if (kg == 0) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t i = i0 + row_of(a);
+            if (i >= I) continue;
+#pragma unroll
+            for (int b = 0; b < 16; ++b) {
+                const int c = c0 + 16 * cg + b;
+                if (c >= C) continue;
+                if (p.S == 1) p.out[i * p.out_si + c * p.out_sc] = acc[a][b];
+                else p.part[((int64_t)sp * I + i) * C + c] = acc[a][b];
+            }
+        }
     }
 }
 
@@ -218,10 +311,16 @@ __global__ void split_reduce_kernel(const float* __restrict__ part, int S, int64
 
 cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,
                                  cudaStream_t s) {
-    const int Cfirst = p.C < 32 ? p.C : 32;
-    const int nCg = (Cfirst + 3) / 4;
     dim3 grid(i_tiles, p.S, c_blocks);
-    contract_simt_kernel<<<grid, nCg * 32, 0, s>>>(p);
+    const bool km = p.L > 1;
+    const bool xa = (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 && p.kchunk % BK == 0;
+    if (km) {
+        if (xa && p.L % 4 == 0) contract_simt_kernel<true, true><<<grid, THREADS, 0, s>>>(p);
+        else contract_simt_kernel<true, false><<<grid, THREADS, 0, s>>>(p);
+    } else {
+        if (xa && p.I % 4 == 0) contract_simt_kernel<false, true><<<grid, THREADS, 0, s>>>(p);
+        else contract_simt_kernel<false, false><<<grid, THREADS, 0, s>>>(p);
+    }
     note_launches(1);
     return cudaGetLastError();
 }

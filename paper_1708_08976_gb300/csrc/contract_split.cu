@@ -57,9 +57,13 @@ constexpr int PS_M = 128;                    // MMA M
 #define MTK_PS_LO_SEP 1
 #endif
 // head: the first prefix with at least 64 rows whose padding is at most 1/MTK_PS_HEAD_PAD
-// of its padded rows
+// of its padded rows; 1/MTK_PS_HEAD_PAD_NEAR when the K-major tile packs several runs and
+// the prefix keeps consecutive runs in one box (see planes_plan)
 #ifndef MTK_PS_HEAD_PAD
 #define MTK_PS_HEAD_PAD 32
+#endif
+#ifndef MTK_PS_HEAD_PAD_NEAR
+#define MTK_PS_HEAD_PAD_NEAR 4
 #endif
 constexpr int PS_GROUP = MTK_PS_GROUP;       // stages per accumulation chain (at most)
 // one MMA tile: the lo plane accumulates into accumulator columns of its own (1) or into
@@ -133,6 +137,9 @@ struct PsParams {
     int64_t tail_rad[MTK_MAXN];
     float* out;
     int64_t out_si, out_sc;
+    int64_t opad, oreal;    // output rows: row j of the view is row (j mod opad) + oreal (j / opad) of
+                            // the output, dropped when j mod opad >= oreal (planes with mode 0
+                            // padded); opad = 0: row j
     float* part;            // partial slabs when nslab > 1: [slab][I][C], or [slab][C][I] (part_cm)
     int part_cm;            // slabs in the output's column-major layout (out_si == 1)
     uint32_t* status;
@@ -675,9 +682,16 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             if (ok && rowvalid) {
                 const int64_t i = w.rho + (int64_t)p.P * (i0 + myil);
                 if (w.direct) {
+                    int64_t io = i;
+                    if (p.opad) {
+                        const int64_t q = i / p.opad, rr = i - q * p.opad;
+                        io = rr < p.oreal ? rr + p.oreal * q : -1;
+                    }
+                    if (io >= 0) {
 #pragma unroll
-                    for (int e = 0; e < 16 * NCH; ++e)
-                        if (e < C) p.out[i * p.out_si + e * p.out_sc] = acc[e];
+                        for (int e = 0; e < 16 * NCH; ++e)
+                            if (e < C) p.out[io * p.out_si + e * p.out_sc] = acc[e];
+                    }
                 } else {
                     float* slab = p.part + ((int64_t)w.sp * U + myg) * I * C;
                     if (p.part_cm) {
@@ -720,6 +734,7 @@ struct PrepArgs {
     int head, C, CP, N;
     const float* fac[MTK_MAXN];
     int64_t frad[MTK_MAXN];
+    int64_t f0_rows;        // rows of the first factor that exist (the rest are taken as zero)
     int64_t H, Hp;
     int nsh;
     uint8_t* img;
@@ -761,7 +776,7 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
             for (int d = 0; d < 8; ++d) {
                 const int64_t h = h0 + d;
                 float w = 0.0f;
-                if (h >= 0 && h < a.H && c < a.C) {
+                if (h >= 0 && h < a.H && c < a.C && dig[0] < a.f0_rows) {
                     w = 1.0f;
                     for (int z = 0; z < a.head; ++z) w *= __ldg(a.fac[z] + dig[z] * a.C + c);
                 }
@@ -819,7 +834,19 @@ struct ReduceShape {
     int C, BI, U, ntiles, s_full, s_last, P, ntc;
     int sk;                 // stream-K: slabs of a tile = its pieces (0: a whole-tile unit wrote it)
     int64_t stot, tot, G;
+    int64_t opad, oreal, Iout;   // output row map (as in PsParams), output rows
 };
+
+// where output f of the slabs' layout goes in the output (-1: a padding row, dropped)
+__device__ __forceinline__ int64_t reduce_out(const ReduceShape& rs, int64_t f, int colmajor) {
+    if (!rs.opad) return f;
+    const int64_t i = colmajor ? f % rs.I : f / rs.C;
+    const int64_t c = colmajor ? f / rs.I : f - i * rs.C;
+    const int64_t q = i / rs.opad, rr = i - q * rs.opad;
+    if (rr >= rs.oreal) return -1;
+    const int64_t io = rr + rs.oreal * q;
+    return colmajor ? c * rs.Iout + io : io * rs.C + c;
+}
 
 // slabs that hold pieces of output f (0: its tile was written whole, nothing to add)
 __device__ __forceinline__ int reduce_slabs(const ReduceShape& rs, int64_t f, int colmajor) {
@@ -869,7 +896,8 @@ __global__ void __launch_bounds__(256) planes_reduce_few_kernel(const float* __r
                 if (ns[j] == 0) continue;
                 float a = 0.0f;
                 for (int sl = 0; sl < ns[j]; ++sl) a += __ldg(part + (int64_t)sl * n + f0 + j);
-                out[f0 + j] = a;
+                const int64_t o = reduce_out(rs, f0 + j, colmajor);
+                if (o >= 0) out[o] = a;
             }
         }
     }
@@ -936,8 +964,12 @@ __global__ void __launch_bounds__(1024) planes_reduce_kernel(const float* __rest
             *reinterpret_cast<float4*>(out + f0) = make_float4(t[0], t[1 % Q], t[2 % Q], t[3 % Q]);
         } else {
 #pragma unroll
-            for (int j = 0; j < Q; ++j)
-                if (f0 + j < n && nsj[j] > 0) out[f0 + j] = t[j];
+            for (int j = 0; j < Q; ++j) {
+                if (f0 + j < n && nsj[j] > 0) {
+                    const int64_t o = reduce_out(rs, f0 + j, colmajor);
+                    if (o >= 0) out[o] = t[j];
+                }
+            }
         }
     }
 }
@@ -1027,6 +1059,63 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const float* __restri
     if (threadIdx.x == 0 && part) part[blockIdx.x] = red[0];
 }
 
+// The split into planes whose mode 0 is padded from I0 to I0p (a multiple of 8) entries:
+// output entries e = i0 + I0p r, four at a time (i0 a multiple of 4, the four in one row),
+// x = X[i0 + I0 r] for i0 < I0 and 0 in the padding; ||X||^2 as in split_planes_kernel
+__global__ void __launch_bounds__(256) split_planes_padded_kernel(const float* __restrict__ X, int64_t I0,
+                                                                  int64_t I0p, int64_t NXp, int64_t pitch,
+                                                                  int64_t chunk, __nv_bfloat16* __restrict__ Xs,
+                                                                  double* __restrict__ part) {
+    const int64_t b0 = (int64_t)blockIdx.x * chunk;
+    const int64_t b1 = (b0 + chunk < NXp) ? b0 + chunk : NXp;
+    __nv_bfloat16* hi = Xs;
+    __nv_bfloat16* lo = Xs + pitch;
+    double ss = 0.0;
+    float S = 0.0f, cmp = 0.0f;
+    int cnt = 0;
+    auto add_sq = [&](float x) {
+        const float pp = x * x;
+        const float ee = fmaf(x, x, -pp);
+        const float t = S + pp;
+        const float z = t - S;
+        cmp += ((S - (t - z)) + (pp - z)) + ee;
+        S = t;
+    };
+    auto flush = [&]() {
+        ss += (double)S;
+        ss += (double)cmp;
+        S = 0.0f;
+        cmp = 0.0f;
+    };
+    const int64_t n4 = (b1 - b0) / 4;                    // b0, b1: multiples of 4 (I0p % 8 == 0)
+    for (int64_t v = threadIdx.x; v < n4; v += blockDim.x) {
+        const int64_t e = b0 + 4 * v;
+        const int64_t r = e / I0p;
+        const int64_t i0 = e - r * I0p;
+        const float* src = X + i0 + I0 * r;
+        float x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = (i0 + j < I0) ? src[j] : 0.0f;
+        uint2 hw, lw;
+        split_pair(x[0], x[1], hw.x, lw.x);
+        split_pair(x[2], x[3], hw.y, lw.y);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) add_sq(x[j]);
+        if (++cnt == 16) { flush(); cnt = 0; }
+        *reinterpret_cast<uint2*>(hi + e) = hw;
+        *reinterpret_cast<uint2*>(lo + e) = lw;
+    }
+    flush();
+    __shared__ double red[256];
+    red[threadIdx.x] = ss;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && part) part[blockIdx.x] = red[0];
+}
+
 __global__ void sum_partials_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s = 0.0;
@@ -1072,21 +1161,34 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-int64_t split_pitch(int64_t NX) { return round_up(NX, 64); }
+int64_t planes_rows0(int64_t I0) { return round_up(I0, 8); }
 
-int split_chunks(int64_t NX) {
-    int64_t nb = (NX + 4095) / 4096;
+void planes_dims(const int64_t* dims, int N, int64_t* pd) {
+    for (int k = 0; k < N; ++k) pd[k] = dims[k];
+    pd[0] = planes_rows0(dims[0]);
+}
+
+int64_t split_pitch(int64_t NXp) { return round_up(NXp, 64); }
+
+int split_chunks(int64_t NXp) {
+    int64_t nb = (NXp + 4095) / 4096;
     if (nb > 1216) nb = 1216;
     if (nb < 1) nb = 1;
     return (int)nb;
 }
 
-cudaError_t launch_split_planes(const float* X, int64_t NX, void* Xs, double* part, double* normX2,
-                                cudaStream_t s) {
+cudaError_t launch_split_planes(const float* X, int64_t I0, int64_t rest, void* Xs, double* part,
+                                double* normX2, cudaStream_t s) {
+    const int64_t I0p = planes_rows0(I0);
+    const int64_t NX = I0p * rest;
     const int nb = split_chunks(NX);
     const int64_t chunk = round_up((NX + nb - 1) / nb, 1024);
     const int grid = (int)((NX + chunk - 1) / chunk);
-    split_planes_kernel<<<grid, 256, 0, s>>>(X, NX, split_pitch(NX), chunk, static_cast<__nv_bfloat16*>(Xs), part);
+    if (I0p == I0)
+        split_planes_kernel<<<grid, 256, 0, s>>>(X, NX, split_pitch(NX), chunk, static_cast<__nv_bfloat16*>(Xs), part);
+    else
+        split_planes_padded_kernel<<<grid, 256, 0, s>>>(X, I0, I0p, NX, split_pitch(NX), chunk,
+                                                        static_cast<__nv_bfloat16*>(Xs), part);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !normX2) return e;
@@ -1124,8 +1226,14 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     // offset H lq): then the image is kept for all 8 shifts, and each stage takes the one
     // that moves its first element to a 16-byte boundary.  The first prefix with >= 64
     // rows and <= 1/32 padding, else the least padding, among those whose images stay
-    // L2-resident.
+    // L2-resident.  A K-major mode with few rows (I_n / P <= 128) packs several runs per
+    // tile, runs lq, lq + 1, ... of one row at a stride of H elements: a short head keeps
+    // them within a few KB, so that each stage reads a few contiguous spans instead of
+    // one 128-byte piece of every run, and that is worth up to 1/4 padding (measured on
+    // 200x200x300x40, mode 3: 349 us with H = 200 against 444 us with H = 40,000).  This
+    // holds when the packed runs sit in one box: one image (8-aligned H, no shifts).
     const int mmax = mn ? nfac : n_left;
+    const bool near_runs = !mn && I / P <= PS_M;
     int best = -1;
     double best_waste = 2.0;
     int64_t prod = 1;
@@ -1136,7 +1244,9 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
         const size_t img = (size_t)nsh * (size_t)(padded / PS_BK) * pl.N * 128;
         if (img > ((size_t)32 << 20)) break;
         const double waste = (double)(padded - prod) / (double)padded;
-        if (prod >= PS_BK && (padded - prod) * MTK_PS_HEAD_PAD <= padded) { best = m; break; }
+        const int64_t hp = (near_runs && nsh == 1 && P == 1 && prod % 8 == 0 && L / prod > 1)
+                               ? MTK_PS_HEAD_PAD_NEAR : MTK_PS_HEAD_PAD;
+        if (prod >= PS_BK && (padded - prod) * hp <= padded) { best = m; break; }
         if (waste < best_waste) { best_waste = waste; best = m; }
     }
     if (best < 0) return pl;
@@ -1277,7 +1387,11 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
                                    const float* const* fac, const int64_t* frad, int nfac, int C,
                                    const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
                                    void* scratch, uint32_t* status, cudaStream_t s,
-                                   unsigned long long wait_ns, int stall, const FactorHook* hook) {
+                                   unsigned long long wait_ns, int stall, const FactorHook* hook,
+                                   int64_t f0_rows, int64_t opad, int64_t oreal) {
+    if (opad < 0 || (opad > 0 && (oreal < 1 || oreal > opad || I % opad != 0))) return cudaErrorInvalidValue;
+    if (opad == oreal) opad = 0;
+    const int64_t Iout = opad ? (I / opad) * oreal : I;
     char* sc = static_cast<char*>(scratch);
     uint8_t* image = reinterpret_cast<uint8_t*>(sc);
     float* qtab = pl.qtab_bytes ? reinterpret_cast<float*>(sc + round_up((int64_t)pl.image_bytes, 256)) : nullptr;
@@ -1295,6 +1409,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
         pa.fac[z] = fac[z];
         pa.frad[z] = frad[z];
     }
+    pa.f0_rows = f0_rows > 0 && f0_rows < frad[0] ? f0_rows : frad[0];
     pa.H = pl.H;
     pa.Hp = (int64_t)pl.spr * PS_BK;
     pa.nsh = pl.nsh;
@@ -1436,10 +1551,12 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     p.out = out;
     p.out_si = out_si;
     p.out_sc = out_sc;
+    p.opad = opad;
+    p.oreal = oreal;
     p.part = part;
-    // slabs in the output's layout; the output is row-major (si = C, sc = 1) or
-    // column-major (si = 1, sc = I)
-    if (!((out_si == C && out_sc == 1) || (out_si == 1 && out_sc == I))) return cudaErrorInvalidValue;
+    // slabs in the output's layout (over the view's rows); the output is row-major
+    // (si = C, sc = 1) or column-major (si = 1, sc = its rows)
+    if (!((out_si == C && out_sc == 1) || (out_si == 1 && out_sc == Iout))) return cudaErrorInvalidValue;
     p.part_cm = (out_si == 1 && C > 1) ? 1 : 0;
     p.status = status;
     p.wait_ns = wait_ns ? wait_ns : kPsWaitNs;
@@ -1479,8 +1596,11 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
         rs.stot = pl.stot;
         rs.tot = (int64_t)pl.ntiles * pl.stot;
         rs.G = pl.grid;
+        rs.opad = opad;
+        rs.oreal = oreal;
+        rs.Iout = Iout;
         const int vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
-                        ((reinterpret_cast<uintptr_t>(part) & 15) == 0);
+                        ((reinterpret_cast<uintptr_t>(part) & 15) == 0) && opad == 0;
         if (n >= 65536 && pl.nslab <= kFewSlabs) {
             const int64_t ng = (n + 3) / 4;
             int64_t blocks = (ng + 255) / 256;

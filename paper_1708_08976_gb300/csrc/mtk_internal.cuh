@@ -92,13 +92,19 @@ cudaError_t launch_tc_image(const float* const* fac, const int64_t* frad, int he
                             int64_t rad0, int64_t rad0p, void* image, cudaStream_t s);
 
 // ---- tensor stored as two BF16 planes (contract_split.cu) --------------------------
-// Planes of an NX-entry tensor: hi = bf16_rn(x) at [0, NX), lo = bf16_rn(x - hi) at
-// [pitch, pitch + NX), pitch = split_pitch(NX) (a multiple of 64 entries).
-int64_t split_pitch(int64_t NX);
-int split_chunks(int64_t NX);          // FP64 partials of ||X||^2 written by the split
-// part: split_chunks(NX) doubles; normX2 (may be NULL): receives ||X||^2
-cudaError_t launch_split_planes(const float* X, int64_t NX, void* Xs, double* part, double* normX2,
-                                cudaStream_t s);
+// The planes hold the tensor with mode 0 padded to I0p = planes_rows0(I0), a multiple of 8
+// (entries with i0 >= I0 are zero), so that every row of every mode-n view is 16-byte
+// aligned: entry (i0, rest) at i0 + I0p rest.  NXp = I0p * (the other dims' product);
+// hi = bf16_rn(x) at [0, NXp), lo = bf16_rn(x - hi) at [pitch, pitch + NXp),
+// pitch = split_pitch(NXp) (a multiple of 64 entries).
+int64_t planes_rows0(int64_t I0);
+void planes_dims(const int64_t* dims, int N, int64_t* pd);   // dims with mode 0 padded
+int64_t split_pitch(int64_t NXp);
+int split_chunks(int64_t NXp);          // FP64 partials of ||X||^2 written by the split
+// X: I0 x rest FP32 (natural order); part: split_chunks(NXp) doubles; normX2 (may be
+// NULL): receives ||X||^2
+cudaError_t launch_split_planes(const float* X, int64_t I0, int64_t rest, void* Xs, double* part,
+                                double* normX2, cudaStream_t s);
 // Plan of the planes contraction for view (L, I, R) and the mode's factor list; ok = 0
 // when the shape is not taken (C > 64; MN-major: I_n not a multiple of 8; K-major:
 // P = 8 / gcd(I^L, 8) not dividing I_n, ...).
@@ -124,13 +130,17 @@ struct FactorHook {
     void* hinv;
     uint32_t* status;
 };
-// wait_ns: limit of the kernel's abortable waits (0: 1 s); stall: the timeout test hook
+// wait_ns: limit of the kernel's abortable waits (0: 1 s); stall: the timeout test hook.
+// f0_rows: rows of fac[0] that exist (a padded mode 0 has frad[0] > f0_rows; the head
+// image takes the rest as zero).  opad, oreal: row j of the view (I rows) is output row
+// (j mod opad) + oreal (j / opad), dropped when j mod opad >= oreal (opad = 0: row j);
+// the output has Iout = (I / opad) oreal rows.
 cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int64_t I, int64_t R,
                                    const float* const* fac, const int64_t* frad, int nfac, int C,
                                    const PlanesPlan& pl, float* out, int64_t out_si, int64_t out_sc,
                                    void* scratch, uint32_t* status, cudaStream_t s,
-                                   unsigned long long wait_ns = 0, int stall = 0,
-                                   const FactorHook* hook = nullptr);
+                                   unsigned long long wait_ns, int stall, const FactorHook* hook,
+                                   int64_t f0_rows, int64_t opad, int64_t oreal);
 
 // ---- batched MTTKRPs in one persistent launch (batched.cu) --------------------------
 typedef mtk_batch_problem BatchedProblem;
@@ -141,6 +151,17 @@ size_t batched_scratch_floats(const BatchedProblem* probs, int P, int64_t kchunk
 // scratch: batched_scratch_floats(...) floats, 256-byte aligned
 cudaError_t launch_batched(const BatchedProblem* probs, int P, int64_t kchunk_target, int ctas, float* scratch,
                            cudaStream_t s);
+
+// ---- FP32 FMA throughput probe (probe.cu) ---------------------------------------------
+cudaError_t launch_ffma_probe(int blocks, int iters, float* out, cudaStream_t s);
+int ffma_probe_threads();
+
+// ---- tensors symmetric in modes 0 and 1, packed (symmetric.cu) ----------------------
+// diag = 1: the n0 (n0 + 1) / 2 entries a >= b; 0: the n0 (n0 - 1) / 2 entries a > b
+int64_t sym_packed_rows(int64_t n0, int diag);      // rounded up to a multiple of 8
+cudaError_t launch_sym_pack(const float* X, int64_t n0, int diag, int64_t rest, float* Xp, cudaStream_t s);
+cudaError_t launch_sym_pair(const float* U0, const float* U1, int64_t n0, int diag, int C, float* W, cudaStream_t s);
+cudaError_t launch_sym_ttv(const float* V, const float* U, int64_t n0, int diag, int C, float* M, cudaStream_t s);
 
 cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C, float* K,
                        int reuse, cudaStream_t s);

@@ -18,9 +18,10 @@ data is not available, a synthetic tensor of its shape stands in for it):
 * ``tiny3``     60x50x40 FP64 uniform[0,1) (seed 0), rank 8 factors uniform[0,1) (seed 1)
 * ``cube512``   512^3 FP32 N(0,1) (seed 2), rank 32 factors N(0,1)/sqrt(32) (seed 3)
 * ``corr4``     200x200x300x40 FP32 correlation-shaped: rank-10 CP with factors
-                uniform[-1,1], modes 0/1 sharing one factor (symmetric), plus
-                N(0, 0.05^2) noise symmetrised in modes 0/1, clipped to [-1,1]
-                (seed 4); rank 25 ALS factors uniform[0,1) (seed 5)
+                uniform[-1,1], modes 0/1 sharing one factor, its FP32 values
+                symmetrised, plus N(0, 0.05^2) noise symmetrised in modes 0/1,
+                clipped to [-1,1] (seed 4): exactly symmetric in modes 0/1;
+                rank 25 ALS factors uniform[0,1) (seed 5)
 * ``cube32x5``  32^5 FP32 rank-16 CP with factors uniform[-1,1] plus N(0, 0.01^2)
                 noise (seed 6); rank 16
 * ``fd5``       6x5x4x3x2 FP64 N(0,1), rank 3 factors uniform[-1,1] (seed 7)
@@ -122,8 +123,10 @@ def corr4(dims=(200, 200, 300, 40), rank_true=10, C=25, seed_x=4, seed_u=5,
         E = g.standard_normal((dims[2], dims[1], dims[0]), dtype=np.float32) * np.float32(noise)
         E = (E + E.transpose(0, 2, 1)) * np.float32(0.5)     # symmetric in modes 0/1
         blk = X[i3]
-        blk += E
-        np.clip(blk, -1.0, 1.0, out=blk)
+        S = blk + blk.transpose(0, 2, 1)                     # the rounded CP part, made
+        S *= np.float32(0.5)                                 # exactly symmetric as well
+        S += E
+        np.clip(S, -1.0, 1.0, out=blk)
     X = X.reshape(-1)
     U = uniform_factors(dims, C, seed_u, np.float32)
     return X, tuple(dims), U

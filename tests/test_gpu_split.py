@@ -2,20 +2,22 @@
 mtk_mttkrp_split, mtk_cp_als_sweep_split) against the FP64 oracle.
 
 * The split itself is checked bit for bit against its definition: hi = bf16_rn(x),
-  lo = bf16_rn(x - hi), with the rounding done by torch on the CPU; ||X||^2 against
+  lo = bf16_rn(x - hi), with the rounding done by torch on the CPU, at i0 + I0p r with
+  mode 0 padded to I0p = the next multiple of 8 and zeros in the padding; ||X||^2 against
   the oracle.
 * The contraction carries each tensor entry as hi + lo (error <= 2^-16 |x|) and each
   KRP entry as three BF16 pieces, so it is held to the bf16x2 bound derived in
   test_gpu_tc.py: 3x the expected representation error plus 2e-6 for FP32
   accumulation.
 The shapes cover each branch of the planes kernel: K-major CTA tiles of up to 128 rows or
-of up to 256 rows as two MMA tiles (one or several per mode, ragged last tile), K-major with the head inside the modes left of n
-(several runs per row), K-major rows in classes i mod P when I^L is not a multiple of 8
-(shifted head images), runs packed into the MMA rows for small I_n, MN-major (mode 0) with
-one to four 64-row boxes per CTA or packed runs, ranks C = 1..64 (one to four 16-column chunks), N = 2..5,
-heads shorter than one 64-k stage, several tail factors, and explicit CTA counts.
+of up to 256 rows as two MMA tiles (one or several per mode, ragged last tile), K-major with
+the head inside the modes left of n (several runs per row), runs packed into the MMA rows for
+small I_n, MN-major (mode 0) with one to four 64-row boxes per CTA or packed runs, ranks
+C = 1..64 (one to four 16-column chunks), N = 2..6, heads shorter than one 64-k stage,
+several tail factors, explicit CTA counts, and I_0 not a multiple of 8 (the planes pad
+mode 0 to the next multiple of 8: U_0's missing rows count as zero, mode 0 and the right
+partial drop the padding rows of their output).
 """
-import math
 
 import numpy as np
 import pytest
@@ -52,20 +54,32 @@ def planes_ref(X32: torch.Tensor):
     return hi.view(torch.int16), lo.view(torch.int16)
 
 
-@pytest.mark.parametrize("n_entries", [1, 7, 64, 1000, 4099, 262147])
-def test_split_planes_bits_and_norm(n_entries):
+@pytest.mark.parametrize("dims", [(1,), (7,), (64,), (1000,), (4099,), (262147,), (8, 9), (5, 7, 3),
+                                  (13, 40), (60, 50, 40), (1, 9, 2), (165, 31, 7), (30, 30, 30, 4)])
+def test_split_planes_bits_and_norm(dims):
+    n_entries = int(np.prod(dims))
     g = np.random.default_rng(n_entries)
     X = (g.standard_normal(n_entries) * np.exp(g.uniform(-20, 20, n_entries))).astype(np.float32)
     X[::13] = 0.0
     Xd = torch.from_numpy(X).cuda()
-    Xs, nx2 = mtk.split_tensor(Xd)
+    Xs, nx2 = mtk.split_tensor(Xd, dims)
     torch.cuda.synchronize()
-    pitch = L.load().mtk_split_pitch(n_entries)
-    assert pitch % 64 == 0 and pitch >= n_entries
+    lib = L.load()
+    I0 = dims[0]
+    I0p = (I0 + 7) // 8 * 8
+    assert lib.mtk_split_rows0(I0) == I0p
+    rest = n_entries // I0
+    pitch = lib.mtk_split_pitch(L.dims_arr(list(dims)), len(dims))
+    assert pitch % 64 == 0 and pitch >= I0p * rest
     hi, lo = planes_ref(Xd)
     got = Xs.cpu()
-    assert torch.equal(got[:n_entries], hi)
-    assert torch.equal(got[pitch:pitch + n_entries], lo)
+    idx = (torch.arange(I0).view(1, I0) + I0p * torch.arange(rest).view(rest, 1)).reshape(-1)
+    assert torch.equal(got[idx], hi)
+    assert torch.equal(got[pitch + idx], lo)
+    pad = torch.ones(pitch, dtype=torch.bool)
+    pad[idx] = False
+    pad[I0p * rest:] = False                         # beyond the padded tensor: not written
+    assert bool((got[:pitch][pad] == 0).all()) and bool((got[pitch:][pad] == 0).all())
     ref = oracle.norm2(X.astype(np.float64))
     assert abs(nx2.item() - ref) <= 1e-12 * ref
 
@@ -73,7 +87,7 @@ def test_split_planes_bits_and_norm(n_entries):
 def run_split(X, dims, U, n, C, splits=0, with_x=True):
     Xd = to_dev(X, torch)
     Ud = factors_dev(U, torch)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     M = mtk.mttkrp(Xd if with_x else None, dims, Ud, n, Xs=Xs, splits=splits)
     torch.cuda.synchronize()
     return M.double().cpu().numpy()
@@ -94,29 +108,32 @@ SHAPES = [
     ((512, 8, 24), 16),           # MN two CTA tiles of 256 rows (two MMA tiles each)
     ((16, 456, 12), 32),          # K-major CTA tiles of 232 + 224 rows (two MMA tiles, ragged)
     ((200, 200, 8), 25),          # K-major 200 rows in one CTA; head of 200 rows: padding k-steps skipped
+    ((60, 50, 40), 8),            # I_0 = 60 padded to 64: mode 0 drops 4 rows, U_0 rows 60..63 zero
+    ((165, 9, 20), 25),           # I_0 = 165 -> 168; mode 0 three tiles (the last ragged)
+    ((5, 24, 40, 8), 16),         # I_0 = 5 -> 8: heads of mostly padding
+    ((30, 30, 30, 4), 12),        # 30 -> 32 with a short head
+    ((7, 6, 5, 4, 3, 2), 9),      # N = 6, every mode
 ]
 
 
-# K-major modes whose I^L is not a multiple of 8: the rows of one class i mod P (P = 8 /
-# gcd(I^L, 8)) are loaded as rows of the super-row view, and every stage takes the head
-# image shifted so that its first element sits on a 16-byte boundary.  (dims, C, modes
-# the planes kernel must take without the FP32 tensor)
-CLASS_SHAPES = [
-    ((12, 6, 10), 8, (1, 2)),          # I^L = 12: P = 2; mode 2 I^L = 72 with shifted runs or one run
-    ((20, 10, 7, 8), 25, (1, 2, 3)),   # P = 2, two classes of 5 rows, packed runs under one shift
-    ((6, 4, 10, 5), 12, (1, 2, 3)),    # I^L = 6: P = 4 classes of one row
-    ((5, 8, 9), 8, (1, 2)),            # I^L = 5: P = 8 classes of one row each
-    ((3, 16, 11, 2), 16, (1, 2, 3)),   # I^L = 3: P = 8, two rows per class
-    ((100, 3000, 3), 25, (1, 2)),      # mode 1: P = 2, 1500 rows per class (6 tiles); mode 2: head
-                                       # of 100 rows (the 300000-row one exceeds the image budget),
-                                       # 3000 runs per row at alternating shifts 0, 4
-    ((30, 30, 4, 6), 33, (2, 3)),      # mode 2: I^L = 900, P = 2; C = 33 (three chunks)
+# Shapes whose I^L (natural layout) is not a multiple of 8 at some mode: with mode 0 padded
+# in the planes every row is aligned.  (dims, C, modes the planes kernel must take without
+# the FP32 tensor)
+UNALIGNED_SHAPES = [
+    ((12, 6, 10), 8, (0, 1, 2)),          # I_0 = 12 -> 16
+    ((20, 10, 7, 8), 25, (0, 1, 2, 3)),   # 20 -> 24, packed runs
+    ((6, 4, 10, 5), 12, (0, 1, 2, 3)),    # 6 -> 8
+    ((5, 8, 9), 8, (0, 1, 2)),            # 5 -> 8
+    ((3, 16, 11, 2), 16, (0, 1, 2, 3)),   # 3 -> 8: heads of 3 real rows in 8
+    ((100, 3000, 3), 25, (0, 1, 2)),      # 100 -> 104; mode 1: 3000 rows (12 tiles); mode 2: head
+                                          # of 104 rows (the 312000-row one exceeds the image budget)
+    ((30, 30, 4, 6), 33, (0, 1, 2, 3)),   # 30 -> 32; C = 33 (three chunks)
 ]
 
 
-@pytest.mark.parametrize("dims,C,modes", CLASS_SHAPES)
-def test_mttkrp_split_row_classes(dims, C, modes):
-    """The planes kernel on K-major modes with unaligned rows or runs, against the
+@pytest.mark.parametrize("dims,C,modes", UNALIGNED_SHAPES)
+def test_mttkrp_split_unaligned(dims, C, modes):
+    """The planes kernel on shapes whose natural rows are not 16-byte aligned, against the
     oracle, without the FP32 tensor to fall back to."""
     X, dims, U = synth.random_case(dims, C, seed=13 * sum(dims) + C)
     Xr = X.astype(np.float32).astype(np.float64)
@@ -143,25 +160,27 @@ def test_mttkrp_split_parity(dims, C):
 
 
 def test_mttkrp_split_without_fp32_tensor():
-    """Shapes the planes kernel takes need no FP32 tensor; others report EUNSUPPORTED."""
-    X, dims, U = synth.random_case((64, 48, 40), 8, seed=5)
-    Xr = X.astype(np.float32).astype(np.float64)
-    Ur = f32_round(U)
-    for n in range(3):
-        ref = oracle.mttkrp(Xr, dims, Ur, n)
-        got = run_split(X, dims, U, n, 8, with_x=False)
-        assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, n, ref)
-    X, dims, U = synth.tiny3()                       # mode 0 has I_0 = 60 (not a multiple of 8)
+    """Shapes the planes kernel takes need no FP32 tensor (60x50x40: I_0 = 60 padded to 64
+    in the planes); others (C > 64) report EUNSUPPORTED, and run the FP32-input path when
+    the FP32 tensor is given."""
+    for shape in ((64, 48, 40), (60, 50, 40)):
+        X, dims, U = synth.random_case(shape, 8, seed=5)
+        Xr = X.astype(np.float32).astype(np.float64)
+        Ur = f32_round(U)
+        for n in range(3):
+            ref = oracle.mttkrp(Xr, dims, Ur, n)
+            got = run_split(X, dims, U, n, 8, with_x=False)
+            assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, n, ref), (shape, n)
+    X, dims, U = synth.random_case((24, 20, 16), 80, seed=6)
     Xd = to_dev(X, torch)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     with pytest.raises(mtk.MtkError) as ei:
         mtk.mttkrp(None, dims, factors_dev(U, torch), 0, Xs=Xs)
     assert ei.value.status == L.MTK_EUNSUPPORTED
-    # with the FP32 tensor the same call runs the FP32-input tensor-core path
     Xr = X.astype(np.float32).astype(np.float64)
     Ur = f32_round(U)
     ref = oracle.mttkrp(Xr, dims, Ur, 0)
-    got = run_split(X, dims, U, 0, 8)
+    got = run_split(X, dims, U, 0, 80)
     assert rel_fro(got, ref) < bf16x2_bound(Xr, dims, Ur, 0, ref)
 
 
@@ -182,7 +201,7 @@ def test_mttkrp_split_deterministic():
     X, dims, U = synth.random_case((72, 64, 50), 25, seed=3)
     Xd = to_dev(X, torch)
     Ud = factors_dev(U, torch)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     for n in range(3):
         a = mtk.mttkrp(Xd, dims, Ud, n, Xs=Xs).clone()
         b = mtk.mttkrp(Xd, dims, Ud, n, Xs=Xs)
@@ -193,7 +212,7 @@ def test_mttkrp_split_deterministic():
 def test_split_rejects_bad_options():
     X, dims, U = synth.random_case((64, 48, 40), 8, seed=5)
     Xd = to_dev(X, torch)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     for kw in ({"precision": "fp32"}, {"precision": "bf16x3"}, {"algo": "two_step"}):
         with pytest.raises(ValueError):
             mtk.mttkrp(Xd, dims, factors_dev(U, torch), 0, Xs=Xs, **kw)
@@ -230,7 +249,7 @@ def test_corr4_split_full_M():
     U64 = [u.astype(np.float64) for u in U]
     Xd = torch.from_numpy(X).cuda()
     Ud = [torch.from_numpy(u).cuda() for u in U]
-    Xs, nx2 = mtk.split_tensor(Xd)
+    Xs, nx2 = mtk.split_tensor(Xd, dims)
     assert abs(nx2.item() - oracle.norm2(X64)) <= 1e-12 * oracle.norm2(X64)
     for n in range(4):
         ref = oracle.mttkrp(X64, dims, U64, n)
@@ -241,7 +260,8 @@ def test_corr4_split_full_M():
         assert err < tol, (n, err, tol)
 
 
-@pytest.mark.parametrize("dims,C", [((24, 16, 20, 8), 8), ((32, 24, 40), 12), ((40, 16, 24, 10), 25)])
+@pytest.mark.parametrize("dims,C", [((24, 16, 20, 8), 8), ((32, 24, 40), 12), ((40, 16, 24, 10), 25),
+                                    ((30, 20, 12, 7), 8), ((13, 31, 9), 10)])
 def test_als_sweep_dimension_tree(dims, C):
     """The dimension-tree sweep (algo two_step on the planes: partials over modes >= 2 and
     over modes 0, 1 shared by two updates each) against the oracle's Gauss-Seidel sweep,
@@ -281,37 +301,26 @@ PARTIAL_SHAPES = [
     ((8, 6, 5, 4, 3), 5),         # N = 5: several factors on each side
     ((64, 48, 40), 33),           # C = 33 (three chunks); MN view of 64 rows (n = 0, right)
     ((200, 200, 12, 5), 25),      # tall right view at n = 1: 40000 rows, many CTAs
-    ((5, 24, 40, 8), 8),          # I_0 = 5: n = 0 right is not taken; n = 1 left: I^L = 5, 8 row classes
-    ((6, 5, 8, 3), 8),            # left views with I^L = 6 and 30 (P = 4 classes); right n = 0, 1 not taken
+    ((5, 24, 40, 8), 8),          # I_0 = 5 (8 in the planes): right partials drop the padding rows
+    ((6, 5, 8, 3), 8),            # I_0 = 6: left views over the padded I^L = 8 and 40
 ]
 
 
 @pytest.mark.parametrize("dims,C", PARTIAL_SHAPES)
 def test_partial_split_parity(dims, C):
     """First step of Algorithm 4 on the planes (mtk_partial_mttkrp_split) against the
-    oracle's partial MTTKRP by its element-wise definition, for every mode and both
-    sides that the planes kernel takes; others must report EUNSUPPORTED."""
+    oracle's partial MTTKRP by its element-wise definition, for every mode and side."""
     X, dims, U = synth.random_case(dims, C, seed=7 * sum(dims) + C)
     Xr = X.astype(np.float32).astype(np.float64)
     Ur = f32_round(U)
     Xd = to_dev(X, torch)
     Ud = factors_dev(U, torch)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     N = len(dims)
     ran = 0
     for n in range(N):
         for right in (True, False):
             if (right and n == N - 1) or (not right and n == 0):
-                continue
-            IL = int(np.prod(dims[:n])) if n else 1
-            IR = int(np.prod(dims[n + 1:]))
-            # right: the MN-major view (1, I^L I_n, I^R) needs I^L I_n a multiple of 8; left:
-            # the K-major view (I^L, I_n I^R, 1) needs P = 8 / gcd(I^L, 8) to divide its rows
-            takes = (IL * dims[n]) % 8 == 0 if right else (dims[n] * IR) % (8 // math.gcd(IL, 8)) == 0
-            if not takes:
-                with pytest.raises(mtk.MtkError) as ei:
-                    mtk.partial_mttkrp_split(Xs, dims, Ud, n, right)
-                assert ei.value.status == L.MTK_EUNSUPPORTED
                 continue
             got = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right)
             torch.cuda.synchronize()
@@ -320,7 +329,7 @@ def test_partial_split_parity(dims, C):
             tol = partial_bound(Xr, dims, Ur, n, right, ref)
             assert err < tol, (dims, C, n, right, err, tol)
             ran += 1
-    assert ran >= 2
+    assert ran == 2 * (N - 1)
 
 
 def test_partial_split_factors_off_side_unused_and_repeatable():
@@ -329,7 +338,7 @@ def test_partial_split_factors_off_side_unused_and_repeatable():
     X, dims, U = synth.random_case((24, 16, 20, 8), 8, seed=3)
     Xd = to_dev(X, torch)
     Ud = factors_dev(U, torch)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     a = mtk.partial_mttkrp_split(Xs, dims, [None, None, Ud[2], Ud[3]], 1, True)
     b = torch.full_like(a, float("nan"))
     mtk.partial_mttkrp_split(Xs, dims, Ud, 1, True, out=b)
@@ -350,7 +359,7 @@ def test_corr4_tree_partials_full():
     U64 = [u.astype(np.float64) for u in U]
     Xd = torch.from_numpy(X).cuda()
     Ud = [torch.from_numpy(u).cuda() for u in U]
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     del Xd
     for n, right in ((1, True), (2, False)):
         got = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right).double().cpu().numpy()
@@ -372,7 +381,7 @@ def test_partial_split_units_back_to_back(splits):
     Ur = f32_round(U)
     Xd = to_dev(X, torch)
     Ud = factors_dev(U, torch)
-    Xs, _ = mtk.split_tensor(Xd)
+    Xs, _ = mtk.split_tensor(Xd, dims)
     for n, right in ((1, True), (2, False)):
         got = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right, splits=splits)
         ref = oracle.partial_mttkrp(Xr, dims, Ur, n, right)

@@ -62,10 +62,10 @@ def test_planes_timeout_reported(torch_cuda, splits):
     X, U = _inputs(dims, C, 5)
     Xd = torch.from_numpy(X).cuda()
     Ud = [torch.from_numpy(u).cuda() for u in U]
-    I = X.size
-    Xs = torch.empty(lib.mtk_split_bytes(I) // 2, dtype=torch.int16, device="cuda")
-    sws = _ws(torch, lib.mtk_split_workspace(I))
-    assert lib.mtk_split_tensor(Xd.data_ptr(), I, Xs.data_ptr(), None, sws.data_ptr(), sws.numel(), stream) == 0
+    d = L.dims_arr(dims)
+    Xs = torch.empty(lib.mtk_split_bytes(d, 3) // 2, dtype=torch.int16, device="cuda")
+    sws = _ws(torch, lib.mtk_split_workspace(d, 3))
+    assert lib.mtk_split_tensor(Xd.data_ptr(), d, 3, Xs.data_ptr(), None, sws.data_ptr(), sws.numel(), stream) == 0
     Xr = X.astype(np.float64)
     Ur = [u.astype(np.float64) for u in U]
     for n in range(3):

@@ -5,8 +5,10 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
+import synth
 from paper_1708_08976_gb300 import _lib as L
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -91,13 +93,20 @@ def test_split_and_batched_calls_rejected_before_launch():
     fake = 0x10000
     d = L.dims_arr([64, 48, 40])
     U = L.ptr_arr([fake, fake, fake])
-    # split: pitch and sizes; null / misaligned planes
-    assert lib.mtk_split_pitch(100) % 64 == 0 and lib.mtk_split_pitch(100) >= 100
-    assert lib.mtk_split_bytes(100) == 4 * lib.mtk_split_pitch(100)
-    assert lib.mtk_split_workspace(0) == 0
-    assert lib.mtk_split_tensor(fake, 100, None, None, fake, 1 << 20, None) == L.MTK_EINVAL
-    assert lib.mtk_split_tensor(fake, 100, fake + 8, None, fake, 1 << 20, None) == L.MTK_EINVAL
-    assert lib.mtk_split_tensor(fake, 100, fake, None, fake, 8, None) == L.MTK_EWORKSPACE
+    # split: mode 0 padded to a multiple of 8, pitch and sizes; bad dims; null / misaligned planes
+    assert [lib.mtk_split_rows0(v) for v in (0, 1, 8, 60, 165, 200)] == [0, 8, 8, 64, 168, 200]
+    d1 = L.dims_arr([100])
+    assert lib.mtk_split_pitch(d1, 1) == 128
+    d5 = L.dims_arr([5, 7, 3])
+    assert lib.mtk_split_pitch(d5, 3) == 192                      # 8 x 21 = 168 padded entries
+    assert lib.mtk_split_bytes(d5, 3) == 4 * 192
+    assert lib.mtk_split_pitch(d, 3) == 64 * 48 * 40
+    assert lib.mtk_split_workspace(L.dims_arr([0, 4]), 2) == 0
+    assert lib.mtk_split_bytes(L.dims_arr([4, 4]), 0) == 0
+    assert lib.mtk_split_tensor(fake, d5, 3, None, None, fake, 1 << 20, None) == L.MTK_EINVAL
+    assert lib.mtk_split_tensor(fake, d5, 3, fake + 8, None, fake, 1 << 20, None) == L.MTK_EINVAL
+    assert lib.mtk_split_tensor(fake, L.dims_arr([5, -1]), 2, fake, None, fake, 1 << 20, None) == L.MTK_EINVAL
+    assert lib.mtk_split_tensor(fake, d5, 3, fake, None, fake, 8, None) == L.MTK_EWORKSPACE
     # MTTKRP on the planes: options other than AUTO/BF16X2 and AUTO/FUSED are refused
     for o in (L.opts(precision=L.PREC_FP32), L.opts(precision=L.PREC_BF16X3), L.opts(algo=L.ALGO_TWO_STEP)):
         assert lib.mtk_mttkrp_split_workspace(d, 3, 8, 0, ctypes.byref(o)) == 0
@@ -161,15 +170,15 @@ def test_partial_split_rejected_before_launch():
         assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 8, 1, 1, ctypes.byref(o)) == 0
         assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 8, 1, 1, fake, fake, 1 << 30, ctypes.byref(o),
                                             None) == L.MTK_EINVAL
-    # shapes outside the planes kernel: C > 64; a left view whose rows do not split into
-    # the classes i mod P of its I^L (I^L = 6: P = 4, 5 x 3 x 3 = 45 rows)
+    # shapes outside the planes kernel: C > 64 (I_0 = 6 is taken: the planes pad mode 0 to 8)
     assert lib.mtk_partial_mttkrp_split_workspace(d, 4, 65, 1, 1, None) == 0
     assert lib.mtk_partial_mttkrp_split(fake, d, 4, U, 65, 1, 1, fake, fake, 1 << 30, None,
                                         None) == L.MTK_EUNSUPPORTED
     d_odd = L.dims_arr([6, 5, 3, 3])
-    assert lib.mtk_partial_mttkrp_split_workspace(d_odd, 4, 8, 1, 0, None) == 0
-    assert lib.mtk_partial_mttkrp_split(fake, d_odd, 4, U, 8, 1, 0, fake, fake, 1 << 30, None,
-                                        None) == L.MTK_EUNSUPPORTED
+    for n in range(1, 4):
+        assert lib.mtk_partial_mttkrp_split_workspace(d_odd, 4, 8, n, 0, None) > 0
+    for n in range(3):
+        assert lib.mtk_partial_mttkrp_split_workspace(d_odd, 4, 8, n, 1, None) > 0
 
 
 @pytest.mark.parametrize("dims,C", [((200, 200, 300, 40), 25), ((24, 16, 20, 8), 8), ((32, 24, 40), 12),
@@ -217,3 +226,49 @@ def test_noalloc_scratch_covers_the_benchmark_shapes():
     d = L.dims_arr([512, 512, 512])
     o = L.opts(algo=L.ALGO_TWO_STEP, precision=L.PREC_FP32)
     assert lib.mtk_mttkrp_workspace(d, 3, 32, 1, ctypes.byref(o)) > limit
+
+
+def test_symmetric_packed_sizes_and_shapes():
+    """Packed rows: n0 (n0 + 1) / 2 (with diagonal) or n0 (n0 - 1) / 2 (without: 200 ->
+    19,900 -> 19,904) rounded up to 8; the symmetric MTTKRP takes every mode of the
+    200x200x300x40 workload and of small 3- to 5-way shapes, and refuses unequal modes 0/1,
+    N = 2 and a diag other than 0/1 (workspace 0) and bad pointers before a launch."""
+    lib = L.load()
+    assert [lib.mtk_sym_packed_rows(n, 1) for n in (1, 2, 3, 4, 12, 200)] == [8, 8, 8, 16, 80, 20104]
+    assert [lib.mtk_sym_packed_rows(n, 0) for n in (1, 2, 3, 5, 12, 200)] == [0, 8, 8, 16, 72, 19904]
+    assert lib.mtk_sym_packed_rows(12, 2) == 0
+    o = L.opts()
+    for dims, C in (((200, 200, 300, 40), 25), ((12, 12, 40), 8), ((13, 13, 24, 5), 16), ((10, 10, 8, 6, 3), 7)):
+        d = L.dims_arr(list(dims))
+        for diag in (0, 1):
+            for n in range(len(dims)):
+                assert lib.mtk_mttkrp_sym_split_workspace(d, len(dims), diag, C, n, ctypes.byref(o)) > 0, (dims, n)
+    assert lib.mtk_mttkrp_sym_split_workspace(L.dims_arr([12, 13, 40]), 3, 1, 8, 0, ctypes.byref(o)) == 0
+    assert lib.mtk_mttkrp_sym_split_workspace(L.dims_arr([12, 12]), 2, 1, 8, 0, ctypes.byref(o)) == 0
+    assert lib.mtk_mttkrp_sym_split_workspace(L.dims_arr([12, 12, 40]), 3, 2, 8, 0, ctypes.byref(o)) == 0
+    fake = ctypes.c_void_p(1 << 20)
+    d = L.dims_arr([12, 12, 40])
+    assert lib.mtk_pack_symmetric(None, d, 3, 1, fake, None) == L.MTK_EINVAL
+    assert lib.mtk_pack_symmetric(fake, L.dims_arr([12, 13, 40]), 3, 1, fake, None) == L.MTK_EINVAL
+    assert lib.mtk_pack_symmetric(fake, d, 3, 2, fake, None) == L.MTK_EINVAL
+    for ptrs, n in (([None, 1 << 20, 1 << 20], 2), ([1 << 20, None, None], 0), ([None, 1 << 20, 1 << 20], 1)):
+        st = lib.mtk_mttkrp_sym_split(fake, d, 3, 1, L.ptr_arr(ptrs), 8, n, fake, fake, 1 << 30, ctypes.byref(o),
+                                      None)
+        assert st == L.MTK_EINVAL, (ptrs, n)
+
+
+def test_corr4_generator_is_exactly_symmetric():
+    """The correlation-shaped generator gives X(a, b, ...) == X(b, a, ...) bit for bit."""
+    X, dims, _ = synth.corr4(dims=(20, 20, 6, 3))
+    Xn = synth.as_natural(X, dims)
+    assert np.array_equal(Xn, Xn.swapaxes(0, 1))
+
+
+def test_ffma_probe_rejects_bad_arguments():
+    lib = L.load()
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.mtk_ffma_probe_out_floats(0) == 0 and lib.mtk_ffma_probe_out_floats(65) == 0
+    assert lib.mtk_ffma_probe_out_floats(1) % 256 == 0
+    for cps, iters, out in ((0, 16, fake), (65, 16, fake), (1, 0, fake), (1, (1 << 24) + 1, fake), (1, 16, None),
+                            (1, 16, ctypes.c_void_p((1 << 20) + 2))):
+        assert lib.mtk_ffma_probe(cps, iters, out, None, None) == L.MTK_EINVAL
