@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="corr4",
-                    choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth", "krp", "corr4-sym"],
+                    choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth", "krp", "corr4-sym",
+                             "dims", "cube512-forms"],
                     help="paper-synth: the paper's equal-dimension tensors (N = 3..6, ~7.3e8 entries, "
                          "C = 25), every mode's MTTKRP timed and checked on sampled rows; krp: the "
                          "Khatri-Rao product with and without reuse (Z = 2..4, ~2e7 rows, C = 25, 50); "
@@ -65,6 +66,10 @@ def parse():
                          "each prints its own line")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run every mode's MTTKRP W+K times (for profiler captures)")
+    ap.add_argument("--dims", default="165,165,165,8",
+                    help="--workload dims: the tensor's dims (entries uniform[-1,1), factors N(0,1)/sqrt(C))")
+    ap.add_argument("--rank", type=int, default=25, help="--workload dims: the rank C")
+    ap.add_argument("--modes", default="", help="--kernel-only: the modes to run (default: all)")
     ap.add_argument("--precision", default="best", help="fp32 | bf16x2 | bf16x3 | planes | best")
     ap.add_argument("--algo", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -93,6 +98,11 @@ def workload(name):
     elif name == "corr4-mid":
         X, dims, U = synth.corr4(dims=(200, 200, 300, 12))
         desc = "corr4-mid: 200x200x300x12 FP32 correlation-shaped (the mode-2 view of corr4 with 12 subjects), rank C=25"
+    elif name == "dims":
+        dims = tuple(int(v) for v in ARGS.dims.split(","))
+        X = synth.uniform_tensor(dims, 31, np.float32, -1.0, 1.0)
+        U = synth.normal_factors(dims, ARGS.rank, 32, np.float32, scale=1.0 / np.sqrt(ARGS.rank))
+        desc = f"dims: {'x'.join(map(str, dims))} FP32 uniform[-1,1), rank C={ARGS.rank}"
     else:
         X, dims, U = synth.cube512()
         desc = "cube512: 512^3 FP32 N(0,1), rank C=32, factors N(0,1)/sqrt(32)"
@@ -499,8 +509,64 @@ def run_sym(args, mtk, torch, dev, hbm_peak):
     return 0
 
 
+ARGS = None
+
+
+def run_forms(args, mtk, torch, dev, hbm_peak):
+    """cube512 (512^3 FP32 N(0,1), C = 32): every mode's MTTKRP in every algorithm
+    (fused, materialised KRP, two-step) and precision form (FP32, bf16x2, bf16x3 on the
+    FP32 tensor; the planes), timed with CUDA events over back-to-back calls (the tensor,
+    512 MiB, is larger than L2) against the HBM roofline, each checked on sampled rows
+    against the FP64 oracle.  The N(0,1) entries cancel heavily in every sum, so the
+    relative error of the split forms is larger here than on the correlation workload."""
+    import oracle
+    X, dims, U = synth.cube512()
+    N, C, I = 3, U[0].shape[1], X.size
+    U64 = [u.astype(np.float64) for u in U]
+    Xd = torch.from_numpy(X).to(dev)
+    Ud = [torch.from_numpy(u).to(dev) for u in U]
+    Xs, _ = mtk.split_tensor(Xd, dims)
+    M = torch.empty((max(dims), C), dtype=torch.float32, device=dev)
+    g = np.random.default_rng(512)
+    rows = [np.unique(np.concatenate([[0, dims[n] - 1], g.integers(0, dims[n], 6)])) for n in range(N)]
+    refs = [oracle.mttkrp_rows_f32(X, dims, U64, n, rows[n]) for n in range(N)]
+    ffma = ffma_peak(mtk, torch)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    out = []
+    forms = [(a, p) for a in ("fused", "materialized", "two_step") for p in ("fp32", "bf16x2", "bf16x3")]
+    forms.append(("fused", "planes"))
+    for algo, prec in forms:
+        modes = []
+        for n in range(N):
+            o = M[: dims[n]]
+            if prec == "planes":
+                fn = lambda: mtk.mttkrp(None, dims, Ud, n, Xs=Xs, out=o)
+            else:
+                fn = lambda: mtk.mttkrp(Xd, dims, Ud, n, algo=algo, precision=prec, out=o)
+            t = time_calls(fn, max(args.steps, 3), warm=max(args.warmup, 1))
+            fn()
+            got = o[torch.as_tensor(rows[n], device=dev)].double().cpu().numpy()
+            err = float(np.linalg.norm(got - refs[n]) / np.linalg.norm(refs[n]))
+            b = 4.0 * I + 4.0 * C * (sum(dims) - dims[n]) + 4.0 * dims[n] * C
+            row = {"n": n, "us": t * 1e6, "tflops": 2.0 * I * C / t / 1e12, "roofline_frac": (b / hbm_peak / 1e9) / t,
+                   "rel_err_sampled_rows": err, "within_1e-5": err <= 1e-5}
+            if prec == "fp32":
+                row["ffma_frac"] = 2.0 * I * C / t / 1e12 / ffma
+            modes.append(row)
+        out.append({"algo": algo, "precision": prec, "modes": modes})
+    clocks = sampler.stop()
+    print(json.dumps({"workload": "cube512-forms: 512^3 FP32 N(0,1), rank C=32, factors N(0,1)/sqrt(32); "
+                      "every algorithm x precision form, per mode", "hbm_peak_gbs": hbm_peak, "ffma_peak_tflops": ffma,
+                      "forms": out, "clocks": clocks}), flush=True)
+    return 0
+
+
 def main():
+    global ARGS
     args = parse()
+    ARGS = args
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -520,6 +586,8 @@ def main():
         return run_krp(args, mtk, torch, dev, hbm_peak)
     if args.workload == "corr4-sym":
         return run_sym(args, mtk, torch, dev, hbm_peak)
+    if args.workload == "cube512-forms":
+        return run_forms(args, mtk, torch, dev, hbm_peak)
     X, dims, U, desc = workload(args.workload)
     N = len(dims)
     C = U[0].shape[1]
@@ -544,7 +612,8 @@ def main():
             print(json.dumps({"kernel_only": True, "workload": desc, "precision": prec, "tree_partials": True,
                               "us": [[n, round(t, 1)] for n, t in ts]}), flush=True)
             return 0
-        for n in range(N):
+        modes = [int(v) for v in args.modes.split(",")] if args.modes else range(N)
+        for n in modes:
             if Xs is not None:
                 fn = lambda: mtk.mttkrp(Xd, dims, U0, n, Xs=Xs)
             else:

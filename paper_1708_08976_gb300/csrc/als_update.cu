@@ -23,17 +23,19 @@
 //  - W = L^{-1} by column elimination (C - 1 steps of independent FMAs, one barrier
 //    each), then H^{-1} = W^T D^{-1} W, all in FP64.  H^{-1} is kept in shared memory as
 //    pairs of FP32 numbers (hi + lo, 48 significant bits).
-//  - After M arrives, each row is U_n(i, :) = M(i, :) H^{-1}: every product of an FP32
-//    entry of M and an FP32 half of H^{-1} formed exactly, the C of them summed in
-//    double-FP32 (about 2^-44 relative), then rounded to FP32 (one warp per row, one
-//    column per lane).
-//  - Every CTA factors H itself (all of them obtain bitwise the same factor and inverse),
-//    so the update needs no second launch.
+//  - H^{-1} comes from als_factor_kernel (one CTA), launched ahead of the mode's MTTKRP
+//    contraction, which it overlaps on an SM the contraction leaves free.  After M
+//    arrives, each row is U_n(i, :) = M(i, :) H^{-1}: every product of an FP32 entry of
+//    M and an FP32 half of H^{-1} formed exactly, the C of them summed in double-FP32
+//    (about 2^-44 relative), then rounded to FP32 (one warp per row, one column per lane).
+//  - Without that kernel (MTTKRPs on the FP32 tensor), every CTA of the update factors H
+//    itself (all of them obtain bitwise the same factor) before griddepcontrol.wait, and
+//    solves each row by L y = m, z = D^{-1} y, L^T u = z in FP64.
 //  - The Gram of the new U_n runs on the FP32 pipe in double-FP32 arithmetic: exact
 //    products (p = a*b, q = fma(a, b, -p)) and two-sum accumulation (Knuth, TAOCP vol. 2,
 //    4.2.2; Dekker 1971), about 2^-44 relative.  The per-CTA partials are added in a
-//    fixed order by a two-level ticket reduction (groups of 8 CTAs, then the groups) and
-//    rounded once to FP64, so results do not depend on scheduling; the last CTA writes
+//    fixed order by a ticket reduction (the last CTA adds all partials when there are at
+//    most 32, else groups of 8 CTAs and then the groups) and rounded once to FP64, so results do not depend on scheduling; the last CTA writes
 //    G_n, which the next mode's update reads as it is.
 #include <string.h>
 

@@ -435,11 +435,31 @@ mtk_opts fallback_opts(const mtk_opts& o) {
     return f;
 }
 
+PlanesPlan partial_plan(const int64_t* dims, int N, int C, int n, int right, const mtk_opts& o, int reserve = 0);
+int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int n,
+                      int right, float* T, void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s,
+                      const FactorHook* hook = nullptr, int reserve = 0);
+
+// Mode 1 whose head (U_0 alone) fills few of its 64-k stages, e.g. I_0 = 30 (32 rows in
+// 64): the MTTKRP is then taken as Algorithm 4's two steps, the contraction over the
+// modes >= 2 on the view (1, I_0 I_1, I^R) (mode-0-like tiles over I_0 I_1 rows, whose
+// head is a prefix of U_2, U_3, ...) and a multi-TTV with U_0.  The tensor is read once
+// either way; the partial is I_0 I_1 C floats.
+bool mode1_two_step(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve) {
+    if (n != 1 || N < 3) return false;
+    const PlanesPlan pl = planes_for(dims, N, C, n, o, reserve);
+    if (!pl.ok || pl.H * 5 >= (int64_t)pl.spr * 64 * 3) return false;      // >= 3/5 of the stages' k used
+    return partial_plan(dims, N, C, 1, 1, o, reserve).ok;
+}
+
 // workspace of one MTTKRP on the planes: the planes kernel's scratch when it takes the
 // shape, else that of the FP32-tensor path it falls back to
 size_t split_mttkrp_bytes(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve = 0) {
     const PlanesPlan pl = planes_for(dims, N, C, n, o, reserve);
     if (!pl.ok) return mttkrp_layout(dims, N, C, n, fallback_opts(o)).total;
+    if (mode1_two_step(dims, N, C, n, o, reserve))
+        return align256(align256(kStatusBytes) + align256((size_t)dims[0] * dims[1] * C * sizeof(float)) +
+                        planes_scratch_bytes(partial_plan(dims, N, C, 1, 1, o, reserve)));
     return align256(align256(kStatusBytes) + planes_scratch_bytes(pl));
 }
 
@@ -456,6 +476,17 @@ int do_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, 
         return do_mttkrp(X, dims, N, U, C, n, M, ws, ws_bytes, status, fallback_opts(o), s);
     }
     if (ws_bytes < split_mttkrp_bytes(dims, N, C, n, o, reserve)) return MTK_EWORKSPACE;
+    if (mode1_two_step(dims, N, C, n, o, reserve)) {
+        // T(i0, i1, c) over modes >= 2, then M_1(i1, c) = sum_i0 T(i0, i1, c) U_0(i0, c)
+        Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+        float* T = static_cast<float*>(cv.take((size_t)dims[0] * dims[1] * C * sizeof(float)));
+        char* inner = static_cast<char*>(cv.take(0)) - kStatusBytes;     // scratch follows T
+        const int st = run_partial_split(Xs, dims, N, U, C, 1, 1, T, inner, status, o, s, hook, reserve);
+        if (st) return st;
+        if (hooked) *hooked = hook != nullptr;
+        if (launch_multi_ttv(T, dims[0], dims[1], 1, U[0], C, 1, M, s) != cudaSuccess) return MTK_ECUDA;
+        return MTK_OK;
+    }
     int64_t pd[MTK_MAXN];
     planes_dims(dims, N, pd);
     const View v = mode_view(pd, N, n);
@@ -499,7 +530,7 @@ bool tree_shape(const int64_t* dims, int N, int C) { return (N == 3 || N == 4) &
 // is formed on chip from the factors, as in a per-mode MTTKRP.
 bool partial_sides_ok(int N, int n, int right) { return right ? n < N - 1 : n > 0; }
 
-PlanesPlan partial_plan(const int64_t* dims, int N, int C, int n, int right, const mtk_opts& o, int reserve = 0) {
+PlanesPlan partial_plan(const int64_t* dims, int N, int C, int n, int right, const mtk_opts& o, int reserve) {
     int64_t pd[MTK_MAXN];
     planes_dims(dims, N, pd);
     const View v = mode_view(pd, N, n);
@@ -531,7 +562,7 @@ size_t tree_scratch(const int64_t* dims, int N, int C, const mtk_opts& o, int re
 // ws: status (unused) then the planes scratch; T: rows x C, C slowest
 int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* const* U, int C, int n,
                       int right, float* T, void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s,
-                      const FactorHook* hook = nullptr, int reserve = 0) {
+                      const FactorHook* hook, int reserve) {
     const PlanesPlan pl = partial_plan(dims, N, C, n, right, o, reserve);
     if (!pl.ok) return MTK_EUNSUPPORTED;
     int64_t pd[MTK_MAXN];

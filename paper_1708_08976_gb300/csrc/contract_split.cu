@@ -1336,36 +1336,32 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     }
     if (mn) pl.ntc = pl.ntiles;
     pl.stot = ((pl.nruns + pl.U - 1) / pl.U) * pl.spr;
-    // CTAs per tile, proportional to the rows each tile reads; at least 4 stages each
+    // Work split.  A stage costs a fixed ~750 cycles besides its bytes, so a ragged last
+    // tile (fewer rows, the same stages) costs nearly as much as a full one: the stages,
+    // not the rows, are shared out.
     const int T = pl.ntiles;
     int64_t smax = pl.stot / 4;
     if (smax < 1) smax = 1;
-    if (T >= ctas) {
-        // more tiles than CTAs (a tall view such as a partial MTTKRP): stream-K.  CTA c takes
-        // the stages [c tot / G, (c + 1) tot / G) of the flattened (tile, stage) space (tot =
-        // T stot, G = ctas), so every CTA has the same work to within one stage; it runs the
-        // tiles its range touches back to back with the rings and TMEM kept live.  A tile
-        // that one CTA covers whole goes straight to the output; the pieces of a tile split
-        // between CTAs are partial slabs, at most ceil(stot / (tot / G)) + 1 of them.
+    int64_t G = ctas;
+    if (T >= 2) {
+        // stream-K.  CTA c takes the stages [c tot / G, (c + 1) tot / G) of the flattened
+        // (tile, stage) space (tot = T stot, G CTAs of at least 4 stages), so every CTA has
+        // the same number of stages to within one; it runs the tiles its range touches back
+        // to back with the rings and TMEM kept live.  A tile that one CTA covers whole goes
+        // straight to the output; the pieces of a tile split between CTAs are partial slabs,
+        // at most ceil(stot / (tot / G)) + 1 of them.
         const int64_t tot = (int64_t)T * pl.stot;
-        const int64_t per = tot / ctas;
+        if (G > tot / 4) G = tot / 4;
+        if (G < 1) G = 1;
+        const int64_t per = tot / G;
         const int64_t kmax = (pl.stot + per - 1) / per + 1;
         pl.sk = 1;
         pl.s_full = pl.s_last = (int)kmax;
-    } else if (T == 1) {
-        pl.s_full = pl.s_last = (int)(ctas < smax ? ctas : smax);
     } else {
-        int64_t sf = (int64_t)ctas * pl.BI / I;
-        if (sf < 1) sf = 1;
-        int64_t sl = ctas - (int64_t)(T - 1) * sf;
-        if (sl < 1) sl = 1;
-        if (sf > smax) sf = smax;
-        if (sl > smax) sl = smax;
-        pl.s_full = (int)sf;
-        pl.s_last = (int)sl;
+        // one tile: its stages split evenly, one slab per CTA
+        pl.s_full = pl.s_last = (int)(ctas < smax ? ctas : smax);
     }
-    pl.grid = (T - 1) * pl.s_full + pl.s_last;          // units; at most ctas CTAs run them
-    if (pl.grid > ctas || pl.sk) pl.grid = ctas;
+    pl.grid = pl.sk ? (int)G : pl.s_full;
     pl.nslab = (pl.s_full > pl.s_last ? pl.s_full : pl.s_last) * pl.U;
     pl.image_bytes = (size_t)pl.nsh * pl.spr * pl.N * 128;
     // table of tail scales Q(q, c) when it is small

@@ -141,3 +141,31 @@ def test_cube32x5_gradient():
     for n in range(5):
         ref = oracle.grad(X64, dims, U64, n)
         assert rel_fro(Ud[n].grad.double().cpu().numpy(), ref) < 1e-5, n
+
+
+def test_corr4_twenty_sweeps(corr):
+    """Twenty CP-ALS sweeps on the full workload, the dimension tree on the planes (the
+    benchmark's form) and the FP32 form, against twenty sweeps of the FP64 oracle from the
+    same start.  The fit after every sweep is compared: the planes' MTTKRP error (2e-6 to
+    5e-6) moves each update by up to cond(H_n) times that, and ALS damps such differences
+    from one sweep to the next, so the fits agree to 1e-5 (bf16x2) and 2e-6 (FP32)."""
+    X, dims, U, Xd, _ = corr
+    X64 = X.astype(np.float64)
+    Uc = [u.astype(np.float64) for u in U]
+    ref_fits = []
+    for _ in range(20):
+        Uc, f = oracle.als_sweep(X64, dims, Uc)
+        ref_fits.append(f)
+    del X64
+    for form, tol in (("planes-tree", 1e-5), ("fp32", 2e-6)):
+        Ud = [torch.from_numpy(u).cuda() for u in U]
+        if form == "planes-tree":
+            als = mtk.ALS(Xd, dims, Ud, presplit=True, algo="two_step")
+        else:
+            als = mtk.ALS(Xd, dims, Ud, precision="fp32")
+        for it in range(20):
+            als.sweep()
+            f = als.fit.item()
+            assert abs(f - ref_fits[it]) < tol, (form, it, f, ref_fits[it])
+        assert als.status() == 0
+    assert ref_fits[-1] >= ref_fits[0] - 1e-12

@@ -390,3 +390,43 @@ def test_partial_split_units_back_to_back(splits):
         assert err < tol, (splits, n, right, err, tol)
         again = mtk.partial_mttkrp_split(Xs, dims, Ud, n, right, splits=splits)
         assert torch.equal(got, again)
+
+
+@pytest.mark.parametrize("dims,C", [((24, 16, 20, 8), 8), ((30, 20, 12, 7), 16), ((13, 31, 9), 10),
+                                    ((8, 6, 5, 4, 3), 5)])
+@pytest.mark.parametrize("algo", ["auto", "fused"])
+def test_mttkrp_all_split(dims, C, algo):
+    """Every mode's MTTKRP with the same factors (mtk_mttkrp_all_split): the dimension tree
+    (N = 3, 4, algo auto) or N planes MTTKRPs, each against the oracle."""
+    X, dims, U = synth.random_case(dims, C, seed=11 * sum(dims) + C)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    Xd = to_dev(X, torch)
+    Ud = factors_dev(U, torch)
+    Xs, _ = mtk.split_tensor(Xd, dims)
+    Ms = mtk.mttkrp_all(Xs, dims, Ud, algo=algo)
+    torch.cuda.synchronize()
+    for n in range(len(dims)):
+        ref = oracle.mttkrp(Xr, dims, Ur, n)
+        err = rel_fro(Ms[n].double().cpu().numpy(), ref)
+        assert err < bf16x2_bound(Xr, dims, Ur, n, ref), (dims, algo, n, err)
+
+
+@pytest.mark.parametrize("dims,C", [((24, 16, 20, 8), 8), ((13, 31, 9), 6)])
+def test_cp_loss_gradient_on_planes(dims, C):
+    """The CP loss and its gradient with the MTTKRPs on the planes (the backward through
+    mttkrp_all: the dimension tree) against the oracle's FP64 gradient.  The factors are
+    random, far from a fixed point, so the gradient U_n H_n - M_n does not cancel: it
+    carries the MTTKRP's bf16x2 error, held to 2e-5."""
+    X, dims, U = synth.random_case(dims, C, seed=5 * sum(dims) + C)
+    Xr = X.astype(np.float32).astype(np.float64)
+    Ur = f32_round(U)
+    Xd = to_dev(X, torch)
+    Xs, _ = mtk.split_tensor(Xd, dims)
+    Ud = [u.requires_grad_(True) for u in factors_dev(U, torch)]
+    loss = mtk.cp_loss(Xd, dims, Ud, Xs=Xs)
+    loss.backward()
+    np.testing.assert_allclose(loss.item(), oracle.loss_explicit(Xr, dims, Ur), rtol=2e-5)
+    for n in range(len(dims)):
+        ref = oracle.grad(Xr, dims, Ur, n)
+        assert rel_fro(Ud[n].grad.double().cpu().numpy(), ref) < 2e-5, n
