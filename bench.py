@@ -39,13 +39,14 @@ METRIC = "Dense MTTKRP TFLOP/s & roofline %, mixed-precision vs FP32 at stated r
 
 # DRAM bytes (read + write) per launch of the planes contraction on the full
 # 200x200x300x40 workload, from ncu dram__bytes_read.sum + dram__bytes_write.sum on the
-# 200x200x30x40 case: reads scaled by the 10x larger tensor; writes are the partial slabs
-# that the full-size plan writes (rows x C x 4 B per unit).
-#   tree: mean of the two partials (n = 1 right: 192.49 MB read, 6 slabs of 4.0 MB
-#         written at full size; n = 2 left: 206.89 MB read, 3.85 MB written) -> 1.9489e9
-#         and 2.0727e9 per full launch.
-#   planes (per-mode MTTKRPs): None, not captured since the last change to the kernel.
-NCU_TRAFFIC_PER_LAUNCH = {"planes": None, "tree": 2.0108e9}
+# 200x200x30x40 case (the same plan shapes, a tensor 10x smaller): reads scaled by 10;
+# writes (the output and the partial slabs of tiles split between CTAs, a few MB) taken
+# as measured.
+#   tree: mean of the two partials (n = 1 right: 193.11 MB read, 3.83 MB written;
+#         n = 2 left: 204.50 MB read, 0.52 MB written) -> 1.9349e9 and 2.0455e9 per
+#         full launch, 1.006x and 1.065x their algorithmic bytes.
+#   planes (per-mode MTTKRPs): None (the bench's dominant kernel is the tree's).
+NCU_TRAFFIC_PER_LAUNCH = {"planes": None, "tree": 1.9902e9}
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -57,7 +58,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="corr4",
                     choices=["corr4", "cube512", "corr4-small", "corr4-mid", "paper-synth", "krp", "corr4-sym",
-                             "dims", "cube512-forms"],
+                             "dims", "cube512-forms", "cube32x5-grad"],
                     help="paper-synth: the paper's equal-dimension tensors (N = 3..6, ~7.3e8 entries, "
                          "C = 25), every mode's MTTKRP timed and checked on sampled rows; krp: the "
                          "Khatri-Rao product with and without reuse (Z = 2..4, ~2e7 rows, C = 25, 50); "
@@ -563,6 +564,61 @@ def run_forms(args, mtk, torch, dev, hbm_peak):
     return 0
 
 
+def run_grad(args, mtk, torch, dev, hbm_peak):
+    """The CP loss and its gradient on 32^5 (rank-16 CP plus noise, C = 16): forward (the
+    mode-4 MTTKRP, the Grams, the loss) and hand-written backward (every mode's MTTKRP and
+    U_n H_n - M_n) through torch.autograd, timed with CUDA events over back-to-back steps.
+    Forms: on the planes with the backward's MTTKRPs from the dimension tree (two passes
+    over the tensor), on the planes one MTTKRP per mode, and on the FP32 tensor (FP32 and
+    bf16x2).  The flops counted are the definition's, (N + 1) x 2 I C per step; the
+    roofline is the HBM time of (N + 1) passes over the 4-byte tensor (the definition), and
+    of 3 passes for the tree form (what it reads).  Each form's gradient is checked against
+    the FP64 oracle's at mode 0."""
+    import oracle
+    X, dims, U = synth.cube32x5()
+    N, C, I = len(dims), U[0].shape[1], X.size
+    Xd = torch.from_numpy(X).to(dev)
+    Xs, _ = mtk.split_tensor(Xd, dims)
+    ref0 = oracle.grad(X.astype(np.float64), dims, [u.astype(np.float64) for u in U], 0)
+    forms = {"planes-tree": {"Xs": Xs}, "planes-per-mode": {"Xs": Xs, "algo": "fused"},
+             "fp32": {"precision": "fp32"}, "bf16x2": {"precision": "bf16x2"}}
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    out = {}
+    for name, opts in forms.items():
+        Ud = [torch.from_numpy(u).to(dev).requires_grad_(True) for u in U]
+
+        def step():
+            for u in Ud:
+                u.grad = None
+            mtk.cp_loss(Xd, dims, Ud, **opts).backward()
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(args.steps, 5)
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3 / reps
+        step()
+        err = float(np.linalg.norm(Ud[0].grad.double().cpu().numpy() - ref0) / np.linalg.norm(ref0))
+        passes = 3 if name == "planes-tree" else N + 1
+        out[name] = {"ms_per_step": t * 1e3, "tflops": (N + 1) * 2.0 * I * C / t / 1e12,
+                     "tensor_passes": passes,
+                     "roofline_frac_definition": ((N + 1) * 4.0 * I / hbm_peak / 1e9) / t,
+                     "roofline_frac_read": (passes * 4.0 * I / hbm_peak / 1e9) / t,
+                     "grad_rel_err_mode0": err}
+    clocks = sampler.stop()
+    print(json.dumps({"workload": "cube32x5-grad: 32^5 FP32 rank-16 CP plus N(0,0.01^2), C=16; CP loss forward + "
+                      "hand-written backward (all-mode MTTKRP) per step", "hbm_peak_gbs": hbm_peak,
+                      "forms": out, "clocks": clocks}), flush=True)
+    return 0
+
+
 def main():
     global ARGS
     args = parse()
@@ -588,6 +644,8 @@ def main():
         return run_sym(args, mtk, torch, dev, hbm_peak)
     if args.workload == "cube512-forms":
         return run_forms(args, mtk, torch, dev, hbm_peak)
+    if args.workload == "cube32x5-grad":
+        return run_grad(args, mtk, torch, dev, hbm_peak)
     X, dims, U, desc = workload(args.workload)
     N = len(dims)
     C = U[0].shape[1]

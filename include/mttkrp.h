@@ -186,11 +186,12 @@ int mtk_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N,
 
 /* Every mode's MTTKRP with the same factors, on the planes (the gradient of the CP loss,
  * Section 2.2, needs all N of them).  M[n] (device, I_n x C row-major) receives the
- * mode-n MTTKRP for n = 0..N-1.  For N = 3, 4 and opts->algo AUTO or TWO_STEP this runs
- * the dimension tree of Algorithm 4: the partial contraction over modes >= 2 (one pass over
- * the tensor) and multi-TTVs give M[0] and M[1]; the contraction over modes 0, 1 (N = 4) or
- * the mode-2 MTTKRP (N = 3) gives the rest, so the tensor is read twice instead of N
- * times.  FUSED, or other N: N planes MTTKRPs.  Xs: from mtk_split_tensor; every mode must
+ * mode-n MTTKRP for n = 0..N-1.  With opts->algo AUTO or TWO_STEP this runs the dimension
+ * tree of Algorithm 4: the partial contraction over modes >= 2 (one pass over the tensor)
+ * and multi-TTVs give M[0] and M[1]; the contraction over modes 0, 1 (N >= 4; for N >= 5
+ * while 4 C <= I_0 I_1) or the mode-2 MTTKRP (N = 3) gives the rest, through multi-TTVs
+ * or one-mode contractions of that partial, so the tensor is read twice instead of N
+ * times.  FUSED, or shapes outside those: N planes MTTKRPs.  Xs: from mtk_split_tensor; every mode must
  * be one the planes kernel takes (else MTK_EUNSUPPORTED and a workspace query of 0).
  * opts: precision AUTO or BF16X2; algo AUTO, FUSED or TWO_STEP.  ws: at least
  * mtk_mttkrp_all_split_workspace(...) bytes. */

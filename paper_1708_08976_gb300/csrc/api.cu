@@ -440,15 +440,21 @@ int run_partial_split(const void* Xs, const int64_t* dims, int N, const float* c
                       int right, float* T, void* ws, uint32_t* status, const mtk_opts& o, cudaStream_t s,
                       const FactorHook* hook = nullptr, int reserve = 0);
 
-// Mode 1 whose head (U_0 alone) fills few of its 64-k stages, e.g. I_0 = 30 (32 rows in
-// 64): the MTTKRP is then taken as Algorithm 4's two steps, the contraction over the
-// modes >= 2 on the view (1, I_0 I_1, I^R) (mode-0-like tiles over I_0 I_1 rows, whose
-// head is a prefix of U_2, U_3, ...) and a multi-TTV with U_0.  The tensor is read once
-// either way; the partial is I_0 I_1 C floats.
-bool mode1_two_step(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve) {
-    if (n != 1 || N < 3) return false;
-    const PlanesPlan pl = planes_for(dims, N, C, n, o, reserve);
-    if (!pl.ok || pl.H * 5 >= (int64_t)pl.spr * 64 * 3) return false;      // >= 3/5 of the stages' k used
+// Modes 0 and 1 whose stages would be poorly filled are taken as Algorithm 4's two steps:
+// the contraction over the modes >= 2 on the view (1, I_0 I_1, I^R) (mode-0-like tiles over
+// I_0 I_1 rows, whose head is a prefix of U_2, U_3, ...) and a multi-TTV with U_1 (mode
+// 0) or U_0 (mode 1).  The tensor is read once either way; the partial is I_0 I_1 C floats.
+//  - mode 0 with I_0 <= 32 (after padding): its 64-row boxes would be half empty;
+//  - mode 1 whose head (U_0 alone) uses under 3/5 of its 64-k stages (I_0 = 30: 32 rows in
+//    64).  A stage costs a fixed ~750 cycles besides its bytes.
+bool two_step_right(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve) {
+    if (n > 1 || N < 3) return false;
+    if (n == 0) {
+        if (planes_rows0(dims[0]) > 32) return false;
+    } else {
+        const PlanesPlan pl = planes_for(dims, N, C, n, o, reserve);
+        if (!pl.ok || pl.H * 5 >= (int64_t)pl.spr * 64 * 3) return false;
+    }
     return partial_plan(dims, N, C, 1, 1, o, reserve).ok;
 }
 
@@ -457,7 +463,7 @@ bool mode1_two_step(const int64_t* dims, int N, int C, int n, const mtk_opts& o,
 size_t split_mttkrp_bytes(const int64_t* dims, int N, int C, int n, const mtk_opts& o, int reserve = 0) {
     const PlanesPlan pl = planes_for(dims, N, C, n, o, reserve);
     if (!pl.ok) return mttkrp_layout(dims, N, C, n, fallback_opts(o)).total;
-    if (mode1_two_step(dims, N, C, n, o, reserve))
+    if (two_step_right(dims, N, C, n, o, reserve))
         return align256(align256(kStatusBytes) + align256((size_t)dims[0] * dims[1] * C * sizeof(float)) +
                         planes_scratch_bytes(partial_plan(dims, N, C, 1, 1, o, reserve)));
     return align256(align256(kStatusBytes) + planes_scratch_bytes(pl));
@@ -476,15 +482,18 @@ int do_mttkrp_split(const void* Xs, const float* X, const int64_t* dims, int N, 
         return do_mttkrp(X, dims, N, U, C, n, M, ws, ws_bytes, status, fallback_opts(o), s);
     }
     if (ws_bytes < split_mttkrp_bytes(dims, N, C, n, o, reserve)) return MTK_EWORKSPACE;
-    if (mode1_two_step(dims, N, C, n, o, reserve)) {
-        // T(i0, i1, c) over modes >= 2, then M_1(i1, c) = sum_i0 T(i0, i1, c) U_0(i0, c)
+    if (two_step_right(dims, N, C, n, o, reserve)) {
+        // T(i0, i1, c) over modes >= 2, then M_0(i0, c) = sum_i1 T(i0, i1, c) U_1(i1, c) or
+        // M_1(i1, c) = sum_i0 T(i0, i1, c) U_0(i0, c)
         Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
         float* T = static_cast<float*>(cv.take((size_t)dims[0] * dims[1] * C * sizeof(float)));
         char* inner = static_cast<char*>(cv.take(0)) - kStatusBytes;     // scratch follows T
         const int st = run_partial_split(Xs, dims, N, U, C, 1, 1, T, inner, status, o, s, hook, reserve);
         if (st) return st;
         if (hooked) *hooked = hook != nullptr;
-        if (launch_multi_ttv(T, dims[0], dims[1], 1, U[0], C, 1, M, s) != cudaSuccess) return MTK_ECUDA;
+        const cudaError_t e = n == 0 ? launch_multi_ttv(T, 1, dims[0], dims[1], U[1], C, 0, M, s)
+                                     : launch_multi_ttv(T, dims[0], dims[1], 1, U[0], C, 1, M, s);
+        if (e != cudaSuccess) return MTK_ECUDA;
         return MTK_OK;
     }
     int64_t pd[MTK_MAXN];
@@ -814,17 +823,35 @@ int mtk_partial_mttkrp_split(const void* Xs, const int64_t* dims, int N, const f
 
 // ---- every mode's MTTKRP with the same factors (the gradient of the CP loss) ----------------
 namespace {
-// the dimension tree takes N = 3, 4 with both partials on the planes kernel; the
-// workspace: status, the partials T_R (I_0 I_1 C) and T_L (I_2 I_3 C, N = 4), then the
-// larger of the partial contractions' scratch and (N = 3) the mode-2 MTTKRP's
+// The dimension tree: the right partial T_R (modes 0, 1 kept) serves modes 0 and 1; for
+// N = 3 mode 2 is one planes MTTKRP; for N >= 4 the left partial T_L (modes 0, 1
+// contracted, modes 2..N-1 kept: prod_{k>=2} I_k C floats) serves the others, through
+// multi-TTVs (N = 4) or one-mode contractions of T_L (N >= 5, while T_L is at most a
+// quarter of the tensor's entries).  Workspace: status, T_R and T_L, two buffers of T_L's
+// size (N >= 5), then the larger of the partial contractions' scratch and (N = 3) the
+// mode-2 MTTKRP's.
+int64_t tree_rest(const int64_t* dims, int N) {
+    int64_t r = 1;
+    for (int k = 2; k < N; ++k) r *= dims[k];
+    return r;
+}
 bool all_tree(const int64_t* dims, int N, int C, const mtk_opts& o) {
-    return o.algo != MTK_ALGO_FUSED && tree_ok(dims, N, C, o);
+    if (o.algo == MTK_ALGO_FUSED || N < 3 || C > 64) return false;
+    if (N <= 4) return tree_ok(dims, N, C, o);
+    if (!partial_plan(dims, N, C, 1, 1, o).ok || !partial_plan(dims, N, C, 2, 0, o).ok) return false;
+    return (int64_t)C * 4 <= dims[0] * dims[1];
 }
 size_t all_split_bytes(const int64_t* dims, int N, int C, const mtk_opts& o) {
     if (all_tree(dims, N, C, o)) {
         size_t t = (size_t)dims[0] * dims[1] * C * sizeof(float);
-        if (N == 4) t += (size_t)dims[2] * dims[3] * C * sizeof(float);
-        size_t inner = tree_scratch(dims, N, C, o);
+        if (N >= 4) t += (size_t)tree_rest(dims, N) * C * sizeof(float);
+        if (N >= 5) t = align256(t) + 2 * align256((size_t)tree_rest(dims, N) * C * sizeof(float));
+        size_t inner = planes_scratch_bytes(partial_plan(dims, N, C, 1, 1, o));
+        if (N >= 4) {
+            const size_t b = planes_scratch_bytes(partial_plan(dims, N, C, 2, 0, o));
+            if (b > inner) inner = b;
+        }
+        inner = align256(align256(kStatusBytes) + inner);
         if (N == 3) {
             const size_t m2 = split_mttkrp_bytes(dims, N, C, 2, o);
             if (m2 > inner) inner = m2;
@@ -880,9 +907,15 @@ int mtk_mttkrp_all_split(const void* Xs, const int64_t* dims, int N, const float
         return MTK_OK;
     }
     Carve cv{static_cast<char*>(ws), kStatusBytes, ws_bytes};
+    const int64_t rest = tree_rest(dims, N);
     float* TR = static_cast<float*>(cv.take((size_t)dims[0] * dims[1] * C * sizeof(float) +
-                                            (N == 4 ? (size_t)dims[2] * dims[3] * C * sizeof(float) : 0)));
-    float* TL = N == 4 ? TR + (size_t)dims[0] * dims[1] * C : nullptr;
+                                            (N >= 4 ? (size_t)rest * C * sizeof(float) : 0)));
+    float* TL = N >= 4 ? TR + (size_t)dims[0] * dims[1] * C : nullptr;
+    float* buf[2] = {nullptr, nullptr};
+    if (N >= 5) {
+        buf[0] = static_cast<float*>(cv.take((size_t)rest * C * sizeof(float)));
+        buf[1] = static_cast<float*>(cv.take((size_t)rest * C * sizeof(float)));
+    }
     // the inner calls carve their scratch after the status word of this block
     char* inner = static_cast<char*>(cv.take(0)) - kStatusBytes;
     const size_t inner_bytes = ws_bytes - (size_t)(inner - static_cast<char*>(ws));
@@ -893,12 +926,39 @@ int mtk_mttkrp_all_split(const void* Xs, const int64_t* dims, int N, const float
         launch_multi_ttv(TR, dims[0], dims[1], 1, U[0], C, 1, M[1], s) != cudaSuccess)
         return MTK_ECUDA;
     if (N == 3) return do_mttkrp_split(Xs, nullptr, dims, N, U, C, 2, M[2], inner, inner_bytes, status, om, s);
-    // modes 2, 3 from the contraction over modes 0, 1
+    // modes 2.. from the contraction over modes 0, 1
     st = run_tree_partial(Xs, dims, N, U, C, 0, TL, inner, status, om, s, nullptr, 0);
     if (st) return st;
-    if (launch_multi_ttv(TL, 1, dims[2], dims[3], U[3], C, 0, M[2], s) != cudaSuccess ||
-        launch_multi_ttv(TL, dims[2], dims[3], 1, U[2], C, 1, M[3], s) != cudaSuccess)
-        return MTK_ECUDA;
+    if (N == 4) {
+        if (launch_multi_ttv(TL, 1, dims[2], dims[3], U[3], C, 0, M[2], s) != cudaSuccess ||
+            launch_multi_ttv(TL, dims[2], dims[3], 1, U[2], C, 1, M[3], s) != cudaSuccess)
+            return MTK_ECUDA;
+        return MTK_OK;
+    }
+    // N >= 5: for each n >= 2, contract T_L's other modes one at a time (the last mode
+    // other than n, else the first), ping-ponging between two buffers; the last step
+    // writes M_n row-major
+    for (int n = 2; n < N; ++n) {
+        int ms[MTK_MAXN];
+        int nm = 0;
+        for (int k = 2; k < N; ++k) ms[nm++] = k;
+        const float* cur = TL;
+        int b = 0;
+        while (nm > 1) {
+            const int p = ms[nm - 1] != n ? nm - 1 : 0;
+            int64_t A = 1, B = 1;
+            for (int q = 0; q < p; ++q) A *= dims[ms[q]];
+            for (int q = p + 1; q < nm; ++q) B *= dims[ms[q]];
+            const bool last = nm == 2;
+            float* dst = last ? M[n] : buf[b];
+            if (launch_ttv_mode(cur, A, dims[ms[p]], B, U[ms[p]], C, dst, last ? 1 : 0, s) != cudaSuccess)
+                return MTK_ECUDA;
+            for (int q = p; q + 1 < nm; ++q) ms[q] = ms[q + 1];
+            --nm;
+            cur = dst;
+            b ^= 1;
+        }
+    }
     return MTK_OK;
 }
 

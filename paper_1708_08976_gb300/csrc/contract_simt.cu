@@ -33,7 +33,10 @@ constexpr int BI = 64;        // i per CTA tile
 constexpr int CB = 32;        // columns per CTA (a column block)
 constexpr int NKG = 8;        // k-groups per CTA (one warp each)
 constexpr int THREADS = 256;
-constexpr int STAGES = 3;
+#ifndef MTK_SIMT_STAGES
+#define MTK_SIMT_STAGES 5
+#endif
+constexpr int STAGES = MTK_SIMT_STAGES;   // X ring depth: 4 stages (32 KB) in flight per CTA
 constexpr int XPK = BK + 4;   // [i][k] stage: row pitch (floats)
 constexpr int XPM = BI + 4;   // [k][i] stage: row pitch
 constexpr int WP = CB + 4;    // W stage row pitch
@@ -82,7 +85,8 @@ __device__ __forceinline__ float tail_product(const KrpOperand& W, int64_t q, in
 template <bool KM, bool VEC>
 __global__ void __launch_bounds__(THREADS, 2)
 contract_simt_kernel(const __grid_constant__ ContractParams p) {
-    __shared__ SimtSmem sm;
+    extern __shared__ __align__(16) uint8_t simt_smem_raw[];
+    SimtSmem& sm = *reinterpret_cast<SimtSmem*>(simt_smem_raw);
     const int t = threadIdx.x;
     const int cg = t & 1, ig = (t >> 1) & 15, kg = t >> 5;
     const int64_t i0 = (int64_t)blockIdx.x * BI;
@@ -96,35 +100,53 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const KrpOperand& W = p.W;
 
     // uniform trackers of the stage start: (l, r) for X, (d0, q) for W
-    int64_t xl = kb % L, xr = kb / L;            // X issue tracker
+    int64_t xl = kb % L, xr = kb / L;            // X issue tracker (scalar copies)
     int64_t wd = kb % W.rad0, wq = kb / W.rad0;  // W generation tracker
     int64_t qcached = -1;
     const int64_t qtot = p.K / W.rad0;           // number of q values (rows of Q)
+
+    // 16-byte copies: each thread issues two words of four floats per stage at fixed
+    // positions of the stage tile, and keeps their tensor offsets, advancing them by
+    // constants from one stage to the next (no 64-bit products in the loop).
+    //  KM: words (ii, k4) and (ii + 32, k4), ii = t / 8, k4 = t % 8: four k of one row of
+    //      the tensor (I^L % 4 == 0); offset l + I^L i + I^L I_n r, l = xl + 4 k4.
+    //  MN: words (kk, i4) and (kk + 16, i4), kk = t / 16, i4 = t % 16: four consecutive i
+    //      of one k; offset k I_n + i.
+    const int vk = KM ? 4 * (t & 7) : (t >> 4);           // k of the word within the stage
+    const int vi = KM ? (t >> 3) : 4 * (t & 15);          // row of the word within the tile
+    const bool vrow0 = KM ? (i0 + vi < I) : (i0 + vi < I);
+    const bool vrow1 = KM ? (i0 + vi + 32 < I) : vrow0;
+    int64_t vl = 0, voff = 0;                             // KM: the word's l; its tensor offset
+    if (VEC) {
+        if (KM) {
+            vl = xl + vk;
+            int64_t r = xr;
+            while (vl >= L) { vl -= L; ++r; }
+            voff = vl + L * (i0 + vi) + L * I * r;
+        } else {
+            voff = (kb + vk) * I + i0 + vi;
+        }
+    }
+    const int64_t vrow_step = KM ? 32 * L : 16 * I;       // offset of the second word
+    const int64_t vwrap = L * (I - 1);                    // KM: end of row (i, r) -> (i, r + 1)
 
     auto issue_x = [&](int s) {
         float* dst = sm.pipe.xs[s % STAGES];
         const int64_t ks = kb + (int64_t)s * BK;
         if (VEC) {
-            // 512 words of four floats: KM (ii, k4) with the four k in one row of the
-            // tensor (I^L % 4 == 0); else (kk, i4) with four consecutive i
-            for (int e = t; e < BI * BK / 4; e += THREADS) {
-                if (KM) {
-                    const int ii = e >> 3, k4 = e & 7;
-                    const int64_t k = ks + 4 * k4, i = i0 + ii;
-                    const bool valid = (k < ke) && (i < I);
-                    int64_t off = 0;
-                    if (valid) {
-                        int64_t l = xl + 4 * k4, r = xr;
-                        while (l >= L) { l -= L; ++r; }
-                        off = l + L * i + L * I * r;
-                    }
-                    cp_async16(dst + ii * XPK + 4 * k4, p.X + off, valid);
-                } else {
-                    const int kk = e >> 4, i4 = e & 15;
-                    const int64_t k = ks + kk, i = i0 + 4 * i4;
-                    const bool valid = (k < ke) && (i < I);
-                    cp_async16(dst + kk * XPM + 4 * i4, p.X + (valid ? k * I + i : 0), valid);
-                }
+            const bool kval = ks + vk < ke;
+            const bool v0 = kval && vrow0, v1 = kval && vrow1;
+            if (KM) {
+                cp_async16(dst + vi * XPK + vk, p.X + (v0 ? voff : 0), v0);
+                cp_async16(dst + (vi + 32) * XPK + vk, p.X + (v1 ? voff + vrow_step : 0), v1);
+                voff += BK;
+                vl += BK;
+                while (vl >= L) { vl -= L; voff += vwrap; }
+            } else {
+                const bool v2 = ks + vk + 16 < ke && vrow0;
+                cp_async16(dst + vk * XPM + vi, p.X + (v0 ? voff : 0), v0);
+                cp_async16(dst + (vk + 16) * XPM + vi, p.X + (v2 ? voff + vrow_step : 0), v2);
+                voff += (int64_t)BK * I;
             }
         } else {
             for (int e = t; e < BK * BI; e += THREADS) {
@@ -147,7 +169,7 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
             }
         }
         cp_async_commit();
-        if (L > 1) { xl += BK; while (xl >= L) { xl -= L; ++xr; } }
+        if (!VEC && L > 1) { xl += BK; while (xl >= L) { xl -= L; ++xr; } }
     };
 
     // W stage s into ws[s & 1].  Thread t forms column cc = t % 32 of rows kk = t / 32 + 8 m
@@ -160,6 +182,9 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int wc = c0 + wcc;
     float wraw[4];
     float q0 = 1.0f, q1 = 1.0f;
+    // the factor entry of the thread's first row kk = wk0 of the stage, advanced with wd
+    const float* wp0 = W.f0 + (wd + wk0) * C + (wc < C ? wc : 0);
+    const int64_t wwrap = W.rad0 * C;
     auto load_w = [&](int s) {
         const int64_t ks = kb + (int64_t)s * BK;
         if (W.ntail > 0 && wq != qcached) {
@@ -172,9 +197,9 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
             const int kk = wk0 + (THREADS / CB) * m;
             float w = 0.0f;
             if (ks + kk < ke && wc < C) {
-                int64_t d = wd + kk;
-                if (W.ntail > 0 && d >= W.rad0) d -= W.rad0;
-                w = __ldg(W.f0 + d * C + wc);
+                const float* ptr = wp0 + (THREADS / CB) * m * C;
+                if (W.ntail > 0 && wd + kk >= W.rad0) ptr -= wwrap;
+                w = __ldg(ptr);
             }
             wraw[m] = w;
         }
@@ -191,7 +216,8 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     };
     auto advance_w = [&]() {
         wd += BK;
-        while (wd >= W.rad0) { wd -= W.rad0; ++wq; }
+        wp0 += BK * C;
+        while (wd >= W.rad0) { wd -= W.rad0; ++wq; wp0 -= wwrap; }
     };
 
     float acc[4][16];
@@ -314,15 +340,18 @@ cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_ti
     dim3 grid(i_tiles, p.S, c_blocks);
     const bool km = p.L > 1;
     const bool xa = (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 && p.kchunk % BK == 0;
-    if (km) {
-        if (xa && p.L % 4 == 0) contract_simt_kernel<true, true><<<grid, THREADS, 0, s>>>(p);
-        else contract_simt_kernel<true, false><<<grid, THREADS, 0, s>>>(p);
-    } else {
-        if (xa && p.I % 4 == 0) contract_simt_kernel<false, true><<<grid, THREADS, 0, s>>>(p);
-        else contract_simt_kernel<false, false><<<grid, THREADS, 0, s>>>(p);
-    }
+    const size_t smem = sizeof(SimtSmem);
+    auto go = [&](auto kernel) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, THREADS, smem, s>>>(p);
+        return cudaSuccess;
+    };
+    cudaError_t e;
+    if (km) e = (xa && p.L % 4 == 0) ? go(contract_simt_kernel<true, true>) : go(contract_simt_kernel<true, false>);
+    else e = (xa && p.I % 4 == 0) ? go(contract_simt_kernel<false, true>) : go(contract_simt_kernel<false, false>);
     note_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, float* out,

@@ -112,11 +112,6 @@ struct PsParams {
     int64_t H;              // head rows (the last chunk of a run holds H - 64 (spr - 1) of them)
     int spr;                // stages per run (H padded to a multiple of 64, / 64)
     int U, BI, MT;          // packed runs, rows per run group (tile rows), 128-row MMA tiles
-    int P;                  // K-major: row classes i mod P, P = 8 / gcd(I^L, 8) (1: aligned rows)
-    int64_t Ic;             // rows per class, I / P
-    int ntc;                // tiles per class (ntiles = P * ntc)
-    int64_t L;              // I^L (K-major)
-    int nsh;                // head images: 1, or 8 shifted ones when run starts are not 16-byte aligned
     int box_mode;           // packed runs (U > 1): 0 one TMA box per run group; 1 one box for all U
                             // groups, runs along r (rows grouped by run); 2 one box, runs along lq
                             // (rows interleaved: tile row m = U i + u)
@@ -153,8 +148,8 @@ struct PsParams {
 // is at most one CTA per SM, so a view with more units than that runs them back to back
 // in each CTA with the rings, barriers and TMEM kept from one unit to the next.
 struct PsUnit {
-    int tile, sp, nst, rho;
-    int64_t t0, i0;         // first stage; first row of the tile within its class (rows rho + P (i0 + m))
+    int tile, sp, nst;
+    int64_t t0, i0;         // first stage; first row of the tile
     bool direct;            // the unit is the whole tile: the result goes straight to the output
 };
 
@@ -200,8 +195,7 @@ __device__ __forceinline__ PsUnit ps_unit(const PsParams& p, int b) {
     }
     u.t0 = p.stot * u.sp / S_t;
     u.nst = (int)(p.stot * (u.sp + 1) / S_t - u.t0);
-    u.rho = u.tile / p.ntc;
-    u.i0 = (int64_t)(u.tile - u.rho * p.ntc) * p.BI;
+    u.i0 = (int64_t)u.tile * p.BI;
     u.direct = p.nslab == 1;
     return u;
 }
@@ -217,8 +211,7 @@ __device__ __forceinline__ PsUnit ps_unit_k(const PsParams& p, const PsIter& it,
     u.nst = (int)(b - a);
     u.direct = (a == ts && b == ts + p.stot) && p.U == 1;   // packed runs always leave slabs
     u.sp = (int)((int64_t)blockIdx.x - sk_cta(ts, p.sk_tot, gridDim.x));      // piece of the tile
-    u.rho = u.tile / p.ntc;
-    u.i0 = (int64_t)(u.tile - u.rho * p.ntc) * p.BI;
+    u.i0 = (int64_t)u.tile * p.BI;
     return u;
 }
 
@@ -281,12 +274,10 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             int64_t sr = 0;
             int j = 0;
             int ng = 0;
-            // K-major: group g of the super-run loads rows rho + P (i0 + m) of run q = (lq, r)
-            // as rows y = i0 + m + Ic r of the super-row view, from column x = H lq + I^L rho
-            // + 64 j - delta, delta = (H lq + I^L rho) mod 8 (the image of the stage is the
-            // head shifted by delta, so x is a multiple of 8: a 16-byte aligned start)
+            // K-major: group g of the super-run loads rows i0 + m of run q = (lq, r) as rows
+            // y = i0 + m + I_n r of the (I^L, I_n I^R) row view, from column x = H lq + 64 j
+            // (a multiple of 8: the planes keep every row 16-byte aligned)
             int gx[PS_MAX_U], gy[PS_MAX_U];
-            int rho = 0;
             int64_t i0 = 0;
             auto set_groups = [&]() {
                 ng = 0;
@@ -296,10 +287,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     for (int g = 0; g < ng; ++g) {
                         const uint32_t q = (uint32_t)(sr * U + g);
                         const uint32_t r = q / Lq;
-                        const int64_t base = p.H * (int64_t)(q - r * Lq) + p.L * rho;
-                        const int64_t dlt = p.nsh > 1 ? (base & 7) : 0;
-                        gx[g] = (int)(base - dlt);
-                        gy[g] = (int)(i0 + p.Ic * (int64_t)r);
+                        gx[g] = (int)(p.H * (int64_t)(q - r * Lq));
+                        gy[g] = (int)(i0 + p.I * (int64_t)r);
                     }
                 }
             };
@@ -309,7 +298,6 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             for (int uk = 0; ok && uk < pit.nk; ++uk) {
                 const PsUnit w = ps_unit_k(p, pit, uk);
                 i0 = w.i0;
-                rho = w.rho;
                 sr = w.t0 / spr;
                 j = (int)(w.t0 - sr * spr);
                 set_groups();
@@ -337,10 +325,8 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                             if (MN) {
                                 tma_load_4d_hint(dst, &xmap, 0, 64 * j, q0, pl, fb, pol_a);
                             } else if (p.box_mode == 1) {
-                                // one run per row (q = r): the class offset and its shift
-                                const int64_t base = p.L * rho;
-                                const int x0 = (int)(base - (p.nsh > 1 ? (base & 7) : 0));
-                                tma_load_4d_hint(dst, &xmap, x0 + 64 * j, (int)i0, q0, pl, fb, pol_a);
+                                // one run per row (q = r)
+                                tma_load_4d_hint(dst, &xmap, 64 * j, (int)i0, q0, pl, fb, pol_a);
                             } else {
                                 const int r = q0 / (int)p.Lq;
                                 tma_load_5d_hint(dst, &xmap, 64 * j, q0 - r * (int)p.Lq, (int)i0, r, pl, fb, pol_a);
@@ -401,16 +387,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             const uint64_t pol_b = MTK_PS_L2_HINTS ? policy_evict_last() : policy_evict_normal();
             for (int uk = 0; ok && uk < pit.nk; ++uk) {
                 const PsUnit w = ps_unit_k(p, pit, uk);
-                int64_t sr = w.t0 / spr;
-                int j = (int)(w.t0 - sr * spr);
-                // first slice of the super-run's image: the head shifted by the run's delta
-                // (every packed run of a super-run has the same delta)
-                auto image_base = [&]() -> int64_t {
-                    if (p.nsh == 1) return 0;
-                    const int64_t lq = (sr * U) % p.Lq;
-                    return ((p.H * lq + p.L * w.rho) & 7) * (int64_t)spr;
-                };
-                int64_t ib = image_base();
+                int j = (int)(w.t0 % spr);
                 for (int s = 0; s < w.nst; ++s) {
                     if (issued >= SB && !mbar_wait(smem_u32(&bempty[slot]), ph, &abort_flag, p.wait_ns)) {
                         ok = false;
@@ -419,17 +396,13 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                     const uint32_t fb = smem_u32(&bfull[slot]);
                     mbar_arrive_expect_tx(fb, (uint32_t)p.b_bytes);
                     bulk_copy_g2s_hint(dsm_s + (uint32_t)(p.b_base + slot * p.b_stage),
-                                       p.bimg + (ib + j) * p.b_bytes, (uint32_t)p.b_bytes, fb, pol_b);
+                                       p.bimg + (int64_t)j * p.b_bytes, (uint32_t)p.b_bytes, fb, pol_b);
                     ++issued;
                     if (++slot == SB) {
                         slot = 0;
                         ph ^= 1u;
                     }
-                    if (++j == spr) {
-                        j = 0;
-                        ++sr;
-                        ib = image_base();
-                    }
+                    if (++j == spr) j = 0;
                 }
             }
             if (!ok) {
@@ -457,8 +430,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             const uint32_t idh = p.idesc_hi, idl = p.idesc_lo;
             const uint32_t ncol = (uint32_t)p.N;
             // k-steps of the last chunk of a run that hold head rows (the rest is padding)
-            // (with shifted images the real rows of a chunk depend on the shift: all k-steps)
-            const int64_t tail_rows = p.nsh > 1 ? PS_BK : p.H - (int64_t)PS_BK * (spr - 1);
+            const int64_t tail_rows = p.H - (int64_t)PS_BK * (spr - 1);
             const int kk_last = (int)((tail_rows + 15) / 16);
             int g = 0, gs = 0;                               // accumulation groups (all units)
             int sa = 0, sb = 0, bi = 0;
@@ -571,7 +543,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
             const PsUnit w = ps_unit_k(p, pit, uk);
             const int64_t i0 = w.i0;
             const int nst = w.nst;
-            const int64_t rows_here = (p.Ic - i0) < BI ? (p.Ic - i0) : BI;
+            const int64_t rows_here = (I - i0) < BI ? (I - i0) : BI;
             const bool rowvalid = myg < U && myil < rows_here;
 #pragma unroll
             for (int e = 0; e < 16 * NCH; ++e) {
@@ -680,7 +652,7 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 }
             }
             if (ok && rowvalid) {
-                const int64_t i = w.rho + (int64_t)p.P * (i0 + myil);
+                const int64_t i = i0 + myil;
                 if (w.direct) {
                     int64_t io = i;
                     if (p.opad) {
@@ -724,10 +696,9 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
 }
 
 // ---- per-call preparation: the B image of the head and the table of tail scales ----
-// Image slice (sh, j) (one 64-k stage) is the 128-byte-swizzled K-major shared-memory
-// image of the N = 3 CP rows n = piece * CP + c, row n holding piece `piece` of
-// Hd(64 j - sh + d, c), d = 0..63 (zero outside the head's H rows and for c >= C); shift
-// sh = 0 only, or sh = 0..7 (slices sh * spr + j) when runs start at any element.  Pieces: w0 = bf16_rn(w),
+// Image slice j (one 64-k stage) is the 128-byte-swizzled K-major shared-memory image of
+// the N = 3 CP rows n = piece * CP + c, row n holding piece `piece` of Hd(64 j + d, c),
+// d = 0..63 (zero outside the head's H rows and for c >= C).  Pieces: w0 = bf16_rn(w),
 // w1 = bf16_rn(w - w0), w2 = bf16_rn(w - w0 - w1).  Q(q, c) = prod over the tail
 // factors of their rows at the digits of q (first tail factor fastest), 0 for c >= C.
 struct PrepArgs {
@@ -736,7 +707,6 @@ struct PrepArgs {
     int64_t frad[MTK_MAXN];
     int64_t f0_rows;        // rows of the first factor that exist (the rest are taken as zero)
     int64_t H, Hp;
-    int nsh;
     uint8_t* img;
     int ntail;
     const float* tail[MTK_MAXN];
@@ -753,19 +723,15 @@ __device__ __forceinline__ void split3(float w, __nv_bfloat16& a, __nv_bfloat16&
 }
 
 __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant__ PrepArgs a) {
-    const int64_t octs = a.Hp / 8;                         // octets of one shifted image
-    const int64_t n_img = a.nsh * octs * a.CP;
+    const int64_t n_img = a.Hp / 8 * a.CP;                 // octets of the image x columns
     const int64_t n_q = a.qtab ? a.nruns * a.CP : 0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_img + n_q;
          it += (int64_t)gridDim.x * blockDim.x) {
         if (it < n_img) {
             const int c = (int)(it % a.CP);
-            const int64_t ro = it / a.CP;
-            const int sh = (int)(ro / octs);
-            const int64_t k0 = (ro - (int64_t)sh * octs) * 8;   // first position of this octet
-            const int64_t h0 = k0 - sh;                         // its head row (may be < 0)
+            const int64_t k0 = it / a.CP * 8;                   // first head row of this octet
             int64_t dig[MTK_MAXN];
-            int64_t rem = h0 < 0 ? 0 : h0;
+            int64_t rem = k0;
             for (int z = 0; z < a.head; ++z) {
                 const int64_t nq = rem / a.frad[z];
                 dig[z] = rem - nq * a.frad[z];
@@ -774,21 +740,19 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
             __nv_bfloat16 pc[3][8];
 #pragma unroll
             for (int d = 0; d < 8; ++d) {
-                const int64_t h = h0 + d;
+                const int64_t h = k0 + d;
                 float w = 0.0f;
-                if (h >= 0 && h < a.H && c < a.C && dig[0] < a.f0_rows) {
+                if (h < a.H && c < a.C && dig[0] < a.f0_rows) {
                     w = 1.0f;
                     for (int z = 0; z < a.head; ++z) w *= __ldg(a.fac[z] + dig[z] * a.C + c);
                 }
                 split3(w, pc[0][d], pc[1][d], pc[2][d]);
-                if (h >= 0) {
-                    for (int z = 0; z < a.head; ++z) {       // next row: mixed-radix increment
-                        if (++dig[z] < a.frad[z]) break;
-                        dig[z] = 0;
-                    }
+                for (int z = 0; z < a.head; ++z) {           // next row: mixed-radix increment
+                    if (++dig[z] < a.frad[z]) break;
+                    dig[z] = 0;
                 }
             }
-            const int64_t slice = (int64_t)sh * (a.Hp / PS_BK) + k0 / PS_BK;
+            const int64_t slice = k0 / PS_BK;
             const int oct = (int)((k0 % PS_BK) / 8);
             uint8_t* base = a.img + slice * (int64_t)(a.N * 128);
 #pragma unroll
@@ -831,7 +795,7 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
 // and up to 32 warps, so that enough loads are in flight.
 struct ReduceShape {
     int64_t I;
-    int C, BI, U, ntiles, s_full, s_last, P, ntc;
+    int C, BI, U, ntiles, s_full, s_last;
     int sk;                 // stream-K: slabs of a tile = its pieces (0: a whole-tile unit wrote it)
     int64_t stot, tot, G;
     int64_t opad, oreal, Iout;   // output row map (as in PsParams), output rows
@@ -851,7 +815,7 @@ __device__ __forceinline__ int64_t reduce_out(const ReduceShape& rs, int64_t f, 
 // slabs that hold pieces of output f (0: its tile was written whole, nothing to add)
 __device__ __forceinline__ int reduce_slabs(const ReduceShape& rs, int64_t f, int colmajor) {
     const int64_t i = colmajor ? f % rs.I : f / rs.C;
-    const int64_t tile = (i % rs.P) * rs.ntc + (i / rs.P) / rs.BI;        // row i = rho + P t
+    const int64_t tile = i / rs.BI;
     if (rs.sk) {
         const int64_t np = sk_cta((tile + 1) * rs.stot - 1, rs.tot, rs.G) - sk_cta(tile * rs.stot, rs.tot, rs.G) + 1;
         return (np > 1 || rs.U > 1) ? (int)np * rs.U : 0;
@@ -1203,49 +1167,40 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     if (C < 1 || C > 64 || nfac < 1) return pl;
     const int64_t lim = ((int64_t)1 << 31) - 1;
     const bool mn = (L == 1);
-    // K-major rows (i, r) start at element I^L (i + I_n r).  When I^L is not a multiple of
-    // 8 they are not 16-byte aligned; rows in one class i mod P (P = 8 / gcd(I^L, 8)) are
-    // I^L P elements apart, a multiple of 8, so a class is loaded as rows of the view with
-    // that pitch ("super-rows" of P rows).  That view covers every r-slice alike when P
-    // divides I_n (taken); otherwise not (yet).
-    int P = 1;
+    // TMA loads start on 16-byte boundaries: MN-major boxes at i = multiples of 64 of rows
+    // of I_n elements, K-major rows (i, r) at element I^L (i + I_n r) and runs at H lq
+    // within them.  The planes keep mode 0 padded to a multiple of 8, so I^L (n >= 1) and
+    // every head (a prefix of the factors, U_0 first) are multiples of 8.
     if (mn) {
         if (I % 8 != 0) return pl;
     } else {
-        if (n_left < 1) return pl;
-        P = (L % 8 == 0) ? 1 : (L % 4 == 0) ? 2 : (L % 2 == 0) ? 4 : 8;
-        if (I % P != 0) return pl;
-        if (P * L > lim) return pl;                    // columns of the super-row view are int
+        if (n_left < 1 || L % 8 != 0 || L > lim) return pl;
     }
     int64_t K = 1;
     for (int z = 0; z < nfac; ++z) K *= frad[z];
     pl.CP = (C + 15) & ~15;
     pl.N = 3 * pl.CP;
-    // head: a prefix of the factor list (K-major: within the modes left of n).  A run of
-    // the head starts at an element whose alignment may vary (class offset I^L rho, run
-    // offset H lq): then the image is kept for all 8 shifts, and each stage takes the one
-    // that moves its first element to a 16-byte boundary.  The first prefix with >= 64
-    // rows and <= 1/32 padding, else the least padding, among those whose images stay
-    // L2-resident.  A K-major mode with few rows (I_n / P <= 128) packs several runs per
+    // head: a prefix of the factor list (K-major: within the modes left of n, a multiple
+    // of 8 rows or all of I^L, so that runs start on 16-byte boundaries).  The first prefix
+    // with >= 64 rows and <= 1/32 padding, else the least padding, among those whose images
+    // stay L2-resident.  A K-major mode with few rows (I_n <= 128) packs several runs per
     // tile, runs lq, lq + 1, ... of one row at a stride of H elements: a short head keeps
-    // them within a few KB, so that each stage reads a few contiguous spans instead of
-    // one 128-byte piece of every run, and that is worth up to 1/4 padding (measured on
-    // 200x200x300x40, mode 3: 349 us with H = 200 against 444 us with H = 40,000).  This
-    // holds when the packed runs sit in one box: one image (8-aligned H, no shifts).
+    // them within a few KB, so that each stage reads a few contiguous spans instead of one
+    // 128-byte piece of every run, and that is worth up to 1/4 padding (measured on
+    // 200x200x300x40, mode 3: 349 us with H = 200 against 444 us with H = 40,000).
     const int mmax = mn ? nfac : n_left;
-    const bool near_runs = !mn && I / P <= PS_M;
+    const bool near_runs = !mn && I <= PS_M;
     int best = -1;
     double best_waste = 2.0;
     int64_t prod = 1;
     for (int m = 1; m <= mmax; ++m) {
         prod *= frad[m - 1];
-        const int nsh = (mn || (P == 1 && (L / prod == 1 || prod % 8 == 0))) ? 1 : 8;
-        const int64_t padded = round_up(prod + (nsh > 1 ? 7 : 0), PS_BK);
-        const size_t img = (size_t)nsh * (size_t)(padded / PS_BK) * pl.N * 128;
+        if (!mn && prod % 8 != 0 && L / prod != 1) continue;
+        const int64_t padded = round_up(prod, PS_BK);
+        const size_t img = (size_t)(padded / PS_BK) * pl.N * 128;
         if (img > ((size_t)32 << 20)) break;
         const double waste = (double)(padded - prod) / (double)padded;
-        const int64_t hp = (near_runs && nsh == 1 && P == 1 && prod % 8 == 0 && L / prod > 1)
-                               ? MTK_PS_HEAD_PAD_NEAR : MTK_PS_HEAD_PAD;
+        const int64_t hp = (near_runs && L / prod > 1) ? MTK_PS_HEAD_PAD_NEAR : MTK_PS_HEAD_PAD;
         if (prod >= PS_BK && (padded - prod) * hp <= padded) { best = m; break; }
         if (waste < best_waste) { best_waste = waste; best = m; }
     }
@@ -1255,17 +1210,12 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     pl.head = best;
     pl.H = H;
     pl.Lq = mn ? 1 : L / H;
-    pl.nsh = (mn || (P == 1 && (pl.Lq == 1 || H % 8 == 0))) ? 1 : 8;
-    pl.spr = (int)(round_up(H + (pl.nsh > 1 ? 7 : 0), PS_BK) / PS_BK);
+    pl.spr = (int)(round_up(H, PS_BK) / PS_BK);
     pl.nruns = K / H;
-    pl.P = P;
-    pl.Ic = I / P;
-    if (H > lim || pl.nruns > lim || I > lim || (!mn && (K / L) > lim) || (!mn && pl.Ic * (K / L) > lim)) return pl;
+    if (H > lim || pl.nruns > lim || I > lim || (!mn && (K / L) > lim) || (!mn && I * (K / L) > lim)) return pl;
     pl.mn = mn ? 1 : 0;
-    // packed runs share the stage's image: with shifted images only when every run of a
-    // class has the same shift (I^L rho mod 8: one run per class row, or H a multiple of 8)
-    const int64_t maxU = (pl.nsh > 1 && !(pl.Lq == 1 || H % 8 == 0)) ? 1 : pl.nruns;
-    const int64_t Ic = pl.Ic;
+    const int64_t maxU = pl.nruns;
+    const int64_t Ic = I;
     // Rows of a CTA tile: up to 256 (two 128-row MMA tiles).  Each stage has a fixed cost
     // besides its bytes, so the tiling carries as many rows per stage as it can: BI rows of
     // i per run group and, when BI <= 128, U run groups of the head (different runs q,
@@ -1312,29 +1262,25 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
             }
         }
         // packed runs in one TMA box when they lie at one stride: consecutive r (one run per
-        // row) or consecutive lq of the same r (a head of a multiple of 8 rows, U dividing
-        // the runs per row; U is lowered to a divisor when that keeps at least half of it)
+        // row) or consecutive lq of the same r (U dividing the runs per row; U is lowered to
+        // a divisor when that keeps at least half of it)
         if (best_u > 1 && pl.Lq == 1) {
             pl.box_mode = 1;
-        } else if (best_u > 1 && P == 1 && pl.nsh == 1) {
-            if (H % 8 == 0) {
-                int64_t u = best_u;
-                while (u > 1 && pl.Lq % u != 0) --u;
-                if (2 * u >= best_u) {
-                    best_u = u;
-                    best_rows = u * best_bi;
-                    pl.box_mode = 2;
-                }
+        } else if (best_u > 1) {
+            int64_t u = best_u;
+            while (u > 1 && pl.Lq % u != 0) --u;
+            if (2 * u >= best_u) {
+                best_u = u;
+                best_rows = u * best_bi;
+                pl.box_mode = 2;
             }
         }
         pl.BI = (int)best_bi;
         pl.U = (int)best_u;
         if (pl.U > PS_MAX_U) return pl;
         pl.MT = best_rows > PS_M ? 2 : 1;
-        pl.ntc = (int)((Ic + pl.BI - 1) / pl.BI);
-        pl.ntiles = P * pl.ntc;
+        pl.ntiles = (int)((Ic + pl.BI - 1) / pl.BI);
     }
-    if (mn) pl.ntc = pl.ntiles;
     pl.stot = ((pl.nruns + pl.U - 1) / pl.U) * pl.spr;
     // Work split.  A stage costs a fixed ~750 cycles besides its bytes, so a ragged last
     // tile (fewer rows, the same stages) costs nearly as much as a full one: the stages,
@@ -1363,7 +1309,7 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
     }
     pl.grid = pl.sk ? (int)G : pl.s_full;
     pl.nslab = (pl.s_full > pl.s_last ? pl.s_full : pl.s_last) * pl.U;
-    pl.image_bytes = (size_t)pl.nsh * pl.spr * pl.N * 128;
+    pl.image_bytes = (size_t)pl.spr * pl.N * 128;
     // table of tail scales Q(q, c) when it is small
     const size_t qbytes = (size_t)pl.nruns * pl.CP * sizeof(float);
     pl.qtab_bytes = (nfac > best && qbytes <= ((size_t)32 << 20)) ? qbytes : 0;
@@ -1408,7 +1354,6 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     pa.f0_rows = f0_rows > 0 && f0_rows < frad[0] ? f0_rows : frad[0];
     pa.H = pl.H;
     pa.Hp = (int64_t)pl.spr * PS_BK;
-    pa.nsh = pl.nsh;
     pa.img = image;
     pa.ntail = nfac - pl.head;
     for (int z = pl.head; z < nfac; ++z) {
@@ -1418,7 +1363,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     pa.nruns = pl.nruns;
     pa.qtab = qtab;
     {
-        const int64_t items = pl.nsh * (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * pl.CP : 0);
+        const int64_t items = (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * pl.CP : 0);
         int64_t blocks = (items + 255) / 256;
         if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         planes_prep_kernel<<<(int)blocks, 256, 0, s>>>(pa);
@@ -1446,10 +1391,9 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_MN_PROMO),
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else if (pl.box_mode == 1) {
-        // packed runs along r (one run per row): (super-row column, class row, r, plane),
-        // box (64, BI, U)
-        const cuuint64_t dims[4] = {(cuuint64_t)(pl.P * L), (cuuint64_t)pl.Ic, (cuuint64_t)R, 2};
-        const cuuint64_t strides[3] = {(cuuint64_t)(pl.P * L) * 2, (cuuint64_t)L * I * 2, (cuuint64_t)pitch * 2};
+        // packed runs along r (one run per row): (l, i, r, plane), box (64, BI, U)
+        const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)I, (cuuint64_t)R, 2};
+        const cuuint64_t strides[3] = {(cuuint64_t)L * 2, (cuuint64_t)L * I * 2, (cuuint64_t)pitch * 2};
         const cuuint32_t box[4] = {64, (cuuint32_t)pl.BI, (cuuint32_t)pl.U, 1};
         r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(Xs), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
@@ -1464,12 +1408,9 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
-        // K-major: super-rows of P consecutive rows (i, r) (I^L P elements, a multiple of 8),
-        // one column per element of the super-row; both planes
-        const int64_t Sw = pl.P * L;
-        const int64_t Y = (I / pl.P) * R;
-        const cuuint64_t dims[3] = {(cuuint64_t)Sw, (cuuint64_t)Y, 2};
-        const cuuint64_t strides[2] = {(cuuint64_t)Sw * 2, (cuuint64_t)pitch * 2};
+        // K-major: rows (i, r) of I^L elements (a multiple of 8); both planes
+        const cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)(I * R), 2};
+        const cuuint64_t strides[2] = {(cuuint64_t)L * 2, (cuuint64_t)pitch * 2};
         const cuuint32_t box[3] = {64, (cuuint32_t)pl.BI, 1};
         r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(Xs), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo(MTK_PS_KM_PROMO),
@@ -1489,11 +1430,6 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     p.U = pl.U;
     p.BI = pl.BI;
     p.MT = pl.MT;
-    p.P = pl.P;
-    p.Ic = pl.Ic;
-    p.ntc = pl.ntc;
-    p.L = L;
-    p.nsh = pl.nsh;
     p.box_mode = pl.box_mode;
     p.C = C;
     p.CP = pl.CP;
@@ -1586,8 +1522,6 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
         rs.ntiles = pl.ntiles;
         rs.s_full = pl.s_full;
         rs.s_last = pl.s_last;
-        rs.P = pl.P;
-        rs.ntc = pl.ntc;
         rs.sk = pl.sk;
         rs.stot = pl.stot;
         rs.tot = (int64_t)pl.ntiles * pl.stot;

@@ -106,14 +106,13 @@ int split_chunks(int64_t NXp);          // FP64 partials of ||X||^2 written by t
 cudaError_t launch_split_planes(const float* X, int64_t I0, int64_t rest, void* Xs, double* part,
                                 double* normX2, cudaStream_t s);
 // Plan of the planes contraction for view (L, I, R) and the mode's factor list; ok = 0
-// when the shape is not taken (C > 64; MN-major: I_n not a multiple of 8; K-major:
-// P = 8 / gcd(I^L, 8) not dividing I_n, ...).
+// when the shape is not taken (C > 64; MN-major: I_n not a multiple of 8; K-major: I^L
+// not a multiple of 8 (the padded planes always have it); a head image above 32 MB, ...).
 struct PlanesPlan {
     int ok, mn, head, spr, U, BI, MT, CP, N, ntiles, s_full, s_last, nslab, grid;
-    int P, ntc, nsh;          // K-major row classes, tiles per class, head image shifts
     int box_mode;             // packed runs: one TMA box per group (0) or for all (1: along r, 2: along lq)
     int sk;                   // stream-K over the (tile, stage) space (tall views)
-    int64_t H, nruns, Lq, stot, Ic;
+    int64_t H, nruns, Lq, stot;
     size_t image_bytes, qtab_bytes, part_bytes;
 };
 PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int C, int n_left, int ctas);
@@ -167,6 +166,9 @@ cudaError_t launch_krp(const float* const* U, const int64_t* rows, int Z, int C,
                        int reuse, cudaStream_t s);
 cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, const float* Ko,
                              int C, int right, float* M, cudaStream_t s);
+// out(a, b, c) = sum_j T(a, j, b, c) K(j, c), c slowest (out_rowmajor: out[(a + A b) C + c])
+cudaError_t launch_ttv_mode(const float* T, int64_t A, int64_t J, int64_t B, const float* K, int C, float* out,
+                            int out_rowmajor, cudaStream_t s);
 cudaError_t launch_gram(const float* U, int64_t I, int C, double* G, double* part,
                         int nchunks, cudaStream_t s);
 int gram_chunks(int64_t I);

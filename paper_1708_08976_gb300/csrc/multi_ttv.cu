@@ -62,7 +62,40 @@ multi_ttv_left_kernel(const float* __restrict__ T, int64_t I, int64_t R,
     }
 }
 
+// One mode of a C-batched tensor contracted with a factor (the dimension tree beyond
+// N = 4: the modes >= 2 of the left partial): out(a, b, c) = sum_j T(a, j, b, c) K(j, c),
+// T and out in natural order with c slowest; out_rowmajor: out as [a + A b][c] instead.
+// One thread per output, consecutive a in consecutive threads (coalesced when A > 1); the
+// sum over j runs in order.
+__global__ void __launch_bounds__(256)
+ttv_mode_kernel(const float* __restrict__ T, int64_t A, int64_t J, int64_t B,
+                const float* __restrict__ K, int C, float* __restrict__ out, int out_rowmajor) {
+    allow_dependent_launch();
+    const int64_t n = A * B * C;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ab = e % (A * B);
+        const int c = (int)(e / (A * B));
+        const int64_t b = ab / A, a = ab - b * A;
+        const float* t = T + a + A * J * (b + B * (int64_t)c);
+        float s = 0.0f;
+        for (int64_t j = 0; j < J; ++j) s = fmaf(t[A * j], __ldg(K + j * C + c), s);
+        if (out_rowmajor) out[ab * C + c] = s;
+        else out[e] = s;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_ttv_mode(const float* T, int64_t A, int64_t J, int64_t B, const float* K, int C, float* out,
+                            int out_rowmajor, cudaStream_t s) {
+    const int64_t n = A * B * C;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+    if (blocks < 1) blocks = 1;
+    ttv_mode_kernel<<<(int)blocks, 256, 0, s>>>(T, A, J, B, K, C, out, out_rowmajor);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_multi_ttv(const float* T, int64_t L, int64_t I, int64_t R, const float* Ko,
                              int C, int right, float* M, cudaStream_t s) {

@@ -393,11 +393,13 @@ def test_partial_split_units_back_to_back(splits):
 
 
 @pytest.mark.parametrize("dims,C", [((24, 16, 20, 8), 8), ((30, 20, 12, 7), 16), ((13, 31, 9), 10),
-                                    ((8, 6, 5, 4, 3), 5)])
+                                    ((8, 6, 5, 4, 3), 5), ((7, 6, 5, 4, 3, 2), 9), ((12, 10, 9, 8, 7), 33)])
 @pytest.mark.parametrize("algo", ["auto", "fused"])
 def test_mttkrp_all_split(dims, C, algo):
     """Every mode's MTTKRP with the same factors (mtk_mttkrp_all_split): the dimension tree
-    (N = 3, 4, algo auto) or N planes MTTKRPs, each against the oracle."""
+    (algo auto: N = 3, 4, and N = 5, 6 with one-mode contractions of the left partial;
+    C = 33 > I_0 I_1 / 4 keeps N = 5 on per-mode MTTKRPs) or N planes MTTKRPs, each against
+    the oracle."""
     X, dims, U = synth.random_case(dims, C, seed=11 * sum(dims) + C)
     Xr = X.astype(np.float32).astype(np.float64)
     Ur = f32_round(U)
