@@ -67,18 +67,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Q(q, c) = prod over tail factors of tail[t](digit_t(q), c)
-__device__ __forceinline__ float tail_product(const KrpOperand& W, int64_t q, int c, int C) {
-    float p = 1.0f;
-    for (int t = 0; t < W.ntail; ++t) {
-        const int64_t rad = W.tail_rad[t];
-        const int64_t d = q % rad;
-        q /= rad;
-        p *= __ldg(W.tail[t] + d * C + c);
-    }
-    return p;
-}
-
 // KM: X stage [i][k] (I^L > 1); else [k][i] (I^L = 1).  VEC: 16-byte copies (KM: I^L a
 // multiple of 4; else I_n a multiple of 4; the tensor 16-byte aligned, split starts at
 // multiples of BK).
@@ -182,14 +170,39 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int wc = c0 + wcc;
     float wraw[4];
     float q0 = 1.0f, q1 = 1.0f;
+    // digits of q = wq over the tail factors (first fastest), kept by +1 steps: wq moves by
+    // at most one per stage (the head has >= BK rows), so no division in the loop
+    int qd[MTK_MAXN];
+    if (W.ntail > 0) {
+        int64_t rem = wq;
+        for (int z = 0; z < W.ntail; ++z) {
+            qd[z] = (int)(rem % W.tail_rad[z]);
+            rem /= W.tail_rad[z];
+        }
+    }
+    // Q(q, wc) from the digits of wq, or (next) of wq + 1: the digits below the first that
+    // does not wrap are 0, that one is one more, the rest are wq's
+    auto q_from = [&](bool next) -> float {
+        float prod = 1.0f;
+        bool carry = next;
+        for (int z = 0; z < W.ntail; ++z) {
+            int d = qd[z];
+            if (carry) {
+                if (++d < W.tail_rad[z]) carry = false;
+                else d = 0;
+            }
+            prod *= __ldg(W.tail[z] + (int64_t)d * C + wc);
+        }
+        return prod;
+    };
     // the factor entry of the thread's first row kk = wk0 of the stage, advanced with wd
     const float* wp0 = W.f0 + (wd + wk0) * C + (wc < C ? wc : 0);
     const int64_t wwrap = W.rad0 * C;
     auto load_w = [&](int s) {
         const int64_t ks = kb + (int64_t)s * BK;
         if (W.ntail > 0 && wq != qcached) {
-            q0 = (wc < C && wq < qtot) ? tail_product(W, wq, wc, C) : 0.0f;
-            q1 = (wc < C && wq + 1 < qtot) ? tail_product(W, wq + 1, wc, C) : 0.0f;
+            q0 = (wc < C && wq < qtot) ? q_from(false) : 0.0f;
+            q1 = (wc < C && wq + 1 < qtot) ? q_from(true) : 0.0f;
             qcached = wq;
         }
 #pragma unroll
@@ -217,7 +230,15 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     auto advance_w = [&]() {
         wd += BK;
         wp0 += BK * C;
-        while (wd >= W.rad0) { wd -= W.rad0; ++wq; wp0 -= wwrap; }
+        while (wd >= W.rad0) {
+            wd -= W.rad0;
+            ++wq;
+            wp0 -= wwrap;
+            for (int z = 0; z < W.ntail; ++z) {             // the digits of wq, +1
+                if (++qd[z] < W.tail_rad[z]) break;
+                qd[z] = 0;
+            }
+        }
     };
 
     float acc[4][16];
@@ -225,6 +246,9 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 16; ++b) acc[a][b] = 0.0f;
+    bool arow[4];                        // K-major: row group a has a row of the tensor
+#pragma unroll
+    for (int a = 0; a < 4; ++a) arow[a] = i0 + 16 * a < I;
 
     for (int s = 0; s < STAGES - 1; ++s) {
         if (s < nst) issue_x(s); else cp_async_commit();
@@ -266,16 +290,20 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float* wr = ws + (4 * kg + j) * WP + 16 * cg;
-            float wv[16];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 v = *reinterpret_cast<const float4*>(wr + 4 * q);
-                wv[4 * q] = v.x; wv[4 * q + 1] = v.y; wv[4 * q + 2] = v.z; wv[4 * q + 3] = v.w;
+                const float4 w4 = *reinterpret_cast<const float4*>(wr + 4 * q);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    // K-major rows ig + 16 a: a group beyond the last row of a ragged tile is
+                    // skipped by the whole warp
+                    if (KM && !arow[a]) continue;
+                    acc[a][4 * q] = fmaf(xv[a][j], w4.x, acc[a][4 * q]);
+                    acc[a][4 * q + 1] = fmaf(xv[a][j], w4.y, acc[a][4 * q + 1]);
+                    acc[a][4 * q + 2] = fmaf(xv[a][j], w4.z, acc[a][4 * q + 2]);
+                    acc[a][4 * q + 3] = fmaf(xv[a][j], w4.w, acc[a][4 * q + 3]);
+                }
             }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 16; ++b) acc[a][b] = fmaf(xv[a][j], wv[b], acc[a][b]);
         }
         if (more) store_w(s + 1);
     }

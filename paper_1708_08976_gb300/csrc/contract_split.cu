@@ -108,7 +108,10 @@ struct PsParams {
     int64_t I;              // output rows (I_n)
     int64_t nruns;          // runs of the head along the contraction
     int64_t Lq;             // K-major: runs per r (I^L / H)
-    int64_t stot;           // stages of one tile: ceil(nruns / U) * spr
+    int64_t gpr;            // box mode 2 with U not dividing Lq: packed groups per r (ceil(Lq / U));
+                            // group sr holds runs lq = (sr mod gpr) U + u < Lq of r = sr / gpr.
+                            // 0: group sr holds runs q = sr U + u
+    int64_t stot;           // stages of one tile: (groups of runs) * spr
     int64_t H;              // head rows (the last chunk of a run holds H - 64 (spr - 1) of them)
     int spr;                // stages per run (H padded to a multiple of 64, / 64)
     int U, BI, MT;          // packed runs, rows per run group (tile rows), 128-row MMA tiles
@@ -327,6 +330,11 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                             } else if (p.box_mode == 1) {
                                 // one run per row (q = r)
                                 tma_load_4d_hint(dst, &xmap, 64 * j, (int)i0, q0, pl, fb, pol_a);
+                            } else if (p.gpr) {
+                                // row-local groups: runs beyond the row's last read the zero fill
+                                const int r = (int)(sr / p.gpr);
+                                const int lq0 = (int)(sr - (int64_t)r * p.gpr) * U;
+                                tma_load_5d_hint(dst, &xmap, 64 * j, lq0, (int)i0, r, pl, fb, pol_a);
                             } else {
                                 const int r = q0 / (int)p.Lq;
                                 tma_load_5d_hint(dst, &xmap, 64 * j, q0 - r * (int)p.Lq, (int)i0, r, pl, fb, pol_a);
@@ -564,8 +572,18 @@ contract_planes_kernel(const __grid_constant__ PsParams p, const __grid_constant
                 if (!(gs == PS_GROUP || run_end || s + 1 == nst)) continue;
                 gs = 0;
                 const int b = db;
-                const int64_t q = sr_s * U + myg;
-                const bool live = rowvalid && q < nruns;
+                int64_t q;
+                bool qok;
+                if (p.gpr) {
+                    const int64_t r = sr_s / p.gpr;
+                    const int64_t lq = (sr_s - r * p.gpr) * U + myg;
+                    q = r * p.Lq + lq;
+                    qok = lq < p.Lq;
+                } else {
+                    q = sr_s * U + myg;
+                    qok = q < nruns;
+                }
+                const bool live = rowvalid && qok;
                 if (live && p.ntail > 0 && q != qcached) {
                     // Q(q, c) = prod_z tail_z(digit_z(q), c): one row of the table, or the
                     // product formed here (digits once, then the columns)
@@ -724,7 +742,9 @@ __device__ __forceinline__ void split3(float w, __nv_bfloat16& a, __nv_bfloat16&
 
 __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant__ PrepArgs a) {
     const int64_t n_img = a.Hp / 8 * a.CP;                 // octets of the image x columns
-    const int64_t n_q = a.qtab ? a.nruns * a.CP : 0;
+    // the table: one item per row q and 4 columns (one 16-byte store), q's digits formed
+    // once per item in 32-bit arithmetic (runs and radices below 2^31)
+    const int64_t n_q = a.qtab ? a.nruns * (a.CP / 4) : 0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_img + n_q;
          it += (int64_t)gridDim.x * blockDim.x) {
         if (it < n_img) {
@@ -768,19 +788,24 @@ __global__ void __launch_bounds__(256) planes_prep_kernel(const __grid_constant_
             }
         } else {
             const int64_t e = it - n_img;
-            const int64_t q = e / a.CP;
-            const int c = (int)(e - q * a.CP);
-            float prod = 0.0f;
-            if (c < a.C) {
-                prod = 1.0f;
-                int64_t rem = q;
-                for (int z = 0; z < a.ntail; ++z) {
-                    const int64_t nq = rem / a.tail_rad[z];
-                    prod *= __ldg(a.tail[z] + (rem - nq * a.tail_rad[z]) * a.C + c);
-                    rem = nq;
-                }
+            const int c4 = a.CP / 4;
+            const uint32_t q = (uint32_t)(e / c4);
+            const int c0 = 4 * (int)(e - (int64_t)q * c4);
+            float prod[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+            uint32_t rem = q;
+            for (int z = 0; z < a.ntail; ++z) {
+                const uint32_t rad = (uint32_t)a.tail_rad[z];
+                const uint32_t nq = rem / rad;
+                const float* row = a.tail[z] + (int64_t)(rem - nq * rad) * a.C;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (c0 + j < a.C) prod[j] *= __ldg(row + c0 + j);
+                rem = nq;
             }
-            a.qtab[e] = prod;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (c0 + j >= a.C) prod[j] = 0.0f;
+            *reinterpret_cast<float4*>(a.qtab + (int64_t)q * a.CP + c0) = make_float4(prod[0], prod[1], prod[2], prod[3]);
         }
     }
 }
@@ -1267,9 +1292,20 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
         if (best_u > 1 && pl.Lq == 1) {
             pl.box_mode = 1;
         } else if (best_u > 1) {
+            // U lowered to a divisor of Lq when that keeps at least 7/8 of it; otherwise the
+            // groups are row-local (ceil(Lq / U) per r, the last one partly empty) when
+            // that wastes under 1/8 of the rows
             int64_t u = best_u;
             while (u > 1 && pl.Lq % u != 0) --u;
-            if (2 * u >= best_u) {
+            const int64_t gpr = (pl.Lq + best_u - 1) / best_u;
+            if (8 * u >= 7 * best_u) {
+                best_u = u;
+                best_rows = u * best_bi;
+                pl.box_mode = 2;
+            } else if (8 * (gpr * best_u - pl.Lq) <= gpr * best_u) {
+                pl.box_mode = 2;
+                pl.gpr = gpr;
+            } else if (2 * u >= best_u) {
                 best_u = u;
                 best_rows = u * best_bi;
                 pl.box_mode = 2;
@@ -1281,7 +1317,7 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
         pl.MT = best_rows > PS_M ? 2 : 1;
         pl.ntiles = (int)((Ic + pl.BI - 1) / pl.BI);
     }
-    pl.stot = ((pl.nruns + pl.U - 1) / pl.U) * pl.spr;
+    pl.stot = (pl.gpr ? (pl.nruns / pl.Lq) * pl.gpr : (pl.nruns + pl.U - 1) / pl.U) * pl.spr;
     // Work split.  A stage costs a fixed ~750 cycles besides its bytes, so a ragged last
     // tile (fewer rows, the same stages) costs nearly as much as a full one: the stages,
     // not the rows, are shared out.
@@ -1363,7 +1399,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     pa.nruns = pl.nruns;
     pa.qtab = qtab;
     {
-        const int64_t items = (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * pl.CP : 0);
+        const int64_t items = (pa.Hp / 8) * pl.CP + (qtab ? pl.nruns * (pl.CP / 4) : 0);
         int64_t blocks = (items + 255) / 256;
         if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         planes_prep_kernel<<<(int)blocks, 256, 0, s>>>(pa);
@@ -1424,6 +1460,7 @@ cudaError_t launch_contract_planes(const void* Xs, int64_t pitch, int64_t L, int
     p.I = I;
     p.nruns = pl.nruns;
     p.Lq = pl.Lq;
+    p.gpr = pl.gpr;
     p.stot = pl.stot;
     p.H = pl.H;
     p.spr = pl.spr;

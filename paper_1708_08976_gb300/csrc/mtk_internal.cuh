@@ -113,6 +113,7 @@ struct PlanesPlan {
     int box_mode;             // packed runs: one TMA box per group (0) or for all (1: along r, 2: along lq)
     int sk;                   // stream-K over the (tile, stage) space (tall views)
     int64_t H, nruns, Lq, stot;
+    int64_t gpr;              // box mode 2: packed groups per r when U does not divide Lq (else 0)
     size_t image_bytes, qtab_bytes, part_bytes;
 };
 PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int C, int n_left, int ctas);

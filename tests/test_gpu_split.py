@@ -113,6 +113,8 @@ SHAPES = [
     ((5, 24, 40, 8), 16),         # I_0 = 5 -> 8: heads of mostly padding
     ((30, 30, 30, 4), 12),        # 30 -> 32 with a short head
     ((7, 6, 5, 4, 3, 2), 9),      # N = 6, every mode
+    ((64, 65, 32, 3), 16),        # mode 2: 65 runs per row packed 8 at a time in row-local groups (the
+                                  # last of each row has one run), no divisor of 65 near 8
 ]
 
 
