@@ -141,7 +141,7 @@ ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int split
     pl.tc = ((precision == MTK_PREC_BF16X2 || precision == MTK_PREC_BF16X3) && tc_ok) ? 1 : 0;
     const int BI = pl.tc ? BI_tc : kSimtBI;
     pl.i_tiles = (int)((I + BI - 1) / BI);
-    pl.c_blocks = pl.tc ? 1 : (C + 31) / 32;
+    pl.c_blocks = pl.tc ? 1 : (C + simt_cta_cols(C) - 1) / simt_cta_cols(C);
     const int64_t quantum = pl.tc ? kTcBK : kBK;            // split boundaries: whole stages
     int64_t S = splits;
     if (S <= 0) {

@@ -30,7 +30,7 @@ namespace {
 
 constexpr int BK = 32;        // k per stage
 constexpr int BI = 64;        // i per CTA tile
-constexpr int CB = 32;        // columns per CTA (a column block)
+constexpr int CB = 32;        // W stage slots per row: two groups of 16, the first TC of each used
 constexpr int NKG = 8;        // k-groups per CTA (one warp each)
 constexpr int THREADS = 256;
 #ifndef MTK_SIMT_STAGES
@@ -70,7 +70,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // KM: X stage [i][k] (I^L > 1); else [k][i] (I^L = 1).  VEC: 16-byte copies (KM: I^L a
 // multiple of 4; else I_n a multiple of 4; the tensor 16-byte aligned, split starts at
 // multiples of BK).
-template <bool KM, bool VEC>
+// TC: columns per thread (8, 13 or 16), so a CTA covers 2 TC columns of M: the fewest
+// that hold C (C = 25 in 26 instead of 32).
+template <bool KM, bool VEC, int TC>
 __global__ void __launch_bounds__(THREADS, 2)
 contract_simt_kernel(const __grid_constant__ ContractParams p) {
     extern __shared__ __align__(16) uint8_t simt_smem_raw[];
@@ -79,7 +81,7 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int cg = t & 1, ig = (t >> 1) & 15, kg = t >> 5;
     const int64_t i0 = (int64_t)blockIdx.x * BI;
     const int sp = blockIdx.y;
-    const int c0 = blockIdx.z * CB;
+    const int c0 = blockIdx.z * 2 * TC;
     const int C = p.C;
     const int64_t L = p.L, I = p.I;
     const int64_t kb = (int64_t)sp * p.kchunk;
@@ -160,14 +162,16 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
         if (!VEC && L > 1) { xl += BK; while (xl >= L) { xl -= L; ++xr; } }
     };
 
-    // W stage s into ws[s & 1].  Thread t forms column cc = t % 32 of rows kk = t / 32 + 8 m
+    // W stage s into ws[s & 1].  Thread t forms slot wcc = t % 32 (column group wcc / 16,
+    // column wcc % 16 of it when below TC, else a zero pad) of rows kk = t / 32 + 8 m
     // (m = 0..3).  The factor entries of the next stage are loaded into registers before
     // the current stage's FMAs and multiplied by the tail scale Q(q, cc) and stored after
     // them, so their L2 latency is hidden.  The head has >= BK rows whenever there is a
     // tail, so a stage spans at most two q; the thread keeps Q(q, cc) for the stage's
     // first q and the next in registers, formed again only when q moves.
     const int wcc = t & (CB - 1), wk0 = t / CB;
-    const int wc = c0 + wcc;
+    const int wsj = wcc & 15;
+    const int wc = wsj < TC ? c0 + (wcc >> 4) * TC + wsj : C;     // C: a pad slot (zero)
     float wraw[4];
     float q0 = 1.0f, q1 = 1.0f;
     // digits of q = wq over the tail factors (first fastest), kept by +1 steps: wq moves by
@@ -241,11 +245,11 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
         }
     };
 
-    float acc[4][16];
+    float acc[4][TC];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 16; ++b) acc[a][b] = 0.0f;
+        for (int b = 0; b < TC; ++b) acc[a][b] = 0.0f;
     bool arow[4];                        // K-major: row group a has a row of the tensor
 #pragma unroll
     for (int a = 0; a < 4; ++a) arow[a] = i0 + 16 * a < I;
@@ -291,17 +295,23 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
         for (int j = 0; j < 4; ++j) {
             const float* wr = ws + (4 * kg + j) * WP + 16 * cg;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 w4 = *reinterpret_cast<const float4*>(wr + 4 * q);
+            for (int q = 0; q < (TC + 3) / 4; ++q) {
+                float w[4];
+                if (4 * q + 3 < TC) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(wr + 4 * q);
+                    w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) w[e] = 4 * q + e < TC ? wr[4 * q + e] : 0.0f;
+                }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     // K-major rows ig + 16 a: a group beyond the last row of a ragged tile is
                     // skipped by the whole warp
                     if (KM && !arow[a]) continue;
-                    acc[a][4 * q] = fmaf(xv[a][j], w4.x, acc[a][4 * q]);
-                    acc[a][4 * q + 1] = fmaf(xv[a][j], w4.y, acc[a][4 * q + 1]);
-                    acc[a][4 * q + 2] = fmaf(xv[a][j], w4.z, acc[a][4 * q + 2]);
-                    acc[a][4 * q + 3] = fmaf(xv[a][j], w4.w, acc[a][4 * q + 3]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (4 * q + e < TC) acc[a][4 * q + e] = fmaf(xv[a][j], w[e], acc[a][4 * q + e]);
                 }
             }
         }
@@ -317,19 +327,14 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<float4*>(&sm.red[kg - half][row_of(a)][16 * cg + 4 * q]) =
-                        make_float4(acc[a][4 * q], acc[a][4 * q + 1], acc[a][4 * q + 2], acc[a][4 * q + 3]);
+                for (int b = 0; b < TC; ++b) sm.red[kg - half][row_of(a)][16 * cg + b] = acc[a][b];
         }
         __syncthreads();
         if (kg < half) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 v = *reinterpret_cast<const float4*>(&sm.red[kg][row_of(a)][16 * cg + 4 * q]);
-                    acc[a][4 * q] += v.x; acc[a][4 * q + 1] += v.y; acc[a][4 * q + 2] += v.z; acc[a][4 * q + 3] += v.w;
-                }
+                for (int b = 0; b < TC; ++b) acc[a][b] += sm.red[kg][row_of(a)][16 * cg + b];
         }
         __syncthreads();
     }
@@ -339,8 +344,8 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
             const int64_t i = i0 + row_of(a);
             if (i >= I) continue;
 #pragma unroll
-            for (int b = 0; b < 16; ++b) {
-                const int c = c0 + 16 * cg + b;
+            for (int b = 0; b < TC; ++b) {
+                const int c = c0 + TC * cg + b;
                 if (c >= C) continue;
                 if (p.S == 1) p.out[i * p.out_si + c * p.out_sc] = acc[a][b];
                 else p.part[((int64_t)sp * I + i) * C + c] = acc[a][b];
@@ -363,9 +368,10 @@ __global__ void split_reduce_kernel(const float* __restrict__ part, int S, int64
 
 }  // namespace
 
-cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,
-                                 cudaStream_t s) {
-    dim3 grid(i_tiles, p.S, c_blocks);
+int simt_cta_cols(int C) { return 2 * (C <= 16 ? 8 : C <= 26 ? 13 : 16); }
+
+template <int TC>
+cudaError_t launch_simt_tc(const ContractParams& p, dim3 grid, cudaStream_t s) {
     const bool km = p.L > 1;
     const bool xa = (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 && p.kchunk % BK == 0;
     const size_t smem = sizeof(SimtSmem);
@@ -375,9 +381,18 @@ cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_ti
         kernel<<<grid, THREADS, smem, s>>>(p);
         return cudaSuccess;
     };
-    cudaError_t e;
-    if (km) e = (xa && p.L % 4 == 0) ? go(contract_simt_kernel<true, true>) : go(contract_simt_kernel<true, false>);
-    else e = (xa && p.I % 4 == 0) ? go(contract_simt_kernel<false, true>) : go(contract_simt_kernel<false, false>);
+    if (km) return (xa && p.L % 4 == 0) ? go(contract_simt_kernel<true, true, TC>) : go(contract_simt_kernel<true, false, TC>);
+    return (xa && p.I % 4 == 0) ? go(contract_simt_kernel<false, true, TC>) : go(contract_simt_kernel<false, false, TC>);
+}
+
+cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,
+                                 cudaStream_t s) {
+    dim3 grid(i_tiles, p.S, c_blocks);
+    const int cols = simt_cta_cols(p.C);
+    if (c_blocks * cols < p.C) return cudaErrorInvalidValue;
+    cudaError_t e = cols == 16 ? launch_simt_tc<8>(p, grid, s)
+                  : cols == 26 ? launch_simt_tc<13>(p, grid, s)
+                               : launch_simt_tc<16>(p, grid, s);
     note_launches(1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -65,6 +65,7 @@ int num_sms();
 // ---- launchers (host side), defined in the .cu files -------------------------
 cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,
                                  cudaStream_t s);
+int simt_cta_cols(int C);              // columns of M per CTA of the FP32 kernel (16, 26 or 32)
 cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, float* out,
                                 int64_t si, int64_t sc, cudaStream_t s);
 // Tensor-core contraction plan.  The factor list is split into a head (the first
