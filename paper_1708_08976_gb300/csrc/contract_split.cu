@@ -62,6 +62,11 @@ constexpr int PS_M = 128;                    // MMA M
 #ifndef MTK_PS_HEAD_PAD
 #define MTK_PS_HEAD_PAD 32
 #endif
+// K-major tiling when the fewest i-tiles are under 3/4 full: 0 the most rows per stage
+// (ties: fewer tiles), 1 the fewest stages
+#ifndef MTK_PS_TILE_MODEL
+#define MTK_PS_TILE_MODEL 0
+#endif
 #ifndef MTK_PS_HEAD_PAD_NEAR
 #define MTK_PS_HEAD_PAD_NEAR 4
 #endif
@@ -1271,7 +1276,25 @@ PlanesPlan planes_plan(int64_t L, int64_t I, const int64_t* frad, int nfac, int 
             if (best_u > maxU) best_u = maxU;
         }
         int64_t best_rows = best_u * best_bi;
-        if (best_rows * 4 < 3 * 2 * PS_M) {
+        if (MTK_PS_TILE_MODEL == 1 && best_rows * 4 < 3 * 2 * PS_M) {
+            // the fewest stages: t i-tiles x ceil(runs / u) groups (ties: fewer tiles)
+            int64_t best_st = t0 * ((pl.nruns + best_u - 1) / best_u);
+            for (int64_t t = t0 + 1; t <= t0 + 64 && t <= (Ic + 7) / 8; ++t) {
+                const int64_t bi = round_up((Ic + t - 1) / t, 8);
+                int64_t u = 1;
+                if (bi <= PS_M) {
+                    u = (2 * PS_M) / bi;
+                    if (u > maxU) u = maxU;
+                }
+                const int64_t st = t * ((pl.nruns + u - 1) / u);
+                if (st < best_st) {
+                    best_st = st;
+                    best_rows = u * bi;
+                    best_bi = bi;
+                    best_u = u;
+                }
+            }
+        } else if (best_rows * 4 < 3 * 2 * PS_M) {
             for (int64_t t = t0 + 1; t <= t0 + 64 && t <= (Ic + 7) / 8; ++t) {
                 const int64_t bi = round_up((Ic + t - 1) / t, 8);
                 int64_t u = 1;

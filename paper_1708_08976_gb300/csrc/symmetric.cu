@@ -60,6 +60,39 @@ __global__ void __launch_bounds__(256) sym_pack_kernel(const float* __restrict__
     }
 }
 
+// The same, by bands of 32 rows a of one slice r, for n0 <= kBandMaxN: the band's entries
+// X(a, b, r), b <= a, are read with a fastest (128-byte runs), staged in shared memory and
+// written as the band's packed rows, one contiguous range of Xp.  The last band also writes
+// the zero padding rows.
+constexpr int kBandRows = 32;
+constexpr int kBandMaxN = 320;
+__global__ void __launch_bounds__(256) sym_pack_band_kernel(const float* __restrict__ X, int n0, int diag,
+                                                            int64_t Pp, float* __restrict__ Xp) {
+    __shared__ float T[kBandMaxN][kBandRows + 1];
+    const int a0 = blockIdx.x * kBandRows;
+    const int a1 = a0 + kBandRows < n0 ? a0 + kBandRows : n0;
+    const int64_t r = blockIdx.y;
+    const float* src = X + (int64_t)n0 * n0 * r;
+    const int nb = diag ? a1 : a1 - 1;                   // columns b < nb hold the band's entries
+    for (int e = threadIdx.x; e < nb * kBandRows; e += blockDim.x) {
+        const int b = e / kBandRows, ao = e - b * kBandRows;
+        if (a0 + ao < a1) T[b][ao] = src[(a0 + ao) + (int64_t)n0 * b];
+    }
+    __syncthreads();
+    const int off = 1 - diag;
+    const int64_t p0 = tri_rows(a0, diag);              // packed rows of the rows a < a0
+    const int64_t p1 = tri_rows(a1, diag);
+    float* dst = Xp + Pp * r;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        int64_t a, b;
+        tri_pair(p, a, b);
+        a += off;
+        dst[p] = T[b][a - a0];
+    }
+    if (a1 == n0)
+        for (int64_t p = p1 + threadIdx.x; p < Pp; p += blockDim.x) dst[p] = 0.0f;
+}
+
 // W (Pp x C, row-major): the pair products of U_0 and U_1, symmetrised; zero padding rows
 __global__ void __launch_bounds__(256) sym_pair_kernel(const float* __restrict__ U0, const float* __restrict__ U1,
                                                        int64_t n0, int diag, int64_t Pp, int C, float* __restrict__ W) {
@@ -117,6 +150,12 @@ int64_t sym_packed_rows(int64_t n0, int diag) { return (tri_rows(n0, diag) + 7) 
 
 cudaError_t launch_sym_pack(const float* X, int64_t n0, int diag, int64_t rest, float* Xp, cudaStream_t s) {
     const int64_t Pp = sym_packed_rows(n0, diag);
+    if (n0 <= kBandMaxN && rest <= 65535) {
+        const dim3 grid((unsigned)((n0 + kBandRows - 1) / kBandRows), (unsigned)rest);
+        sym_pack_band_kernel<<<grid, 256, 0, s>>>(X, (int)n0, diag, Pp, Xp);
+        note_launches(1);
+        return cudaGetLastError();
+    }
     sym_pack_kernel<<<grid_for(Pp * rest, 256), 256, 0, s>>>(X, n0, diag, Pp, rest, Xp);
     note_launches(1);
     return cudaGetLastError();

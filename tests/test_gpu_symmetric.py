@@ -80,6 +80,7 @@ SHAPES = [
     ((33, (16, 5)), 12),
     ((10, (8, 6, 3)), 7),
     ((9, (40,)), 64),
+    ((330, (2,)), 8),             # n0 above the banded packing's limit (320): the per-entry packing
 ]
 
 
