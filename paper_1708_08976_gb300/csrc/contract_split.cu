@@ -62,10 +62,11 @@ constexpr int PS_M = 128;                    // MMA M
 #ifndef MTK_PS_HEAD_PAD
 #define MTK_PS_HEAD_PAD 32
 #endif
-// K-major tiling when the fewest i-tiles are under 3/4 full: 0 the most rows per stage
-// (ties: fewer tiles), 1 the fewest stages
+// K-major tiling when the fewest i-tiles are under 3/4 full: 1 the fewest stages (measured:
+// 165^4 mode 1 from 0.70 to 0.81 of the roofline, the other modes unchanged or better);
+// 0 the most rows per stage (ties: fewer tiles)
 #ifndef MTK_PS_TILE_MODEL
-#define MTK_PS_TILE_MODEL 0
+#define MTK_PS_TILE_MODEL 1
 #endif
 #ifndef MTK_PS_HEAD_PAD_NEAR
 #define MTK_PS_HEAD_PAD_NEAR 4

@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(256) sym_pack_kernel(const float* __restrict__
 
 // The same, by bands of 32 rows a of one slice r, for n0 <= kBandMaxN: the band's entries
 // X(a, b, r), b <= a, are read with a fastest (128-byte runs), staged in shared memory and
-// written as the band's packed rows, one contiguous range of Xp.  The last band also writes
-// the zero padding rows.
+// written row by row of a (each packed row contiguous, the band's rows one contiguous range
+// of Xp), with no index decoding per entry.  The last band also writes the zero padding.
 constexpr int kBandRows = 32;
 constexpr int kBandMaxN = 320;
 __global__ void __launch_bounds__(256) sym_pack_band_kernel(const float* __restrict__ X, int n0, int diag,
@@ -79,18 +79,17 @@ __global__ void __launch_bounds__(256) sym_pack_band_kernel(const float* __restr
         if (a0 + ao < a1) T[b][ao] = src[(a0 + ao) + (int64_t)n0 * b];
     }
     __syncthreads();
-    const int off = 1 - diag;
-    const int64_t p0 = tri_rows(a0, diag);              // packed rows of the rows a < a0
-    const int64_t p1 = tri_rows(a1, diag);
+    // one warp per row a of the band, lanes along its packed row (b = 0..a, or 0..a-1)
     float* dst = Xp + Pp * r;
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        int64_t a, b;
-        tri_pair(p, a, b);
-        a += off;
-        dst[p] = T[b][a - a0];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ao = warp; ao < a1 - a0; ao += (int)(blockDim.x >> 5)) {
+        const int a = a0 + ao;
+        const int len = diag ? a + 1 : a;
+        float* row = dst + tri_rows(a, diag);           // the packed rows of the rows before a
+        for (int b = lane; b < len; b += 32) row[b] = T[b][ao];
     }
     if (a1 == n0)
-        for (int64_t p = p1 + threadIdx.x; p < Pp; p += blockDim.x) dst[p] = 0.0f;
+        for (int64_t p = tri_rows(n0, diag) + threadIdx.x; p < Pp; p += blockDim.x) dst[p] = 0.0f;
 }
 
 // W (Pp x C, row-major): the pair products of U_0 and U_1, symmetrised; zero padding rows
