@@ -42,11 +42,11 @@ METRIC = "Dense MTTKRP TFLOP/s & roofline %, mixed-precision vs FP32 at stated r
 # 200x200x30x40 case (the same plan shapes, a tensor 10x smaller): reads scaled by 10;
 # writes (the output and the partial slabs of tiles split between CTAs, a few MB) taken
 # as measured.
-#   tree: mean of the two partials (n = 1 right: 193.11 MB read, 3.83 MB written;
-#         n = 2 left: 204.50 MB read, 0.52 MB written) -> 1.9349e9 and 2.0455e9 per
-#         full launch, 1.006x and 1.065x their algorithmic bytes.
+#   tree: mean of the two partials (n = 1 right: 192.32 MB read, 3.86 MB written;
+#         n = 2 left: 204.49 MB read, 0.09 MB written) -> 1.9271e9 and 2.0450e9 per
+#         full launch, 1.002x and 1.065x their algorithmic bytes.
 #   planes (per-mode MTTKRPs): None (the bench's dominant kernel is the tree's).
-NCU_TRAFFIC_PER_LAUNCH = {"planes": None, "tree": 1.9902e9}
+NCU_TRAFFIC_PER_LAUNCH = {"planes": None, "tree": 1.9861e9}
 L2_BYTES = 129 * 1024 * 1024
 
 
