@@ -70,6 +70,8 @@ def _load():
         "oracle_residual2_explicit": (dbl, [P, P, i32, P, i32]),
         "oracle_residual2_identity": (dbl, [dbl, P, P, i64, P, i32, P, i32]),
         "oracle_als_sweep": (i32, [P, P, i32, P, i32, P]),
+        "oracle_als_sweep_opt": (i32, [P, P, i32, P, i32, i32, P]),
+        "oracle_normalize_columns": (None, [P, i64, i32, P]),
         "oracle_grad": (i32, [P, P, i32, P, i32, i32, P]),
         "oracle_num_threads": (i32, []),
         "oracle_set_num_threads": (None, [i32]),
@@ -285,17 +287,32 @@ def residual2_identity(normX2, Mm, Um, dims, U) -> float:
                                                Mm.shape[0], d.ctypes.data, len(d), _ptrs(Us), C))
 
 
-def als_sweep(X, dims, U):
-    """One CP-ALS sweep (Section 2.2). Returns (new factor list, fit)."""
+def als_sweep(X, dims, U, normalize=False):
+    """One CP-ALS sweep (Section 2.2). Returns (new factor list, fit).  normalize: every
+    factor but the last scaled to unit column norms after its update (an optional step
+    the paper does not have; the last factor carries the weights)."""
     lib = _load()
     d = _dims(dims)
     C = _rank(U)
     Us = [u.copy() for u in _factors(U, d, C)]
     X = _f64(X).ravel()
     fit = ctypes.c_double(0.0)
-    _check(lib.oracle_als_sweep(X.ctypes.data, d.ctypes.data, len(d), _ptrs(Us), C,
-                                ctypes.byref(fit)), "als_sweep")
+    if normalize:
+        _check(lib.oracle_als_sweep_opt(X.ctypes.data, d.ctypes.data, len(d), _ptrs(Us), C, 1,
+                                        ctypes.byref(fit)), "als_sweep")
+    else:
+        _check(lib.oracle_als_sweep(X.ctypes.data, d.ctypes.data, len(d), _ptrs(Us), C,
+                                    ctypes.byref(fit)), "als_sweep")
     return Us, fit.value
+
+
+def normalize_columns(U):
+    """(U with unit 2-norm columns, the C norms); zero columns stay zero."""
+    lib = _load()
+    Un = np.ascontiguousarray(np.array(U, dtype=np.float64))
+    lam = np.zeros(Un.shape[1])
+    lib.oracle_normalize_columns(Un.ctypes.data, Un.shape[0], Un.shape[1], lam.ctypes.data)
+    return Un, lam
 
 
 def grad(X, dims, U, n) -> np.ndarray:

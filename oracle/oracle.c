@@ -518,8 +518,33 @@ double oracle_residual2_identity(double normX2, const double* Mm, const double* 
  * identity above at the last mode.  On a non-positive-definite H the sweep
  * stops with OR_ENOTPD and that factor is left unchanged.
  */
-int oracle_als_sweep(const double* X, const int64_t* dims, int N, double* const* U,
-                     int C, double* fit) {
+/*
+ * Column normalisation of a factor, an optional step of CP-ALS.  The paper's ALS
+ * (Section 2.2) has none; the reading adopted here is the usual one of CP-ALS codes:
+ * lambda_c = ||U(:, c)||_2 and U(:, c) / lambda_c, a column of zeros left as it is
+ * (lambda_c = 0).  U is I x C row-major; lambda (may be NULL) receives the C norms.
+ */
+void oracle_normalize_columns(double* U, int64_t I, int C, double* lambda) {
+    for (int c = 0; c < C; ++c) {
+        double s = 0.0;
+        for (int64_t i = 0; i < I; ++i) s += U[i * C + c] * U[i * C + c];
+        const double l = sqrt(s);
+        if (lambda) lambda[c] = l;
+        if (l > 0.0)
+            for (int64_t i = 0; i < I; ++i) U[i * C + c] /= l;
+    }
+}
+
+/*
+ * One CP-ALS sweep (Section 2.2): for n = 0..N-1 in order, M = MTTKRP(X, n) with the
+ * factors as they are at that point (the ones before n already updated), H = Hadamard
+ * of the Grams of the other factors, U_n = M H^{-1} by Cholesky.  normalize != 0: after
+ * its update every factor but the last is scaled to unit column norms (the last one then
+ * carries the weights, so [[U_0, ..., U_{N-1}]] is the model without a separate lambda).
+ * fit (may be NULL): 1 - ||X - [[U]]|| / ||X||.
+ */
+int oracle_als_sweep_opt(const double* X, const int64_t* dims, int N, double* const* U,
+                         int C, int normalize, double* fit) {
     int st = check_args(dims, N, C, 0);
     if (st) return st;
     int64_t maxI = 0;
@@ -535,6 +560,7 @@ int oracle_als_sweep(const double* X, const int64_t* dims, int N, double* const*
         st = oracle_cholesky(H, C, L);
         if (st) break;
         oracle_chol_solve(L, C, M, dims[n], U[n]);
+        if (normalize && n < N - 1) oracle_normalize_columns(U[n], dims[n], C, NULL);
     }
     if (!st && fit) {
         const int64_t I = prod_dims(dims, 0, N);
@@ -545,6 +571,11 @@ int oracle_als_sweep(const double* X, const int64_t* dims, int N, double* const*
     }
     free(M); free(H); free(L);
     return st;
+}
+
+int oracle_als_sweep(const double* X, const int64_t* dims, int N, double* const* U,
+                     int C, double* fit) {
+    return oracle_als_sweep_opt(X, dims, N, U, C, 0, fit);
 }
 
 /*

@@ -267,6 +267,36 @@ def test_als_sweep_matches_numpy_and_fixed_point():
     assert abs(fit_a - 1.0) < 1e-6
 
 
+@pytest.mark.parametrize("dims,C", [((7, 6, 5), 3), ((6, 5, 4, 3), 4), ((5, 4, 3, 3, 2), 2)])
+def test_als_sweep_normalized_same_model(dims, C):
+    """The optional column normalisation leaves the model unchanged: ALS is equivariant
+    under column scaling (scaling U_k by a diagonal D multiplies M_n and H_n so that the
+    next U_n comes out scaled by D^{-1}), so over several sweeps the normalised and plain
+    runs give the same reconstruction [[U]] and fit; the normalised factors but the last
+    have unit columns, the last one carries the weights."""
+    X, dims, U = synth.random_case(dims, C, seed=31 + len(dims), dist="uniform")
+    Ua, Ub = U, U
+    N = len(dims)
+    for _ in range(3):
+        Ua, fa = oracle.als_sweep(X, dims, Ua)
+        Ub, fb = oracle.als_sweep(X, dims, Ub, normalize=True)
+        Ta, _ = cp_full(Ua)
+        Tb, _ = cp_full(Ub)
+        np.testing.assert_allclose(Tb, Ta, rtol=1e-9, atol=1e-11 * np.abs(Ta).max())
+        assert abs(fa - fb) < 1e-10
+        for k in range(N - 1):
+            np.testing.assert_allclose(np.linalg.norm(Ub[k], axis=0), 1.0, rtol=1e-13)
+        assert np.abs(np.linalg.norm(Ub[N - 1], axis=0) - 1.0).max() > 1e-3
+    # the normalisation step alone: unit columns, the norms returned, zero columns kept
+    g = np.random.default_rng(5)
+    A = g.standard_normal((9, 4))
+    A[:, 2] = 0.0
+    An, lam = oracle.normalize_columns(A)
+    np.testing.assert_allclose(lam, [np.sqrt(np.sum(A[:, c] ** 2)) for c in range(4)], rtol=1e-15)
+    np.testing.assert_allclose(An[:, [0, 1, 3]] * lam[[0, 1, 3]], A[:, [0, 1, 3]], rtol=1e-15)
+    assert np.all(An[:, 2] == 0.0)
+
+
 def test_residual_identity():
     X, dims, U = synth.random_case((6, 5, 4), 4, seed=15)
     for m in range(3):
