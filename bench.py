@@ -6,7 +6,7 @@ Workload (default): the correlation-shaped 4-way FP32 tensor 200x200x300x40
 C = 25.  One step = one CP-ALS sweep through the C ABI: for each of the 4 modes
 the MTTKRP, the FP64 factor update and the Gram of the new factor, then the fit.
 The tensor is split once into its two BF16 planes (timed apart, and inside every
-e2e step); the sweep runs on the planes either with per-mode MTTKRPs or with the
+e2e step, where the split reads the step's tensor from pinned host memory); the sweep runs on the planes either with per-mode MTTKRPs or with the
 dimension tree (two partial contractions shared by two modes each), and the
 faster form is reported.  Metric = useful MTTKRP flops (4 modes x 2*I*C) per
 second of the whole sweep.
@@ -580,7 +580,8 @@ def run_grad(args, mtk, torch, dev, hbm_peak):
     Xd = torch.from_numpy(X).to(dev)
     Xs, _ = mtk.split_tensor(Xd, dims)
     ref0 = oracle.grad(X.astype(np.float64), dims, [u.astype(np.float64) for u in U], 0)
-    forms = {"planes-tree": {"Xs": Xs}, "planes-per-mode": {"Xs": Xs, "algo": "fused"},
+    forms = {"planes-tree": {"Xs": Xs}, "planes-tree-graph": {"Xs": Xs},
+             "planes-per-mode": {"Xs": Xs, "algo": "fused"},
              "fp32": {"precision": "fp32"}, "bf16x2": {"precision": "bf16x2"}}
     sampler = ClockSampler(dev.index)
     sampler.start()
@@ -596,6 +597,21 @@ def run_grad(args, mtk, torch, dev, hbm_peak):
         for _ in range(max(args.warmup, 3)):
             step()
         torch.cuda.synchronize()
+        if name.endswith("graph"):
+            # forward and backward recorded once (the gradients land in the .grad tensors
+            # allocated during the capture); each step replays the graph
+            g_ = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(torch.cuda.current_stream(dev))
+            for u in Ud:
+                u.grad = None
+            with torch.cuda.graph(g_, stream=side, capture_error_mode="thread_local"):
+                mtk.cp_loss(Xd, dims, Ud, **opts).backward()
+            torch.cuda.current_stream(dev).wait_stream(side)
+            step = g_.replay
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = max(args.steps, 5)
         e0.record()
@@ -606,7 +622,7 @@ def run_grad(args, mtk, torch, dev, hbm_peak):
         t = e0.elapsed_time(e1) * 1e-3 / reps
         step()
         err = float(np.linalg.norm(Ud[0].grad.double().cpu().numpy() - ref0) / np.linalg.norm(ref0))
-        passes = 3 if name == "planes-tree" else N + 1
+        passes = 3 if name.startswith("planes-tree") else N + 1
         out[name] = {"ms_per_step": t * 1e3, "tflops": (N + 1) * 2.0 * I * C / t / 1e12,
                      "tensor_passes": passes,
                      "roofline_frac_definition": ((N + 1) * 4.0 * I / hbm_peak / 1e9) / t,
@@ -735,19 +751,30 @@ def main():
     # the sweep forms to time: per-mode MTTKRPs, and on the planes the dimension tree
     # (the partial contraction over modes >= 2 shared by the updates of U_0 and U_1, the
     # one over modes 0, 1 by those of U_2 and U_3: the tensor is read twice per sweep)
+    # "tree-graph": the same tree sweep recorded once in a CUDA graph and replayed
     forms_sweep = ["per-mode"]
     if planes and len(dims) in (3, 4) and args.sweep in ("best", "tree"):
-        forms_sweep = ["tree"] if args.sweep == "tree" else ["per-mode", "tree"]
+        forms_sweep = ["tree", "tree-graph"] if args.sweep == "tree" else ["per-mode", "tree", "tree-graph"]
     sweeps = {}
+    graph_launches = 0
     for fs in forms_sweep:
         Uw = [u.clone() for u in U0]
-        algo = "two_step" if fs == "tree" else args.algo
+        algo = "two_step" if fs.startswith("tree") else args.algo
         a_ = mtk.ALS(Xd, dims, Uw, algo=algo, precision="auto" if planes else prec, presplit=planes)
         for _ in range(args.warmup):
             a_.sweep()
         torch.cuda.synchronize()
         if a_.status() != 0:
             raise RuntimeError(f"device status {a_.status()} after warm-up ({fs})")
+        if fs.endswith("graph"):
+            l0 = lib.mtk_launch_count()
+            a_.capture()
+            graph_launches = lib.mtk_launch_count() - l0      # kernels in one replay
+            for _ in range(args.warmup):
+                a_.replay()
+            torch.cuda.synchronize()
+            if a_.status() != 0:
+                raise RuntimeError(f"device status {a_.status()} after warm-up ({fs})")
         for a, b in zip(Uw, U0):
             a.copy_(b)
         sweeps[fs] = (a_, Uw)
@@ -765,13 +792,14 @@ def main():
         l0 = lib.mtk_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("timed_sweeps" if fs == forms_sweep[-1] else "timed_sweeps_" + fs)
+        run = a_.replay if fs.endswith("graph") else a_.sweep
         e0.record(stream)
         for _ in range(args.steps):
-            a_.sweep()
+            run()
         e1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        launches_by[fs] = lib.mtk_launch_count() - l0
+        launches_by[fs] = lib.mtk_launch_count() - l0 + (graph_launches * args.steps if fs.endswith("graph") else 0)
         if world > 1:
             torch.distributed.barrier()
         sweep_ms[fs] = e0.elapsed_time(e1) / args.steps
@@ -794,7 +822,7 @@ def main():
     # with the dimension tree the step's dominant kernel is the partial contraction on
     # the planes (each call: prep, contraction, slab reduce), timed the same way
     partials = []
-    if best_form == "tree":
+    if best_form.startswith("tree"):
         for n, right in tree_partials(N):
             fn = lambda: mtk.partial_mttkrp_split(als.Xs, dims, U0, n, right)
             partials.append((n, right, time_calls(fn, max(args.steps, 5), stream=stream)))
@@ -810,19 +838,26 @@ def main():
         Uh = [torch.from_numpy(u).pin_memory() for u in U]
         Uo = [torch.empty_like(u).pin_memory() for u in Uh]
         fit_h = torch.empty((), dtype=torch.float64).pin_memory()
-        Xe = torch.empty_like(Xd)
         Ue = [torch.empty_like(u) for u in U0]
-        alse = mtk.ALS(Xe, dims, Ue, algo="two_step" if best_form == "tree" else args.algo,
+        # planes: the split reads the pinned host tensor in place (the host-to-device
+        # transfer of X and its split are one pass; X never occupies device memory);
+        # otherwise X is copied to the device and its norm taken there
+        Xe = Xh if planes else torch.empty_like(Xd)
+        alse = mtk.ALS(Xe, dims, Ue, algo="two_step" if best_form.startswith("tree") else args.algo,
                        precision="auto" if planes else prec, presplit=planes)
         ksteps = max(3, min(args.steps, 5))
         for it in range(ksteps + 1):
             if it == 1:
                 torch.cuda.synchronize()
                 a = time.perf_counter()
-            Xe.copy_(Xh, non_blocking=True)
+            if not planes:
+                Xe.copy_(Xh, non_blocking=True)
             for d_, h_ in zip(Ue, Uh):
                 d_.copy_(h_, non_blocking=True)
-            alse.resplit()          # ||X||^2 (and the BF16 planes) of this step's tensor
+            if planes:
+                alse.resplit(Xh)    # this step's tensor: BF16 planes and ||X||^2 from host memory
+            else:
+                alse.resplit()      # ||X||^2 of this step's tensor
             alse.sweep()
             for h_, d_ in zip(Uo, Ue):
                 h_.copy_(d_, non_blocking=True)
@@ -832,7 +867,10 @@ def main():
         h2d = X.nbytes + sum(u.nbytes for u in U)
         d2h = sum(u.nbytes for u in U) + 8
         e2e = {"value": world * flops_step / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3}
+               "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3,
+               "tensor_transfer": ("read in place from pinned host memory by the split kernel "
+                                   "(mtk_split_tensor on the host pointer)") if planes else
+                                  "cudaMemcpyAsync from pinned host memory"}
 
     batch = None
     if not args.no_batch:

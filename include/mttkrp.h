@@ -80,7 +80,14 @@ typedef struct {
                           contraction kernel first waits on a barrier that nothing
                           completes, so that this wait runs out after wait_us and the call
                           reports MTK_ETIMEOUT (the output is not valid then). */
-    int reserved[3];   /* set to 0 */
+    int normalize;     /* CP-ALS sweeps only.  1: after its update, every factor but the
+                          last is scaled to unit 2-norm columns (its Gram with it); the
+                          last factor then carries the weights, so [[U_0, ..., U_{N-1}]]
+                          is the model without a separate lambda, and the sweep's result
+                          is the same model as without the scaling (ALS is equivariant
+                          under column scaling).  Needs C <= 64 (else MTK_EUNSUPPORTED).
+                          0: no scaling (the paper's sweep). */
+    int reserved[2];   /* set to 0 */
 } mtk_opts;            /* NULL = all defaults */
 
 /* status helpers --------------------------------------------------------- */
@@ -160,6 +167,10 @@ int mtk_mttkrp_noalloc(const float* X, const int64_t* dims, int N, const float* 
  * multiple of 8.  Xs: device, 16-byte aligned, caller-owned.  normX2 (device double, may
  * be NULL) receives ||X||^2 from the same pass (exact squares, compensated FP32 sums of 64
  * entries added in FP64, fixed order).  ws: at least mtk_split_workspace(dims, N) bytes.
+ * X: device memory, or pinned (page-locked) host memory, which the split reads in place
+ * through its mapping into the device address space: the transfer from the host and the
+ * split are then one pass, and the FP32 tensor never occupies device memory.  Pageable
+ * host memory: MTK_EINVAL.
  * Bad dims (N outside 1..8, a dim < 1, more than 2^46 padded entries): the size queries
  * return 0 and the split MTK_EINVAL. */
 int64_t mtk_split_rows0(int64_t I0);
@@ -334,7 +345,8 @@ int mtk_cp_als_sweep(const float* X, const int64_t* dims, int N, float* const* U
                      const mtk_opts* opts, void* stream);
 
 /* The same sweep with every MTTKRP on the tensor's BF16 planes (mtk_mttkrp_split).
- * Xs: from mtk_split_tensor.  X: the FP32 tensor or NULL (see mtk_mttkrp_split).  opts
+ * Xs: from mtk_split_tensor.  X: the FP32 tensor or NULL (see mtk_mttkrp_split); device
+ * or pinned host memory (read in place, for the modes the planes do not take).  opts
  * as for mtk_mttkrp_split, and algo MTK_ALGO_TWO_STEP selects the dimension tree for
  * N = 3 or 4 (Section 6 of the paper, reuse of partial MTTKRPs across modes): the partial
  * contraction over modes >= 2 serves the updates of U_0 and U_1, the one over modes 0 and

@@ -25,7 +25,7 @@ PREC_AUTO, PREC_FP32, PREC_BF16X2, PREC_BF16X3 = 0, 1, 2, 3
 
 class MtkOpts(ctypes.Structure):
     _fields_ = [("algo", I32), ("precision", I32), ("splits", I32), ("wait_us", I32), ("test_stall", I32),
-                ("reserved", I32 * 3)]
+                ("normalize", I32), ("reserved", I32 * 2)]
 
 
 OPTS_P = ctypes.POINTER(MtkOpts)
@@ -127,13 +127,14 @@ def check(st: int, what: str) -> None:
         raise MtkError(st, what)
 
 
-def opts(algo=ALGO_AUTO, precision=PREC_AUTO, splits=0, wait_us=0, test_stall=0):
+def opts(algo=ALGO_AUTO, precision=PREC_AUTO, splits=0, wait_us=0, test_stall=0, normalize=0):
     o = MtkOpts()
     o.algo = int(algo)
     o.precision = int(precision)
     o.splits = int(splits)
     o.wait_us = int(wait_us)
     o.test_stall = int(test_stall)
+    o.normalize = int(normalize)
     return o
 
 

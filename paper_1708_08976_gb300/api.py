@@ -33,6 +33,18 @@ def _req(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
     return t
 
 
+def _req_src(t: torch.Tensor, name: str) -> torch.Tensor:
+    """A tensor the library reads in place: a CUDA tensor, or a pinned host tensor (read
+    through its mapping into the device address space)."""
+    if isinstance(t, torch.Tensor) and not t.is_cuda and t.is_pinned():
+        if t.dtype != torch.float32:
+            raise TypeError(f"{name} must be {torch.float32}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+    return _req(t, torch.float32, name)
+
+
 def _opts(algo="auto", precision="auto", splits=0):
     return L.opts(ALGOS[algo] if isinstance(algo, str) else algo,
                   PRECISIONS[precision] if isinstance(precision, str) else precision, splits)
@@ -103,12 +115,20 @@ def _rank(U, skip=None):
 
 
 def split_tensor(X: torch.Tensor, dims: Sequence[int], *, out: Optional[torch.Tensor] = None,
-                 normX2: Optional[torch.Tensor] = None, ws: Optional[Workspace] = None):
+                 normX2: Optional[torch.Tensor] = None, ws: Optional[Workspace] = None,
+                 device=None):
     """Split an FP32 tensor (natural order, dims) into its two BF16 planes (hi, lo) for
     mtk_mttkrp_split, mode 0 padded to a multiple of 8.  Returns (Xs, normX2): Xs an int16
     tensor holding the planes' 16-bit words, normX2 a device FP64 scalar with ||X||^2 from
-    the same pass."""
-    _req(X, torch.float32, "X")
+    the same pass.  X may be a pinned host tensor: the split then reads it in place over the
+    host link (one pass, no device copy of X); the planes go to `device` (default: the
+    device of `out`, else the current CUDA device)."""
+    _req_src(X, "X")
+    if X.is_cuda:
+        device = X.device
+    elif device is None:
+        device = out.device if out is not None else torch.device("cuda", torch.cuda.current_device())
+    device = torch.device(device)
     lib = L.load()
     dims = [int(d) for d in dims]
     d = L.dims_arr(dims)
@@ -122,16 +142,16 @@ def split_tensor(X: torch.Tensor, dims: Sequence[int], *, out: Optional[torch.Te
         raise ValueError("X is smaller than dims")
     nwords = nb // 2
     if out is None:
-        out = torch.empty(nwords, dtype=torch.int16, device=X.device)
+        out = torch.empty(nwords, dtype=torch.int16, device=device)
     _req(out, torch.int16, "out")
     if out.numel() < nwords:
         raise ValueError(f"split planes need {nwords} 16-bit words")
     if normX2 is None:
-        normX2 = torch.empty((), dtype=torch.float64, device=X.device)
-    ws = ws or default_workspace(X.device)
+        normX2 = torch.empty((), dtype=torch.float64, device=device)
+    ws = ws or default_workspace(device)
     wp, wb = ws.ptr(lib.mtk_split_workspace(d, len(dims)))
     L.check(lib.mtk_split_tensor(X.data_ptr(), d, len(dims), out.data_ptr(), normX2.data_ptr(), wp, wb,
-                                 _stream(X.device)), "mtk_split_tensor")
+                                 _stream(device)), "mtk_split_tensor")
     return out, normX2
 
 
@@ -615,45 +635,64 @@ class BatchedMTTKRP:
 class ALS:
     """CP-ALS driver: holds the workspace, ||X||^2 and the device fit scalar.
     presplit=True splits X into its BF16 planes once (with ||X||^2 in the same pass) and
-    runs every MTTKRP on them (mtk_cp_als_sweep_split); precision is then bf16x2."""
+    runs every MTTKRP on them (mtk_cp_als_sweep_split); precision is then bf16x2.
+    normalize=True scales every factor but the last to unit columns after its update (the
+    last one carries the weights; the model is the same as without).  capture() records
+    one sweep in a CUDA graph, replay() runs it."""
 
-    def __init__(self, X, dims, U, *, algo="auto", precision="auto", splits=0, presplit=False):
-        self.X = _req(X, torch.float32, "X")
+    def __init__(self, X, dims, U, *, algo="auto", precision="auto", splits=0, presplit=False,
+                 normalize=False):
         self.presplit = bool(presplit)
+        # with presplit, X may be a pinned host tensor: only its planes live on the device
+        self.X = _req_src(X, "X") if self.presplit else _req(X, torch.float32, "X")
+        self.device = X.device if X.is_cuda else U[0].device
         self.dims = [int(d) for d in dims]
         self.U = list(U)
         self.C = _rank(self.U)
         _factor_ptrs(self.U, self.dims, self.C)
         self.opts = _opts(algo, precision, splits)
+        self.opts.normalize = int(bool(normalize))
+        self.graph = None
         lib = L.load()
         self._d = L.dims_arr(self.dims)
         need = lib.mtk_cp_als_workspace(self._d, len(self.dims), self.C, L.ctypes.byref(self.opts))
         if need == 0:
             raise ValueError("invalid CP-ALS shape or options")
-        self.ws = Workspace(X.device)
+        self.ws = Workspace(self.device)
         self.ws.get(need)
         self.need = need
         self.Xs = None
         if self.presplit:
-            self.Xs, self.normX2 = split_tensor(X, self.dims, ws=Workspace(X.device))
+            self.Xs, self.normX2 = split_tensor(X, self.dims, ws=Workspace(self.device), device=self.device)
         else:
-            self.normX2 = norm2(X, ws=Workspace(X.device))
-        self.fit = torch.zeros((), dtype=torch.float64, device=X.device)
+            self.normX2 = norm2(X, ws=Workspace(self.device))
+        self.fit = torch.zeros((), dtype=torch.float64, device=self.device)
         self._uptrs = L.ptr_arr([u.data_ptr() for u in self.U])
 
-    def resplit(self) -> None:
-        """Re-split X (after its contents changed) and refresh ||X||^2."""
+    def resplit(self, X: Optional[torch.Tensor] = None) -> None:
+        """Re-split the tensor (after its contents changed) and refresh ||X||^2.  With X (a
+        tensor of the same dims) the planes are made from X instead, which then becomes the
+        tensor of the sweep; X may be a pinned host tensor (read in place over the host link,
+        so that a new tensor needs no device copy)."""
+        if X is not None:
+            if not self.presplit:
+                raise ValueError("resplit(X) needs presplit=True")
+            _req_src(X, "X")
+            if X.numel() < self.X.numel():
+                raise ValueError("X is smaller than dims")
+            self.X = X
         if self.presplit:
-            split_tensor(self.X, self.dims, out=self.Xs, normX2=self.normX2, ws=Workspace(self.X.device))
+            split_tensor(self.X, self.dims, out=self.Xs, normX2=self.normX2, ws=Workspace(self.device),
+                         device=self.device)
         else:
-            norm2(self.X, out=self.normX2, ws=Workspace(self.X.device))
+            norm2(self.X, out=self.normX2, ws=Workspace(self.device))
 
     def sweep(self, with_fit: bool = True) -> None:
         lib = L.load()
         wp, wb = self.ws.ptr(self.need)
         nx = self.normX2.data_ptr() if with_fit else None
         fit = self.fit.data_ptr() if with_fit else None
-        st = _stream(self.X.device)
+        st = _stream(self.device)
         if self.presplit:
             L.check(lib.mtk_cp_als_sweep_split(self.Xs.data_ptr(), self.X.data_ptr(), self._d, len(self.dims),
                                                self._uptrs, self.C, nx, fit, wp, wb, L.ctypes.byref(self.opts), st),
@@ -661,6 +700,25 @@ class ALS:
         else:
             L.check(lib.mtk_cp_als_sweep(self.X.data_ptr(), self._d, len(self.dims), self._uptrs, self.C, nx, fit,
                                          wp, wb, L.ctypes.byref(self.opts), st), "mtk_cp_als_sweep")
+
+    def capture(self, with_fit: bool = True):
+        """Record one sweep in a CUDA graph: its launches with their arguments (factors,
+        planes, workspace and fit stay where they are), the programmatic dependencies
+        between them included.  replay() then runs the sweep as one graph launch."""
+        self.ws.get(self.need)
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+            self.sweep(with_fit)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        self.graph = g
+        return g
+
+    def replay(self) -> None:
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
 
     def status(self) -> int:
         return self.ws.status()

@@ -215,6 +215,17 @@ __device__ void write_gram(const float2* fin, const int* tri, int npairs, int C,
     }
 }
 
+// the same with the columns of U scaled by sc: G(i, k) sc_i sc_k (exact scales: FP32 numbers)
+__device__ void write_gram_scaled(const float2* fin, const int* tri, int npairs, int C, const float* sc, double* G) {
+    for (int x = threadIdx.x; x < npairs; x += blockDim.x) {
+        const float2 v = fin[x];
+        const int i = tri[x] >> 8, k = tri[x] & 255;
+        const double g = ((double)v.x + (double)v.y) * ((double)sc[i] * (double)sc[k]);
+        G[i * C + k] = g;
+        G[k * C + i] = g;
+    }
+}
+
 // index of (a, b) in the pair list (build_pairs order)
 __device__ __forceinline__ int pair_index(int a, int b, int C) {
     const int i = a > b ? a : b, k = a > b ? b : a;
@@ -240,6 +251,7 @@ struct UpdParams {
     uint32_t* status;
     const float2* hinv;          // H^{-1} formed by als_factor_kernel (C x C pairs), then its not-pd
                                  // flag (an int at hinv + C*C); null: H is factored here
+    int normalize;               // with gram, without the fit: U_n and G_n scaled to unit columns
 };
 
 // ---- the factorisation, on shared memory, by all threads of the CTA ------------------------
@@ -396,6 +408,7 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
     __shared__ double red[kAppThreads / 32];
     __shared__ int tri[kMaxPairs];
     __shared__ float ur[kAppRows][kUpdMaxC];
+    __shared__ float nsc[kUpdMaxC];
     __shared__ int flag;
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -529,6 +542,24 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
     }
     if (!ticket_reduce(p.part, p.gsum, fin, p.tk + kTicketUpd, (int)blockIdx.x, (int)gridDim.x, npairs, &flag))
         return;
+    if (p.normalize && !fit && !bad) {
+        // the last CTA scales U_n to unit columns, s_c = fp32(1 / ||U_n(:, c)||) from the
+        // new Gram's diagonal (1 for a zero column), and writes G_n of the scaled factor
+        // (with H not positive definite U_n stays as it was, unscaled)
+        for (int c = t; c < C; c += kAppThreads) {
+            const float2 w = fin[pair_index(c, c, C)];
+            const double g = (double)w.x + (double)w.y;
+            nsc[c] = g > 0.0 ? (float)(1.0 / sqrt(g)) : 1.0f;
+        }
+        __syncthreads();
+        for (int64_t i = warp; i < p.In; i += kAppThreads / 32) {
+            float* urow = p.Un + i * C;               // rows of every CTA: read through L2
+            if (j0 < C) urow[j0] = __fmul_rn(__ldcg(urow + j0), nsc[j0]);
+            if (j1 < C) urow[j1] = __fmul_rn(__ldcg(urow + j1), nsc[j1]);
+        }
+        write_gram_scaled(fin, tri, npairs, C, nsc, p.Gn);
+        return;
+    }
     write_gram(fin, tri, npairs, C, p.Gn);
     if (!fit) return;
     // ---- fit: y2 = sum_ab prod_k G_k(a, b) with the new G_n (fin); <M, U_n> from the
@@ -713,6 +744,7 @@ cudaError_t launch_als_update(const AlsUpdateArgs& a, cudaStream_t s) {
     p.r2 = a.r2;
     p.status = a.status;
     p.hinv = static_cast<const float2*>(a.hinv);
+    p.normalize = a.normalize && a.Gn && !a.normX2 ? 1 : 0;
     const size_t smem = (size_t)a.C * a.C * sizeof(double) + (size_t)a.C * a.C * sizeof(float2) + pair_bytes(a.C);
     if (smem > 48 * 1024) {
         const cudaError_t e =

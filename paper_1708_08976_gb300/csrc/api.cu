@@ -95,6 +95,25 @@ mtk_opts defaults(const mtk_opts* o) {
 
 bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
 
+// The tensor as the kernels address it: device memory as it is; pinned host memory through
+// its mapping into the device address space, so that a kernel reads it over the host link
+// in the same pass that uses it; pageable host memory is refused (MTK_EINVAL)
+int device_view(const float* X, const float** out) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, X) != cudaSuccess) {
+        cudaGetLastError();
+        return MTK_ECUDA;
+    }
+    if (a.type == cudaMemoryTypeUnregistered) return MTK_EINVAL;
+    if (a.type == cudaMemoryTypeHost) {
+        if (!a.devicePointer) return MTK_EINVAL;
+        *out = static_cast<const float*>(a.devicePointer);
+        return MTK_OK;
+    }
+    *out = X;
+    return MTK_OK;
+}
+
 // limit of the contraction kernels' abortable device waits (0: the kernels' 1 s default)
 unsigned long long wait_limit_ns(const mtk_opts& o) {
     return o.wait_us > 0 ? (unsigned long long)o.wait_us * 1000ull : 0ull;
@@ -769,7 +788,10 @@ int mtk_split_tensor(const float* X, const int64_t* dims, int N, void* Xs, doubl
     double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + align256(kStatusBytes));
     int64_t rest = 1;
     for (int k = 1; k < N; ++k) rest *= dims[k];
-    if (launch_split_planes(X, dims[0], rest, Xs, part, normX2, (cudaStream_t)stream) != cudaSuccess)
+    const float* Xv = nullptr;
+    const int st = device_view(X, &Xv);
+    if (st) return st;
+    if (launch_split_planes(Xv, dims[0], rest, Xs, part, normX2, (cudaStream_t)stream) != cudaSuccess)
         return MTK_ECUDA;
     return MTK_OK;
 }
@@ -1317,6 +1339,8 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
     mtk_opts o = defaults(opts);
     if (o.algo < 0 || o.precision < MTK_PREC_FP32 || o.precision > MTK_PREC_BF16X3) return MTK_EINVAL;
     if (Xs && check_split_opts(opts, true) != MTK_OK) return MTK_EINVAL;
+    if (o.normalize < 0 || o.normalize > 1) return MTK_EINVAL;
+    if (o.normalize && !als_update_supported(C)) return MTK_EUNSUPPORTED;
     const int split_form = Xs ? 1 : 0;
     const bool tree = Xs && o.algo == MTK_ALGO_TWO_STEP && tree_ok(dims, N, C, o, als_layout(dims, N, C, o, split_form).reserve);
     const AlsLayout a = als_layout(dims, N, C, o, tree ? 2 : split_form);
@@ -1408,6 +1432,7 @@ int als_sweep(const float* X, const void* Xs, const int64_t* dims, int N, float*
             ua.status = status;
             ua.programmatic = true;
             ua.hinv = hooked ? hinv : nullptr;
+            ua.normalize = o.normalize != 0 && !last;
             if (launch_als_update(ua, s) != cudaSuccess) return MTK_ECUDA;
             continue;
         }
@@ -1437,7 +1462,12 @@ int mtk_cp_als_sweep_split(const void* Xs, const float* X, const int64_t* dims, 
                            int C, const double* normX2, double* fit, void* ws, size_t ws_bytes,
                            const mtk_opts* opts, void* stream) {
     if (!Xs) return MTK_EINVAL;
-    return als_sweep(X, Xs, dims, N, U, C, normX2, fit, ws, ws_bytes, opts, stream);
+    const float* Xv = nullptr;
+    if (X) {
+        const int st = device_view(X, &Xv);
+        if (st) return st;
+    }
+    return als_sweep(Xv, Xs, dims, N, U, C, normX2, fit, ws, ws_bytes, opts, stream);
 }
 
 int mtk_cp_residual(const double* normX2, const float* M, const float* Um, int64_t Im,

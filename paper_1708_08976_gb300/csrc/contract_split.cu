@@ -982,6 +982,15 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hw, uint3
     hw = *reinterpret_cast<const uint32_t*>(&h);
     lw = *reinterpret_cast<const uint32_t*>(&l);
 }
+__device__ __forceinline__ void split_one(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(x);
+    l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+#ifndef MTK_SPLIT_UNROLL
+#define MTK_SPLIT_UNROLL 4
+#endif
+constexpr int SPLIT_UNROLL = MTK_SPLIT_UNROLL;   // 16-byte loads in flight per thread
 
 __global__ void __launch_bounds__(256) split_planes_kernel(const float* __restrict__ X, int64_t NX, int64_t pitch,
                                                            int64_t chunk, __nv_bfloat16* __restrict__ Xs,
@@ -1013,34 +1022,44 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const float* __restri
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((reinterpret_cast<uintptr_t>(Xs) & 15) == 0) &&
                      (pitch % 4 == 0) && (chunk % 4 == 0);
     if (vec) {
+        // SPLIT_UNROLL loads of 16 bytes in flight per thread (one at a time left the copy at
+        // about 0.57 of the HBM bandwidth); a thread still visits v = tid, tid + 256, ... in
+        // order, so the sum of squares is the same for any unroll
         const int64_t n4 = (b1 - b0) / 4;
-        for (int64_t v = threadIdx.x; v < n4; v += blockDim.x) {
-            const int64_t e = b0 + 4 * v;
-            const float4 x = *reinterpret_cast<const float4*>(X + e);
-            uint2 hw, lw;
-            split_pair(x.x, x.y, hw.x, lw.x);
-            split_pair(x.z, x.w, hw.y, lw.y);
-            add_sq(x.x);
-            add_sq(x.y);
-            add_sq(x.z);
-            add_sq(x.w);
-            if (++cnt == 16) { flush(); cnt = 0; }
-            *reinterpret_cast<uint2*>(hi + e) = hw;
-            *reinterpret_cast<uint2*>(lo + e) = lw;
+        for (int64_t v0 = threadIdx.x; v0 < n4; v0 += SPLIT_UNROLL * (int64_t)blockDim.x) {
+            float4 xv[SPLIT_UNROLL];
+#pragma unroll
+            for (int u = 0; u < SPLIT_UNROLL; ++u) {
+                const int64_t v = v0 + u * (int64_t)blockDim.x;
+                xv[u] = v < n4 ? __ldcs(reinterpret_cast<const float4*>(X + b0 + 4 * v)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < SPLIT_UNROLL; ++u) {
+                const int64_t v = v0 + u * (int64_t)blockDim.x;
+                if (v >= n4) break;
+                const int64_t e = b0 + 4 * v;
+                const float4 x = xv[u];
+                uint2 hw, lw;
+                split_pair(x.x, x.y, hw.x, lw.x);
+                split_pair(x.z, x.w, hw.y, lw.y);
+                add_sq(x.x);
+                add_sq(x.y);
+                add_sq(x.z);
+                add_sq(x.w);
+                if (++cnt == 16) { flush(); cnt = 0; }
+                *reinterpret_cast<uint2*>(hi + e) = hw;
+                *reinterpret_cast<uint2*>(lo + e) = lw;
+            }
         }
         for (int64_t e = b0 + 4 * n4 + threadIdx.x; e < b1; e += blockDim.x) {
             const float x = X[e];
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            hi[e] = h;
-            lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+            split_one(x, hi[e], lo[e]);
             add_sq(x);
         }
     } else {
         for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
             const float x = X[e];
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            hi[e] = h;
-            lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+            split_one(x, hi[e], lo[e]);
             add_sq(x);
             if (++cnt == 64) { flush(); cnt = 0; }
         }
@@ -1086,22 +1105,32 @@ __global__ void __launch_bounds__(256) split_planes_padded_kernel(const float* _
         cmp = 0.0f;
     };
     const int64_t n4 = (b1 - b0) / 4;                    // b0, b1: multiples of 4 (I0p % 8 == 0)
-    for (int64_t v = threadIdx.x; v < n4; v += blockDim.x) {
-        const int64_t e = b0 + 4 * v;
-        const int64_t r = e / I0p;
-        const int64_t i0 = e - r * I0p;
-        const float* src = X + i0 + I0 * r;
-        float x[4];
+    for (int64_t v0 = threadIdx.x; v0 < n4; v0 += SPLIT_UNROLL * (int64_t)blockDim.x) {
+        float xv[SPLIT_UNROLL][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = (i0 + j < I0) ? src[j] : 0.0f;
-        uint2 hw, lw;
-        split_pair(x[0], x[1], hw.x, lw.x);
-        split_pair(x[2], x[3], hw.y, lw.y);
+        for (int u = 0; u < SPLIT_UNROLL; ++u) {
+            const int64_t v = v0 + u * (int64_t)blockDim.x;
+            const int64_t e = b0 + 4 * v;
+            const int64_t r = e / I0p;
+            const int64_t i0 = e - r * I0p;
+            const float* src = X + i0 + I0 * r;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) add_sq(x[j]);
-        if (++cnt == 16) { flush(); cnt = 0; }
-        *reinterpret_cast<uint2*>(hi + e) = hw;
-        *reinterpret_cast<uint2*>(lo + e) = lw;
+            for (int j = 0; j < 4; ++j) xv[u][j] = (v < n4 && i0 + j < I0) ? __ldcs(src + j) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < SPLIT_UNROLL; ++u) {
+            const int64_t v = v0 + u * (int64_t)blockDim.x;
+            if (v >= n4) break;
+            const int64_t e = b0 + 4 * v;
+            uint2 hw, lw;
+            split_pair(xv[u][0], xv[u][1], hw.x, lw.x);
+            split_pair(xv[u][2], xv[u][3], hw.y, lw.y);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) add_sq(xv[u][j]);
+            if (++cnt == 16) { flush(); cnt = 0; }
+            *reinterpret_cast<uint2*>(hi + e) = hw;
+            *reinterpret_cast<uint2*>(lo + e) = lw;
+        }
     }
     flush();
     __shared__ double red[256];
@@ -1114,12 +1143,15 @@ __global__ void __launch_bounds__(256) split_planes_padded_kernel(const float* _
     if (threadIdx.x == 0 && part) part[blockIdx.x] = red[0];
 }
 
+// one warp: lane l adds part[l], part[l + 32], ... in order, then a fixed shuffle tree
+// (a chain of n dependent FP64 adds on one thread took ~40 us for n = 1216)
 __global__ void sum_partials_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < n; ++k) s += part[k];
-        *out = s;
-    }
+    const int l = threadIdx.x;
+    double s = 0.0;
+    for (int k = l; k < n; k += 32) s += part[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0 && blockIdx.x == 0) *out = s;
 }
 
 // block: warp 0 tensor producer, warp 1 MMA issuer (TMEM owner), warp 2 image producer,

@@ -189,12 +189,14 @@ norm2_partial_kernel(const float* __restrict__ X, int64_t I, double* __restrict_
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// one warp: lane l adds part[l], part[l + 32], ... in order, then a fixed shuffle tree
 __global__ void sum_chunks_kernel(const double* __restrict__ part, int n, double* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < n; ++k) s += part[k];
-        *out = s;
-    }
+    const int l = threadIdx.x;
+    double s = 0.0;
+    for (int k = l; k < n; k += 32) s += part[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0 && blockIdx.x == 0) *out = s;
 }
 
 // r2 = ||X||^2 - 2 <M, U> + sum_{a,b} prod_k G_k(a,b)  (= ||X - [[U]]||^2 when M is the

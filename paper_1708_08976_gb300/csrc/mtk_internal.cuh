@@ -208,6 +208,7 @@ struct AlsUpdateArgs {
     uint32_t* status;
     bool programmatic;
     const void* hinv;          // H^{-1} from launch_als_factor (null: factored in the update)
+    bool normalize;            // scale U_n (and G_n) to unit columns; not with the fit
 };
 bool als_update_supported(int C);
 // H_n^{-1} (and its not-positive-definite flag) for a later update, in one CTA that

@@ -84,6 +84,70 @@ def test_split_planes_bits_and_norm(dims):
     assert abs(nx2.item() - ref) <= 1e-12 * ref
 
 
+def test_split_special_values():
+    """The rounding of the split against torch's round-to-nearest-even on the CPU, bit for
+    bit, at the edges: signed zeros, subnormals, ties to even in the normal and subnormal
+    ranges, the largest finite numbers (rounding up to infinity), infinities and NaN; both
+    the 4-wide path (I_0 % 8 == 0) and the padded one."""
+    f = np.float32
+    tiny = np.float32(2.0 ** -149)
+    vals = [0.0, -0.0, tiny, -tiny, 3 * tiny, 2.0 ** -126, -(2.0 ** -126) * (1 + 2.0 ** -8),
+            2.0 ** -133 * (1 + 2.0 ** -8), 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8),
+            1 + 2.0 ** -8 + 2.0 ** -20, 1 - 2.0 ** -24, np.finfo(f).max, -np.finfo(f).max,
+            3.3895314e38, 3.3961514e38, np.inf, -np.inf, np.nan, 65504.0, 1e-30, -7.0e-39]
+    base = np.array(vals, dtype=f)
+    g = np.random.default_rng(3)
+    for I0 in (8, 13):
+        n = I0 * 24
+        X = (g.standard_normal(n) * np.exp(g.uniform(-80, 80, n))).astype(f)
+        X[: base.size * 5: 5] = base
+        dims = (I0, 24)
+        Xd = torch.from_numpy(X).cuda()
+        Xs, _ = mtk.split_tensor(Xd, dims)
+        torch.cuda.synchronize()
+        lib = L.load()
+        I0p = lib.mtk_split_rows0(I0)
+        pitch = lib.mtk_split_pitch(L.dims_arr(list(dims)), 2)
+        hi, lo = planes_ref(Xd)
+        got = Xs.cpu()
+        idx = (torch.arange(I0).view(1, I0) + I0p * torch.arange(24).view(24, 1)).reshape(-1)
+        for a, b in ((got[idx], hi), (got[pitch + idx], lo)):
+            # NaN encodings differ between implementations: NaN where torch has NaN, the
+            # same bits everywhere else
+            na, nb = bf16_isnan(a), bf16_isnan(b)
+            assert torch.equal(na, nb), I0
+            assert torch.equal(a[~na], b[~nb]), I0
+
+
+def bf16_isnan(v: torch.Tensor) -> torch.Tensor:
+    w = v.to(torch.int32) & 0xFFFF
+    return ((w & 0x7F80) == 0x7F80) & ((w & 0x7F) != 0)
+
+
+@pytest.mark.parametrize("dims", [(165, 31, 7), (64, 48, 40), (1000,)])
+def test_split_from_pinned_host_memory(dims):
+    """The split reads a pinned host tensor in place: the same planes and the same ||X||^2,
+    bit for bit, as from the device copy; pageable host memory is refused before any launch."""
+    n_entries = int(np.prod(dims))
+    X = np.random.default_rng(7 + n_entries).standard_normal(n_entries).astype(np.float32)
+    Xh = torch.from_numpy(X).pin_memory()
+    Xs_d, nx_d = mtk.split_tensor(Xh.cuda(), dims)
+    Xs_h, nx_h = mtk.split_tensor(Xh, dims, device="cuda")
+    torch.cuda.synchronize()
+    lib = L.load()
+    d = L.dims_arr(list(dims))
+    nxp = lib.mtk_split_rows0(dims[0]) * (n_entries // dims[0])
+    pitch = lib.mtk_split_pitch(d, len(dims))
+    assert Xs_h.is_cuda
+    for a in (0, pitch):                             # the written entries of hi and lo
+        assert torch.equal(Xs_h[a:a + nxp], Xs_d[a:a + nxp])
+    assert nx_h.item() == nx_d.item()
+    ws = torch.zeros(lib.mtk_split_workspace(d, len(dims)), dtype=torch.uint8, device="cuda")
+    st = lib.mtk_split_tensor(X.ctypes.data, d, len(dims), Xs_h.data_ptr(), None, ws.data_ptr(), ws.numel(),
+                              torch.cuda.current_stream().cuda_stream)
+    assert st == L.MTK_EINVAL
+
+
 def run_split(X, dims, U, n, C, splits=0, with_x=True):
     Xd = to_dev(X, torch)
     Ud = factors_dev(U, torch)
@@ -220,10 +284,13 @@ def test_split_rejects_bad_options():
             mtk.mttkrp(Xd, dims, factors_dev(U, torch), 0, Xs=Xs, **kw)
 
 
-@pytest.mark.parametrize("case", ["tiny3", "all_planes"])
+@pytest.mark.parametrize("case", ["tiny3", "all_planes", "tiny3_host", "all_planes_host"])
 def test_als_sweep_split(case):
     """One CP-ALS sweep on the planes against the oracle's sweep (tiny3 has a mode that
-    falls back to the FP32 tensor)."""
+    falls back to the FP32 tensor).  *_host: X is a pinned host tensor, split in place and
+    (tiny3) read in place by the fallback mode."""
+    host = case.endswith("_host")
+    case = case.replace("_host", "")
     if case == "tiny3":
         X, dims, U = synth.tiny3()
     else:
@@ -231,7 +298,7 @@ def test_als_sweep_split(case):
     Xr = X.astype(np.float32).astype(np.float64)
     Ur = f32_round(U)
     ref_U, ref_fit = oracle.als_sweep(Xr, dims, Ur)
-    Xd = to_dev(X, torch)
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).pin_memory() if host else to_dev(X, torch)
     Ud = factors_dev(U, torch)
     als = mtk.ALS(Xd, dims, Ud, presplit=True)
     als.sweep()
