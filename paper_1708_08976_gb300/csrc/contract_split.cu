@@ -999,26 +999,11 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const float* __restri
     const int64_t b1 = (b0 + chunk < NX) ? b0 + chunk : NX;
     __nv_bfloat16* hi = Xs;
     __nv_bfloat16* lo = Xs + pitch;
-    // ||X||^2: each square is exact as p + e (p = x*x, e = fma(x, x, -p)); the p are summed
-    // with two-sum compensation in FP32 and (sum, compensation) are flushed into an FP64
-    // total every 64 entries, so the FP64 pipe (slow on this part) sees 2 adds per 64 entries
-    double ss = 0.0;
-    float S = 0.0f, cmp = 0.0f;
+    // ||X||^2 (SquareSum: no FP64 arithmetic until the end)
+    SquareSum sq;
     int cnt = 0;
-    auto add_sq = [&](float x) {
-        const float pp = x * x;
-        const float ee = fmaf(x, x, -pp);
-        const float t = S + pp;
-        const float z = t - S;
-        cmp += ((S - (t - z)) + (pp - z)) + ee;
-        S = t;
-    };
-    auto flush = [&]() {
-        ss += (double)S;
-        ss += (double)cmp;
-        S = 0.0f;
-        cmp = 0.0f;
-    };
+    auto add_sq = [&](float x) { sq.add(x); };
+    auto flush = [&]() { sq.flush(); };
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((reinterpret_cast<uintptr_t>(Xs) & 15) == 0) &&
                      (pitch % 4 == 0) && (chunk % 4 == 0);
     if (vec) {
@@ -1064,10 +1049,9 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const float* __restri
             if (++cnt == 64) { flush(); cnt = 0; }
         }
     }
-    flush();
     // fixed-order block reduction
     __shared__ double red[256];
-    red[threadIdx.x] = ss;
+    red[threadIdx.x] = sq.value();
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -1087,23 +1071,10 @@ __global__ void __launch_bounds__(256) split_planes_padded_kernel(const float* _
     const int64_t b1 = (b0 + chunk < NXp) ? b0 + chunk : NXp;
     __nv_bfloat16* hi = Xs;
     __nv_bfloat16* lo = Xs + pitch;
-    double ss = 0.0;
-    float S = 0.0f, cmp = 0.0f;
+    SquareSum sq;
     int cnt = 0;
-    auto add_sq = [&](float x) {
-        const float pp = x * x;
-        const float ee = fmaf(x, x, -pp);
-        const float t = S + pp;
-        const float z = t - S;
-        cmp += ((S - (t - z)) + (pp - z)) + ee;
-        S = t;
-    };
-    auto flush = [&]() {
-        ss += (double)S;
-        ss += (double)cmp;
-        S = 0.0f;
-        cmp = 0.0f;
-    };
+    auto add_sq = [&](float x) { sq.add(x); };
+    auto flush = [&]() { sq.flush(); };
     const int64_t n4 = (b1 - b0) / 4;                    // b0, b1: multiples of 4 (I0p % 8 == 0)
     for (int64_t v0 = threadIdx.x; v0 < n4; v0 += SPLIT_UNROLL * (int64_t)blockDim.x) {
         float xv[SPLIT_UNROLL][4];
@@ -1132,9 +1103,8 @@ __global__ void __launch_bounds__(256) split_planes_padded_kernel(const float* _
             *reinterpret_cast<uint2*>(lo + e) = lw;
         }
     }
-    flush();
     __shared__ double red[256];
-    red[threadIdx.x] = ss;
+    red[threadIdx.x] = sq.value();
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];

@@ -160,27 +160,46 @@ norm2_partial_kernel(const float* __restrict__ X, int64_t I, double* __restrict_
     __shared__ double red[256];
     const int64_t a = (int64_t)blockIdx.x * kNormChunk;
     const int64_t b = (a + kNormChunk < I) ? a + kNormChunk : I;
-    double acc = 0.0;
+    // exact squares, compensated FP32 sums of 64 entries, a double-FP32 total (SquareSum):
+    // no FP64 arithmetic in the loop (this part's FP64 pipe is narrow)
+    SquareSum sq;
+    int cnt = 0;
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     if (vec) {
-        // a is a multiple of 4 (kNormChunk is), so X + a stays 16-byte aligned
+        // a is a multiple of 4 (kNormChunk is), so X + a stays 16-byte aligned; four 16-byte
+        // loads in flight per thread
         const int64_t nv = (b - a) / 4;
         const float4* xv = reinterpret_cast<const float4*>(X + a);
-        for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
-            const float4 q = xv[v];
-            acc += (double)(q.x * q.x + q.y * q.y) + (double)(q.z * q.z + q.w * q.w);
+        for (int64_t v0 = threadIdx.x; v0 < nv; v0 += 4 * (int64_t)blockDim.x) {
+            float4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t v = v0 + u * (int64_t)blockDim.x;
+                q[u] = v < nv ? __ldcs(xv + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                sq.add(q[u].x);
+                sq.add(q[u].y);
+                sq.add(q[u].z);
+                sq.add(q[u].w);
+            }
+            if (++cnt == 4) {
+                sq.flush();
+                cnt = 0;
+            }
         }
-        for (int64_t e = a + nv * 4 + threadIdx.x; e < b; e += blockDim.x) {
-            const float q = X[e];
-            acc += (double)(q * q);
-        }
+        for (int64_t e = a + nv * 4 + threadIdx.x; e < b; e += blockDim.x) sq.add(X[e]);
     } else {
         for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
-            const float q = X[e];
-            acc += (double)(q * q);
+            sq.add(X[e]);
+            if (++cnt == 64) {
+                sq.flush();
+                cnt = 0;
+            }
         }
     }
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = sq.value();
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
