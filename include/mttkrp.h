@@ -227,7 +227,7 @@ int mtk_ffma_probe(int ctas_per_sm, int iters, float* out, double* flops, void* 
  * (n0 (n0 + 1) / 2 rows).  diag = 0 (the paper's layout: 200 regions -> 19,900 rows): only
  * a > b, p = a (a - 1) / 2 + b (n0 (n0 - 1) / 2 rows), and the tensor is taken to be zero
  * on its diagonal a = b.  Pp = mtk_sym_packed_rows(n0, diag) is the row count rounded up to
- * a multiple of 8; the padding rows hold zeros.  The packed tensor has about half the
+ * a multiple of 8, or of 64 from 2048 rows on; the padding rows hold zeros.  The packed tensor has about half the
  * entries of the full one.
  * mtk_pack_symmetric: Xp (device, Pp * prod(dims[2..N-1]) floats) from the full tensor X
  * (device, natural order); only the entries with a >= b (a > b) are read: the tensor is

@@ -51,7 +51,8 @@ def packed_numpy(X, dims, diag):
     n0 = dims[0]
     rest = int(np.prod(dims[2:]))
     rows = n0 * (n0 + 1) // 2 if diag else n0 * (n0 - 1) // 2
-    Pp = (rows + 7) // 8 * 8
+    m = 64 if rows >= 2048 else 8
+    Pp = (rows + m - 1) // m * m
     X3 = X.reshape(rest, n0, n0)                   # [r, b, a]
     out = np.zeros((rest, Pp), dtype=X.dtype)
     p = 0

@@ -234,9 +234,11 @@ def test_symmetric_packed_sizes_and_shapes():
     200x200x300x40 workload and of small 3- to 5-way shapes, and refuses unequal modes 0/1,
     N = 2 and a diag other than 0/1 (workspace 0) and bad pointers before a launch."""
     lib = L.load()
-    assert [lib.mtk_sym_packed_rows(n, 1) for n in (1, 2, 3, 4, 12, 200)] == [8, 8, 8, 16, 80, 20104]
+    assert [lib.mtk_sym_packed_rows(n, 1) for n in (1, 2, 3, 4, 12, 200)] == [8, 8, 8, 16, 80, 20160]
     assert [lib.mtk_sym_packed_rows(n, 0) for n in (1, 2, 3, 5, 12, 200)] == [0, 8, 8, 16, 72, 19904]
     assert lib.mtk_sym_packed_rows(12, 2) == 0
+    # from 2048 rows on, a multiple of 64: 63 * 64 / 2 = 2016 rows -> 2016, 64 * 65 / 2 = 2080 -> 2112
+    assert [lib.mtk_sym_packed_rows(n, 1) for n in (62, 63, 64)] == [1960, 2016, 2112]
     o = L.opts()
     for dims, C in (((200, 200, 300, 40), 25), ((12, 12, 40), 8), ((13, 13, 24, 5), 16), ((10, 10, 8, 6, 3), 7)):
         d = L.dims_arr(list(dims))
