@@ -8,40 +8,48 @@
 // the same kernel is the GEMM of the materialised-KRP path and of the 2-step
 // partial MTTKRP (Algorithm 4).
 //
-// Decomposition: grid = (i-tiles of 64, contraction splits S, column blocks of
-// 32).  Each CTA owns a contiguous k-range (the private partial result of
-// Algorithm 3), stages X tiles through a 3-deep cp.async ring (16-byte copies when
-// the rows allow it, else 4-byte ones; zero-filled outside the tensor) and generates
-// the matching 32 x 32 block of W in shared memory.  Its 256 threads are 8 k-groups
-// (one per warp, four k of every 32-k stage each) x 16 row groups x 2 column groups:
-// a thread accumulates a 4 x 16 register tile, reading per k one 16-byte word of X
-// (or a word of four k) and four broadcast words of W, so 20 shared loads feed 256
-// FMAs per stage.  The eight k-groups are summed in shared memory in a fixed tree
-// order; partials of the S splits are summed in split order by split_reduce_kernel
-// (the parallel reduction of Algorithm 3), so results are deterministic.
+// Decomposition: grid = (i-tiles of 64, contraction splits S, column blocks of 2 TC).
+// Each CTA owns a contiguous k-range (the private partial result of Algorithm 3), stages
+// X tiles of 64 k through a 4-deep cp.async ring (16-byte copies when the rows allow it,
+// else 4-byte ones; zero-filled outside the tensor) and generates the matching 64 x 2 TC
+// block of W in shared memory.  Its 256 threads are 8 k-groups (one per warp, eight k of
+// every 64-k stage each) x 16 row groups x 2 column groups: a thread accumulates the rows
+// ig + 16 a (a = 0..3) x TC columns, so a row group past the end of a ragged tile is
+// skipped by a whole warp.  Per stage a thread issues 8 x 4 x TC FMAs against 8 (K-major)
+// or 32 (MN-major) shared loads of X and 8 x ceil(TC / 4) of W.  The eight k-groups are
+// summed in shared memory in a fixed tree order; partials of the S splits are summed in
+// split order by split_reduce_kernel (the parallel reduction of Algorithm 3), so results
+// are deterministic.
 //
-// Layouts of an X stage: rows of i with k contiguous ([i][k]) when the view has
-// I^L > 1 (consecutive k are consecutive l in the tensor), columns of i ([k][i]) when
-// I^L = 1 (consecutive i are contiguous).
+// Layouts of an X stage: rows of i with k contiguous ([i][k]) when the view has I^L > 1
+// (consecutive k are consecutive l in the tensor), columns of i ([k][i]) when I^L = 1
+// (consecutive i are contiguous).
+//
+// 64-k stages (32 before) halve the per-FMA share of the per-stage work (copies, the W
+// block, the barrier); with the row groups ig + 16 a the ragged last tile of a mode with
+// few rows costs at most 15 extra rows instead of up to 63.
 #include "mtk_internal.cuh"
 
 namespace mtk {
 namespace {
 
-constexpr int BK = 32;        // k per stage
+constexpr int BK = 64;        // k per stage (the planner's split quantum and minimum head)
 constexpr int BI = 64;        // i per CTA tile
 constexpr int CB = 32;        // W stage slots per row: two groups of 16, the first TC of each used
 constexpr int NKG = 8;        // k-groups per CTA (one warp each)
+constexpr int KPG = BK / NKG; // k per group per stage
 constexpr int THREADS = 256;
 #ifndef MTK_SIMT_STAGES
-#define MTK_SIMT_STAGES 5
+#define MTK_SIMT_STAGES 4
 #endif
-constexpr int STAGES = MTK_SIMT_STAGES;   // X ring depth: 4 stages (32 KB) in flight per CTA
+constexpr int STAGES = MTK_SIMT_STAGES;   // X ring depth (3 stages, 52 KB, in flight per CTA)
 constexpr int XPK = BK + 4;   // [i][k] stage: row pitch (floats)
 constexpr int XPM = BI + 4;   // [k][i] stage: row pitch
 constexpr int WP = CB + 4;    // W stage row pitch
 constexpr int RP = CB + 4;    // reduction row pitch
 constexpr int XSTAGE = (BI * XPK > BK * XPM) ? BI * XPK : BK * XPM;
+constexpr int XWORDS = BK * BI / 4 / THREADS;   // 16-byte copies per thread per stage (4)
+constexpr int WROWS = BK * CB / THREADS;        // W values per thread per stage (8)
 
 struct __align__(16) SimtSmem {
     union {
@@ -88,6 +96,7 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int64_t ke = (kb + p.kchunk < p.K) ? kb + p.kchunk : p.K;
     const int nst = (int)((ke - kb + BK - 1) / BK);
     const KrpOperand& W = p.W;
+    const int rows_left = (I - i0) < BI ? (int)(I - i0) : BI;      // valid rows of this tile
 
     // uniform trackers of the stage start: (l, r) for X, (d0, q) for W
     int64_t xl = kb % L, xr = kb / L;            // X issue tracker (scalar copies)
@@ -95,17 +104,15 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     int64_t qcached = -1;
     const int64_t qtot = p.K / W.rad0;           // number of q values (rows of Q)
 
-    // 16-byte copies: each thread issues two words of four floats per stage at fixed
-    // positions of the stage tile, and keeps their tensor offsets, advancing them by
-    // constants from one stage to the next (no 64-bit products in the loop).
-    //  KM: words (ii, k4) and (ii + 32, k4), ii = t / 8, k4 = t % 8: four k of one row of
-    //      the tensor (I^L % 4 == 0); offset l + I^L i + I^L I_n r, l = xl + 4 k4.
-    //  MN: words (kk, i4) and (kk + 16, i4), kk = t / 16, i4 = t % 16: four consecutive i
-    //      of one k; offset k I_n + i.
-    const int vk = KM ? 4 * (t & 7) : (t >> 4);           // k of the word within the stage
-    const int vi = KM ? (t >> 3) : 4 * (t & 15);          // row of the word within the tile
-    const bool vrow0 = KM ? (i0 + vi < I) : (i0 + vi < I);
-    const bool vrow1 = KM ? (i0 + vi + 32 < I) : vrow0;
+    // 16-byte copies: each thread issues XWORDS words of four floats per stage at fixed
+    // positions of the stage tile, 16 rows apart, and keeps the first word's tensor offset,
+    // advancing it by constants from one stage to the next (no 64-bit products in the loop).
+    //  KM: words (vi + 16 m, vk), vi = t / 16, vk = 4 (t % 16): four k of one row of the
+    //      tensor (I^L % 4 == 0); offset l + I^L i + I^L I_n r, l = xl + vk.
+    //  MN: words (vk + 16 m, vi), vk = t / 16, vi = 4 (t % 16): four consecutive i of one k;
+    //      offset k I_n + i.
+    const int vk = KM ? 4 * (t & 15) : (t >> 4);          // k of the word within the stage
+    const int vi = KM ? (t >> 4) : 4 * (t & 15);          // row of the word within the tile
     int64_t vl = 0, voff = 0;                             // KM: the word's l; its tensor offset
     if (VEC) {
         if (KM) {
@@ -117,37 +124,43 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
             voff = (kb + vk) * I + i0 + vi;
         }
     }
-    const int64_t vrow_step = KM ? 32 * L : 16 * I;       // offset of the second word
+    const int64_t vstep = KM ? 16 * L : 16 * I;           // offset between a thread's words
     const int64_t vwrap = L * (I - 1);                    // KM: end of row (i, r) -> (i, r + 1)
 
-    auto issue_x = [&](int s) {
-        float* dst = sm.pipe.xs[s % STAGES];
+    auto issue_x = [&](int s, int slot) {
+        float* dst = sm.pipe.xs[slot];
         const int64_t ks = kb + (int64_t)s * BK;
+        const int kvalid = (ke - ks) < BK ? (int)(ke - ks) : BK;   // k of this stage in the range
         if (VEC) {
-            const bool kval = ks + vk < ke;
-            const bool v0 = kval && vrow0, v1 = kval && vrow1;
             if (KM) {
-                cp_async16(dst + vi * XPK + vk, p.X + (v0 ? voff : 0), v0);
-                cp_async16(dst + (vi + 32) * XPK + vk, p.X + (v1 ? voff + vrow_step : 0), v1);
+                const bool kval = vk < kvalid;
+#pragma unroll
+                for (int m = 0; m < XWORDS; ++m) {
+                    const bool v = kval && vi + 16 * m < rows_left;
+                    cp_async16(dst + (vi + 16 * m) * XPK + vk, p.X + (v ? voff + m * vstep : 0), v);
+                }
                 voff += BK;
                 vl += BK;
                 while (vl >= L) { vl -= L; voff += vwrap; }
             } else {
-                const bool v2 = ks + vk + 16 < ke && vrow0;
-                cp_async16(dst + vk * XPM + vi, p.X + (v0 ? voff : 0), v0);
-                cp_async16(dst + (vk + 16) * XPM + vi, p.X + (v2 ? voff + vrow_step : 0), v2);
+                const bool ival = vi < rows_left;
+#pragma unroll
+                for (int m = 0; m < XWORDS; ++m) {
+                    const bool v = ival && vk + 16 * m < kvalid;
+                    cp_async16(dst + (vk + 16 * m) * XPM + vi, p.X + (v ? voff + m * vstep : 0), v);
+                }
                 voff += (int64_t)BK * I;
             }
         } else {
             for (int e = t; e < BK * BI; e += THREADS) {
                 int kk, ii;
                 if (KM) { kk = e % BK; ii = e / BK; } else { ii = e % BI; kk = e / BI; }
-                const int64_t k = ks + kk, i = i0 + ii;
-                const bool valid = (k < ke) && (i < I);
+                const int64_t i = i0 + ii;
+                const bool valid = (kk < kvalid) && (ii < rows_left);
                 int64_t off = 0;
                 if (valid) {
                     if (L == 1) {
-                        off = k * I;
+                        off = (ks + kk) * I;
                     } else {
                         int64_t l = xl + kk, r = xr;
                         while (l >= L) { l -= L; ++r; }
@@ -164,16 +177,18 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
 
     // W stage s into ws[s & 1].  Thread t forms slot wcc = t % 32 (column group wcc / 16,
     // column wcc % 16 of it when below TC, else a zero pad) of rows kk = t / 32 + 8 m
-    // (m = 0..3).  The factor entries of the next stage are loaded into registers before
+    // (m = 0..7).  The factor entries of the next stage are loaded into registers before
     // the current stage's FMAs and multiplied by the tail scale Q(q, cc) and stored after
     // them, so their L2 latency is hidden.  The head has >= BK rows whenever there is a
-    // tail, so a stage spans at most two q; the thread keeps Q(q, cc) for the stage's
-    // first q and the next in registers, formed again only when q moves.
+    // tail, so a stage spans at most two q: rows kk < wlim of the stage have the stage's
+    // first q, the others the next; the thread keeps Q(q, cc) for both in registers, formed
+    // again only when q moves.
     const int wcc = t & (CB - 1), wk0 = t / CB;
     const int wsj = wcc & 15;
     const int wc = wsj < TC ? c0 + (wcc >> 4) * TC + wsj : C;     // C: a pad slot (zero)
-    float wraw[4];
+    float wraw[WROWS];
     float q0 = 1.0f, q1 = 1.0f;
+    int wlim = BK, wkval = BK;                   // rows before the q step; rows in the range
     // digits of q = wq over the tail factors (first fastest), kept by +1 steps: wq moves by
     // at most one per stage (the head has >= BK rows), so no division in the loop
     int qd[MTK_MAXN];
@@ -204,18 +219,20 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int64_t wwrap = W.rad0 * C;
     auto load_w = [&](int s) {
         const int64_t ks = kb + (int64_t)s * BK;
+        wkval = (ke - ks) < BK ? (int)(ke - ks) : BK;
+        wlim = (W.ntail > 0 && W.rad0 - wd < BK) ? (int)(W.rad0 - wd) : BK;
         if (W.ntail > 0 && wq != qcached) {
             q0 = (wc < C && wq < qtot) ? q_from(false) : 0.0f;
             q1 = (wc < C && wq + 1 < qtot) ? q_from(true) : 0.0f;
             qcached = wq;
         }
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < WROWS; ++m) {
             const int kk = wk0 + (THREADS / CB) * m;
             float w = 0.0f;
-            if (ks + kk < ke && wc < C) {
+            if (kk < wkval && wc < C) {
                 const float* ptr = wp0 + (THREADS / CB) * m * C;
-                if (W.ntail > 0 && wd + kk >= W.rad0) ptr -= wwrap;
+                if (kk >= wlim) ptr -= wwrap;
                 w = __ldg(ptr);
             }
             wraw[m] = w;
@@ -224,10 +241,10 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     auto store_w = [&](int s) {
         float* dst = &sm.pipe.ws[s & 1][0][0];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < WROWS; ++m) {
             const int kk = wk0 + (THREADS / CB) * m;
             float w = wraw[m];
-            if (W.ntail > 0) w *= (wd + kk >= W.rad0) ? q1 : q0;
+            if (W.ntail > 0) w *= kk >= wlim ? q1 : q0;
             dst[kk * WP + wcc] = w;
         }
     };
@@ -250,22 +267,26 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < TC; ++b) acc[a][b] = 0.0f;
-    bool arow[4];                        // K-major: row group a has a row of the tensor
+    bool arow[4];                        // row group a (rows ig + 16 a) has a row of the tensor
 #pragma unroll
-    for (int a = 0; a < 4; ++a) arow[a] = i0 + 16 * a < I;
+    for (int a = 0; a < 4; ++a) arow[a] = 16 * a < rows_left;
 
+    int islot = 0;                       // ring slot of the next stage to issue
     for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < nst) issue_x(s); else cp_async_commit();
+        if (s < nst) issue_x(s, islot); else cp_async_commit();
+        islot = islot + 1 == STAGES ? 0 : islot + 1;
     }
     if (nst > 0) {
         load_w(0);
         store_w(0);
     }
 
+    int cslot = 0;                       // ring slot of the stage being consumed
     for (int s = 0; s < nst; ++s) {
         cp_async_wait<STAGES - 2>();
         __syncthreads();
-        if (s + STAGES - 1 < nst) issue_x(s + STAGES - 1); else cp_async_commit();
+        if (s + STAGES - 1 < nst) issue_x(s + STAGES - 1, islot); else cp_async_commit();
+        islot = islot + 1 == STAGES ? 0 : islot + 1;
         // the next stage's factor entries, in flight during this stage's FMAs
         const bool more = s + 1 < nst;
         if (more) {
@@ -273,45 +294,41 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
             load_w(s + 1);
         }
 
-        const float* xs = sm.pipe.xs[s % STAGES];
+        const float* xs = sm.pipe.xs[cslot];
         const float* ws = &sm.pipe.ws[s & 1][0][0];
-        float xv[4][4];                  // [row a][k j]
-        if (KM) {
-            // rows ig + 16 a (16 consecutive rows per load: conflict-free words)
+        cslot = cslot + 1 == STAGES ? 0 : cslot + 1;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float4 v = *reinterpret_cast<const float4*>(xs + (ig + 16 * a) * XPK + 4 * kg);
-                xv[a][0] = v.x; xv[a][1] = v.y; xv[a][2] = v.z; xv[a][3] = v.w;
-            }
-        } else {
-            // rows 4 ig .. 4 ig + 3
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float4 v = *reinterpret_cast<const float4*>(xs + (4 * kg + j) * XPM + 4 * ig);
-                xv[0][j] = v.x; xv[1][j] = v.y; xv[2][j] = v.z; xv[3][j] = v.w;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float* wr = ws + (4 * kg + j) * WP + 16 * cg;
-#pragma unroll
-            for (int q = 0; q < (TC + 3) / 4; ++q) {
-                float w[4];
-                if (4 * q + 3 < TC) {
-                    const float4 w4 = *reinterpret_cast<const float4*>(wr + 4 * q);
-                    w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) w[e] = 4 * q + e < TC ? wr[4 * q + e] : 0.0f;
-                }
+        for (int h = 0; h < KPG / 4; ++h) {
+            float xv[4][4];              // [row group a][k j of this half]
+            if (KM) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    // K-major rows ig + 16 a: a group beyond the last row of a ragged tile is
-                    // skipped by the whole warp
-                    if (KM && !arow[a]) continue;
+                    const float4 v = *reinterpret_cast<const float4*>(xs + (ig + 16 * a) * XPK + KPG * kg + 4 * h);
+                    xv[a][0] = v.x; xv[a][1] = v.y; xv[a][2] = v.z; xv[a][3] = v.w;
+                }
+            } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (4 * q + e < TC) acc[a][4 * q + e] = fmaf(xv[a][j], w[e], acc[a][4 * q + e]);
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xv[a][j] = xs[(KPG * kg + 4 * h + j) * XPM + ig + 16 * a];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float* wr = ws + (KPG * kg + 4 * h + j) * WP + 16 * cg;
+                float w[TC];
+#pragma unroll
+                for (int q = 0; q < TC / 4; ++q) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(wr + 4 * q);
+                    w[4 * q] = w4.x; w[4 * q + 1] = w4.y; w[4 * q + 2] = w4.z; w[4 * q + 3] = w4.w;
+                }
+#pragma unroll
+                for (int e = (TC / 4) * 4; e < TC; ++e) w[e] = wr[e];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    // a row group past the last row of a ragged tile is skipped by the whole warp
+                    if (!arow[a]) continue;
+#pragma unroll
+                    for (int b = 0; b < TC; ++b) acc[a][b] = fmaf(xv[a][j], w[b], acc[a][b]);
                 }
             }
         }
@@ -321,27 +338,26 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     __syncthreads();
 
     // fixed-order reduction over the k-groups: (g, g + 4), then (g, g + 2), then (0, 1)
-    auto row_of = [&](int a) { return KM ? ig + 16 * a : 4 * ig + a; };
     for (int half = NKG / 2; half >= 1; half >>= 1) {
         if (kg >= half && kg < 2 * half) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < TC; ++b) sm.red[kg - half][row_of(a)][16 * cg + b] = acc[a][b];
+                for (int b = 0; b < TC; ++b) sm.red[kg - half][ig + 16 * a][16 * cg + b] = acc[a][b];
         }
         __syncthreads();
         if (kg < half) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < TC; ++b) acc[a][b] += sm.red[kg][row_of(a)][16 * cg + b];
+                for (int b = 0; b < TC; ++b) acc[a][b] += sm.red[kg][ig + 16 * a][16 * cg + b];
         }
         __syncthreads();
     }
     if (kg == 0) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const int64_t i = i0 + row_of(a);
+            const int64_t i = i0 + ig + 16 * a;
             if (i >= I) continue;
 #pragma unroll
             for (int b = 0; b < TC; ++b) {
