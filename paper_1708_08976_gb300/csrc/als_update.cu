@@ -474,18 +474,32 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
             } else if (!bad) {
                 // L y = m, z = D^{-1} y, L^T u = z in FP64, one column per lane, the solved
                 // entry broadcast by a shuffle
+                // (the second column per lane only when C > 32: a uniform branch, so that the
+                // FP64 pipe, narrow on this part, issues no dead instructions)
                 double s0 = (double)m0, s1 = (double)m1;
-                for (int k = 0; k < C; ++k) {
-                    const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
-                    if (j0 > k && j0 < C) s0 = fma(-A[k * C + j0], y, s0);
-                    if (j1 > k && j1 < C) s1 = fma(-A[k * C + j1], y, s1);
-                }
-                if (j0 < C) s0 *= dinv[j0];
-                if (j1 < C) s1 *= dinv[j1];
-                for (int k = C - 1; k >= 0; --k) {
-                    const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
-                    if (j0 < k) s0 = fma(-A[k * C + j0], y, s0);
-                    if (j1 < k && j1 < C) s1 = fma(-A[k * C + j1], y, s1);
+                if (C > 32) {
+                    for (int k = 0; k < C; ++k) {
+                        const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
+                        if (j0 > k) s0 = fma(-A[k * C + j0], y, s0);
+                        if (j1 > k && j1 < C) s1 = fma(-A[k * C + j1], y, s1);
+                    }
+                    s0 *= dinv[j0];
+                    if (j1 < C) s1 *= dinv[j1];
+                    for (int k = C - 1; k >= 0; --k) {
+                        const double y = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
+                        if (j0 < k) s0 = fma(-A[k * C + j0], y, s0);
+                        if (j1 < k && j1 < C) s1 = fma(-A[k * C + j1], y, s1);
+                    }
+                } else {
+                    for (int k = 0; k < C; ++k) {
+                        const double y = __shfl_sync(0xffffffffu, s0, k);
+                        if (j0 > k && j0 < C) s0 = fma(-A[k * C + j0], y, s0);
+                    }
+                    if (j0 < C) s0 *= dinv[j0];
+                    for (int k = C - 1; k >= 0; --k) {
+                        const double y = __shfl_sync(0xffffffffu, s0, k);
+                        if (j0 < k) s0 = fma(-A[k * C + j0], y, s0);
+                    }
                 }
                 u0 = (float)s0;
                 u1 = (float)s1;

@@ -37,7 +37,6 @@ namespace {
 
 constexpr int kBK = 64;           // the W operand needs rad0 >= kBK (or no tail factors)
 constexpr int kTcBK = 64;         // k per tensor-core stage; tensor-core splits are multiples
-constexpr int kSimtBI = 64;
 constexpr int kNoAllocMaxDevices = 64;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -158,13 +157,13 @@ ContractPlan plan_contract(int64_t I, int64_t K, int C, int precision, int split
     ContractPlan pl;
     pl.image_bytes = 0;
     pl.tc = ((precision == MTK_PREC_BF16X2 || precision == MTK_PREC_BF16X3) && tc_ok) ? 1 : 0;
-    const int BI = pl.tc ? BI_tc : kSimtBI;
+    const int BI = pl.tc ? BI_tc : simt_tile_rows(I);
     pl.i_tiles = (int)((I + BI - 1) / BI);
     pl.c_blocks = pl.tc ? 1 : (C + simt_cta_cols(C) - 1) / simt_cta_cols(C);
     const int64_t quantum = pl.tc ? kTcBK : kBK;            // split boundaries: whole stages
     int64_t S = splits;
     if (S <= 0) {
-        const int64_t target = (int64_t)num_sms() * 2;                    // CTAs resident per wave
+        const int64_t target = (int64_t)num_sms() * (pl.tc ? 2 : simt_ctas_per_sm(I));   // CTAs per wave
         const int64_t tiles = (int64_t)pl.i_tiles * pl.c_blocks;
         S = target / tiles;
         const int64_t maxS = (K + 4 * kTcBK - 1) / (4 * kTcBK);   // >= 4 stages per split

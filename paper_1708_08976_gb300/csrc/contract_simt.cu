@@ -34,7 +34,6 @@ namespace mtk {
 namespace {
 
 constexpr int BK = 64;        // k per stage (the planner's split quantum and minimum head)
-constexpr int BI = 64;        // i per CTA tile
 constexpr int CB = 32;        // W stage slots per row: two groups of 16, the first TC of each used
 constexpr int NKG = 8;        // k-groups per CTA (one warp each)
 constexpr int KPG = BK / NKG; // k per group per stage
@@ -44,20 +43,28 @@ constexpr int THREADS = 256;
 #endif
 constexpr int STAGES = MTK_SIMT_STAGES;   // X ring depth (3 stages, 52 KB, in flight per CTA)
 constexpr int XPK = BK + 4;   // [i][k] stage: row pitch (floats)
-constexpr int XPM = BI + 4;   // [k][i] stage: row pitch
 constexpr int WP = CB + 4;    // W stage row pitch
 constexpr int RP = CB + 4;    // reduction row pitch
-constexpr int XSTAGE = (BI * XPK > BK * XPM) ? BI * XPK : BK * XPM;
-constexpr int XWORDS = BK * BI / 4 / THREADS;   // 16-byte copies per thread per stage (4)
 constexpr int WROWS = BK * CB / THREADS;        // W values per thread per stage (8)
 
+// RA rows per thread (rows ig + 16 a, a < RA): a CTA tile of BI = 16 RA rows
+template <int RA>
+struct SimtTile {
+    static constexpr int BI = 16 * RA;
+    static constexpr int XPM = BI + 4;          // [k][i] stage: row pitch
+    static constexpr int XSTAGE = (BI * XPK > BK * XPM) ? BI * XPK : BK * XPM;
+    static constexpr int XWORDS = BK * BI / 4 / THREADS;   // 16-byte copies per thread per stage
+    static constexpr int MN_WPR = BI / 4;                  // MN: 16-byte words per k row
+};
+
+template <int RA>
 struct __align__(16) SimtSmem {
     union {
         struct {
-            float xs[STAGES][XSTAGE];
+            float xs[STAGES][SimtTile<RA>::XSTAGE];
             float ws[2][BK][WP];
         } pipe;
-        float red[NKG / 2][BI][RP];
+        float red[NKG / 2][SimtTile<RA>::BI][RP];
     };
 };
 
@@ -79,12 +86,18 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // multiple of 4; else I_n a multiple of 4; the tensor 16-byte aligned, split starts at
 // multiples of BK).
 // TC: columns per thread (8, 13 or 16), so a CTA covers 2 TC columns of M: the fewest
-// that hold C (C = 25 in 26 instead of 32).
-template <bool KM, bool VEC, int TC>
-__global__ void __launch_bounds__(THREADS, 2)
+// that hold C (C = 25 in 26 instead of 32).  RA: rows per thread (4: 64-row tiles, two
+// CTAs per SM; 8 would give 128-row tiles, one CTA per SM, twice the FMAs per shared load
+// of W, and measured slower).
+template <bool KM, bool VEC, int TC, int RA>
+__global__ void __launch_bounds__(THREADS, RA == 4 ? 2 : 1)
 contract_simt_kernel(const __grid_constant__ ContractParams p) {
+    constexpr int BI = SimtTile<RA>::BI;
+    constexpr int XPM = SimtTile<RA>::XPM;
+    constexpr int XWORDS = SimtTile<RA>::XWORDS;
+    constexpr int WPR = SimtTile<RA>::MN_WPR;
     extern __shared__ __align__(16) uint8_t simt_smem_raw[];
-    SimtSmem& sm = *reinterpret_cast<SimtSmem*>(simt_smem_raw);
+    SimtSmem<RA>& sm = *reinterpret_cast<SimtSmem<RA>*>(simt_smem_raw);
     const int t = threadIdx.x;
     const int cg = t & 1, ig = (t >> 1) & 15, kg = t >> 5;
     const int64_t i0 = (int64_t)blockIdx.x * BI;
@@ -105,14 +118,15 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     const int64_t qtot = p.K / W.rad0;           // number of q values (rows of Q)
 
     // 16-byte copies: each thread issues XWORDS words of four floats per stage at fixed
-    // positions of the stage tile, 16 rows apart, and keeps the first word's tensor offset,
-    // advancing it by constants from one stage to the next (no 64-bit products in the loop).
+    // positions of the stage tile and keeps the first word's tensor offset, advancing it by
+    // constants from one stage to the next (no 64-bit products in the loop).
     //  KM: words (vi + 16 m, vk), vi = t / 16, vk = 4 (t % 16): four k of one row of the
     //      tensor (I^L % 4 == 0); offset l + I^L i + I^L I_n r, l = xl + vk.
-    //  MN: words (vk + 16 m, vi), vk = t / 16, vi = 4 (t % 16): four consecutive i of one k;
-    //      offset k I_n + i.
-    const int vk = KM ? 4 * (t & 15) : (t >> 4);          // k of the word within the stage
-    const int vi = KM ? (t >> 4) : 4 * (t & 15);          // row of the word within the tile
+    //  MN: words (vk + (256 / WPR) m, vi), vk = t / WPR, vi = 4 (t % WPR): four consecutive
+    //      i of one k (WPR = BI / 4 words per k row); offset k I_n + i.
+    constexpr int MN_KSTEP = THREADS / WPR;               // MN: k between a thread's words
+    const int vk = KM ? 4 * (t & 15) : (t / WPR);         // k of the word within the stage
+    const int vi = KM ? (t >> 4) : 4 * (t % WPR);         // row of the word within the tile
     int64_t vl = 0, voff = 0;                             // KM: the word's l; its tensor offset
     if (VEC) {
         if (KM) {
@@ -124,7 +138,7 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
             voff = (kb + vk) * I + i0 + vi;
         }
     }
-    const int64_t vstep = KM ? 16 * L : 16 * I;           // offset between a thread's words
+    const int64_t vstep = KM ? 16 * L : MN_KSTEP * I;     // offset between a thread's words
     const int64_t vwrap = L * (I - 1);                    // KM: end of row (i, r) -> (i, r + 1)
 
     auto issue_x = [&](int s, int slot) {
@@ -146,8 +160,8 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
                 const bool ival = vi < rows_left;
 #pragma unroll
                 for (int m = 0; m < XWORDS; ++m) {
-                    const bool v = ival && vk + 16 * m < kvalid;
-                    cp_async16(dst + (vk + 16 * m) * XPM + vi, p.X + (v ? voff + m * vstep : 0), v);
+                    const bool v = ival && vk + MN_KSTEP * m < kvalid;
+                    cp_async16(dst + (vk + MN_KSTEP * m) * XPM + vi, p.X + (v ? voff + m * vstep : 0), v);
                 }
                 voff += (int64_t)BK * I;
             }
@@ -262,14 +276,14 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
         }
     };
 
-    float acc[4][TC];
+    float acc[RA][TC];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
         for (int b = 0; b < TC; ++b) acc[a][b] = 0.0f;
-    bool arow[4];                        // row group a (rows ig + 16 a) has a row of the tensor
+    bool arow[RA];                       // row group a (rows ig + 16 a) has a row of the tensor
 #pragma unroll
-    for (int a = 0; a < 4; ++a) arow[a] = 16 * a < rows_left;
+    for (int a = 0; a < RA; ++a) arow[a] = 16 * a < rows_left;
 
     int islot = 0;                       // ring slot of the next stage to issue
     for (int s = 0; s < STAGES - 1; ++s) {
@@ -299,10 +313,10 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
         cslot = cslot + 1 == STAGES ? 0 : cslot + 1;
 #pragma unroll
         for (int h = 0; h < KPG / 4; ++h) {
-            float xv[4][4];              // [row group a][k j of this half]
+            float xv[RA][4];             // [row group a][k j of this half]
             if (KM) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < RA; ++a) {
                     const float4 v = *reinterpret_cast<const float4*>(xs + (ig + 16 * a) * XPK + KPG * kg + 4 * h);
                     xv[a][0] = v.x; xv[a][1] = v.y; xv[a][2] = v.z; xv[a][3] = v.w;
                 }
@@ -310,7 +324,7 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) xv[a][j] = xs[(KPG * kg + 4 * h + j) * XPM + ig + 16 * a];
+                    for (int a = 0; a < RA; ++a) xv[a][j] = xs[(KPG * kg + 4 * h + j) * XPM + ig + 16 * a];
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -324,7 +338,7 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
 #pragma unroll
                 for (int e = (TC / 4) * 4; e < TC; ++e) w[e] = wr[e];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < RA; ++a) {
                     // a row group past the last row of a ragged tile is skipped by the whole warp
                     if (!arow[a]) continue;
 #pragma unroll
@@ -341,14 +355,14 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     for (int half = NKG / 2; half >= 1; half >>= 1) {
         if (kg >= half && kg < 2 * half) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < RA; ++a)
 #pragma unroll
                 for (int b = 0; b < TC; ++b) sm.red[kg - half][ig + 16 * a][16 * cg + b] = acc[a][b];
         }
         __syncthreads();
         if (kg < half) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < RA; ++a)
 #pragma unroll
                 for (int b = 0; b < TC; ++b) acc[a][b] += sm.red[kg][ig + 16 * a][16 * cg + b];
         }
@@ -356,7 +370,7 @@ contract_simt_kernel(const __grid_constant__ ContractParams p) {
     }
     if (kg == 0) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < RA; ++a) {
             const int64_t i = i0 + ig + 16 * a;
             if (i >= I) continue;
 #pragma unroll
@@ -385,20 +399,32 @@ __global__ void split_reduce_kernel(const float* __restrict__ part, int S, int64
 }  // namespace
 
 int simt_cta_cols(int C) { return 2 * (C <= 16 ? 8 : C <= 26 ? 13 : 16); }
+// 64-row tiles, two CTAs per SM, for every I: 128-row tiles (RA = 8, one CTA per SM) were
+// measured 1.03-1.24x slower on 200x200x300x40 and 512^3
+int simt_tile_rows(int64_t) { return 64; }
+int simt_ctas_per_sm(int64_t) { return 2; }
 
-template <int TC>
-cudaError_t launch_simt_tc(const ContractParams& p, dim3 grid, cudaStream_t s) {
+template <int TC, int RA>
+cudaError_t launch_simt_ra(const ContractParams& p, dim3 grid, cudaStream_t s) {
     const bool km = p.L > 1;
     const bool xa = (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 && p.kchunk % BK == 0;
-    const size_t smem = sizeof(SimtSmem);
+    const size_t smem = sizeof(SimtSmem<RA>);
     auto go = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kernel<<<grid, THREADS, smem, s>>>(p);
         return cudaSuccess;
     };
-    if (km) return (xa && p.L % 4 == 0) ? go(contract_simt_kernel<true, true, TC>) : go(contract_simt_kernel<true, false, TC>);
-    return (xa && p.I % 4 == 0) ? go(contract_simt_kernel<false, true, TC>) : go(contract_simt_kernel<false, false, TC>);
+    if (km)
+        return (xa && p.L % 4 == 0) ? go(contract_simt_kernel<true, true, TC, RA>)
+                                    : go(contract_simt_kernel<true, false, TC, RA>);
+    return (xa && p.I % 4 == 0) ? go(contract_simt_kernel<false, true, TC, RA>)
+                                : go(contract_simt_kernel<false, false, TC, RA>);
+}
+
+template <int TC>
+cudaError_t launch_simt_tc(const ContractParams& p, dim3 grid, cudaStream_t s) {
+    return launch_simt_ra<TC, 4>(p, grid, s);
 }
 
 cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,

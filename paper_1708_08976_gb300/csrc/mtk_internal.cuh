@@ -66,6 +66,8 @@ int num_sms();
 cudaError_t launch_contract_simt(const ContractParams& p, int c_blocks, int i_tiles,
                                  cudaStream_t s);
 int simt_cta_cols(int C);              // columns of M per CTA of the FP32 kernel (16, 26 or 32)
+int simt_tile_rows(int64_t I);         // rows of M per CTA of the FP32 kernel (64 or 128)
+int simt_ctas_per_sm(int64_t I);       // resident CTAs per SM of that kernel (2 or 1)
 cudaError_t launch_split_reduce(const float* part, int S, int64_t I, int C, float* out,
                                 int64_t si, int64_t sc, cudaStream_t s);
 // Tensor-core contraction plan.  The factor list is split into a head (the first
