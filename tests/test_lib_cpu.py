@@ -81,6 +81,12 @@ def test_null_and_misaligned_pointers_rejected_before_launch():
     assert lib.mtk_khatri_rao(U, L.dims_arr([3]), 0, 2, fake, 1, None) == L.MTK_EINVAL
     # fit requested without ||X||^2
     assert lib.mtk_cp_als_sweep(fake, d, 3, U, 2, None, fake, fake, 1 << 30, None, None) == L.MTK_EINVAL
+    # the column normalisation: 0 or 1, and only where the one-launch update runs (C <= 64)
+    o = L.opts(normalize=2)
+    assert lib.mtk_cp_als_sweep(fake, d, 3, U, 2, None, None, fake, 1 << 30, ctypes.byref(o), None) == L.MTK_EINVAL
+    o = L.opts(normalize=1)
+    assert lib.mtk_cp_als_sweep(fake, d, 3, U, 65, None, None, fake, 1 << 30, ctypes.byref(o),
+                                None) == L.MTK_EUNSUPPORTED
     # solve with n out of range
     G = L.ptr_arr([fake, fake, fake])
     assert lib.mtk_gram_hadamard_solve(G, 3, 2, 3, fake, 4, fake, None, fake, 1 << 20, None) == L.MTK_EINVAL
