@@ -456,17 +456,27 @@ als_update_kernel(const __grid_constant__ UpdParams p) {
                 // U_n(i, :) = M(i, :) H^{-1}: products of an FP32 entry and an FP32 pair,
                 // each formed exactly, summed in double-FP32 (about 2^-44 relative)
                 float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
-                for (int k = 0; k < C; ++k) {
-                    const float mk = __shfl_sync(0xffffffffu, k < 32 ? m0 : m1, k & 31);
-                    if (j0 < C) {
+                if (C > 32) {
+                    for (int k = 0; k < C; ++k) {
+                        const float mk = __shfl_sync(0xffffffffu, k < 32 ? m0 : m1, k & 31);
                         const float2 w = Hv[k * C + j0];
                         df_madd(h0, l0, mk, w.x);
                         l0 = fmaf(mk, w.y, l0);
+                        if (j1 < C) {
+                            const float2 v = Hv[k * C + j1];
+                            df_madd(h1, l1, mk, v.x);
+                            l1 = fmaf(mk, v.y, l1);
+                        }
                     }
-                    if (j1 < C) {
-                        const float2 w = Hv[k * C + j1];
-                        df_madd(h1, l1, mk, w.x);
-                        l1 = fmaf(mk, w.y, l1);
+                } else {
+                    // one column per lane (the second column is past C for every lane)
+                    for (int k = 0; k < C; ++k) {
+                        const float mk = __shfl_sync(0xffffffffu, m0, k);
+                        if (j0 < C) {
+                            const float2 w = Hv[k * C + j0];
+                            df_madd(h0, l0, mk, w.x);
+                            l0 = fmaf(mk, w.y, l0);
+                        }
                     }
                 }
                 u0 = __fadd_rn(h0, l0);
