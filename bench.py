@@ -568,21 +568,24 @@ def run_grad(args, mtk, torch, dev, hbm_peak):
     """The CP loss and its gradient on 32^5 (rank-16 CP plus noise, C = 16): forward (the
     mode-4 MTTKRP, the Grams, the loss) and hand-written backward (every mode's MTTKRP and
     U_n H_n - M_n) through torch.autograd, timed with CUDA events over back-to-back steps.
-    Forms: on the planes with the backward's MTTKRPs from the dimension tree (two passes
-    over the tensor), on the planes one MTTKRP per mode, and on the FP32 tensor (FP32 and
-    bf16x2).  The flops counted are the definition's, (N + 1) x 2 I C per step; the
-    roofline is the HBM time of (N + 1) passes over the 4-byte tensor (the definition), and
-    of 3 passes for the tree form (what it reads).  Each form's gradient is checked against
-    the FP64 oracle's at mode 0."""
+    Forms: on the planes with every mode's MTTKRP from the dimension tree, in the forward
+    (two passes over the tensor), also replayed from a CUDA graph; on the planes one MTTKRP
+    per mode; and on the FP32 tensor (FP32 and bf16x2).  ||X||^2 is computed once, with the
+    planes, and passed to the loss.  The flops counted are the definition's, (N + 1) x 2 I C
+    per step; roofline_frac_definition is the HBM time of (N + 1) passes over the 4-byte
+    tensor (the definition) over the step time, roofline_frac_read that of the passes the
+    form makes (2 for the tree, N per mode).  Each form's gradient is checked against the
+    FP64 oracle's at mode 0."""
     import oracle
     X, dims, U = synth.cube32x5()
     N, C, I = len(dims), U[0].shape[1], X.size
     Xd = torch.from_numpy(X).to(dev)
-    Xs, _ = mtk.split_tensor(Xd, dims)
+    # the planes and ||X||^2, once per tensor (X is a constant of the loss)
+    Xs, nx2 = mtk.split_tensor(Xd, dims)
     ref0 = oracle.grad(X.astype(np.float64), dims, [u.astype(np.float64) for u in U], 0)
-    forms = {"planes-tree": {"Xs": Xs}, "planes-tree-graph": {"Xs": Xs},
-             "planes-per-mode": {"Xs": Xs, "algo": "fused"},
-             "fp32": {"precision": "fp32"}, "bf16x2": {"precision": "bf16x2"}}
+    forms = {"planes-tree": {"Xs": Xs, "normX2": nx2}, "planes-tree-graph": {"Xs": Xs, "normX2": nx2},
+             "planes-per-mode": {"Xs": Xs, "algo": "fused", "normX2": nx2},
+             "fp32": {"precision": "fp32", "normX2": nx2}, "bf16x2": {"precision": "bf16x2", "normX2": nx2}}
     sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
@@ -614,15 +617,19 @@ def run_grad(args, mtk, torch, dev, hbm_peak):
             torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = max(args.steps, 5)
+        torch.cuda.nvtx.range_push("grad_" + name)
         e0.record()
         for _ in range(reps):
             step()
         e1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         t = e0.elapsed_time(e1) * 1e-3 / reps
         step()
         err = float(np.linalg.norm(Ud[0].grad.double().cpu().numpy() - ref0) / np.linalg.norm(ref0))
-        passes = 3 if name.startswith("planes-tree") else N + 1
+        # passes over the tensor per step: the tree's two partial contractions, or one
+        # MTTKRP per mode (the forward's last-mode MTTKRP serves the backward too)
+        passes = 2 if name.startswith("planes-tree") else N
         out[name] = {"ms_per_step": t * 1e3, "tflops": (N + 1) * 2.0 * I * C / t / 1e12,
                      "tensor_passes": passes,
                      "roofline_frac_definition": ((N + 1) * 4.0 * I / hbm_peak / 1e9) / t,

@@ -726,19 +726,23 @@ class ALS:
 
 def _per_mode(opts):
     """mttkrp options of one mode: on the planes the algorithm is the fused one (the
-    dimension tree, algo "two_step", belongs to mttkrp_all)."""
+    dimension tree, algo "two_step", belongs to mttkrp_all); normX2 is the loss's own."""
+    drop = {"normX2"}
     if opts.get("Xs") is not None and opts.get("algo") == "two_step":
-        return {k: v for k, v in opts.items() if k != "algo"}
-    return opts
+        drop.add("algo")
+    return {k: v for k, v in opts.items() if k not in drop}
 
 
 class CPLoss(torch.autograd.Function):
     """f(U_0..U_{N-1}) = 0.5 ||X - [[U_0..U_{N-1}]]||^2 with a hand-written backward:
     df/dU_n = U_n Hadamard_{k!=n}(U_k^T U_k) - MTTKRP(X, n), for every mode n.
     X is treated as a constant.  Usage: CPLoss.apply(X, dims, opts_dict, *U).
-    With opts["Xs"] (the planes of X from split_tensor) every MTTKRP runs on the planes,
-    and the backward takes all N of them from mttkrp_all: the dimension tree for N = 3, 4
-    (two passes over the tensor instead of N)."""
+    With opts["Xs"] (the planes of X from split_tensor) every MTTKRP runs on the planes;
+    when the gradients of several factors are wanted, the forward takes all N MTTKRPs at
+    once from mttkrp_all (the dimension tree for N >= 3: two passes over the tensor instead
+    of N + 1), the loss from the last one, and the backward reuses them.  opts["normX2"]:
+    ||X||^2 as a device FP64 scalar computed once (split_tensor returns it), else the
+    forward computes it, one more pass over X."""
 
     @staticmethod
     def forward(ctx, X, dims, opts, *U):
@@ -747,13 +751,22 @@ class CPLoss(torch.autograd.Function):
         opts = dict(opts or {})
         G = [gram(u) for u in U]
         Xs = opts.get("Xs")
-        M = mttkrp(None if Xs is not None else X, dims, list(U), N - 1, **_per_mode(opts))
-        nx2 = norm2(X)
+        nx2 = opts.get("normX2")
+        if nx2 is None:
+            nx2 = norm2(X)
+        want = [bool(ctx.needs_input_grad[3 + n]) for n in range(N)]
+        Ms = None
+        if Xs is not None and sum(want[:N - 1]) > 1:
+            Ms = mttkrp_all(Xs, dims, list(U), algo=opts.get("algo", "auto"))
+            M = Ms[N - 1]
+        else:
+            M = mttkrp(None if Xs is not None else X, dims, list(U), N - 1, **_per_mode(opts))
         loss = cp_loss_value(nx2, M, U[N - 1], G)
         ctx.save_for_backward(X, *U)
         ctx.dims = dims
         ctx.opts = opts
         ctx.M_last = M
+        ctx.Ms = Ms
         ctx.G = G
         return loss
 
@@ -765,9 +778,7 @@ class CPLoss(torch.autograd.Function):
         scale = go.detach().to(torch.float32).contiguous()
         Xs = opts.get("Xs")
         want = [ctx.needs_input_grad[3 + n] for n in range(N)]
-        Ms = None
-        if Xs is not None and sum(want[:N - 1]) > 1:
-            Ms = mttkrp_all(Xs, dims, list(U), algo=opts.get("algo", "auto"))
+        Ms = ctx.Ms                      # every mode's MTTKRP, from the forward
         grads = []
         for n in range(N):
             if not want[n]:
@@ -784,5 +795,6 @@ class CPLoss(torch.autograd.Function):
 
 def cp_loss(X, dims, U, **opts):
     """0.5 ||X - [[U]]||^2 as an autograd scalar (CPLoss); opts go to mttkrp (Xs: the
-    planes, which also route the backward through mttkrp_all)."""
+    planes, which also route the MTTKRPs through mttkrp_all; normX2: ||X||^2 computed
+    once)."""
     return CPLoss.apply(X, list(dims), opts, *U)

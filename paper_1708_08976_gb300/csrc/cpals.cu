@@ -153,20 +153,28 @@ apply_inverse_kernel(const double* __restrict__ Hinv, const int* __restrict__ fl
     }
 }
 
-constexpr int64_t kNormChunk = 1 << 20;   // entries per CTA
+// entries per CTA: a multiple of 1024 giving at most 1216 CTAs (8 per SM of this part) of at
+// least 4096 entries; a function of I alone, so the fixed-order sum does not depend on the
+// device.  (1 M entries per CTA left a 134 MB tensor to 32 CTAs and took 314 us.)
+int64_t norm2_chunk(int64_t I) {
+    int64_t nb = (I + 4095) / 4096;
+    if (nb > 1216) nb = 1216;
+    if (nb < 1) nb = 1;
+    return ((I + nb - 1) / nb + 1023) / 1024 * 1024;
+}
 
 __global__ void __launch_bounds__(256)
-norm2_partial_kernel(const float* __restrict__ X, int64_t I, double* __restrict__ part) {
+norm2_partial_kernel(const float* __restrict__ X, int64_t I, int64_t chunk, double* __restrict__ part) {
     __shared__ double red[256];
-    const int64_t a = (int64_t)blockIdx.x * kNormChunk;
-    const int64_t b = (a + kNormChunk < I) ? a + kNormChunk : I;
+    const int64_t a = (int64_t)blockIdx.x * chunk;
+    const int64_t b = (a + chunk < I) ? a + chunk : I;
     // exact squares, compensated FP32 sums of 64 entries, a double-FP32 total (SquareSum):
     // no FP64 arithmetic in the loop (this part's FP64 pipe is narrow)
     SquareSum sq;
     int cnt = 0;
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     if (vec) {
-        // a is a multiple of 4 (kNormChunk is), so X + a stays 16-byte aligned; four 16-byte
+        // a is a multiple of 4 (the chunk is), so X + a stays 16-byte aligned; four 16-byte
         // loads in flight per thread
         const int64_t nv = (b - a) / 4;
         const float4* xv = reinterpret_cast<const float4*>(X + a);
@@ -323,11 +331,14 @@ cudaError_t launch_chol_solve(const double* const* G, int N, int C, int n, const
     return cudaGetLastError();
 }
 
-int norm2_chunks(int64_t I) { return (int)((I + kNormChunk - 1) / kNormChunk); }
+int norm2_chunks(int64_t I) {
+    const int64_t c = norm2_chunk(I);
+    return (int)((I + c - 1) / c);
+}
 
 cudaError_t launch_norm2(const float* X, int64_t I, double* part, int nchunks, double* out,
                          cudaStream_t s) {
-    norm2_partial_kernel<<<nchunks, 256, 0, s>>>(X, I, part);
+    norm2_partial_kernel<<<nchunks, 256, 0, s>>>(X, I, norm2_chunk(I), part);
     note_launches(1);
     sum_chunks_kernel<<<1, 32, 0, s>>>(part, nchunks, out);
     note_launches(1);
