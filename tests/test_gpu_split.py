@@ -501,3 +501,13 @@ def test_cp_loss_gradient_on_planes(dims, C):
     for n in range(len(dims)):
         ref = oracle.grad(Xr, dims, Ur, n)
         assert rel_fro(Ud[n].grad.double().cpu().numpy(), ref) < 2e-5, n
+    # ||X||^2 passed in (from the split), and only one factor's gradient wanted (the forward
+    # then takes the last mode's MTTKRP alone and the backward mode 0's): the same numbers
+    _, nx2 = mtk.split_tensor(Xd, dims)
+    Uo = [u.detach().clone() for u in Ud]
+    Uo[0].requires_grad_(True)
+    loss1 = mtk.cp_loss(Xd, dims, Uo, Xs=Xs, normX2=nx2)
+    loss1.backward()
+    np.testing.assert_allclose(loss1.item(), oracle.loss_explicit(Xr, dims, Ur), rtol=2e-5)
+    assert rel_fro(Uo[0].grad.double().cpu().numpy(), oracle.grad(Xr, dims, Ur, 0)) < 2e-5
+    assert all(u.grad is None for u in Uo[1:])
