@@ -7,8 +7,9 @@ C = 25.  One step = one CP-ALS sweep through the C ABI: for each of the 4 modes
 the MTTKRP, the FP64 factor update and the Gram of the new factor, then the fit.
 The tensor is split once into its two BF16 planes (timed apart, and inside every
 e2e step, where the split reads the step's tensor from pinned host memory); the sweep runs on the planes either with per-mode MTTKRPs or with the
-dimension tree (two partial contractions shared by two modes each), and the
-faster form is reported.  Metric = useful MTTKRP flops (4 modes x 2*I*C) per
+dimension tree (two partial contractions shared by two modes each), the tree
+also replayed from a CUDA graph of the whole sweep, and the fastest form is
+reported.  Metric = useful MTTKRP flops (4 modes x 2*I*C) per
 second of the whole sweep.
 
 Roofline: the dominant kernel is timed alone with CUDA events on its launch

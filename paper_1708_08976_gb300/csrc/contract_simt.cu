@@ -3,7 +3,7 @@
 // This is the plain-FP32 form of the 1-step MTTKRP (Algorithms 2/3): the mode-n
 // matricization is consumed in place as R row-major I x L blocks (Fig. 2), and
 // the KRP rows W(k, :) are generated on chip from the factor rows (Algorithm 3
-// forms K_R(j,:) kr K_L per block; here a block of 32 consecutive k is formed in
+// forms K_R(j,:) kr K_L per block; here a block of 64 consecutive k is formed in
 // shared memory and never written to HBM).  With a single materialised factor
 // the same kernel is the GEMM of the materialised-KRP path and of the 2-step
 // partial MTTKRP (Algorithm 4).
