@@ -280,3 +280,21 @@ def test_ffma_probe_rejects_bad_arguments():
     for cps, iters, out in ((0, 16, fake), (65, 16, fake), (1, 0, fake), (1, (1 << 24) + 1, fake), (1, 16, None),
                             (1, 16, ctypes.c_void_p((1 << 20) + 2))):
         assert lib.mtk_ffma_probe(cps, iters, out, None, None) == L.MTK_EINVAL
+
+
+def test_norm_and_split_partials_bounded():
+    """||X||^2 (mtk_norm2, the split) is summed over at most 1216 fixed chunks of at least
+    4096 entries (whatever the device), so the workspace of the partial sums stays small and
+    a 134 MB tensor is not left to a few CTAs."""
+    lib = L.load()
+    status = 256
+    cap = status + (1216 * 8 + 255) // 256 * 256
+    for I in (1, 4095, 4096, 4097, 1 << 20, 33554432, 480000000, 3 << 30):
+        w = lib.mtk_norm2_workspace(I)
+        assert status + 256 <= w <= cap, (I, w)
+    # a 32^5 tensor (33.5 M entries) gets the full 1216-way split, not 32 chunks of 1 M
+    assert lib.mtk_norm2_workspace(33554432) == cap
+    assert lib.mtk_norm2_workspace(0) == 0
+    for dims in ((200, 200, 300, 40), (900, 900, 900), (5,)):
+        w = lib.mtk_split_workspace(L.dims_arr(list(dims)), len(dims))
+        assert status + 256 <= w <= cap, (dims, w)
